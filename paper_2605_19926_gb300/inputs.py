@@ -1,0 +1,68 @@
+"""Seeded synthetic inputs: workload presets and random action streams.
+
+This module holds no arithmetic of the method. It only names workload
+parameters and draws the uniformly random actions that drive an episode
+rollout (the paper times its environments under a uniform random policy,
+App. A.1). Both the CUDA path and the oracle consume what it produces.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+N_ACTIONS = 7  # noop, forward, back, strafe-left, strafe-right, turn-left, turn-right
+
+TASK_ROOMS = 0
+TASK_MAZE_KEYDOOR = 1
+
+_COMMON = dict(
+    frame_h=64,
+    frame_w=64,
+    turns_per_rev=72,  # 5 degree turns
+    fov_deg=60.0,
+    move_step=0.1,
+    radius=0.2,
+)
+
+
+def rooms(n_envs: int = 1, map_side: int = 16, wall_prob: float = 0.25, seed: int = 0, max_sprites: int = 0,
+          frame_h: int = 64, frame_w: int = 64) -> dict:
+    """Random-wall rooms: border walls, interior walls with probability ``wall_prob``,
+    no reward and no episode end (a single env, 16 x 16 map, 64 x 64 frame by default)."""
+    return dict(_COMMON, task=TASK_ROOMS, n_envs=n_envs, map_side=map_side, wall_prob=wall_prob,
+                max_sprites=max_sprites, horizon=0, step_reward=0.0, key_reward=0.0, goal_reward=0.0,
+                seed=seed, frame_h=frame_h, frame_w=frame_w)
+
+
+def maze_keydoor(n_envs: int = 4096, map_side: int = 32, seed: int = 1, horizon: int = 500,
+                 frame_h: int = 64, frame_w: int = 64) -> dict:
+    """Random DFS mazes with one key, one locked door and a goal at the farthest
+    cell; +1 key, +10 goal, -0.001 per step, auto-reset after ``horizon`` steps."""
+    return dict(_COMMON, task=TASK_MAZE_KEYDOOR, n_envs=n_envs, map_side=map_side, wall_prob=0.0,
+                max_sprites=2, horizon=horizon, step_reward=-0.001, key_reward=1.0, goal_reward=10.0,
+                seed=seed, frame_h=frame_h, frame_w=frame_w)
+
+
+# The two workloads the tests and the benchmark run.
+def single_env_rooms() -> dict:
+    """1 env, 16 x 16 random rooms (p = 0.25), 64 x 64 RGB, 1000 random steps, seed 0."""
+    return rooms(n_envs=1, map_side=16, wall_prob=0.25, seed=0)
+
+
+def batched_keydoor_mazes(n_envs: int = 4096) -> dict:
+    """4096 envs, 32 x 32 DFS key-door mazes, 64 x 64 RGB, horizon 500, 10,000 random steps, seed 1."""
+    return maze_keydoor(n_envs=n_envs, map_side=32, seed=1, horizon=500)
+
+
+def actions(seed: int, step: int, n_envs: int) -> np.ndarray:
+    """Uniform random actions in [0, 7) for one step of ``n_envs`` envs (uint8)."""
+    rng = np.random.default_rng([int(seed) & 0xFFFFFFFF, int(step) & 0xFFFFFFFF, 0x4A58])
+    return rng.integers(0, N_ACTIONS, size=n_envs, dtype=np.uint8)
+
+
+def action_stream(seed: int, n_steps: int, n_envs: int, first_step: int = 0) -> np.ndarray:
+    """[n_steps, n_envs] uint8 actions; row i equals ``actions(seed, first_step + i, n_envs)``."""
+    out = np.empty((n_steps, n_envs), np.uint8)
+    for i in range(n_steps):
+        out[i] = actions(seed, first_step + i, n_envs)
+    return out
