@@ -1,0 +1,351 @@
+"""Benchmark: batched env step + render (frames/s) on GB300.
+
+Workload: 4096 envs, 32 x 32 random DFS key-door mazes, 64 x 64 RGB frames,
+horizon 500 with auto-reset, uniform random actions (seed 1). A step is one
+fused launch that moves, collides, picks up, rewards, resets and renders all
+envs. Steps are replayed from a CUDA graph of 128 launches; each launch writes
+its frames into slot (step mod 128) of a 6.4 GB rollout buffer, so the frame
+stream never fits the 126 MB L2 and every byte goes to HBM.
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle on the
+same workload instead (the method's only other implementation here).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s incl. render (frames/s) at 64x64 RGB"
+GRAPH_STEPS = 128  # launches per CUDA graph = rollout buffer slots
+KERNEL_SOURCES = ["paper_2605_19926_gb300/csrc/jx_kernels.cu", "paper_2605_19926_gb300/csrc/jx_internal.h"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def shard_config(cfg: dict, rank: int) -> dict:
+    """Each rank steps its own independent envs (weak scaling): same shape, its own seed."""
+    out = dict(cfg)
+    out["seed"] = int(cfg["seed"]) + rank
+    return out
+
+
+def algorithmic_bytes_per_env_step(cfg: dict) -> int:
+    """Compulsory HBM bytes of one env-step: the frame written; the state read
+    and written; action, reward and done. The map (re-read from L2 every step)
+    and episode regeneration (once per horizon) are excluded."""
+    H, W, K = cfg["frame_h"], cfg["frame_w"], cfg["max_sprites"]
+    frame = 3 * H * W
+    state_read = 2 + 2 + 4 + 4 + 4 + 2 + 4 + 4 + 1 + 12 + 1 + K * (4 + 4 + 1)  # cells, fracs, theta0, turn, t,
+    # episode, flags, objects, sprite count, sprite table
+    state_write = 2 + 2 + 4 + 4 + 2 + 4 + 1  # cells, fracs, turn, t, flags
+    io = 1 + 4 + 1  # action, reward, done
+    return frame + state_read + state_write + io
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def time_oracle(cfg: dict, n_envs: int, n_steps: int, seed: int, nthreads: int) -> tuple[float, int]:
+    """Oracle env-steps/s over n_envs x n_steps of the workload (frames rendered)."""
+    import oracle
+
+    ocfg = oracle.make_config(**cfg)
+    from paper_2605_19926_gb300 import inputs
+
+    envs = oracle.generate(ocfg, np.arange(n_envs), nthreads=nthreads)
+    acts = [inputs.actions(seed, s, n_envs) for s in range(n_steps)]
+    t0 = time.perf_counter()
+    for s in range(n_steps):
+        oracle.step(ocfg, np.arange(n_envs), envs, acts[s], frames=True, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return n_envs * n_steps / dt, nthreads
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, cfg: dict):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    n_envs = args.ref_envs
+    cores = cpu_cores()
+    # W untimed warm-up steps, then K steps, each over a bounded sample of the envs
+    time_oracle(cfg, n_envs, args.warmup, seed=cfg["seed"], nthreads=cores)
+    t0 = time.perf_counter()
+    value, used = time_oracle(cfg, n_envs, args.steps, seed=cfg["seed"], nthreads=cores)
+    t_total = time.perf_counter() - t0
+    steps_total = args.steps
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": args.gpus,
+        "steps": steps_total, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / steps_total,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "4096 envs, 32x32 DFS key-door mazes, 64x64 RGB, horizon 500, random actions",
+                   "sample_envs": n_envs},
+        "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": used, "kind": "oracle",
+                         "sample": f"{n_envs} envs x {steps_total} steps of the workload (frames rendered)"},
+        "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=16)
+    ap.add_argument("--impl", default="jx", choices=["jx", "reference"])
+    ap.add_argument("--n-envs", type=int, default=4096)
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--latency-steps", type=int, default=300)
+    ap.add_argument("--cpu-envs", type=int, default=4096)
+    ap.add_argument("--cpu-steps", type=int, default=600)
+    ap.add_argument("--ref-envs", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    from paper_2605_19926_gb300 import inputs
+
+    base_cfg = inputs.batched_keydoor_mazes(args.n_envs)
+    if args.impl == "reference":
+        run_reference(args, base_cfg)
+        return
+
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2605_19926_gb300 import build
+
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2605_19926_gb300 import jx
+
+    cfg = shard_config(base_cfg, rank)
+    N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
+    dev = torch.device("cuda", local)
+    env = jx.Env(cfg, local)
+    total_steps = args.warmup + args.steps
+    # inputs resident in HBM before timing: the whole action stream
+    acts_host = inputs.action_stream(cfg["seed"], total_steps, N)
+    acts = torch.from_numpy(acts_host).to(dev)
+    ring_acts = torch.empty((GRAPH_STEPS, N), dtype=torch.uint8, device=dev)
+    frames = torch.empty((GRAPH_STEPS, N, H, W, 3), dtype=torch.uint8, device=dev)  # 6.4 GB rollout buffer
+    rewards = torch.empty((GRAPH_STEPS, N), dtype=torch.float32, device=dev)
+    dones = torch.empty((GRAPH_STEPS, N), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        env.reset(frames[0], stream)
+        for s in range(args.warmup):
+            env.step(acts[s], frames[s % GRAPH_STEPS], rewards[s % GRAPH_STEPS], dones[s % GRAPH_STEPS], stream)
+    stream.synchronize()
+
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        for i in range(GRAPH_STEPS):
+            env.step(ring_acts[i], frames[i], rewards[i], dones[i], torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    # the capture itself ran nothing; the env state is still after the warm-up
+
+    n_full, rem = divmod(args.steps, GRAPH_STEPS)
+    launches_before = env.launch_count()
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        s = args.warmup
+        for c in range(n_full):
+            ring_acts.copy_(acts[s: s + GRAPH_STEPS], non_blocking=True)
+            graph.replay()
+            s += GRAPH_STEPS
+        for i in range(rem):
+            env.step(acts[s], frames[i], rewards[i], dones[i], stream)
+            s += 1
+        ev1.record(stream)
+    stream.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    eager_launches = env.launch_count() - launches_before
+    gpu_launches = n_full * GRAPH_STEPS + eager_launches
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = t_max / args.steps
+    value = world * N * args.steps / (t_max / 1e3)
+
+    # per-step latency (eager launch + kernel, one step at a time)
+    lat = []
+    with torch.cuda.stream(stream):
+        for i in range(args.latency_steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            env.step(acts[(args.warmup + i) % total_steps], frames[i % GRAPH_STEPS], rewards[i % GRAPH_STEPS],
+                     dones[i % GRAPH_STEPS], stream)
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+    lat.sort()
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+
+    # end to end through the public host-buffer entry point
+    h_act = torch.empty(N, dtype=torch.uint8).pin_memory()
+    h_frames = torch.empty((N, H, W, 3), dtype=torch.uint8).pin_memory()
+    h_rew = torch.empty(N, dtype=torch.float32).pin_memory()
+    h_done = torch.empty(N, dtype=torch.uint8).pin_memory()
+    for i in range(3):
+        h_act.numpy()[:] = acts_host[i]
+        env.step_host(h_act, h_frames, h_rew, h_done, stream)
+    t0 = time.perf_counter()
+    for i in range(args.e2e_steps):
+        h_act.numpy()[:] = acts_host[(i + 3) % total_steps]
+        env.step_host(h_act, h_frames, h_rew, h_done, stream)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * N * args.e2e_steps / e2e_s  # every rank runs the same count; host clock per rank
+
+    bytes_per_launch = algorithmic_bytes_per_env_step(cfg) * N
+    achieved = bytes_per_launch / (ms_per_step / 1e3) / 1e9
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    traffic = None
+    if os.path.exists(TRAFFIC_FILE):
+        tf = json.load(open(TRAFFIC_FILE))
+        if tf.get("kernel_source_sha") == kernel_source_sha() and tf.get("n_envs") == N:
+            traffic = tf.get("dram_bytes_per_launch")
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+
+        oracle.build()
+        v, cores = time_oracle(base_cfg, args.cpu_envs, args.cpu_steps, seed=base_cfg["seed"], nthreads=cpu_cores())
+        cpu = {"value": v, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_envs} envs x {args.cpu_steps} steps of the workload (frames rendered)"}
+    shape = env.launch_shape()
+    line = {
+        "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "4096 envs per GPU, 32x32 random DFS key-door mazes, 64x64 RGB uint8, horizon 500, "
+                               "auto-reset, uniform random actions, seed 1",
+                   "n_envs_per_gpu": N, "map_side": cfg["map_side"], "frame": f"{H}x{W}x3",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "frames written to a 128-slot rollout buffer (6.4 GB) > L2",
+                   "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
+                              "cuda_graph_steps": GRAPH_STEPS}},
+        "p50_step_ms": p50, "p99_step_ms": p99,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": bytes_per_launch},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": N,
+                "d2h_bytes_per_step": N * H * W * 3 + 4 * N + N},
+        "gpu_launches": gpu_launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * jx.h — C ABI of the GB300-native batched first-person environment library.
+ *
+ * The library steps N independent Wolfenstein-3D-style environments at once
+ * and renders one uint8 RGB frame per environment (JAXenstein, arxiv
+ * 2605.19926: reset/step environment interface, Sec. 1 and Sec. 3.1; DDA
+ * ray casting over a tile map, Sec. 2.1; wall slices shaded from the hit
+ * distance, Sec. 2 and Sec. 2.1; fixed sprites, Fig. 1; key / locked door /
+ * goal tasks, Table 1 and Table 2; native low-resolution frames, Sec. 3.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All compute runs in hand-written CUDA kernels on the env's device. There
+ *   is no CPU path: every entry point that computes fails with JX_ECUDA when
+ *   no usable device is present.
+ * - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *   stream. Calls taking device pointers only enqueue work on that stream and
+ *   return at once (asynchronous); they never synchronise and never allocate,
+ *   so they may be captured into a CUDA graph.
+ * - Device pointers (prefix d_) must point to memory on the env's device.
+ *   Host pointers (prefix h_) are ordinary or pinned host memory.
+ * - The library owns all environment state (positions, headings, maps,
+ *   sprites) in device memory; the caller owns its output buffers and streams.
+ * - Status codes are returned; nothing traps. A human-readable message for
+ *   the last failing call on the calling thread is in jx_last_error().
+ * - Kernels that meet bad data (an action outside 0..6) record it in a device
+ *   error word and treat the action as a no-op; jx_sync_status reads the word.
+ *
+ * Frame layout: [N][H][W][3] uint8 (NHWC, RGB), env-major and row-major; one
+ * frame is 3*H*W bytes. Frame buffers must be 16-byte aligned.
+ */
+#ifndef JX_H
+#define JX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jx_env jx_env; /* opaque handle */
+
+typedef enum {
+  JX_OK = 0,
+  JX_EINVAL = 1,   /* bad argument or configuration */
+  JX_ENOMEM = 2,   /* device or host allocation failed */
+  JX_ECUDA = 3,    /* a CUDA runtime call failed (no device, launch error, ...) */
+  JX_ETIMEOUT = 4, /* a bounded wait gave up */
+  JX_EBUDGET = 5,  /* refused by a memory budget */
+  JX_EDEVICE = 6   /* the device error word was set by a kernel */
+} jx_status;
+
+enum { JX_TASK_ROOMS = 0, JX_TASK_MAZE_KEYDOOR = 1 };
+
+enum {
+  JX_ACT_NOOP = 0,
+  JX_ACT_FORWARD = 1,
+  JX_ACT_BACK = 2,
+  JX_ACT_STRAFE_LEFT = 3,
+  JX_ACT_STRAFE_RIGHT = 4,
+  JX_ACT_TURN_LEFT = 5,
+  JX_ACT_TURN_RIGHT = 6
+};
+
+/* Environment configuration (one value for all N environments).
+ *  n_envs        number of environments N (>= 1)
+ *  task          JX_TASK_ROOMS: border walls, interior walls with probability
+ *                wall_prob, optional decorative sprites; JX_TASK_MAZE_KEYDOOR:
+ *                random DFS maze with one key, one locked door and a goal at
+ *                the cell farthest from the spawn (Table 1 "key-door")
+ *  map_side      S, the map is S x S cells; rooms: 3..128; mazes: even, 6..128
+ *  frame_h       H rows, 1..256
+ *  frame_w       W columns, a multiple of 16, 16..256
+ *  max_sprites   K sprite slots per env, 0..16 (mazes need >= 2: key and goal)
+ *  horizon       episode length limit in steps, 0 = no limit
+ *  turns_per_rev a turn action rotates by 2*pi / turns_per_rev (72 = 5 degrees)
+ *  wall_prob     interior wall probability of the rooms task, [0, 1]
+ *  fov_deg       horizontal field of view in degrees, (0, 180)
+ *  move_step     cells moved by one move action, [0, 0.5]
+ *  radius        half-size of the agent's collision box, [0, 0.49]
+ *  step_reward, key_reward, goal_reward: reward of a step is
+ *                step_reward + key_reward [key picked] + goal_reward [goal reached],
+ *                rounded once to float32
+ *  seed          master seed of all map, spawn and heading draws */
+typedef struct {
+  int32_t n_envs;
+  int32_t task;
+  int32_t map_side;
+  int32_t frame_h;
+  int32_t frame_w;
+  int32_t max_sprites;
+  int32_t horizon;
+  int32_t turns_per_rev;
+  double wall_prob;
+  double fov_deg;
+  double move_step;
+  double radius;
+  double step_reward;
+  double key_reward;
+  double goal_reward;
+  uint64_t seed;
+} jx_config;
+
+/* Create N environments on CUDA device `device` and allocate their state in
+ * its memory (no episode is generated yet: call jx_reset). The config is
+ * validated before any CUDA call, so JX_EINVAL needs no GPU. *out receives
+ * the handle, owned by the caller until jx_destroy. */
+jx_status jx_create(const jx_config* cfg, int device, jx_env** out);
+
+/* Free the env's device memory and the handle. NULL is accepted. Waits for
+ * the env's outstanding work on the device first. */
+jx_status jx_destroy(jx_env* env);
+
+/* Start episode 0 of every environment: generate its map, spawn, heading and
+ * sprites from (seed, env index, episode), then render the first frame of
+ * each into d_frames ([N][H][W][3]). Asynchronous on `stream`. */
+jx_status jx_reset(jx_env* env, void* stream, uint8_t* d_frames);
+
+/* One environment step of all N environments, fused in one kernel:
+ * action -> movement with wall collision -> key pickup / goal -> reward ->
+ * episode end -> auto-reset of ended episodes (next episode's map) -> render.
+ *  d_actions [N] uint8 in 0..6 (see JX_ACT_*), read;
+ *  d_frames  [N][H][W][3] uint8, written: the frame after the step (for an
+ *            env whose episode ended, the first frame of its next episode);
+ *  d_rewards [N] float32, written: the reward of the step just taken;
+ *  d_dones   [N] uint8, written: 1 where the step ended the episode.
+ * Asynchronous on `stream`; allocates nothing; capturable in a CUDA graph. */
+jx_status jx_step(jx_env* env, void* stream, const uint8_t* d_actions, uint8_t* d_frames, float* d_rewards,
+                  uint8_t* d_dones);
+
+/* Render the current state of all environments into d_frames (no state change). */
+jx_status jx_render(jx_env* env, void* stream, uint8_t* d_frames);
+
+/* jx_step with host buffers: copies h_actions to the device, steps, copies
+ * frames, rewards and dones back into the host buffers and waits for the
+ * stream. Uses device staging buffers owned by the env (allocated on first
+ * use). Host buffers of pinned memory give the fastest copies. */
+jx_status jx_step_host(jx_env* env, void* stream, const uint8_t* h_actions, uint8_t* h_frames, float* h_rewards,
+                       uint8_t* h_dones);
+
+/* Per-column ray results of the current state (test and debug hook):
+ *  d_hits [N][W][4] int32: hit cell x, hit cell y, side (0: x face, 1: y face),
+ *         slice height h in rows;
+ *  d_perp [N][W] float32: perpendicular distance of the hit. */
+jx_status jx_debug_rays(jx_env* env, void* stream, int32_t* d_hits, float* d_perp);
+
+/* State access (checkpoint / resume and lockstep testing). The state is one
+ * device block of struct-of-arrays fields; jx_state_field gives each field's
+ * byte offset and size inside it (fields: JX_F_*). jx_get_state copies the
+ * whole block to the host and waits; jx_set_state copies it back and waits.
+ * `bytes` must equal jx_state_bytes. */
+enum {
+  JX_F_CELL_X = 0,   /* int16  [N]   cell column of the position            */
+  JX_F_CELL_Y = 1,   /* int16  [N]   cell row of the position               */
+  JX_F_FRAC_X = 2,   /* float  [N]   x - cell_x in [0, 1)                   */
+  JX_F_FRAC_Y = 3,   /* float  [N]   y - cell_y in [0, 1)                   */
+  JX_F_THETA0 = 4,   /* float  [N]   heading at episode start (radians)     */
+  JX_F_TURN = 5,     /* int16  [N]   heading = theta0 + turn * 2pi/turns_per_rev */
+  JX_F_T = 6,        /* int32  [N]   steps taken in the episode             */
+  JX_F_EPISODE = 7,  /* uint32 [N]   episode counter                        */
+  JX_F_FLAGS = 8,    /* uint8  [N]   bit 0: key held                        */
+  JX_F_OBJ = 9,      /* int16  [N][6] key x, key y, goal x, goal y, door x, door y (-1: none) */
+  JX_F_NSPR = 10,    /* uint8  [N]   sprites in use                         */
+  JX_F_SPR_X = 11,   /* float  [N][K] sprite x (absolute map coordinate)    */
+  JX_F_SPR_Y = 12,   /* float  [N][K] sprite y                              */
+  JX_F_SPR_TYPE = 13, /* uint8 [N][K] 0 none, 1 key, 2 goal, 3 distractor   */
+  JX_F_MAP = 14,     /* uint8  [N][S][S] 0 floor, 1..4 wall types, 5 locked door */
+  JX_F_COUNT = 15
+};
+jx_status jx_state_bytes(const jx_env* env, size_t* bytes);
+jx_status jx_state_field(const jx_env* env, int32_t field, size_t* offset, size_t* bytes);
+jx_status jx_get_state(jx_env* env, void* h_buf, size_t bytes);
+jx_status jx_set_state(jx_env* env, const void* h_buf, size_t bytes);
+
+/* Wait for `stream`, then read and clear the device error word: JX_OK, or
+ * JX_EDEVICE when a kernel recorded bad data since the last call. */
+jx_status jx_sync_status(jx_env* env, void* stream);
+
+/* Number of kernel launches this env has issued since creation. */
+jx_status jx_launch_count(const jx_env* env, uint64_t* count);
+
+/* Launch shape of the fused step kernel: grid blocks, threads per block,
+ * dynamic shared memory bytes per block. */
+jx_status jx_launch_shape(const jx_env* env, int32_t* grid, int32_t* block, int32_t* smem_bytes);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* jx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JX_H */

@@ -1,0 +1,449 @@
+// jx_api.cu — host side of the C ABI declared in include/jx.h: argument
+// validation, the struct-of-arrays state block in device memory, per-env
+// constant tables, launch shapes and the checkpoint / test hooks.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/jx.h"
+#include "jx_internal.h"
+
+struct jx_env {
+  jx_config cfg;
+  int device = 0;
+  int num_sms = 0;
+  int blocks_per_sm = 0;
+  int grid = 0;
+  int smem_block = 0;
+  jx::Params base{};
+  // struct-of-arrays state block
+  uint8_t* state = nullptr;
+  size_t state_bytes = 0;
+  size_t field_off[JX_F_COUNT] = {};
+  size_t field_size[JX_F_COUNT] = {};
+  // device error word, turn table, column table
+  uint8_t* aux = nullptr;
+  // maze generation work space, one slot per resident warp
+  uint8_t* scratch = nullptr;
+  // staging buffers of jx_step_host
+  uint8_t* stage = nullptr;
+  size_t stage_frames_off = 0, stage_rewards_off = 0, stage_dones_off = 0;
+  std::atomic<uint64_t> launches{0};
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+jx_status fail(jx_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+jx_status cuda_fail(cudaError_t err, const char* what) {
+  return fail(JX_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(err), cudaGetErrorString(err));
+}
+
+// Makes the env's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+jx_status validate(const jx_config* c) {
+  if (!c) return fail(JX_EINVAL, "config is NULL");
+  if (c->n_envs < 1) return fail(JX_EINVAL, "n_envs must be >= 1 (got %d)", c->n_envs);
+  if (c->task != JX_TASK_ROOMS && c->task != JX_TASK_MAZE_KEYDOOR)
+    return fail(JX_EINVAL, "unknown task %d", c->task);
+  if (c->map_side < 3 || c->map_side > jx::kMaxSide)
+    return fail(JX_EINVAL, "map_side must be in [3, %d] (got %d)", jx::kMaxSide, c->map_side);
+  if (c->task == JX_TASK_MAZE_KEYDOOR && (c->map_side < 6 || c->map_side % 2 != 0))
+    return fail(JX_EINVAL, "maze map_side must be even and >= 6 (got %d)", c->map_side);
+  if (c->frame_h < 1 || c->frame_h > jx::kMaxH)
+    return fail(JX_EINVAL, "frame_h must be in [1, %d] (got %d)", jx::kMaxH, c->frame_h);
+  if (c->frame_w < 16 || c->frame_w > jx::kMaxW || c->frame_w % 16 != 0)
+    return fail(JX_EINVAL, "frame_w must be a multiple of 16 in [16, %d] (got %d)", jx::kMaxW, c->frame_w);
+  if (c->max_sprites < 0 || c->max_sprites > jx::kMaxSprites)
+    return fail(JX_EINVAL, "max_sprites must be in [0, %d] (got %d)", jx::kMaxSprites, c->max_sprites);
+  if (c->task == JX_TASK_MAZE_KEYDOOR && c->max_sprites < 2)
+    return fail(JX_EINVAL, "the maze task needs max_sprites >= 2 (key and goal)");
+  if (c->horizon < 0) return fail(JX_EINVAL, "horizon must be >= 0");
+  if (c->turns_per_rev < 1 || c->turns_per_rev > 32767) return fail(JX_EINVAL, "turns_per_rev must be in [1, 32767]");
+  if (!(c->wall_prob >= 0.0 && c->wall_prob <= 1.0)) return fail(JX_EINVAL, "wall_prob must be in [0, 1]");
+  if (!(c->fov_deg > 0.0 && c->fov_deg < 180.0)) return fail(JX_EINVAL, "fov_deg must be in (0, 180)");
+  if (!(c->move_step >= 0.0 && c->move_step <= 0.5)) return fail(JX_EINVAL, "move_step must be in [0, 0.5]");
+  if (!(c->radius >= 0.0 && c->radius <= 0.49)) return fail(JX_EINVAL, "radius must be in [0, 0.49]");
+  if (!std::isfinite(c->step_reward) || !std::isfinite(c->key_reward) || !std::isfinite(c->goal_reward))
+    return fail(JX_EINVAL, "rewards must be finite");
+  return JX_OK;
+}
+
+// Field sizes of the state block, in JX_F_* order.
+void layout(jx_env* env) {
+  const size_t N = env->cfg.n_envs, K = env->cfg.max_sprites, S = env->cfg.map_side;
+  const size_t sizes[JX_F_COUNT] = {
+      2 * N,      // cell_x
+      2 * N,      // cell_y
+      4 * N,      // frac_x
+      4 * N,      // frac_y
+      4 * N,      // theta0
+      2 * N,      // turn
+      4 * N,      // t
+      4 * N,      // episode
+      N,          // flags
+      12 * N,     // obj
+      N,          // nspr
+      4 * N * K,  // spr_x
+      4 * N * K,  // spr_y
+      N * K,      // spr_type
+      N * S * S,  // map
+  };
+  size_t off = 0;
+  for (int f = 0; f < JX_F_COUNT; ++f) {
+    env->field_off[f] = off;
+    env->field_size[f] = sizes[f];
+    off += align256(sizes[f] > 0 ? sizes[f] : 1);
+  }
+  env->state_bytes = off;
+}
+
+template <class T>
+T* field_ptr(jx_env* env, int f) {
+  return reinterpret_cast<T*>(env->state + env->field_off[f]);
+}
+
+jx_status check_env(const jx_env* env) {
+  if (!env) return fail(JX_EINVAL, "env is NULL");
+  return JX_OK;
+}
+
+jx_status run(jx_env* env, const jx::Params& p, int mode, void* stream) {
+  DeviceGuard g(env->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaError_t err = jx::launch(p, mode, env->grid, static_cast<cudaStream_t>(stream));
+  if (err != cudaSuccess) return cuda_fail(err, "kernel launch");
+  env->launches.fetch_add(1, std::memory_order_relaxed);
+  return JX_OK;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* jx_last_error(void) { return g_last_error.c_str(); }
+
+jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
+  if (!out) return fail(JX_EINVAL, "out is NULL");
+  *out = nullptr;
+  jx_status st = validate(cfg);
+  if (st != JX_OK) return st;
+  int ndev = 0;
+  cudaError_t err = cudaGetDeviceCount(&ndev);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(JX_EINVAL, "device %d out of range (%d devices)", device, ndev);
+
+  jx_env* env = new (std::nothrow) jx_env();
+  if (!env) return fail(JX_ENOMEM, "host allocation failed");
+  env->cfg = *cfg;
+  env->device = device;
+  DeviceGuard g(device);
+  if (g.err != cudaSuccess) {
+    delete env;
+    return cuda_fail(g.err, "cudaSetDevice");
+  }
+  layout(env);
+
+  const jx_config& c = *cfg;
+  const int W = c.frame_w, tpr = c.turns_per_rev;
+  // aux block: error word | turn table | column table
+  const size_t aux_err = 0, aux_turn = 256, aux_col = align256(aux_turn + 8 * (size_t)tpr);
+  const size_t aux_bytes = align256(aux_col + 4 * (size_t)W);
+  if ((err = cudaMalloc(&env->state, env->state_bytes)) != cudaSuccess ||
+      (err = cudaMalloc(&env->aux, aux_bytes)) != cudaSuccess) {
+    jx_destroy(env);
+    return fail(JX_ENOMEM, "cudaMalloc of %zu state bytes failed: %s", env->state_bytes, cudaGetErrorString(err));
+  }
+  cudaMemset(env->state, 0, env->state_bytes);
+  {
+    // per-env constant tables, computed in double and rounded once
+    std::string host(aux_bytes, '\0');
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    float* turn = reinterpret_cast<float*>(&host[aux_turn]);
+    for (int k = 0; k < tpr; ++k) {
+      double a = two_pi * (double)k / (double)tpr;
+      turn[2 * k] = (float)std::cos(a);
+      turn[2 * k + 1] = (float)std::sin(a);
+    }
+    float* colk = reinterpret_cast<float*>(&host[aux_col]);
+    const double t = std::tan(0.5 * c.fov_deg * 3.14159265358979323846 / 180.0);
+    for (int col = 0; col < W; ++col) colk[col] = (float)((2.0 * (col + 0.5) / W - 1.0) * t);
+    err = cudaMemcpy(env->aux, host.data(), aux_bytes, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
+      jx_destroy(env);
+      return cuda_fail(err, "cudaMemcpy of tables");
+    }
+  }
+
+  jx::Params& p = env->base;
+  p.st.cell_x = field_ptr<int16_t>(env, JX_F_CELL_X);
+  p.st.cell_y = field_ptr<int16_t>(env, JX_F_CELL_Y);
+  p.st.frac_x = field_ptr<float>(env, JX_F_FRAC_X);
+  p.st.frac_y = field_ptr<float>(env, JX_F_FRAC_Y);
+  p.st.theta0 = field_ptr<float>(env, JX_F_THETA0);
+  p.st.turn = field_ptr<int16_t>(env, JX_F_TURN);
+  p.st.t = field_ptr<int32_t>(env, JX_F_T);
+  p.st.episode = field_ptr<uint32_t>(env, JX_F_EPISODE);
+  p.st.flags = field_ptr<uint8_t>(env, JX_F_FLAGS);
+  p.st.obj = field_ptr<int16_t>(env, JX_F_OBJ);
+  p.st.nspr = field_ptr<uint8_t>(env, JX_F_NSPR);
+  p.st.spr_x = field_ptr<float>(env, JX_F_SPR_X);
+  p.st.spr_y = field_ptr<float>(env, JX_F_SPR_Y);
+  p.st.spr_type = field_ptr<uint8_t>(env, JX_F_SPR_TYPE);
+  p.st.map = field_ptr<uint8_t>(env, JX_F_MAP);
+  p.err = reinterpret_cast<uint32_t*>(env->aux + aux_err);
+  p.turn_cs = reinterpret_cast<const float2*>(env->aux + aux_turn);
+  p.col_k = reinterpret_cast<const float*>(env->aux + aux_col);
+  p.n = c.n_envs;
+  p.S = c.map_side;
+  p.H = c.frame_h;
+  p.W = W;
+  p.K = c.max_sprites;
+  p.horizon = c.horizon;
+  p.tpr = tpr;
+  p.task = c.task;
+  // frame staging: blocks of rows up to 3 KB, two per warp
+  int rows = 3072 / (3 * W);
+  p.rows_per_block = rows < 1 ? 1 : (rows > c.frame_h ? c.frame_h : rows);
+  p.frame_block_bytes = p.rows_per_block * 3 * W;
+  p.map_smem_bytes = (c.map_side * c.map_side + 15) & ~15;
+  p.move = (float)c.move_step;
+  p.radius = (float)c.radius;
+  p.tan_half = (float)std::tan(0.5 * c.fov_deg * 3.14159265358979323846 / 180.0);
+  for (int ev = 0; ev < 4; ++ev)
+    p.reward_lut[ev] =
+        (float)(c.step_reward + ((ev & 1) ? c.key_reward : 0.0) + ((ev & 2) ? c.goal_reward : 0.0));
+  p.seed = c.seed;
+  // wall iff k * 2^-53 < wall_prob for the 53-bit integer k = draw >> 11
+  p.wall_thr = (uint64_t)std::ceil(c.wall_prob * 9007199254740992.0);
+
+  cudaDeviceProp prop;
+  if ((err = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) {
+    jx_destroy(env);
+    return cuda_fail(err, "cudaGetDeviceProperties");
+  }
+  env->num_sms = prop.multiProcessorCount;
+  env->smem_block = jx::block_smem_bytes(p);
+  if ((size_t)env->smem_block > prop.sharedMemPerBlockOptin) {
+    jx_destroy(env);
+    return fail(JX_EINVAL, "configuration needs %d bytes of shared memory per block (limit %zu)", env->smem_block,
+                prop.sharedMemPerBlockOptin);
+  }
+  int bps = 0;
+  for (int mode = 0; mode < 4; ++mode) {
+    int b = 0;
+    if ((err = jx::kernel_blocks_per_sm(p, mode, &b)) != cudaSuccess) {
+      jx_destroy(env);
+      return cuda_fail(err, "occupancy query");
+    }
+    bps = mode == 0 || b < bps ? b : bps;
+  }
+  if (bps < 1) {
+    jx_destroy(env);
+    return fail(JX_EINVAL, "kernel cannot be resident with %d bytes of shared memory", env->smem_block);
+  }
+  env->blocks_per_sm = bps;
+  const long need = (c.n_envs + jx::kWarpsPerBlock - 1) / jx::kWarpsPerBlock;
+  const long cap = (long)bps * env->num_sms;
+  env->grid = (int)(need < cap ? need : cap);
+  // maze work space: one slot per warp of the grid
+  p.gen_scratch_stride = jx::gen_scratch_bytes(c.task, c.map_side);
+  if (p.gen_scratch_stride > 0) {
+    size_t bytes = p.gen_scratch_stride * (size_t)env->grid * jx::kWarpsPerBlock;
+    if ((err = cudaMalloc(&env->scratch, bytes)) != cudaSuccess) {
+      jx_destroy(env);
+      return fail(JX_ENOMEM, "cudaMalloc of %zu scratch bytes failed", bytes);
+    }
+  }
+  p.gen_scratch = env->scratch;
+  if ((err = cudaDeviceSynchronize()) != cudaSuccess) {
+    jx_destroy(env);
+    return cuda_fail(err, "create");
+  }
+  *out = env;
+  return JX_OK;
+}
+
+jx_status jx_destroy(jx_env* env) {
+  if (!env) return JX_OK;
+  {
+    DeviceGuard g(env->device);
+    cudaDeviceSynchronize();
+    if (env->state) cudaFree(env->state);
+    if (env->aux) cudaFree(env->aux);
+    if (env->scratch) cudaFree(env->scratch);
+    if (env->stage) cudaFree(env->stage);
+  }
+  delete env;
+  return JX_OK;
+}
+
+jx_status jx_reset(jx_env* env, void* stream, uint8_t* d_frames) {
+  if (jx_status st = check_env(env)) return st;
+  if (!d_frames || !aligned16(d_frames)) return fail(JX_EINVAL, "d_frames must be a 16-byte aligned device pointer");
+  jx::Params p = env->base;
+  p.frames = d_frames;
+  return run(env, p, jx::MODE_RESET, stream);
+}
+
+jx_status jx_step(jx_env* env, void* stream, const uint8_t* d_actions, uint8_t* d_frames, float* d_rewards,
+                  uint8_t* d_dones) {
+  if (jx_status st = check_env(env)) return st;
+  if (!d_actions || !d_rewards || !d_dones) return fail(JX_EINVAL, "NULL device pointer");
+  if (!d_frames || !aligned16(d_frames)) return fail(JX_EINVAL, "d_frames must be a 16-byte aligned device pointer");
+  jx::Params p = env->base;
+  p.actions = d_actions;
+  p.frames = d_frames;
+  p.rewards = d_rewards;
+  p.dones = d_dones;
+  return run(env, p, jx::MODE_STEP, stream);
+}
+
+jx_status jx_render(jx_env* env, void* stream, uint8_t* d_frames) {
+  if (jx_status st = check_env(env)) return st;
+  if (!d_frames || !aligned16(d_frames)) return fail(JX_EINVAL, "d_frames must be a 16-byte aligned device pointer");
+  jx::Params p = env->base;
+  p.frames = d_frames;
+  return run(env, p, jx::MODE_RENDER, stream);
+}
+
+jx_status jx_debug_rays(jx_env* env, void* stream, int32_t* d_hits, float* d_perp) {
+  if (jx_status st = check_env(env)) return st;
+  if (!d_hits || !d_perp || !aligned16(d_hits)) return fail(JX_EINVAL, "d_hits (16-byte aligned) and d_perp needed");
+  jx::Params p = env->base;
+  p.dbg_hits = d_hits;
+  p.dbg_perp = d_perp;
+  return run(env, p, jx::MODE_RAYS, stream);
+}
+
+jx_status jx_step_host(jx_env* env, void* stream, const uint8_t* h_actions, uint8_t* h_frames, float* h_rewards,
+                       uint8_t* h_dones) {
+  if (jx_status st = check_env(env)) return st;
+  if (!h_actions || !h_frames || !h_rewards || !h_dones) return fail(JX_EINVAL, "NULL host pointer");
+  DeviceGuard g(env->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  const size_t N = env->cfg.n_envs;
+  const size_t frame_bytes = N * 3 * (size_t)env->cfg.frame_h * env->cfg.frame_w;
+  if (!env->stage) {
+    env->stage_frames_off = align256(N);
+    env->stage_rewards_off = env->stage_frames_off + align256(frame_bytes);
+    env->stage_dones_off = env->stage_rewards_off + align256(4 * N);
+    cudaError_t err = cudaMalloc(&env->stage, env->stage_dones_off + align256(N));
+    if (err != cudaSuccess) {
+      env->stage = nullptr;
+      return fail(JX_ENOMEM, "cudaMalloc of host-step staging failed");
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t* d_act = env->stage;
+  uint8_t* d_frames = env->stage + env->stage_frames_off;
+  float* d_rew = reinterpret_cast<float*>(env->stage + env->stage_rewards_off);
+  uint8_t* d_done = env->stage + env->stage_dones_off;
+  cudaError_t err = cudaMemcpyAsync(d_act, h_actions, N, cudaMemcpyHostToDevice, s);
+  if (err != cudaSuccess) return cuda_fail(err, "copy of actions");
+  jx_status st = jx_step(env, stream, d_act, d_frames, d_rew, d_done);
+  if (st != JX_OK) return st;
+  if ((err = cudaMemcpyAsync(h_frames, d_frames, frame_bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(h_rewards, d_rew, 4 * N, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(h_dones, d_done, N, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(err, "copy of results");
+  if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "host step");
+  return JX_OK;
+}
+
+jx_status jx_state_bytes(const jx_env* env, size_t* bytes) {
+  if (jx_status st = check_env(env)) return st;
+  if (!bytes) return fail(JX_EINVAL, "bytes is NULL");
+  *bytes = env->state_bytes;
+  return JX_OK;
+}
+
+jx_status jx_state_field(const jx_env* env, int32_t field, size_t* offset, size_t* bytes) {
+  if (jx_status st = check_env(env)) return st;
+  if (field < 0 || field >= JX_F_COUNT) return fail(JX_EINVAL, "unknown field %d", field);
+  if (offset) *offset = env->field_off[field];
+  if (bytes) *bytes = env->field_size[field];
+  return JX_OK;
+}
+
+jx_status jx_get_state(jx_env* env, void* h_buf, size_t bytes) {
+  if (jx_status st = check_env(env)) return st;
+  if (!h_buf || bytes != env->state_bytes)
+    return fail(JX_EINVAL, "buffer must be %zu bytes (got %zu)", env->state_bytes, bytes);
+  DeviceGuard g(env->device);
+  cudaError_t err = cudaDeviceSynchronize();
+  if (err == cudaSuccess) err = cudaMemcpy(h_buf, env->state, bytes, cudaMemcpyDeviceToHost);
+  return err == cudaSuccess ? JX_OK : cuda_fail(err, "get_state");
+}
+
+jx_status jx_set_state(jx_env* env, const void* h_buf, size_t bytes) {
+  if (jx_status st = check_env(env)) return st;
+  if (!h_buf || bytes != env->state_bytes)
+    return fail(JX_EINVAL, "buffer must be %zu bytes (got %zu)", env->state_bytes, bytes);
+  DeviceGuard g(env->device);
+  cudaError_t err = cudaDeviceSynchronize();
+  if (err == cudaSuccess) err = cudaMemcpy(env->state, h_buf, bytes, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaDeviceSynchronize();
+  return err == cudaSuccess ? JX_OK : cuda_fail(err, "set_state");
+}
+
+jx_status jx_sync_status(jx_env* env, void* stream) {
+  if (jx_status st = check_env(env)) return st;
+  DeviceGuard g(env->device);
+  cudaError_t err = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (err != cudaSuccess) return cuda_fail(err, "stream");
+  uint32_t word = 0;
+  if ((err = cudaMemcpy(&word, env->base.err, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(err, "error word");
+  if (word) {
+    cudaMemset(env->base.err, 0, 4);
+    return fail(JX_EDEVICE, "device error word 0x%x (1: action outside 0..6)", word);
+  }
+  return JX_OK;
+}
+
+jx_status jx_launch_count(const jx_env* env, uint64_t* count) {
+  if (jx_status st = check_env(env)) return st;
+  if (!count) return fail(JX_EINVAL, "count is NULL");
+  *count = env->launches.load(std::memory_order_relaxed);
+  return JX_OK;
+}
+
+jx_status jx_launch_shape(const jx_env* env, int32_t* grid, int32_t* block, int32_t* smem_bytes) {
+  if (jx_status st = check_env(env)) return st;
+  if (grid) *grid = env->grid;
+  if (block) *block = jx::kThreads;
+  if (smem_bytes) *smem_bytes = env->smem_block;
+  return JX_OK;
+}
+
+}  // extern "C"

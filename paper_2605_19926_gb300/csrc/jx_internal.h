@@ -1,0 +1,84 @@
+// jx_internal.h — parameters shared by the host API (jx_api.cu) and the
+// kernels (jx_kernels.cu). Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace jx {
+
+constexpr int kMaxSprites = 16;
+constexpr int kMaxSide = 128;
+constexpr int kMaxH = 256;
+constexpr int kMaxW = 256;
+constexpr int kWarpsPerBlock = 4;
+constexpr int kThreads = kWarpsPerBlock * 32;
+constexpr int kRingBuffers = 2;  // frame row-block staging buffers per warp
+
+enum Mode { MODE_STEP = 0, MODE_RESET = 1, MODE_RENDER = 2, MODE_RAYS = 3 };
+
+enum Purpose : uint32_t {
+  P_WALL = 1,
+  P_SPAWN = 2,
+  P_HEADING = 3,
+  P_DFS = 4,
+  P_KEY = 5,
+  P_NSPRITES = 6,
+  P_SPRITE_CELL = 7
+};
+
+// Device pointers into the struct-of-arrays state block.
+struct State {
+  int16_t* cell_x;
+  int16_t* cell_y;
+  float* frac_x;
+  float* frac_y;
+  float* theta0;
+  int16_t* turn;
+  int32_t* t;
+  uint32_t* episode;
+  uint8_t* flags;
+  int16_t* obj;  // [N][6]
+  uint8_t* nspr;
+  float* spr_x;  // [N][K]
+  float* spr_y;
+  uint8_t* spr_type;
+  uint8_t* map;  // [N][S][S]
+};
+
+struct Params {
+  State st;
+  uint32_t* err;          // device error word
+  const float2* turn_cs;  // [turns_per_rev] (cos, sin) of turn * 2 pi / turns_per_rev
+  const float* col_k;     // [W] (2 (c + 1/2) / W - 1) * tan(fov / 2)
+  uint8_t* gen_scratch;   // [warps][gen_scratch_stride], maze generation work space
+  size_t gen_scratch_stride;
+  const uint8_t* actions;
+  uint8_t* frames;
+  float* rewards;
+  uint8_t* dones;
+  int32_t* dbg_hits;
+  float* dbg_perp;
+  int32_t n, S, H, W, K, horizon, tpr, task;
+  int32_t rows_per_block;  // rows per staged frame block
+  int32_t frame_block_bytes;
+  int32_t map_smem_bytes;  // S * S rounded up to 16
+  float move, radius, tan_half;
+  float reward_lut[4];
+  uint64_t seed;
+  uint64_t wall_thr;  // an interior cell is a wall iff (draw >> 11) < wall_thr
+};
+
+// Shared memory bytes one warp needs, and per block.
+int warp_smem_bytes(const Params& p);
+inline int block_smem_bytes(const Params& p) { return warp_smem_bytes(p) * kWarpsPerBlock; }
+size_t gen_scratch_bytes(int task, int S);
+
+// Configure (attributes) and query occupancy of the kernel for `mode`.
+cudaError_t kernel_blocks_per_sm(const Params& p, int mode, int* blocks);
+// Launch the fused kernel for `mode`.
+cudaError_t launch(const Params& p, int mode, int grid, cudaStream_t stream);
+
+}  // namespace jx

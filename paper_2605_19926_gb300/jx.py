@@ -1,0 +1,239 @@
+"""Thin ctypes binding over ``libjx.so`` (the C ABI in ``include/jx.h``).
+
+Argument marshalling only: every step of the environment runs in the CUDA
+kernels behind the C ABI. Tensors are passed as raw device pointers, streams
+as ``cudaStream_t`` handles. There is no CPU fallback: importing this module
+raises when the compiled library is missing, and every compute call raises
+``JxError`` when the library reports a failure (for example, no GPU).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjx.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, EDEVICE = range(7)
+TASK_ROOMS, TASK_MAZE_KEYDOOR = 0, 1
+
+# State fields (JX_F_*), name -> (index, numpy dtype, per-env shape builder)
+FIELDS = {
+    "cell_x": (0, np.int16), "cell_y": (1, np.int16), "frac_x": (2, np.float32), "frac_y": (3, np.float32),
+    "theta0": (4, np.float32), "turn": (5, np.int16), "t": (6, np.int32), "episode": (7, np.uint32),
+    "flags": (8, np.uint8), "obj": (9, np.int16), "nspr": (10, np.uint8), "spr_x": (11, np.float32),
+    "spr_y": (12, np.float32), "spr_type": (13, np.uint8), "map": (14, np.uint8),
+}
+
+# Entry points declared in include/jx.h (checked by the ABI test).
+SYMBOLS = [
+    "jx_create", "jx_destroy", "jx_reset", "jx_step", "jx_render", "jx_step_host", "jx_debug_rays",
+    "jx_state_bytes", "jx_state_field", "jx_get_state", "jx_set_state", "jx_sync_status", "jx_launch_count",
+    "jx_launch_shape", "jx_last_error",
+]
+
+
+class JxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"jx status {status}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("n_envs", ctypes.c_int32), ("task", ctypes.c_int32), ("map_side", ctypes.c_int32),
+        ("frame_h", ctypes.c_int32), ("frame_w", ctypes.c_int32), ("max_sprites", ctypes.c_int32),
+        ("horizon", ctypes.c_int32), ("turns_per_rev", ctypes.c_int32), ("wall_prob", ctypes.c_double),
+        ("fov_deg", ctypes.c_double), ("move_step", ctypes.c_double), ("radius", ctypes.c_double),
+        ("step_reward", ctypes.c_double), ("key_reward", ctypes.c_double), ("goal_reward", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Config":
+        c = cls()
+        for name, _ in cls._fields_:
+            if name in d:
+                setattr(c, name, d[name])
+        return c
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2605_19926_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+    sig = {
+        "jx_create": [P, ctypes.c_int, P],
+        "jx_destroy": [P],
+        "jx_reset": [P, P, P],
+        "jx_step": [P, P, P, P, P, P],
+        "jx_render": [P, P, P],
+        "jx_step_host": [P, P, P, P, P, P],
+        "jx_debug_rays": [P, P, P, P],
+        "jx_state_bytes": [P, P],
+        "jx_state_field": [P, i32, P, P],
+        "jx_get_state": [P, P, sz],
+        "jx_set_state": [P, P, sz],
+        "jx_sync_status": [P, P],
+        "jx_launch_count": [P, P],
+        "jx_launch_shape": [P, P, P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.jx_last_error.argtypes = []
+    L.jx_last_error.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def last_error() -> str:
+    return lib.jx_last_error().decode()
+
+
+def _check(status: int):
+    if status != OK:
+        raise JxError(status, last_error())
+
+
+def _ptr(t) -> int | None:
+    """Raw pointer of a torch tensor / numpy array / int."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+@dataclass
+class Shape:
+    grid: int
+    block: int
+    smem: int
+
+
+class Env:
+    """N environments on one GPU (``jx_create`` ... ``jx_destroy``)."""
+
+    def __init__(self, cfg: dict, device: int = 0):
+        self.cfg = dict(cfg)
+        self._c = Config.from_dict(cfg)
+        h = ctypes.c_void_p()
+        _check(lib.jx_create(ctypes.byref(self._c), device, ctypes.byref(h)))
+        self._h = h
+        self.device = device
+        self.n = int(cfg["n_envs"])
+        self.H, self.W, self.S, self.K = int(cfg["frame_h"]), int(cfg["frame_w"]), int(cfg["map_side"]), int(
+            cfg["max_sprites"])
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.jx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- compute
+    def reset(self, frames, stream=None):
+        _check(lib.jx_reset(self._h, _stream(stream), _ptr(frames)))
+
+    def step(self, actions, frames, rewards, dones, stream=None):
+        _check(lib.jx_step(self._h, _stream(stream), _ptr(actions), _ptr(frames), _ptr(rewards), _ptr(dones)))
+
+    def render(self, frames, stream=None):
+        _check(lib.jx_render(self._h, _stream(stream), _ptr(frames)))
+
+    def step_host(self, actions, frames, rewards, dones, stream=None):
+        _check(lib.jx_step_host(self._h, _stream(stream), _ptr(actions), _ptr(frames), _ptr(rewards), _ptr(dones)))
+
+    def debug_rays(self, hits, perp, stream=None):
+        _check(lib.jx_debug_rays(self._h, _stream(stream), _ptr(hits), _ptr(perp)))
+
+    def sync_status(self, stream=None):
+        _check(lib.jx_sync_status(self._h, _stream(stream)))
+
+    # ------------------------------------------------------------------ state
+    def state_bytes(self) -> int:
+        n = ctypes.c_size_t()
+        _check(lib.jx_state_bytes(self._h, ctypes.byref(n)))
+        return n.value
+
+    def field(self, name: str) -> tuple[int, int]:
+        off, nb = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib.jx_state_field(self._h, FIELDS[name][0], ctypes.byref(off), ctypes.byref(nb)))
+        return off.value, nb.value
+
+    def get_state(self) -> np.ndarray:
+        buf = np.empty(self.state_bytes(), np.uint8)
+        _check(lib.jx_get_state(self._h, buf.ctypes.data, buf.nbytes))
+        return buf
+
+    def set_state(self, buf: np.ndarray):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(lib.jx_set_state(self._h, buf.ctypes.data, buf.nbytes))
+
+    def fields(self, blob: np.ndarray) -> dict:
+        """Views of every state field inside a ``get_state`` blob."""
+        out = {}
+        N, K, S = self.n, self.K, self.S
+        shapes = {"obj": (N, 6), "spr_x": (N, K), "spr_y": (N, K), "spr_type": (N, K), "map": (N, S, S)}
+        for name, (_, dt) in FIELDS.items():
+            off, nb = self.field(name)
+            a = blob[off: off + nb].view(dt)
+            out[name] = a.reshape(shapes.get(name, (N,)))
+        return out
+
+    # ------------------------------------------------------------------- info
+    def launch_count(self) -> int:
+        n = ctypes.c_uint64()
+        _check(lib.jx_launch_count(self._h, ctypes.byref(n)))
+        return n.value
+
+    def launch_shape(self) -> Shape:
+        g, b, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.jx_launch_shape(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(s)))
+        return Shape(g.value, b.value, s.value)
+
+
+def validate_config(cfg: dict) -> tuple[int, str]:
+    """Run ``jx_create``'s validation (which precedes any CUDA call) on ``cfg``.
+
+    Returns (status, message); a valid config on a machine without a GPU
+    returns ECUDA from the device query that follows validation.
+    """
+    c = Config.from_dict(cfg)
+    h = ctypes.c_void_p()
+    st = lib.jx_create(ctypes.byref(c), 0, ctypes.byref(h))
+    if st == OK:
+        lib.jx_destroy(h)
+    return st, last_error()

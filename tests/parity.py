@@ -1,0 +1,221 @@
+"""Lockstep parity harness: the CUDA path (through the C ABI) against the oracle.
+
+Tolerances (from the accuracy rules the hot path is held to):
+- bit-exact: rewards (float32), done flags, key/door state, episode counters,
+  generated maps, spawn cells and object cells; hit cell and hit side of every
+  ray the oracle does not flag as a corner ray (a finite-precision tie within
+  1e-5 cells could change it); corner rays must stay <= 0.1%;
+- pose within 1e-5 absolute; perpendicular distance within 1e-5 relative;
+- pixels: at most 1e-4 of all pixels may differ, and only pixels the oracle
+  flags as lying on an edge that finite precision can move (slice edges whose
+  height rounding is within tolerance, sprite silhouette edges, corner-ray
+  columns).
+Steps whose collision or pickup decision the oracle flags as a near tie
+(within 1e-5 cells) are excluded for that env and counted (<= 0.1%).
+"""
+
+from __future__ import annotations
+
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2605_19926_gb300 import inputs, jx
+
+TOL_POSE = 1e-5
+TOL_PERP_REL = 1e-5
+PIXEL_FRAC = 1e-4
+CORNER_FRAC = 1e-3
+NEAR_TIE_FRAC = 1e-3
+NTHREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+def oracle_cfg(cfg: dict) -> np.ndarray:
+    return oracle.make_config(**cfg)
+
+
+def to_oracle(env: jx.Env, blob: np.ndarray, idx=None) -> np.ndarray:
+    """Decode the GPU state blob into oracle env records (exactly)."""
+    f = env.fields(blob)
+    N, S, K = env.n, env.S, env.K
+    idx = np.arange(N) if idx is None else np.asarray(idx)
+    o = np.zeros(len(idx), oracle.ENV_DTYPE)
+    o["x"] = f["cell_x"][idx].astype(np.float64) + f["frac_x"][idx].astype(np.float64)
+    o["y"] = f["cell_y"][idx].astype(np.float64) + f["frac_y"][idx].astype(np.float64)
+    o["theta0"] = f["theta0"][idx].astype(np.float64)
+    o["turn"] = f["turn"][idx]
+    o["t"] = f["t"][idx]
+    o["episode"] = f["episode"][idx]
+    o["has_key"] = f["flags"][idx] & 1
+    obj = f["obj"][idx].astype(np.int32)
+    for k, name in enumerate(("key_x", "key_y", "goal_x", "goal_y", "door_x", "door_y")):
+        o[name] = obj[:, k]
+    o["n_sprites"] = f["nspr"][idx]
+    if K:
+        o["spr_x"][:, :K] = f["spr_x"][idx]
+        o["spr_y"][:, :K] = f["spr_y"][idx]
+        o["spr_type"][:, :K] = f["spr_type"][idx]
+    o["map"][:, : S * S] = f["map"][idx].reshape(len(idx), S * S)
+    return o
+
+
+@dataclass
+class Stats:
+    pixels: int = 0
+    pixel_mismatch: int = 0
+    rays: int = 0
+    corner_rays: int = 0
+    env_steps: int = 0
+    near_ties: int = 0
+    key_events: int = 0
+    goal_events: int = 0
+    resets: int = 0
+    notes: list = field(default_factory=list)
+
+    def check(self):
+        assert self.pixel_mismatch <= PIXEL_FRAC * max(self.pixels, 1), self
+        assert self.corner_rays <= CORNER_FRAC * max(self.rays, 1), self
+        assert self.near_ties <= max(2, NEAR_TIE_FRAC * self.env_steps), self
+
+
+def compare_generated(gpu: np.ndarray, ref: np.ndarray, S: int, K: int, where: str = ""):
+    """A freshly generated episode: everything exact (theta0 is the float32 rounding of the FP64 value)."""
+    n = S * S
+    assert (gpu["map"][:, :n] == ref["map"][:, :n]).all(), f"maps differ {where}"
+    for name in ("key_x", "key_y", "goal_x", "goal_y", "door_x", "door_y", "n_sprites", "turn", "t", "episode",
+                 "has_key"):
+        assert (gpu[name] == ref[name]).all(), f"{name} differs {where}"
+    assert (gpu["x"] == ref["x"]).all() and (gpu["y"] == ref["y"]).all(), f"spawn differs {where}"
+    assert (gpu["theta0"].astype(np.float32) == ref["theta0"].astype(np.float32)).all(), f"theta0 differs {where}"
+    if K:
+        assert (gpu["spr_type"][:, :K] == ref["spr_type"][:, :K]).all()
+        assert (gpu["spr_x"][:, :K] == ref["spr_x"][:, :K].astype(np.float32)).all()
+        assert (gpu["spr_y"][:, :K] == ref["spr_y"][:, :K].astype(np.float32)).all()
+
+
+def compare_frames(gpu_frames: np.ndarray, ref: dict, stats: Stats, mask=None):
+    of, amb = ref["frames"], ref["ambiguous"].astype(bool)
+    if mask is not None:
+        gpu_frames, of, amb = gpu_frames[mask], of[mask], amb[mask]
+    mism = (gpu_frames != of).any(axis=-1)
+    bad = mism & ~amb
+    if bad.any():
+        e, y, x = np.argwhere(bad)[0]
+        raise AssertionError(f"pixel ({e},{y},{x}) gpu {gpu_frames[e, y, x]} oracle {of[e, y, x]} not an edge")
+    stats.pixels += mism.size
+    stats.pixel_mismatch += int(mism.sum())
+
+
+def compare_rays(hits: np.ndarray, perp: np.ndarray, ref: dict, stats: Stats, mask=None):
+    rays = ref["rays"]
+    if mask is not None:
+        hits, perp, rays = hits[mask], perp[mask], rays[mask]
+    corner = rays["corner"].astype(bool)
+    ok = ~corner
+    assert (hits[..., 0][ok] == rays["cell_x"][ok]).all(), "hit cell x"
+    assert (hits[..., 1][ok] == rays["cell_y"][ok]).all(), "hit cell y"
+    assert (hits[..., 2][ok] == rays["side"][ok]).all(), "hit side"
+    po, pg = rays["perp"][ok], perp[ok].astype(np.float64)
+    diff = np.where(po == pg, 0.0, np.abs(pg - po))
+    rel = np.where(po > 0, diff / np.where(po > 0, po, 1.0), diff)
+    assert rel.max(initial=0.0) <= TOL_PERP_REL, f"perp rel err {rel.max()}"
+    hok = ok & ~rays["h_ambiguous"].astype(bool)
+    assert (hits[..., 3][hok] == rays["h"][hok]).all(), "slice height"
+    stats.rays += corner.size
+    stats.corner_rays += int(corner.sum())
+
+
+class Run:
+    """One CUDA env batch plus its torch output buffers."""
+
+    def __init__(self, cfg: dict, device: int = 0):
+        self.cfg = cfg
+        self.env = jx.Env(cfg, device)
+        self.ocfg = oracle_cfg(cfg)
+        N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
+        dev = torch.device("cuda", device)
+        self.frames = torch.zeros((N, H, W, 3), dtype=torch.uint8, device=dev)
+        self.rewards = torch.zeros(N, dtype=torch.float32, device=dev)
+        self.dones = torch.zeros(N, dtype=torch.uint8, device=dev)
+        self.hits = torch.zeros((N, W, 4), dtype=torch.int32, device=dev)
+        self.perp = torch.zeros((N, W), dtype=torch.float32, device=dev)
+        self.actions = torch.zeros(N, dtype=torch.uint8, device=dev)
+        self.dev = dev
+
+    def state(self, idx=None) -> np.ndarray:
+        return to_oracle(self.env, self.env.get_state(), idx)
+
+    def rays(self):
+        self.env.debug_rays(self.hits, self.perp)
+        torch.cuda.synchronize()
+        return self.hits.cpu().numpy(), self.perp.cpu().numpy()
+
+    def reset(self):
+        self.env.reset(self.frames)
+        torch.cuda.synchronize()
+
+    def step(self, actions: np.ndarray):
+        self.actions.copy_(torch.from_numpy(actions))
+        self.env.step(self.actions, self.frames, self.rewards, self.dones)
+        torch.cuda.synchronize()
+        return self.frames.cpu().numpy(), self.rewards.cpu().numpy(), self.dones.cpu().numpy()
+
+
+def check_reset(run: Run, stats: Stats, idx=None):
+    N = run.cfg["n_envs"]
+    idx = np.arange(N) if idx is None else np.asarray(idx)
+    run.reset()
+    gpu = run.state(idx)
+    ref = oracle.generate(run.ocfg, idx.astype(np.int32), 0, nthreads=NTHREADS)
+    compare_generated(gpu, ref, run.env.S, run.env.K, "at reset")
+    # render parity on the exact same state (the GPU's, decoded)
+    out = oracle.render(run.ocfg, gpu, nthreads=NTHREADS)
+    compare_frames(run.frames.cpu().numpy()[idx], out, stats)
+    hits, perp = run.rays()
+    compare_rays(hits[idx], perp[idx], out, stats)
+
+
+def lockstep(run: Run, stats: Stats, n_steps: int, seed: int, first_step: int = 0, idx=None, check_every: int = 1):
+    """Step the GPU batch; on checked steps, step the oracle from the GPU's
+    pre-step state (of envs ``idx``) and compare rewards, dones, poses and
+    regenerated episodes; then render the GPU's post-step state in the oracle
+    and compare frames and rays."""
+    N = run.cfg["n_envs"]
+    idx = np.arange(N) if idx is None else np.asarray(idx)
+    for s in range(first_step, first_step + n_steps):
+        a = inputs.actions(seed, s, N)
+        check = (s - first_step) % check_every == 0
+        if check:
+            prev = run.state(idx)
+        frames, rewards, dones = run.step(a)
+        if not check:
+            continue
+        cur = run.state(idx)
+        ref = oracle.step(run.ocfg, idx.astype(np.int32), prev, a[idx], nthreads=NTHREADS)
+        ev = ref["events"]
+        near = (ev & oracle.EV_NEAR_TIE) != 0
+        ok = ~near
+        stats.env_steps += len(idx)
+        stats.near_ties += int(near.sum())
+        stats.key_events += int(((ev & oracle.EV_KEY) != 0)[ok].sum())
+        stats.goal_events += int(((ev & oracle.EV_GOAL) != 0)[ok].sum())
+        assert (rewards[idx][ok] == ref["rewards"][ok]).all(), f"rewards differ at step {s}"
+        assert (dones[idx][ok] == ref["dones"][ok]).all(), f"dones differ at step {s}"
+        done = (ref["dones"] == 1) & ok
+        stats.resets += int(done.sum())
+        if done.any():
+            compare_generated(cur[done], prev[done], run.env.S, run.env.K, f"after auto-reset at step {s}")
+        live = ok & ~done
+        for name in ("turn", "t", "episode", "has_key"):
+            assert (cur[name][live] == prev[name][live]).all(), f"{name} differs at step {s}"
+        for name in ("x", "y"):
+            err = np.abs(cur[name][live] - prev[name][live])
+            assert err.max(initial=0.0) <= TOL_POSE, f"{name} err {err.max()} at step {s}"
+        # render parity on the exact post-step state of the GPU
+        rr = oracle.render(run.ocfg, cur, nthreads=NTHREADS)
+        compare_frames(frames[idx], rr, stats)
+        hits, perp = run.rays()
+        compare_rays(hits[idx], perp[idx], rr, stats)

@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point the header declares, and validates configurations before
+touching CUDA."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+import torch
+
+from paper_2605_19926_gb300 import build, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "jx.h")
+
+
+@pytest.fixture(scope="module")
+def jx():
+    build.build()
+    from paper_2605_19926_gb300 import jx as mod
+
+    return mod
+
+
+def _declared():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:jx_status|const char\*)\s+(jx_\w+)\s*\(", text, re.M)))
+
+
+def test_header_declares_expected_entry_points(jx):
+    assert _declared() == sorted(jx.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(jx):
+    out = subprocess.run(["nm", "-D", "--defined-only", jx.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (jx_\w+)$", out, re.M))
+    for name in _declared():
+        assert name in exported, name
+        assert getattr(jx.lib, name) is not None
+
+
+def test_field_enum_matches_header(jx):
+    text = open(HEADER).read()
+    enum = dict((m.group(1).lower(), int(m.group(2))) for m in re.finditer(r"JX_F_(\w+) = (\d+)", text))
+    assert enum.pop("count") == len(jx.FIELDS)
+    assert {k: v[0] for k, v in jx.FIELDS.items()} == enum
+
+
+def test_config_struct_matches_header(jx):
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct \{(.*?)\} jx_config;", text, re.S).group(1)
+    names = []
+    for decl in re.findall(r"^\s*(?:int32_t|double|uint64_t)\s+([^;]+);", body, re.M):
+        names += [n.strip() for n in decl.split(",")]
+    assert names == [f[0] for f in jx.Config._fields_]
+    assert ctypes.sizeof(jx.Config) == 8 * 4 + 7 * 8 + 8
+
+
+BAD = [
+    (dict(n_envs=0), "n_envs"),
+    (dict(task=7), "task"),
+    (dict(map_side=2), "map_side"),
+    (dict(map_side=129), "map_side"),
+    (dict(frame_w=40), "frame_w"),
+    (dict(frame_w=272), "frame_w"),
+    (dict(frame_h=0), "frame_h"),
+    (dict(max_sprites=17), "max_sprites"),
+    (dict(turns_per_rev=0), "turns_per_rev"),
+    (dict(fov_deg=180.0), "fov_deg"),
+    (dict(move_step=0.6), "move_step"),
+    (dict(radius=0.5), "radius"),
+    (dict(wall_prob=1.5), "wall_prob"),
+    (dict(horizon=-1), "horizon"),
+    (dict(step_reward=float("nan")), "rewards"),
+]
+
+
+@pytest.mark.parametrize("patch,word", BAD)
+def test_invalid_config_rejected_before_cuda(jx, patch, word):
+    cfg = dict(inputs.rooms(n_envs=4), **patch)
+    st, msg = jx.validate_config(cfg)
+    assert st == jx.EINVAL and word in msg
+
+
+def test_maze_constraints(jx):
+    for patch in (dict(map_side=7), dict(map_side=4), dict(max_sprites=1)):
+        st, msg = jx.validate_config(dict(inputs.maze_keydoor(n_envs=4), **patch))
+        assert st == jx.EINVAL, patch
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU failure path")
+def test_valid_config_without_gpu_fails_loudly(jx):
+    st, msg = jx.validate_config(inputs.batched_keydoor_mazes(16))
+    assert st == jx.ECUDA and msg
+    with pytest.raises(jx.JxError):
+        jx.Env(inputs.single_env_rooms())

@@ -1,0 +1,185 @@
+"""CUDA path vs the FP64 oracle, through the C ABI, on seeded synthetic inputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_19926_gb300 import inputs
+from parity import NTHREADS, Run, Stats, check_reset, compare_frames, compare_rays, lockstep, to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2605_19926_gb300 import build
+
+    build.build()
+    assert torch.cuda.is_available()
+
+
+CASES = {
+    "rooms16": inputs.rooms(n_envs=5, map_side=16, wall_prob=0.25, seed=0),
+    "rooms16_sprites_40x48": inputs.rooms(n_envs=33, map_side=16, wall_prob=0.3, seed=4, max_sprites=8, frame_h=40,
+                                          frame_w=48),
+    "maze32_ragged": inputs.maze_keydoor(n_envs=37, map_side=32, seed=1, horizon=60),
+    "maze8_events": inputs.maze_keydoor(n_envs=64, map_side=8, seed=3, horizon=80),
+    "maze18_96x128": inputs.maze_keydoor(n_envs=9, map_side=18, seed=7, horizon=30, frame_h=96, frame_w=128),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_reset_matches_oracle(name):
+    run = Run(CASES[name])
+    stats = Stats()
+    check_reset(run, stats)
+    stats.check()
+
+
+def test_single_env_rooms_1000_steps():
+    """1 env, 16 x 16 random rooms, 64 x 64, 1000 uniform random steps, seed 0."""
+    cfg = inputs.single_env_rooms()
+    run = Run(cfg)
+    stats = Stats()
+    check_reset(run, stats)
+    lockstep(run, stats, 1000, seed=0)
+    stats.check()
+
+
+@pytest.mark.parametrize("name,steps", [("maze32_ragged", 150), ("maze8_events", 300),
+                                        ("rooms16_sprites_40x48", 120), ("maze18_96x128", 70)])
+def test_lockstep(name, steps):
+    run = Run(CASES[name])
+    stats = Stats()
+    check_reset(run, stats)
+    lockstep(run, stats, steps, seed=11)
+    stats.check()
+    if name == "maze8_events":
+        assert stats.key_events > 0 and stats.goal_events > 0 and stats.resets > 0, stats
+    if name in ("maze32_ragged", "maze18_96x128"):
+        assert stats.resets > 0
+
+
+def test_full_size_batched_mazes_sampled():
+    """4096 envs, 32 x 32 key-door mazes, 64 x 64 frames, in the benchmark's launch
+    shape: 64 sampled envs checked in lockstep around the start and across the
+    500-step horizon (all envs reset there)."""
+    cfg = inputs.batched_keydoor_mazes()
+    run = Run(cfg)
+    stats = Stats()
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(cfg["n_envs"], 64, replace=False))
+    idx[-1] = cfg["n_envs"] - 1
+    check_reset(run, stats, idx)
+    lockstep(run, stats, 8, seed=1, first_step=0, idx=idx)
+    lockstep(run, stats, 488, seed=1, first_step=8, idx=idx, check_every=61)
+    lockstep(run, stats, 8, seed=1, first_step=496, idx=idx)
+    assert stats.resets >= 60
+    stats.check()
+
+
+def test_render_only_and_state_roundtrip():
+    cfg = inputs.maze_keydoor(n_envs=20, map_side=16, seed=2, horizon=0)
+    run = Run(cfg)
+    run.reset()
+    for s in range(30):
+        run.step(inputs.actions(9, s, 20))
+    blob = run.env.get_state()
+    run.env.set_state(blob)
+    assert (run.env.get_state() == blob).all()
+    run.env.render(run.frames)
+    torch.cuda.synchronize()
+    gpu = run.frames.cpu().numpy()
+    ref = oracle.render(run.ocfg, to_oracle(run.env, blob), nthreads=NTHREADS)
+    stats = Stats()
+    compare_frames(gpu, ref, stats)
+    stats.check()
+
+
+def test_degenerate_poses_axis_rays_and_boundaries():
+    """Rays exactly along the axes, positions exactly on cell boundaries, key held."""
+    cfg = inputs.maze_keydoor(n_envs=8, map_side=16, seed=6, horizon=0)
+    run = Run(cfg)
+    run.reset()
+    blob = run.env.get_state()
+    f = run.env.fields(blob)
+    f["theta0"][:] = 0.0
+    f["turn"][:] = np.arange(8) * 9  # multiples of 45 degrees
+    f["frac_x"][::2] = 0.0
+    f["frac_y"][1::2] = 0.0
+    f["flags"][4:] = 1
+    run.env.set_state(blob)
+    run.env.render(run.frames)
+    torch.cuda.synchronize()
+    ref = oracle.render(run.ocfg, to_oracle(run.env, blob), nthreads=NTHREADS)
+    stats = Stats()
+    compare_frames(run.frames.cpu().numpy(), ref, stats)
+    hits, perp = run.rays()
+    compare_rays(hits, perp, ref, stats)
+    stats.check()
+
+
+@pytest.mark.parametrize("patch", [dict(wall_prob=1.0), dict(wall_prob=0.0), dict(horizon=1), dict(move_step=0.0),
+                                   dict(radius=0.0)])
+def test_edge_configs(patch):
+    cfg = dict(inputs.rooms(n_envs=6, map_side=12, seed=8, max_sprites=3), **patch)
+    run = Run(cfg)
+    stats = Stats()
+    check_reset(run, stats)
+    lockstep(run, stats, 40, seed=2)
+    stats.check()
+
+
+def test_max_sizes():
+    """128 x 128 maze, 16 sprite slots, 256 x 256 frames."""
+    cfg = dict(inputs.maze_keydoor(n_envs=3, map_side=128, seed=12, horizon=0, frame_h=256, frame_w=256),
+               max_sprites=16)
+    run = Run(cfg)
+    stats = Stats()
+    check_reset(run, stats)
+    lockstep(run, stats, 5, seed=3)
+    stats.check()
+
+
+def test_invalid_action_is_reported_and_ignored():
+    from paper_2605_19926_gb300 import jx
+
+    cfg = inputs.rooms(n_envs=4, map_side=12, seed=1)
+    run = Run(cfg)
+    run.reset()
+    before = run.env.get_state()
+    run.step(np.array([9, 0, 0, 200], np.uint8))
+    with pytest.raises(jx.JxError) as ei:
+        run.env.sync_status()
+    assert ei.value.status == jx.EDEVICE
+    run.env.sync_status()  # cleared
+    after = run.env.fields(run.env.get_state())
+    b = run.env.fields(before)
+    assert (after["frac_x"] == b["frac_x"]).all() and (after["t"] == b["t"] + 1).all()
+
+
+def test_step_host_matches_device_step():
+    cfg = inputs.maze_keydoor(n_envs=50, map_side=16, seed=4, horizon=25)
+    a, b = Run(cfg), Run(cfg)
+    a.reset()
+    b.reset()
+    hf = torch.zeros((50, 64, 64, 3), dtype=torch.uint8).pin_memory()
+    hr = torch.zeros(50, dtype=torch.float32).pin_memory()
+    hd = torch.zeros(50, dtype=torch.uint8).pin_memory()
+    for s in range(60):
+        act = inputs.actions(4, s, 50)
+        f, r, d = a.step(act)
+        b.env.step_host(torch.from_numpy(act), hf, hr, hd)
+        assert (hf.numpy() == f).all() and (hr.numpy() == r).all() and (hd.numpy() == d).all()
+
+
+def test_same_seed_same_frames():
+    cfg = inputs.maze_keydoor(n_envs=16, map_side=16, seed=21, horizon=20)
+    a, b = Run(cfg), Run(cfg)
+    a.reset()
+    b.reset()
+    for s in range(45):
+        act = inputs.actions(3, s, 16)
+        fa, ra, da = a.step(act)
+        fb, rb, db = b.step(act)
+        assert (fa == fb).all() and (ra == rb).all() and (da == db).all()
