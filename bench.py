@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/s incl. render (frames/s) at 64x64 RGB"
-GRAPH_STEPS = 128  # launches per CUDA graph = rollout buffer slots
+GRAPH_STEPS = 128  # default launches per CUDA graph = rollout buffer slots
 KERNEL_SOURCES = ["paper_2605_19926_gb300/csrc/jx_kernels.cu", "paper_2605_19926_gb300/csrc/jx_internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -178,6 +178,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=600)
     ap.add_argument("--ref-envs", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ring-slots", type=int, default=GRAPH_STEPS,
+                    help="rollout buffer slots = launches per CUDA graph (smaller for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -208,31 +210,32 @@ def main():
     N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
     dev = torch.device("cuda", local)
     env = jx.Env(cfg, local)
+    ring = args.ring_slots
     total_steps = args.warmup + args.steps
     # inputs resident in HBM before timing: the whole action stream
     acts_host = inputs.action_stream(cfg["seed"], total_steps, N)
     acts = torch.from_numpy(acts_host).to(dev)
-    ring_acts = torch.empty((GRAPH_STEPS, N), dtype=torch.uint8, device=dev)
-    frames = torch.empty((GRAPH_STEPS, N, H, W, 3), dtype=torch.uint8, device=dev)  # 6.4 GB rollout buffer
-    rewards = torch.empty((GRAPH_STEPS, N), dtype=torch.float32, device=dev)
-    dones = torch.empty((GRAPH_STEPS, N), dtype=torch.uint8, device=dev)
+    ring_acts = torch.empty((ring, N), dtype=torch.uint8, device=dev)
+    frames = torch.empty((ring, N, H, W, 3), dtype=torch.uint8, device=dev)  # 6.4 GB rollout buffer at 128 slots
+    rewards = torch.empty((ring, N), dtype=torch.float32, device=dev)
+    dones = torch.empty((ring, N), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.synchronize()
 
     with torch.cuda.stream(stream):
         env.reset(frames[0], stream)
         for s in range(args.warmup):
-            env.step(acts[s], frames[s % GRAPH_STEPS], rewards[s % GRAPH_STEPS], dones[s % GRAPH_STEPS], stream)
+            env.step(acts[s], frames[s % ring], rewards[s % ring], dones[s % ring], stream)
     stream.synchronize()
 
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
-        for i in range(GRAPH_STEPS):
+        for i in range(ring):
             env.step(ring_acts[i], frames[i], rewards[i], dones[i], torch.cuda.current_stream())
     torch.cuda.synchronize()
     # the capture itself ran nothing; the env state is still after the warm-up
 
-    n_full, rem = divmod(args.steps, GRAPH_STEPS)
+    n_full, rem = divmod(args.steps, ring)
     launches_before = env.launch_count()
     clocks = ClockSampler(local)
     if world > 1:
@@ -245,9 +248,9 @@ def main():
         ev0.record(stream)
         s = args.warmup
         for c in range(n_full):
-            ring_acts.copy_(acts[s: s + GRAPH_STEPS], non_blocking=True)
+            ring_acts.copy_(acts[s: s + ring], non_blocking=True)
             graph.replay()
-            s += GRAPH_STEPS
+            s += ring
         for i in range(rem):
             env.step(acts[s], frames[i], rewards[i], dones[i], stream)
             s += 1
@@ -256,7 +259,7 @@ def main():
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     eager_launches = env.launch_count() - launches_before
-    gpu_launches = n_full * GRAPH_STEPS + eager_launches
+    gpu_launches = n_full * ring + eager_launches
     t_max = ms
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -272,8 +275,8 @@ def main():
         for i in range(args.latency_steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            env.step(acts[(args.warmup + i) % total_steps], frames[i % GRAPH_STEPS], rewards[i % GRAPH_STEPS],
-                     dones[i % GRAPH_STEPS], stream)
+            env.step(acts[(args.warmup + i) % total_steps], frames[i % ring], rewards[i % ring], dones[i % ring],
+                     stream)
             b.record(stream)
             b.synchronize()
             lat.append(a.elapsed_time(b))
@@ -329,9 +332,9 @@ def main():
                                "auto-reset, uniform random actions, seed 1",
                    "n_envs_per_gpu": N, "map_side": cfg["map_side"], "frame": f"{H}x{W}x3",
                    "parallelism": f"replicas x{world}",
-                   "l2": "frames written to a 128-slot rollout buffer (6.4 GB) > L2",
+                   "l2": f"frames written to a {ring}-slot rollout buffer ({ring * N * H * W * 3 / 1e9:.1f} GB) > L2",
                    "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
-                              "cuda_graph_steps": GRAPH_STEPS}},
+                              "cuda_graph_steps": ring}},
         "p50_step_ms": p50, "p99_step_ms": p99,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,

@@ -178,7 +178,16 @@ def check_reset(run: Run, stats: Stats, idx=None):
     compare_rays(hits[idx], perp[idx], out, stats)
 
 
-def lockstep(run: Run, stats: Stats, n_steps: int, seed: int, first_step: int = 0, idx=None, check_every: int = 1):
+def forward_biased_actions(seed: int, step: int, n: int) -> np.ndarray:
+    """60% forward, otherwise a turn or a strafe: a walk that travels far enough
+    to reach keys, doors and goals within a short test."""
+    rng = np.random.default_rng([seed, step, 77])
+    other = rng.choice(np.array([3, 4, 5, 6], np.uint8), size=n)
+    return np.where(rng.random(n) < 0.6, np.uint8(1), other).astype(np.uint8)
+
+
+def lockstep(run: Run, stats: Stats, n_steps: int, seed: int, first_step: int = 0, idx=None, check_every: int = 1,
+             action_fn=inputs.actions):
     """Step the GPU batch; on checked steps, step the oracle from the GPU's
     pre-step state (of envs ``idx``) and compare rewards, dones, poses and
     regenerated episodes; then render the GPU's post-step state in the oracle
@@ -186,7 +195,7 @@ def lockstep(run: Run, stats: Stats, n_steps: int, seed: int, first_step: int = 
     N = run.cfg["n_envs"]
     idx = np.arange(N) if idx is None else np.asarray(idx)
     for s in range(first_step, first_step + n_steps):
-        a = inputs.actions(seed, s, N)
+        a = action_fn(seed, s, N)
         check = (s - first_step) % check_every == 0
         if check:
             prev = run.state(idx)
