@@ -231,10 +231,6 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
   p.horizon = c.horizon;
   p.tpr = tpr;
   p.task = c.task;
-  // frame staging: blocks of rows up to 3 KB, two per warp
-  int rows = 3072 / (3 * W);
-  p.rows_per_block = rows < 1 ? 1 : (rows > c.frame_h ? c.frame_h : rows);
-  p.frame_block_bytes = p.rows_per_block * 3 * W;
   p.map_smem_bytes = (c.map_side * c.map_side + 15) & ~15;
   p.move = (float)c.move_step;
   p.radius = (float)c.radius;
@@ -252,6 +248,25 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
     return cuda_fail(err, "cudaGetDeviceProperties");
   }
   env->num_sms = prop.multiProcessorCount;
+  // Frame staging: the largest row block (at most 16 rows, at least 1) with
+  // which kMinBlocksPerSm blocks still fit in one SM's shared memory.
+  {
+    const int rowb = 3 * W;
+    p.rows_per_block = 1;
+    p.frame_block_bytes = rowb;
+    const size_t per_sm = prop.sharedMemPerMultiprocessor;
+    const size_t reserved = prop.reservedSharedMemPerBlock;
+    for (int rows = c.frame_h < 16 ? c.frame_h : 16; rows >= 1; --rows) {
+      jx::Params q = p;
+      q.rows_per_block = rows;
+      q.frame_block_bytes = rows * rowb;
+      if ((size_t)(jx::block_smem_bytes(q) + reserved) * jx::kMinBlocksPerSm <= per_sm) {
+        p.rows_per_block = rows;
+        p.frame_block_bytes = rows * rowb;
+        break;
+      }
+    }
+  }
   env->smem_block = jx::block_smem_bytes(p);
   if ((size_t)env->smem_block > prop.sharedMemPerBlockOptin) {
     jx_destroy(env);

@@ -16,6 +16,7 @@ constexpr int kMaxW = 256;
 constexpr int kWarpsPerBlock = 4;
 constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kRingBuffers = 2;  // frame row-block staging buffers per warp
+constexpr int kMinBlocksPerSm = 7; // register budget: 7 blocks of 4 warps resident per SM
 
 enum Mode { MODE_STEP = 0, MODE_RESET = 1, MODE_RENDER = 2, MODE_RAYS = 3 };
 
@@ -71,9 +72,8 @@ struct Params {
   uint64_t wall_thr;  // an interior cell is a wall iff (draw >> 11) < wall_thr
 };
 
-// Shared memory bytes one warp needs, and per block.
-int warp_smem_bytes(const Params& p);
-inline int block_smem_bytes(const Params& p) { return warp_smem_bytes(p) * kWarpsPerBlock; }
+// Dynamic shared memory bytes of one block.
+int block_smem_bytes(const Params& p);
 size_t gen_scratch_bytes(int task, int S);
 
 // Configure (attributes) and query occupancy of the kernel for `mode`.

@@ -83,30 +83,55 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_
 __device__ __forceinline__ void bulk_wait_read_all_but_one() {
   asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
 }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
 
 // ------------------------------------------------------------- warp smem --
 __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; }
 
+// Shared memory of a block: a head shared by its warps (per-column ray
+// coefficients and the palette), then one region per warp.
 struct WarpSmem {
-  uint8_t* ring;      // kRingBuffers * frame_block_bytes
-  uint8_t* map;       // map_smem_bytes
-  uint32_t* col_rgb;  // [W]
-  uint32_t* col_tb;   // [W] top | bot << 16
-  float* zbuf;        // [W]
-  float4* spr_a;      // [K] x0, width, top, height (pixels)
+  uint8_t* ring;      // kRingBuffers * frame_block_bytes (also the maze work space)
+  uint8_t* map;       // map_smem_bytes, row-major cell values
+  uint32_t* col_rgb;  // [W] wall colour, chunk-interleaved (see col_slot)
+  int32_t* col_top;   // [W] first wall row, chunk-interleaved
+  int32_t* col_bot;   // [W] first floor row, chunk-interleaved
+  float* zbuf;        // [W] by column
+  float4* spr_a;      // [K] x0, top, 1 / width, 1 / height (pixels)
+  int4* spr_rect;     // [K] pixel rectangle to test: first/last column, first/last row
   float* spr_ty;      // [K] depth
   uint32_t* spr_rgb;  // [K]
   int32_t* spr_kind;  // [K] type
   int32_t* order;     // [K] visible sprites, far to near
 };
 
+struct BlockHead {
+  float* col_k;      // [W]
+  uint32_t* wall;    // [2][8] wall colours by face and cell value
+  uint32_t* sprite;  // [4] sprite colours by type
+};
+
+constexpr int kPaletteWords = 2 * 8 + 4;
+__host__ __device__ __forceinline__ int block_head_bytes(const Params& p) {
+  return align16(4 * p.W) + align16(4 * kPaletteWords);
+}
+
+__device__ __forceinline__ BlockHead carve_head(uint8_t* base, const Params& p) {
+  BlockHead h;
+  h.col_k = (float*)base;
+  h.wall = (uint32_t*)(base + align16(4 * p.W));
+  h.sprite = h.wall + 16;
+  return h;
+}
+
 __host__ __device__ __forceinline__ int warp_bytes(const Params& p) {
   int b = kRingBuffers * p.frame_block_bytes;
   b += p.map_smem_bytes;
-  b += align16(4 * p.W) * 3;
+  b += align16(4 * p.W) * 4;
   int K = p.K > 0 ? p.K : 1;
-  b += align16(16 * K) + align16(4 * K) * 4;
+  b += align16(16 * K) * 2 + align16(4 * K) * 4;
   return align16(b);
 }
 
@@ -120,11 +145,15 @@ __device__ __forceinline__ WarpSmem carve(uint8_t* base, const Params& p) {
   q += p.map_smem_bytes;
   w.col_rgb = (uint32_t*)q;
   q += align16(4 * p.W);
-  w.col_tb = (uint32_t*)q;
+  w.col_top = (int32_t*)q;
+  q += align16(4 * p.W);
+  w.col_bot = (int32_t*)q;
   q += align16(4 * p.W);
   w.zbuf = (float*)q;
   q += align16(4 * p.W);
   w.spr_a = (float4*)q;
+  q += align16(16 * K);
+  w.spr_rect = (int4*)q;
   q += align16(16 * K);
   w.spr_ty = (float*)q;
   q += align16(4 * K);
@@ -134,6 +163,14 @@ __device__ __forceinline__ WarpSmem carve(uint8_t* base, const Params& p) {
   q += align16(4 * K);
   w.order = (int32_t*)q;
   return w;
+}
+
+// Column data is stored so that the lanes filling one row (8 columns each)
+// read consecutive 16-byte groups: half g (columns 4g..4g+3 of the group) of
+// column group c sits at word (g * groups + c) * 4.
+__device__ __forceinline__ int col_slot(int col, int groups) {
+  const int c = col >> 3, j = col & 7;
+  return (((j >> 2) * groups + c) << 2) | (j & 3);
 }
 
 // ------------------------------------------------------------ env state ----
@@ -146,8 +183,16 @@ struct Env {
   int has_key;
   int key_x, key_y, goal_x, goal_y, door_x, door_y;
   int nspr;
+  int action;
 };
 
+// Lane j's sprite slot (prefetched with the state).
+struct SpriteIn {
+  float x, y;
+  int type;
+};
+
+template <int MODE>
 __device__ __forceinline__ Env load_env(const Params& p, int e) {
   Env r;
   const State& st = p.st;
@@ -170,16 +215,31 @@ __device__ __forceinline__ Env load_env(const Params& p, int e) {
   r.door_y = o[5];
   int ns = st.nspr[e];
   r.nspr = ns > p.K ? p.K : ns;
+  r.action = MODE == MODE_STEP ? (int)p.actions[e] : 0;
   return r;
 }
 
+__device__ __forceinline__ SpriteIn load_sprite(const Params& p, int e, int lane) {
+  SpriteIn q{0.f, 0.f, 0};
+  if (lane < p.K) {
+    size_t i = (size_t)e * p.K + lane;
+    q.x = p.st.spr_x[i];
+    q.y = p.st.spr_y[i];
+    q.type = p.st.spr_type[i];
+  }
+  return q;
+}
+
 // heading = theta0 + turn * 2 pi / turns_per_rev, by rotating (cos, sin)(theta0)
-__device__ __forceinline__ void heading(const Params& p, const Env& r, float& c, float& s) {
+__device__ __forceinline__ void heading(const Params& p, float th0, int turn, float& c, float& s) {
   float s0, c0;
-  sincosf(r.th0, &s0, &c0);
-  float2 cs = p.turn_cs[r.turn];
+  sincosf(th0, &s0, &c0);
+  float2 cs = p.turn_cs[turn];
   c = fmaf(c0, cs.x, -s0 * cs.y);
   s = fmaf(s0, cs.x, c0 * cs.y);
+}
+__device__ __forceinline__ void heading(const Params& p, const Env& r, float& c, float& s) {
+  heading(p, r.th0, r.turn, c, s);
 }
 
 __device__ __forceinline__ void stage_map(const Params& p, int e, uint8_t* smap, int lane) {
@@ -272,7 +332,7 @@ __device__ void write_episode_state(const Params& p, int e, uint32_t ep, int cel
 // Rooms: border walls; interior wall iff a 53-bit uniform draw < wall_prob;
 // wall type 1 + (draw mod 4); spawn and decorative sprites on uniformly
 // chosen free cells (row-major enumeration).
-__device__ void gen_rooms(const Params& p, int e, uint32_t ep, uint8_t* smap, int lane) {
+__device__ __noinline__ void gen_rooms(const Params& p, int e, uint32_t ep, uint8_t* smap, int lane) {
   const int S = p.S, n = S * S;
   const uint64_t kw = stream_key(p.seed, (uint32_t)e, ep, P_WALL);
   for (int i = lane; i < n; i += 32) {
@@ -346,7 +406,7 @@ __device__ __forceinline__ MazeScratch maze_scratch(uint8_t* q, int n) {
 // the DFS tree, a node's BFS distance from the spawn is its tree depth, and
 // the nodes reachable without crossing the door are those outside the
 // subtree below the door (a DFS discovery / finish interval test).
-__device__ void gen_maze(const Params& p, int e, uint32_t ep, uint8_t* smap, uint8_t* scratch, int lane) {
+__device__ __noinline__ void gen_maze(const Params& p, int e, uint32_t ep, uint8_t* smap, uint8_t* scratch, int lane) {
   const int S = p.S, n_cells = S * S;
   const int nn = (S - 2) / 2, n = nn * nn;
   MazeScratch m = maze_scratch(scratch, n);
@@ -442,12 +502,22 @@ __device__ void gen_maze(const Params& p, int e, uint32_t ep, uint8_t* smap, uin
   __syncwarp();
 }
 
-__device__ __forceinline__ void generate(const Params& p, int e, uint32_t ep, uint8_t* smap, uint8_t* scratch,
-                                         int lane) {
-  if (p.task == 0)
-    gen_rooms(p, e, ep, smap, lane);
-  else
-    gen_maze(p, e, ep, smap, scratch, lane);
+// The maze work space lives in the warp's frame staging ring when it fits
+// (32 x 32 mazes need 3.4 KB), else in the global per-warp slot.
+__device__ __noinline__ void generate(const Params& p, int e, uint32_t ep, const WarpSmem& ws, uint8_t* scratch,
+                                      int lane) {
+  if (p.task == 0) {
+    gen_rooms(p, e, ep, ws.map, lane);
+  } else {
+    const int nn = (p.S - 2) / 2;
+    uint8_t* work = scratch;
+    if (maze_scratch_bytes(nn * nn) <= (size_t)(kRingBuffers * p.frame_block_bytes)) {
+      if (lane == 0) bulk_wait_read_all();  // the ring's pending frame stores have read it
+      __syncwarp();
+      work = ws.ring;
+    }
+    gen_maze(p, e, ep, ws.map, work, lane);
+  }
 }
 
 // ------------------------------------------------------------------ step ----
@@ -485,15 +555,14 @@ __device__ __forceinline__ void renormalise(int& c, float& f) {
 }
 
 // Returns true when the episode ended (the caller regenerates).
-__device__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, int lane) {
-  int a = p.actions[e];
+__device__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, int lane, float& c, float& s) {
+  int a = r.action;
   if (a > 6) {
     if (lane == 0) atomicOr(p.err, 1u);
     a = 0;
   }
   if (a == 5) r.turn = r.turn == 0 ? p.tpr - 1 : r.turn - 1;
   if (a == 6) r.turn = r.turn + 1 == p.tpr ? 0 : r.turn + 1;
-  float c, s;
   heading(p, r, c, s);
   const float ms = p.move;
   float dx = 0.f, dy = 0.f;
@@ -546,13 +615,17 @@ __device__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, in
 }
 
 // ---------------------------------------------------------------- render ----
+// DDA (Sec. 2.1), one crossing per iteration. The next x boundary is at
+// t = (kx + gx) / ax, the next y boundary at (ky + gy) / ay; the
+// cross-multiplied forms are compared, so no division is needed.
 struct Ray {
-  int mx, my, sx, sy, kx, ky, side;
+  int mx, my, sx, sy, side;
+  float kx, ky;  // boundaries crossed so far (exact small integers)
   float ax, ay, gx, gy, gxay, gyax;
   bool done;
 };
 
-__device__ __forceinline__ void ray_init(Ray& q, const Env& r, float rx, float ry) {
+__device__ __forceinline__ void ray_init(Ray& q, const Env& r, float rx, float ry, bool valid) {
   q.mx = r.cx;
   q.my = r.cy;
   q.sx = rx < 0.f ? -1 : 1;
@@ -561,145 +634,128 @@ __device__ __forceinline__ void ray_init(Ray& q, const Env& r, float rx, float r
   q.ay = fabsf(ry);
   q.gx = rx < 0.f ? r.fx : 1.f - r.fx;
   q.gy = ry < 0.f ? r.fy : 1.f - r.fy;
-  q.gxay = q.gx * q.ay;
-  q.gyax = q.gy * q.ax;
-  q.kx = q.ky = 0;
+  // an axis the ray never crosses compares as +infinity
+  const float inf = __int_as_float(0x7f800000);
+  q.gxay = q.ax == 0.f ? inf : q.gx * q.ay;
+  q.gyax = q.ay == 0.f ? inf : q.gy * q.ax;
+  q.kx = q.ky = 0.f;
   q.side = -1;
-  q.done = false;
+  q.done = !valid;
 }
 
-// One DDA crossing: the next x boundary is at t = (kx + gx) / ax, the next y
-// boundary at (ky + gy) / ay; compare the cross-multiplied forms.
 __device__ __forceinline__ void ray_advance(Ray& q, const uint8_t* smap, int S) {
-  float lhs = fmaf((float)q.kx, q.ay, q.gxay);
-  float rhs = fmaf((float)q.ky, q.ax, q.gyax);
-  bool take_x = q.ay == 0.f || (q.ax != 0.f && lhs < rhs);
-  if (take_x) {
-    q.mx += q.sx;
-    q.kx += 1;
-    q.side = 0;
-  } else {
-    q.my += q.sy;
-    q.ky += 1;
-    q.side = 1;
-  }
-  bool out = q.mx < 0 || q.my < 0 || q.mx >= S || q.my >= S;
+  const float lhs = fmaf(q.kx, q.ay, q.gxay);
+  const float rhs = fmaf(q.ky, q.ax, q.gyax);
+  const bool tx = lhs < rhs;
+  q.mx += tx ? q.sx : 0;
+  q.my += tx ? 0 : q.sy;
+  q.kx += tx ? 1.f : 0.f;
+  q.ky += tx ? 0.f : 1.f;
+  q.side = tx ? 0 : 1;
+  const bool out = (unsigned)q.mx >= (unsigned)S || (unsigned)q.my >= (unsigned)S;
   q.done = out || smap[q.my * S + q.mx] != 0;
 }
 
-__device__ __forceinline__ float ray_perp(const Ray& q) {
-  if (q.side == 0) return ((float)(q.kx - 1) + q.gx) / q.ax;
-  if (q.side == 1) return ((float)(q.ky - 1) + q.gy) / q.ay;
-  return __int_as_float(0x7f800000);  // no hit
-}
-
-struct Column {
-  int h, top, bot;
-  uint32_t rgb;
-};
-
-__device__ __forceinline__ Column column_of(const Ray& q, float perp, const uint8_t* smap, int S, int H) {
-  Column col;
+// Slice of a finished ray: perp, rows and colour into the column arrays.
+template <int MODE>
+__device__ __forceinline__ void finish_column(const Params& p, int e, const Ray& q, int col, const WarpSmem& ws,
+                                              const BlockHead& hd) {
+  const int S = p.S, H = p.H;
+  float perp;
+  if (q.side == 0)
+    perp = __fdividef((q.kx - 1.f) + q.gx, q.ax);
+  else if (q.side == 1)
+    perp = __fdividef((q.ky - 1.f) + q.gy, q.ay);
+  else
+    perp = __int_as_float(0x7f800000);  // no hit
+  // h = floor(H / perp + 1/2), clamped; top = floor((H - h) / 2)
   int h;
   if (perp > 0.f) {
-    float v = (float)H / perp + 0.5f;
+    const float v = __fdividef((float)H, perp) + 0.5f;
     h = v >= 1048576.f ? kHMax : (int)floorf(v);
   } else {
     h = kHMax;
   }
-  int top = (H - h) >> 1;  // arithmetic shift: floor division by 2
-  int bot = top + h;
-  col.h = h;
-  col.top = top < 0 ? 0 : (top > H ? H : top);
-  col.bot = bot < 0 ? 0 : (bot > H ? H : bot);
+  const int top = (H - h) >> 1;  // arithmetic shift: floor division by 2
+  const int bot = top + h;
   int v = 1;
-  if (q.side >= 0 && q.mx >= 0 && q.my >= 0 && q.mx < S && q.my < S) v = smap[q.my * S + q.mx];
-  col.rgb = c_wall[q.side == 1 ? 1 : 0][v > 7 ? 7 : v];
-  return col;
+  const bool inside = (unsigned)q.mx < (unsigned)S && (unsigned)q.my < (unsigned)S;
+  if (q.side >= 0 && inside) v = ws.map[q.my * S + q.mx];
+  const int slot = col_slot(col, p.W >> 3);
+  ws.col_rgb[slot] = hd.wall[(q.side == 1 ? 8 : 0) + (v > 7 ? 7 : v)];
+  ws.col_top[slot] = top < 0 ? 0 : (top > H ? H : top);
+  ws.col_bot[slot] = bot < 0 ? 0 : (bot > H ? H : bot);
+  ws.zbuf[col] = perp;
+  if (MODE == MODE_RAYS) {
+    int4 hv = make_int4(q.side >= 0 ? q.mx : -1, q.side >= 0 ? q.my : -1, q.side, h);
+    reinterpret_cast<int4*>(p.dbg_hits)[(size_t)e * p.W + col] = hv;
+    p.dbg_perp[(size_t)e * p.W + col] = perp;
+  }
 }
 
-// Cast every column's ray; lanes take columns lane, lane + 32, ...; two rays
-// per lane advance together and the warp stops when a ballot says all hit.
+// Cast every column's ray. Lanes take columns lane and lane + 32 of each 64,
+// both rays advance in the same loop, and the warp leaves the loop when a
+// ballot says every ray has hit.
 template <int MODE>
-__device__ void cast_columns(const Params& p, int e, const Env& r, float c, float s, const WarpSmem& ws, int lane) {
-  const int W = p.W, S = p.S, H = p.H;
-  const uint8_t* smap = ws.map;
+__device__ void cast_columns(const Params& p, int e, const Env& r, float c, float s, const WarpSmem& ws,
+                             const BlockHead& hd, int lane) {
+  const int W = p.W, S = p.S;
   const int max_it = 4 * S + 8;
   for (int base = 0; base < W; base += 64) {
     const int c0 = base + lane, c1 = base + 32 + lane;
-    Ray q0, q1;
     const bool v0 = c0 < W, v1 = c1 < W;
-    {
-      float k = v0 ? p.col_k[c0] : 0.f;
-      ray_init(q0, r, fmaf(-k, s, c), fmaf(k, c, s));
-      q0.done = !v0;
-    }
-    {
-      float k = v1 ? p.col_k[c1] : 0.f;
-      ray_init(q1, r, fmaf(-k, s, c), fmaf(k, c, s));
-      q1.done = !v1;
-    }
+    const float k0 = hd.col_k[v0 ? c0 : 0], k1 = hd.col_k[v1 ? c1 : 0];
+    Ray q0, q1;
+    ray_init(q0, r, fmaf(-k0, s, c), fmaf(k0, c, s), v0);
+    ray_init(q1, r, fmaf(-k1, s, c), fmaf(k1, c, s), v1);
     for (int it = 0; it < max_it; ++it) {
-      if (!q0.done) ray_advance(q0, smap, S);
-      if (!q1.done) ray_advance(q1, smap, S);
+      if (!q0.done) ray_advance(q0, ws.map, S);
+      if (!q1.done) ray_advance(q1, ws.map, S);
       if (__all_sync(0xffffffffu, q0.done && q1.done)) break;
     }
-    if (v0) {
-      float perp = ray_perp(q0);
-      Column col = column_of(q0, perp, smap, S, H);
-      ws.col_rgb[c0] = col.rgb;
-      ws.col_tb[c0] = (uint32_t)col.top | ((uint32_t)col.bot << 16);
-      ws.zbuf[c0] = perp;
-      if (MODE == MODE_RAYS) {
-        int4 hv = make_int4(q0.side >= 0 ? q0.mx : -1, q0.side >= 0 ? q0.my : -1, q0.side, col.h);
-        reinterpret_cast<int4*>(p.dbg_hits)[(size_t)e * W + c0] = hv;
-        p.dbg_perp[(size_t)e * W + c0] = perp;
-      }
-    }
-    if (v1) {
-      float perp = ray_perp(q1);
-      Column col = column_of(q1, perp, smap, S, H);
-      ws.col_rgb[c1] = col.rgb;
-      ws.col_tb[c1] = (uint32_t)col.top | ((uint32_t)col.bot << 16);
-      ws.zbuf[c1] = perp;
-      if (MODE == MODE_RAYS) {
-        int4 hv = make_int4(q1.side >= 0 ? q1.mx : -1, q1.side >= 0 ? q1.my : -1, q1.side, col.h);
-        reinterpret_cast<int4*>(p.dbg_hits)[(size_t)e * W + c1] = hv;
-        p.dbg_perp[(size_t)e * W + c1] = perp;
-      }
-    }
+    if (v0) finish_column<MODE>(p, e, q0, c0, ws, hd);
+    if (v1) finish_column<MODE>(p, e, q1, c1, ws, hd);
   }
+  __syncwarp();
 }
 
 // Project sprites (lane j takes sprite j) and order the visible ones far to
 // near (equal depths: higher index first, so the lower index is drawn last).
-__device__ int project_sprites(const Params& p, int e, const Env& r, float c, float s, const WarpSmem& ws,
-                               int lane) {
+__device__ int project_sprites(const Params& p, const Env& r, const SpriteIn& sp, float c, float s,
+                               const WarpSmem& ws, const BlockHead& hd, int lane) {
   const int W = p.W, H = p.H;
   bool vis = false;
   float ty = 0.f;
   if (lane < r.nspr) {
-    size_t i = (size_t)e * p.K + lane;
-    int type = p.st.spr_type[i];
-    float vx = (p.st.spr_x[i] - (float)r.cx) - r.fx;
-    float vy = (p.st.spr_y[i] - (float)r.cy) - r.fy;
+    const int type = sp.type;
+    const float vx = (sp.x - (float)r.cx) - r.fx;
+    const float vy = (sp.y - (float)r.cy) - r.fy;
     ty = fmaf(vx, c, vy * s);
-    float tx = fmaf(-vx, s, vy * c) / p.tan_half;
+    const float tx = fmaf(-vx, s, vy * c) / p.tan_half;
     vis = type != 0 && !(type == kSprKey && r.has_key) && ty > 0.1f;
     if (vis) {
-      float scx = 0.5f * (float)W * (1.f + tx / ty);
-      float hw = 0.5f * (float)W * 0.25f / (p.tan_half * ty);
-      ws.spr_a[lane] = make_float4(scx - hw, 2.f * hw, 0.5f * (float)H, 0.5f * (float)H / ty);
+      const float scx = 0.5f * (float)W * (1.f + tx / ty);
+      const float hw = 0.5f * (float)W * 0.25f / (p.tan_half * ty);
+      const float wd = 2.f * hw, ht = 0.5f * (float)H / ty;
+      const float x0 = scx - hw, top = 0.5f * (float)H;
+      ws.spr_a[lane] = make_float4(x0, top, 1.f / wd, 1.f / ht);
+      // pixel centres that can fall inside [x0, x0 + wd) x [top, top + ht), one pixel of slack
+      const int cA = (int)floorf(fmaxf(x0 - 1.f, -1.f));
+      const int cB = (int)floorf(fminf(x0 + wd + 1.f, (float)W));
+      const int rA = (int)floorf(fmaxf(top - 1.f, -1.f));
+      const int rB = (int)floorf(fminf(top + ht + 1.f, (float)H));
+      ws.spr_rect[lane] =
+          make_int4(cA < 0 ? 0 : cA, cB > W - 1 ? W - 1 : cB, rA < 0 ? 0 : rA, rB > H - 1 ? H - 1 : rB);
       ws.spr_ty[lane] = ty;
-      ws.spr_rgb[lane] = c_sprite[type & 3];
+      ws.spr_rgb[lane] = hd.sprite[type & 3];
       ws.spr_kind[lane] = type;
     }
   }
   const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
   int rank = 0;
   for (int k = 0; k < r.nspr; ++k) {
-    float tk = __shfl_sync(0xffffffffu, ty, k);
-    bool vk = (vmask >> k) & 1;
+    const float tk = __shfl_sync(0xffffffffu, ty, k);
+    const bool vk = (vmask >> k) & 1;
     if (vis && vk && (tk > ty || (tk == ty && k > lane))) ++rank;
   }
   if (vis) ws.order[rank] = lane;
@@ -707,76 +763,85 @@ __device__ int project_sprites(const Params& p, int e, const Env& r, float c, fl
   return __popc(vmask);
 }
 
-__device__ __forceinline__ bool sprite_mask(int kind, float u, float v) {
-  float a = fmaf(2.f, u, -1.f), b = fmaf(2.f, v, -1.f);
-  if (kind == kSprKey) return fabsf(a) + fabsf(b) < 1.f;
-  if (kind == kSprGoal) return true;
-  return fmaf(a, a, b * b) < 1.f;
+// Pack 8 pixel colours (0x00BBGGRR) into 24 bytes of RGB.
+__device__ __forceinline__ void store24(uint8_t* dst, const uint32_t px[8]) {
+  uint2* d = reinterpret_cast<uint2*>(dst);
+  d[0] = make_uint2(__byte_perm(px[0], px[1], 0x4210), __byte_perm(px[1], px[2], 0x5421));
+  d[1] = make_uint2(__byte_perm(px[2], px[3], 0x6542), __byte_perm(px[4], px[5], 0x4210));
+  d[2] = make_uint2(__byte_perm(px[5], px[6], 0x5421), __byte_perm(px[6], px[7], 0x6542));
 }
 
-// Fill rows [r0, r1) of the frame into `buf` (row-major RGB).
-__device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, uint8_t* buf, int r0, int r1,
-                                          int nvis, int lane) {
-  const int W = p.W, rowb = 3 * W;
-  const int lpr = W >> 4;     // lanes per row, 16 pixels (48 bytes) each
-  const int rpp = 32 / lpr;   // rows per pass
-  const int my_row = lane / lpr, chunk = lane - my_row * lpr;
+// The lane's 8 columns. Because every slice is centred, a row above H/2 is
+// ceiling or wall and a row at or below it is wall or floor: one compare per
+// pixel.
+struct Group {
+  int top[8], bot[8];
+  uint32_t rgb[8];
+};
+
+__device__ __forceinline__ void load_group(const WarpSmem& ws, int g, int groups, Group& gr) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int slot = (h * groups + g) << 2;
+    const int4 t4 = *reinterpret_cast<const int4*>(ws.col_top + slot);
+    const int4 b4 = *reinterpret_cast<const int4*>(ws.col_bot + slot);
+    const uint4 c4 = *reinterpret_cast<const uint4*>(ws.col_rgb + slot);
+    gr.top[4 * h + 0] = t4.x, gr.top[4 * h + 1] = t4.y, gr.top[4 * h + 2] = t4.z, gr.top[4 * h + 3] = t4.w;
+    gr.bot[4 * h + 0] = b4.x, gr.bot[4 * h + 1] = b4.y, gr.bot[4 * h + 2] = b4.z, gr.bot[4 * h + 3] = b4.w;
+    gr.rgb[4 * h + 0] = c4.x, gr.rgb[4 * h + 1] = c4.y, gr.rgb[4 * h + 2] = c4.z, gr.rgb[4 * h + 3] = c4.w;
+  }
+}
+
+// Fill rows [r0, r1) of the frame into `buf` (row-major RGB), then draw the
+// sprites over them.
+__device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, const Group& gr, uint8_t* buf,
+                                          int r0, int r1, int nvis, int lane) {
+  const int W = p.W, H = p.H, rowb = 3 * W, mid = H >> 1;
+  const int groups = W >> 3;    // lanes per row, 8 pixels (24 bytes) each
+  const int rpp = 32 / groups;  // rows per pass
+  const int my_row = lane / groups, g = lane - my_row * groups;
   if (my_row < rpp) {
-    uint32_t crgb[16], ctb[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      crgb[k] = ws.col_rgb[chunk * 16 + k];
-      ctb[k] = ws.col_tb[chunk * 16 + k];
-    }
     for (int row = r0 + my_row; row < r1; row += rpp) {
-      uint32_t px[16];
+      uint32_t px[8];
+      if (row < mid) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        int top = (int)(ctb[k] & 0xffffu), bot = (int)(ctb[k] >> 16);
-        px[k] = row < top ? kCeil : (row < bot ? crgb[k] : kFloor);
-      }
-      uint32_t w[12];
+        for (int k = 0; k < 8; ++k) px[k] = row < gr.top[k] ? kCeil : gr.rgb[k];
+      } else {
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        w[3 * g + 0] = __byte_perm(px[4 * g + 0], px[4 * g + 1], 0x4210);
-        w[3 * g + 1] = __byte_perm(px[4 * g + 1], px[4 * g + 2], 0x5421);
-        w[3 * g + 2] = __byte_perm(px[4 * g + 2], px[4 * g + 3], 0x6542);
+        for (int k = 0; k < 8; ++k) px[k] = row < gr.bot[k] ? gr.rgb[k] : kFloor;
       }
-      uint4* dst = reinterpret_cast<uint4*>(buf + (row - r0) * rowb + chunk * 48);
-      dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-      dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
-      dst[2] = make_uint4(w[8], w[9], w[10], w[11]);
+      store24(buf + (row - r0) * rowb + g * 24, px);
     }
   }
   __syncwarp();
-  // sprites, far to near, each pixel tested at its centre
+  // sprites, far to near; lanes take columns, each pixel tested at its centre
   for (int oi = 0; oi < nvis; ++oi) {
     const int j = ws.order[oi];
-    const float4 a = ws.spr_a[j];
+    const int4 rc = ws.spr_rect[j];
+    const int rA = rc.z < r0 ? r0 : rc.z;
+    const int rB = rc.w > r1 - 1 ? r1 - 1 : rc.w;
+    if (rc.x > rc.y || rA > rB) continue;
+    const float4 a = ws.spr_a[j];  // x0, top, 1/width, 1/height
     const float ty = ws.spr_ty[j];
-    const uint32_t col_rgb = ws.spr_rgb[j];
+    const uint32_t rgbv = ws.spr_rgb[j];
     const int kind = ws.spr_kind[j];
-    int cA = (int)floorf(fmaxf(a.x - 1.f, -1.f));
-    int cB = (int)floorf(fminf(a.x + a.y + 1.f, (float)W));
-    int rA = (int)floorf(fmaxf(a.z - 1.f, -1.f));
-    int rB = (int)floorf(fminf(a.z + a.w + 1.f, (float)p.H));
-    cA = cA < 0 ? 0 : cA;
-    cB = cB > W - 1 ? W - 1 : cB;
-    rA = rA < r0 ? r0 : rA;
-    rB = rB > r1 - 1 ? r1 - 1 : rB;
-    if (cA > cB || rA > rB) continue;
-    const int ncols = cB - cA + 1;
-    const int npx = ncols * (rB - rA + 1);
-    for (int i = lane; i < npx; i += 32) {
-      int row = rA + i / ncols;
-      int col = cA + (i - (row - rA) * ncols);
-      float u = ((float)col + 0.5f - a.x) / a.y;
-      float v = ((float)row + 0.5f - a.z) / a.w;
-      if (u >= 0.f && u < 1.f && v >= 0.f && v < 1.f && sprite_mask(kind, u, v) && ty < ws.zbuf[col]) {
-        uint8_t* px = buf + (row - r0) * rowb + col * 3;
-        px[0] = (uint8_t)(col_rgb & 255);
-        px[1] = (uint8_t)((col_rgb >> 8) & 255);
-        px[2] = (uint8_t)((col_rgb >> 16) & 255);
+    for (int col = rc.x + lane; col <= rc.y; col += 32) {
+      const float u = ((float)col + 0.5f - a.x) * a.z;
+      if (!(u >= 0.f && u < 1.f && ty < ws.zbuf[col])) continue;
+      const float au = fabsf(fmaf(2.f, u, -1.f));
+      uint8_t* px = buf + col * 3;
+      for (int row = rA; row <= rB; ++row) {
+        const float v = ((float)row + 0.5f - a.y) * a.w;
+        const float bv = fabsf(fmaf(2.f, v, -1.f));
+        bool in = v >= 0.f && v < 1.f;
+        if (kind == kSprKey) in = in && au + bv < 1.f;
+        else if (kind != kSprGoal) in = in && fmaf(au, au, bv * bv) < 1.f;
+        if (in) {
+          uint8_t* q = px + (row - r0) * rowb;
+          q[0] = (uint8_t)(rgbv & 255);
+          q[1] = (uint8_t)((rgbv >> 8) & 255);
+          q[2] = (uint8_t)((rgbv >> 16) & 255);
+        }
       }
     }
     __syncwarp();
@@ -784,20 +849,22 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
 }
 
 template <int MODE>
-__device__ void render_env(const Params& p, int e, const Env& r, const WarpSmem& ws, int lane, int& slot) {
-  float c, s;
-  heading(p, r, c, s);
-  cast_columns<MODE>(p, e, r, c, s, ws, lane);
+__device__ void render_env(const Params& p, int e, const Env& r, const SpriteIn& sp, float c, float s,
+                           const WarpSmem& ws, const BlockHead& hd, int lane, int& slot) {
+  cast_columns<MODE>(p, e, r, c, s, ws, hd, lane);
   if (MODE == MODE_RAYS) return;
-  const int nvis = project_sprites(p, e, r, c, s, ws, lane);  // ends with __syncwarp
-  const int H = p.H, rowb = 3 * p.W;
+  const int nvis = project_sprites(p, r, sp, c, s, ws, hd, lane);  // ends with __syncwarp
+  const int H = p.H, rowb = 3 * p.W, groups = p.W >> 3;
+  Group gr;
+  const int my_row = lane / groups;
+  if (my_row < 32 / groups) load_group(ws, lane - my_row * groups, groups, gr);
   uint8_t* frame = p.frames + (size_t)e * H * rowb;
   for (int r0 = 0; r0 < H; r0 += p.rows_per_block) {
     const int r1 = r0 + p.rows_per_block < H ? r0 + p.rows_per_block : H;
     uint8_t* buf = ws.ring + slot * p.frame_block_bytes;
     if (lane == 0) bulk_wait_read_all_but_one();
     __syncwarp();
-    fill_block(p, ws, buf, r0, r1, nvis, lane);
+    fill_block(p, ws, gr, buf, r0, r1, nvis, lane);
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) bulk_store(frame + (size_t)r0 * rowb, buf, (uint32_t)((r1 - r0) * rowb));
@@ -805,41 +872,60 @@ __device__ void render_env(const Params& p, int e, const Env& r, const WarpSmem&
   }
 }
 
+// The locked door opens (for rays) once the key is held.
+__device__ __forceinline__ void open_door(const Params& p, const Env& r, const WarpSmem& ws, int lane) {
+  if (r.has_key && r.door_x >= 0 && r.door_y >= 0 && r.door_x < p.S && r.door_y < p.S) {
+    if (lane == 0 && ws.map[r.door_y * p.S + r.door_x] == kDoor) ws.map[r.door_y * p.S + r.door_x] = 0;
+    __syncwarp();
+  }
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) env_kernel(const __grid_constant__ Params p) {
+__global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __grid_constant__ Params p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const WarpSmem ws = carve(smem_raw + warp * warp_bytes(p), p);
+  const BlockHead hd = carve_head(smem_raw, p);
+  for (int i = threadIdx.x; i < p.W; i += kThreads) hd.col_k[i] = p.col_k[i];
+  if (threadIdx.x < 16) hd.wall[threadIdx.x] = c_wall[threadIdx.x >> 3][threadIdx.x & 7];
+  if (threadIdx.x < 4) hd.sprite[threadIdx.x] = c_sprite[threadIdx.x];
+  __syncthreads();
+  const WarpSmem ws = carve(smem_raw + block_head_bytes(p) + warp * warp_bytes(p), p);
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
   uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;
   int slot = 0;
   for (int e = gw; e < p.n; e += nw) {
     Env r;
+    SpriteIn sp;
+    float c, s;
     if (MODE == MODE_RESET) {
-      generate(p, e, 0u, ws.map, scratch, lane);
-      r = load_env(p, e);
+      generate(p, e, 0u, ws, scratch, lane);
+      r = load_env<MODE>(p, e);
+      sp = load_sprite(p, e, lane);
+      heading(p, r, c, s);
     } else {
-      r = load_env(p, e);
+      r = load_env<MODE>(p, e);
+      sp = load_sprite(p, e, lane);
       stage_map(p, e, ws.map, lane);
       if (MODE == MODE_STEP) {
-        if (step_env(p, e, r, ws.map, lane)) {
+        if (step_env(p, e, r, ws.map, lane, c, s)) {
           const uint32_t ep = r.ep + 1;
           __syncwarp();
-          generate(p, e, ep, ws.map, scratch, lane);
-          r = load_env(p, e);
+          generate(p, e, ep, ws, scratch, lane);
+          r = load_env<MODE>(p, e);
+          sp = load_sprite(p, e, lane);
+          heading(p, r, c, s);
         }
+      } else {
+        heading(p, r, c, s);
       }
     }
-    // the locked door opens (for rays) once the key is held
-    if (r.has_key && r.door_x >= 0 && r.door_y >= 0 && r.door_x < p.S && r.door_y < p.S) {
-      if (lane == 0 && ws.map[r.door_y * p.S + r.door_x] == kDoor) ws.map[r.door_y * p.S + r.door_x] = 0;
-      __syncwarp();
-    }
-    render_env<MODE>(p, e, r, ws, lane, slot);
+    open_door(p, r, ws, lane);
+    render_env<MODE>(p, e, r, sp, c, s, ws, hd, lane, slot);
     __syncwarp();
   }
-  if (lane == 0) bulk_wait_all();
+  // shared memory stays allocated until the bulk stores have read it
+  if (lane == 0) bulk_wait_read_all();
 }
 
 template <int MODE>
@@ -852,7 +938,7 @@ cudaError_t blocks_per_sm_for(const Params& p, int* blocks) {
 
 }  // namespace
 
-int warp_smem_bytes(const Params& p) { return warp_bytes(p); }
+int block_smem_bytes(const Params& p) { return block_head_bytes(p) + warp_bytes(p) * kWarpsPerBlock; }
 
 size_t gen_scratch_bytes(int task, int S) {
   if (task != 1) return 0;
