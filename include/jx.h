@@ -149,7 +149,10 @@ jx_status jx_debug_rays(jx_env* env, void* stream, int32_t* d_hits, float* d_per
  * device block of struct-of-arrays fields; jx_state_field gives each field's
  * byte offset and size inside it (fields: JX_F_*). jx_get_state copies the
  * whole block to the host and waits; jx_set_state copies it back and waits.
- * `bytes` must equal jx_state_bytes. */
+ * `bytes` must equal jx_state_bytes. jx_set_state checks that every position
+ * lies inside the map (cell in [0, S), fraction in [0, 1)) and returns
+ * JX_EINVAL otherwise; it recomputes the derived fields (JX_F_COS0, JX_F_SIN0)
+ * from theta0 and leaves the caller's buffer untouched. */
 enum {
   JX_F_CELL_X = 0,   /* int16  [N]   cell column of the position            */
   JX_F_CELL_Y = 1,   /* int16  [N]   cell row of the position               */
@@ -166,7 +169,9 @@ enum {
   JX_F_SPR_Y = 12,   /* float  [N][K] sprite y                              */
   JX_F_SPR_TYPE = 13, /* uint8 [N][K] 0 none, 1 key, 2 goal, 3 distractor   */
   JX_F_MAP = 14,     /* uint8  [N][S][S] 0 floor, 1..4 wall types, 5 locked door */
-  JX_F_COUNT = 15
+  JX_F_COS0 = 15,    /* float  [N]   cos(theta0), derived: jx_set_state recomputes it */
+  JX_F_SIN0 = 16,    /* float  [N]   sin(theta0), derived: jx_set_state recomputes it */
+  JX_F_COUNT = 17
 };
 jx_status jx_state_bytes(const jx_env* env, size_t* bytes);
 jx_status jx_state_field(const jx_env* env, int32_t field, size_t* offset, size_t* bytes);

@@ -115,6 +115,8 @@ void layout(jx_env* env) {
       4 * N * K,  // spr_y
       N * K,      // spr_type
       N * S * S,  // map
+      4 * N,      // cos0
+      4 * N,      // sin0
   };
   size_t off = 0;
   for (int f = 0; f < JX_F_COUNT; ++f) {
@@ -220,6 +222,8 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
   p.st.spr_y = field_ptr<float>(env, JX_F_SPR_Y);
   p.st.spr_type = field_ptr<uint8_t>(env, JX_F_SPR_TYPE);
   p.st.map = field_ptr<uint8_t>(env, JX_F_MAP);
+  p.st.cos0 = field_ptr<float>(env, JX_F_COS0);
+  p.st.sin0 = field_ptr<float>(env, JX_F_SIN0);
   p.err = reinterpret_cast<uint32_t*>(env->aux + aux_err);
   p.turn_cs = reinterpret_cast<const float2*>(env->aux + aux_turn);
   p.col_k = reinterpret_cast<const float*>(env->aux + aux_col);
@@ -235,6 +239,7 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
   p.move = (float)c.move_step;
   p.radius = (float)c.radius;
   p.tan_half = (float)std::tan(0.5 * c.fov_deg * 3.14159265358979323846 / 180.0);
+  p.inv_tan_half = (float)(1.0 / std::tan(0.5 * c.fov_deg * 3.14159265358979323846 / 180.0));
   for (int ev = 0; ev < 4; ++ev)
     p.reward_lut[ev] =
         (float)(c.step_reward + ((ev & 1) ? c.key_reward : 0.0) + ((ev & 2) ? c.goal_reward : 0.0));
@@ -248,15 +253,18 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
     return cuda_fail(err, "cudaGetDeviceProperties");
   }
   env->num_sms = prop.multiProcessorCount;
-  // Frame staging: the largest row block (at most 16 rows, at least 1) with
-  // which kMinBlocksPerSm blocks still fit in one SM's shared memory.
+  // Frame staging: the largest row block (at most 16 rows, at least 1, a
+  // multiple of the rows one fill pass covers when possible) with which
+  // kMinBlocksPerSm blocks still fit in one SM's shared memory.
   {
     const int rowb = 3 * W;
+    const int pass_rows = 32 / (W / 8) > 0 ? 32 / (W / 8) : 1;
     p.rows_per_block = 1;
     p.frame_block_bytes = rowb;
     const size_t per_sm = prop.sharedMemPerMultiprocessor;
     const size_t reserved = prop.reservedSharedMemPerBlock;
     for (int rows = c.frame_h < 16 ? c.frame_h : 16; rows >= 1; --rows) {
+      if (rows < c.frame_h && rows >= pass_rows && rows % pass_rows != 0) continue;
       jx::Params q = p;
       q.rows_per_block = rows;
       q.frame_block_bytes = rows * rowb;
@@ -424,9 +432,28 @@ jx_status jx_set_state(jx_env* env, const void* h_buf, size_t bytes) {
   if (jx_status st = check_env(env)) return st;
   if (!h_buf || bytes != env->state_bytes)
     return fail(JX_EINVAL, "buffer must be %zu bytes (got %zu)", env->state_bytes, bytes);
+  // a private copy: positions checked, derived heading fields recomputed
+  std::string blob(static_cast<const char*>(h_buf), bytes);
+  auto fld = [&](int f) { return &blob[env->field_off[f]]; };
+  const int N = env->cfg.n_envs, S = env->cfg.map_side;
+  const int16_t* cx = reinterpret_cast<const int16_t*>(fld(JX_F_CELL_X));
+  const int16_t* cy = reinterpret_cast<const int16_t*>(fld(JX_F_CELL_Y));
+  const float* fx = reinterpret_cast<const float*>(fld(JX_F_FRAC_X));
+  const float* fy = reinterpret_cast<const float*>(fld(JX_F_FRAC_Y));
+  const float* th = reinterpret_cast<const float*>(fld(JX_F_THETA0));
+  float* c0 = reinterpret_cast<float*>(fld(JX_F_COS0));
+  float* s0 = reinterpret_cast<float*>(fld(JX_F_SIN0));
+  for (int i = 0; i < N; ++i) {
+    if (cx[i] < 0 || cx[i] >= S || cy[i] < 0 || cy[i] >= S || !(fx[i] >= 0.f && fx[i] < 1.f) ||
+        !(fy[i] >= 0.f && fy[i] < 1.f))
+      return fail(JX_EINVAL, "env %d: position outside the map (cell %d,%d frac %g,%g)", i, cx[i], cy[i], fx[i], fy[i]);
+    if (!std::isfinite(th[i])) return fail(JX_EINVAL, "env %d: theta0 is not finite", i);
+    c0[i] = (float)std::cos((double)th[i]);
+    s0[i] = (float)std::sin((double)th[i]);
+  }
   DeviceGuard g(env->device);
   cudaError_t err = cudaDeviceSynchronize();
-  if (err == cudaSuccess) err = cudaMemcpy(env->state, h_buf, bytes, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(env->state, blob.data(), bytes, cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaDeviceSynchronize();
   return err == cudaSuccess ? JX_OK : cuda_fail(err, "set_state");
 }

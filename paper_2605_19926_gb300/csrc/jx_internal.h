@@ -47,6 +47,8 @@ struct State {
   float* spr_y;
   uint8_t* spr_type;
   uint8_t* map;  // [N][S][S]
+  float* cos0;   // [N] cos(theta0), derived
+  float* sin0;   // [N] sin(theta0), derived
 };
 
 struct Params {
@@ -66,7 +68,7 @@ struct Params {
   int32_t rows_per_block;  // rows per staged frame block
   int32_t frame_block_bytes;
   int32_t map_smem_bytes;  // S * S rounded up to 16
-  float move, radius, tan_half;
+  float move, radius, tan_half, inv_tan_half;
   float reward_lut[4];
   uint64_t seed;
   uint64_t wall_thr;  // an interior cell is a wall iff (draw >> 11) < wall_thr

@@ -107,27 +107,18 @@ struct WarpSmem {
   int32_t* order;     // [K] visible sprites, far to near
 };
 
+// Palette copy of each warp: wall colours [face][cell value], then sprite
+// colours by type.
 struct BlockHead {
-  float* col_k;      // [W]
-  uint32_t* wall;    // [2][8] wall colours by face and cell value
-  uint32_t* sprite;  // [4] sprite colours by type
+  uint32_t* wall;    // [2][8]
+  uint32_t* sprite;  // [4]
 };
 
 constexpr int kPaletteWords = 2 * 8 + 4;
-__host__ __device__ __forceinline__ int block_head_bytes(const Params& p) {
-  return align16(4 * p.W) + align16(4 * kPaletteWords);
-}
-
-__device__ __forceinline__ BlockHead carve_head(uint8_t* base, const Params& p) {
-  BlockHead h;
-  h.col_k = (float*)base;
-  h.wall = (uint32_t*)(base + align16(4 * p.W));
-  h.sprite = h.wall + 16;
-  return h;
-}
+__host__ __device__ __forceinline__ int block_head_bytes(const Params&) { return 0; }
 
 __host__ __device__ __forceinline__ int warp_bytes(const Params& p) {
-  int b = kRingBuffers * p.frame_block_bytes;
+  int b = kRingBuffers * p.frame_block_bytes + align16(4 * kPaletteWords);
   b += p.map_smem_bytes;
   b += align16(4 * p.W) * 4;
   int K = p.K > 0 ? p.K : 1;
@@ -135,12 +126,15 @@ __host__ __device__ __forceinline__ int warp_bytes(const Params& p) {
   return align16(b);
 }
 
-__device__ __forceinline__ WarpSmem carve(uint8_t* base, const Params& p) {
+__device__ __forceinline__ WarpSmem carve(uint8_t* base, const Params& p, BlockHead& hd) {
   WarpSmem w;
   int K = p.K > 0 ? p.K : 1;
   uint8_t* q = base;
   w.ring = q;
   q += kRingBuffers * p.frame_block_bytes;
+  hd.wall = (uint32_t*)q;
+  hd.sprite = hd.wall + 16;
+  q += align16(4 * kPaletteWords);
   w.map = q;
   q += p.map_smem_bytes;
   w.col_rgb = (uint32_t*)q;
@@ -177,7 +171,7 @@ __device__ __forceinline__ int col_slot(int col, int groups) {
 struct Env {
   int cx, cy;    // cell of the position
   float fx, fy;  // position inside the cell, [0, 1)
-  float th0;
+  float c0, s0;  // cos, sin of theta0
   int turn, t;
   uint32_t ep;
   int has_key;
@@ -200,7 +194,8 @@ __device__ __forceinline__ Env load_env(const Params& p, int e) {
   r.cy = st.cell_y[e];
   r.fx = st.frac_x[e];
   r.fy = st.frac_y[e];
-  r.th0 = st.theta0[e];
+  r.c0 = st.cos0[e];
+  r.s0 = st.sin0[e];
   int turn = st.turn[e] % p.tpr;
   r.turn = turn < 0 ? turn + p.tpr : turn;
   r.t = st.t[e];
@@ -230,16 +225,12 @@ __device__ __forceinline__ SpriteIn load_sprite(const Params& p, int e, int lane
   return q;
 }
 
-// heading = theta0 + turn * 2 pi / turns_per_rev, by rotating (cos, sin)(theta0)
-__device__ __forceinline__ void heading(const Params& p, float th0, int turn, float& c, float& s) {
-  float s0, c0;
-  sincosf(th0, &s0, &c0);
-  float2 cs = p.turn_cs[turn];
-  c = fmaf(c0, cs.x, -s0 * cs.y);
-  s = fmaf(s0, cs.x, c0 * cs.y);
-}
+// heading = theta0 + turn * 2 pi / turns_per_rev: (cos, sin)(theta0), kept in
+// the state, rotated by the table entry of `turn`
 __device__ __forceinline__ void heading(const Params& p, const Env& r, float& c, float& s) {
-  heading(p, r.th0, r.turn, c, s);
+  const float2 cs = p.turn_cs[r.turn];
+  c = fmaf(r.c0, cs.x, -r.s0 * cs.y);
+  s = fmaf(r.s0, cs.x, r.c0 * cs.y);
 }
 
 __device__ __forceinline__ void stage_map(const Params& p, int e, uint8_t* smap, int lane) {
@@ -306,7 +297,12 @@ __device__ void write_episode_state(const Params& p, int e, uint32_t ep, int cel
     st.cell_y[e] = (int16_t)(cell / S);
     st.frac_x[e] = 0.5f;
     st.frac_y[e] = 0.5f;
-    st.theta0[e] = (float)((double)(draw_at(kh, 0) >> 40) * kHeadingScale);
+    const float th0 = (float)((double)(draw_at(kh, 0) >> 40) * kHeadingScale);
+    double sd, cd;
+    sincos((double)th0, &sd, &cd);
+    st.theta0[e] = th0;
+    st.cos0[e] = (float)cd;
+    st.sin0[e] = (float)sd;
     st.turn[e] = 0;
     st.t[e] = 0;
     st.episode[e] = ep;
@@ -370,18 +366,17 @@ __device__ __noinline__ void gen_rooms(const Params& p, int e, uint32_t ep, uint
   __syncwarp();
 }
 
-// Work space of one maze generation in global scratch (n = nodes).
+// Work space of one maze generation (n = nodes): the per-carve draws, the
+// DFS stack of node cells, and each node's DFS discovery / finish counters.
 struct MazeScratch {
-  uint32_t* rnd;  // [n] high 32 bits of the per-carve draws
-  uint16_t* stack;
-  uint16_t* parent;
-  uint16_t* depth;
-  uint16_t* disc;
-  uint16_t* fin;
-  uint8_t* visited;
+  uint32_t* rnd;     // [n] high 32 bits of the per-carve draws
+  uint16_t* stack;   // [n] node cells packed as y << 8 | x
+  uint16_t* disc;    // [n] push counter when the node was discovered
+  uint16_t* fin;     // [n] push counter when the node was finished
+  int32_t* result;   // [4] goal node, its depth, the door's two path nodes (packed cells)
 };
 __host__ __device__ __forceinline__ size_t maze_scratch_bytes(int n) {
-  return (size_t)align16(4 * n) + 5 * (size_t)align16(2 * n) + (size_t)align16(n);
+  return (size_t)align16(4 * n) + 3 * (size_t)align16(2 * n) + 16;
 }
 __device__ __forceinline__ MazeScratch maze_scratch(uint8_t* q, int n) {
   MazeScratch m;
@@ -389,23 +384,22 @@ __device__ __forceinline__ MazeScratch maze_scratch(uint8_t* q, int n) {
   q += align16(4 * n);
   m.stack = (uint16_t*)q;
   q += align16(2 * n);
-  m.parent = (uint16_t*)q;
-  q += align16(2 * n);
-  m.depth = (uint16_t*)q;
-  q += align16(2 * n);
   m.disc = (uint16_t*)q;
   q += align16(2 * n);
   m.fin = (uint16_t*)q;
   q += align16(2 * n);
-  m.visited = q;
+  m.result = (int32_t*)q;
   return m;
 }
 
 // Key-door maze: depth-first backtracker over the nodes at odd coordinates,
-// N/E/S/W neighbour order, one draw per carved passage. Because the maze is
-// the DFS tree, a node's BFS distance from the spawn is its tree depth, and
-// the nodes reachable without crossing the door are those outside the
-// subtree below the door (a DFS discovery / finish interval test).
+// N/E/S/W neighbour order, one draw per carved passage. A node is unvisited
+// while its cell is still a wall. Because the maze is the DFS tree, a node's
+// BFS distance from the spawn is its stack depth when pushed, and the stack at
+// that moment is its path from the spawn: the goal (deepest node, ties to
+// the smallest row-major index) and the two path nodes around the door are
+// recorded during the walk. The nodes reachable without crossing the door are
+// those outside the door's subtree (a discovery / finish interval test).
 __device__ __noinline__ void gen_maze(const Params& p, int e, uint32_t ep, uint8_t* smap, uint8_t* scratch, int lane) {
   const int S = p.S, n_cells = S * S;
   const int nn = (S - 2) / 2, n = nn * nn;
@@ -414,72 +408,62 @@ __device__ __noinline__ void gen_maze(const Params& p, int e, uint32_t ep, uint8
   for (int i = lane; i < n_cells; i += 32) smap[i] = (uint8_t)(1 + (draw_at(kw, (uint32_t)i) & 3));
   const uint64_t kd = stream_key(p.seed, (uint32_t)e, ep, P_DFS);
   for (int j = lane; j < n - 1; j += 32) m.rnd[j] = (uint32_t)(draw_at(kd, (uint32_t)j) >> 32);
-  for (int i = lane; i < n; i += 32) m.visited[i] = 0;
   const int start = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_SPAWN), 0), (uint32_t)n);
   __syncwarp();
   if (lane == 0) {
-    int sp = 0, carved = 0, pushes = 0;
-    m.stack[sp++] = (uint16_t)start;
-    m.visited[start] = 1;
-    m.parent[start] = (uint16_t)start;
-    m.depth[start] = 0;
-    m.disc[start] = (uint16_t)pushes++;
-    smap[(2 * (start / nn) + 1) * S + 2 * (start % nn) + 1] = 0;
-    while (sp > 0) {
-      int v = m.stack[sp - 1];
-      int vx = v % nn, vy = v / nn;
-      int cand[4], k = 0;
-      if (vy > 0 && !m.visited[v - nn]) cand[k++] = v - nn;
-      if (vx < nn - 1 && !m.visited[v + 1]) cand[k++] = v + 1;
-      if (vy < nn - 1 && !m.visited[v + nn]) cand[k++] = v + nn;
-      if (vx > 0 && !m.visited[v - 1]) cand[k++] = v - 1;
-      if (k == 0) {
+    int vx = 2 * (start % nn) + 1, vy = 2 * (start / nn) + 1, v = start;
+    smap[vy * S + vx] = 0;
+    int sp = 0, pushes = 0, carved = 0;
+    m.stack[sp++] = (uint16_t)(vy << 8 | vx);
+    m.disc[v] = (uint16_t)pushes++;
+    int best_v = start, best_d = 0, door_a = vy << 8 | vx, door_b = door_a;
+    for (;;) {
+      const int c = vy * S + vx;
+      const uint32_t open = (uint32_t)(vy > 1 && smap[c - 2 * S] != 0) | ((uint32_t)(vx < S - 3 && smap[c + 2] != 0) << 1) |
+                            ((uint32_t)(vy < S - 3 && smap[c + 2 * S] != 0) << 2) |
+                            ((uint32_t)(vx > 1 && smap[c - 2] != 0) << 3);
+      if (open == 0) {
         m.fin[v] = (uint16_t)pushes;
-        --sp;
+        if (--sp == 0) break;
+        const int top = m.stack[sp - 1];
+        vx = top & 0xff;
+        vy = top >> 8;
+        v = (vy >> 1) * nn + (vx >> 1);
         continue;
       }
-      int w = cand[below32(m.rnd[carved], (uint32_t)k)];
-      ++carved;
-      int cvx = 2 * vx + 1, cvy = 2 * vy + 1;
-      int cwx = 2 * (w % nn) + 1, cwy = 2 * (w / nn) + 1;
-      smap[((cvy + cwy) >> 1) * S + ((cvx + cwx) >> 1)] = 0;
-      smap[cwy * S + cwx] = 0;
-      m.visited[w] = 1;
-      m.parent[w] = (uint16_t)v;
-      m.depth[w] = (uint16_t)(m.depth[v] + 1);
-      m.disc[w] = (uint16_t)pushes++;
-      m.stack[sp++] = (uint16_t)w;
+      // the r-th unvisited neighbour in N, E, S, W order
+      uint32_t bits = open;
+      for (uint32_t r = below32(m.rnd[carved++], (uint32_t)__popc(open)); r > 0; --r) bits &= bits - 1;
+      const int d = __ffs(bits) - 1;
+      const int dx = d == 1 ? 1 : (d == 3 ? -1 : 0), dy = d == 0 ? -1 : (d == 2 ? 1 : 0);
+      smap[c + dy * S + dx] = 0;
+      vx += 2 * dx;
+      vy += 2 * dy;
+      smap[vy * S + vx] = 0;
+      v = (vy >> 1) * nn + (vx >> 1);
+      const int depth = sp;
+      m.stack[sp++] = (uint16_t)(vy << 8 | vx);
+      m.disc[v] = (uint16_t)pushes++;
+      if (depth > best_d || (depth == best_d && v < best_v)) {
+        best_v = v;
+        best_d = depth;
+        const int j = (depth + 1) / 2;  // the door sits on edge ceil(depth / 2) of the path
+        door_a = m.stack[j - 1];
+        door_b = m.stack[j];
+      }
     }
+    m.result[0] = best_v;
+    m.result[1] = best_d;
+    m.result[2] = door_a;
+    m.result[3] = door_b;
   }
   __syncwarp();
-  // goal: deepest node, ties to the smallest (row-major) index
-  int best_d = -1, best_i = 0x7fffffff;
-  for (int i = lane; i < n; i += 32) {
-    int d = m.depth[i];
-    if (d > best_d) {
-      best_d = d;
-      best_i = i;
-    }
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    int od = __shfl_xor_sync(0xffffffffu, best_d, off);
-    int oi = __shfl_xor_sync(0xffffffffu, best_i, off);
-    if (od > best_d || (od == best_d && oi < best_i)) {
-      best_d = od;
-      best_i = oi;
-    }
-  }
-  const int goal = best_i;
-  // door on edge ceil(m/2) of the m-edge spawn-to-goal path
-  const int medges = best_d;
-  const int j = (medges + 1) / 2;
-  int pj = goal;
-  for (int k = 0; k < medges - j; ++k) pj = m.parent[pj];
-  const int pj1 = m.parent[pj];
-  const int dxc = (2 * (pj % nn) + 1 + 2 * (pj1 % nn) + 1) >> 1;
-  const int dyc = (2 * (pj / nn) + 1 + 2 * (pj1 / nn) + 1) >> 1;
+  const int goal = m.result[0];
+  const int door_a = m.result[2], door_b = m.result[3];
+  const int dxc = ((door_a & 0xff) + (door_b & 0xff)) >> 1, dyc = ((door_a >> 8) + (door_b >> 8)) >> 1;
   if (lane == 0) smap[dyc * S + dxc] = (uint8_t)kDoor;
   // key: uniform over spawn-side nodes except the spawn
+  const int pj = ((door_b >> 8) >> 1) * nn + ((door_b & 0xff) >> 1);
   const int d0 = m.disc[pj], d1 = m.fin[pj];
   auto side = [&](int v) {
     int dv = m.disc[v];
@@ -704,7 +688,7 @@ __device__ void cast_columns(const Params& p, int e, const Env& r, float c, floa
   for (int base = 0; base < W; base += 64) {
     const int c0 = base + lane, c1 = base + 32 + lane;
     const bool v0 = c0 < W, v1 = c1 < W;
-    const float k0 = hd.col_k[v0 ? c0 : 0], k1 = hd.col_k[v1 ? c1 : 0];
+    const float k0 = __ldg(p.col_k + (v0 ? c0 : 0)), k1 = __ldg(p.col_k + (v1 ? c1 : 0));
     Ray q0, q1;
     ray_init(q0, r, fmaf(-k0, s, c), fmaf(k0, c, s), v0);
     ray_init(q1, r, fmaf(-k1, s, c), fmaf(k1, c, s), v1);
@@ -721,6 +705,8 @@ __device__ void cast_columns(const Params& p, int e, const Env& r, float c, floa
 
 // Project sprites (lane j takes sprite j) and order the visible ones far to
 // near (equal depths: higher index first, so the lower index is drawn last).
+// A sprite at depth ty is 0.25 W / (tan(fov/2) ty) columns wide, centred on
+// column (W/2)(1 + tx/ty), and (H/2) / ty rows high from row H/2 down.
 __device__ int project_sprites(const Params& p, const Env& r, const SpriteIn& sp, float c, float s,
                                const WarpSmem& ws, const BlockHead& hd, int lane) {
   const int W = p.W, H = p.H;
@@ -731,14 +717,15 @@ __device__ int project_sprites(const Params& p, const Env& r, const SpriteIn& sp
     const float vx = (sp.x - (float)r.cx) - r.fx;
     const float vy = (sp.y - (float)r.cy) - r.fy;
     ty = fmaf(vx, c, vy * s);
-    const float tx = fmaf(-vx, s, vy * c) / p.tan_half;
     vis = type != 0 && !(type == kSprKey && r.has_key) && ty > 0.1f;
     if (vis) {
-      const float scx = 0.5f * (float)W * (1.f + tx / ty);
-      const float hw = 0.5f * (float)W * 0.25f / (p.tan_half * ty);
-      const float wd = 2.f * hw, ht = 0.5f * (float)H / ty;
-      const float x0 = scx - hw, top = 0.5f * (float)H;
-      ws.spr_a[lane] = make_float4(x0, top, 1.f / wd, 1.f / ht);
+      const float inv_ty = __frcp_rn(ty);
+      const float tx = fmaf(-vx, s, vy * c) * p.inv_tan_half;
+      const float wd = 0.25f * (float)W * p.inv_tan_half * inv_ty;
+      const float ht = 0.5f * (float)H * inv_ty;
+      const float x0 = fmaf(0.5f * (float)W, fmaf(tx, inv_ty, 1.f), -0.5f * wd);
+      const float top = 0.5f * (float)H;
+      ws.spr_a[lane] = make_float4(x0, top, ty * (4.f * p.tan_half / (float)W), ty * (2.f / (float)H));
       // pixel centres that can fall inside [x0, x0 + wd) x [top, top + ht), one pixel of slack
       const int cA = (int)floorf(fmaxf(x0 - 1.f, -1.f));
       const int cB = (int)floorf(fminf(x0 + wd + 1.f, (float)W));
@@ -814,7 +801,9 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
     }
   }
   __syncwarp();
-  // sprites, far to near; lanes take columns, each pixel tested at its centre
+  // sprites, far to near; lanes take columns. For a column, the covered rows
+  // are those whose centre has v in [0, 1) with |2v - 1| below the mask's
+  // half-height at this u (key: 1 - |2u - 1|, disc: sqrt(1 - (2u - 1)^2)).
   for (int oi = 0; oi < nvis; ++oi) {
     const int j = ws.order[oi];
     const int4 rc = ws.spr_rect[j];
@@ -829,14 +818,11 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
       const float u = ((float)col + 0.5f - a.x) * a.z;
       if (!(u >= 0.f && u < 1.f && ty < ws.zbuf[col])) continue;
       const float au = fabsf(fmaf(2.f, u, -1.f));
+      const float half = kind == kSprKey ? 1.f - au : (kind == kSprGoal ? 2.f : sqrtf(fmaxf(0.f, fmaf(-au, au, 1.f))));
       uint8_t* px = buf + col * 3;
       for (int row = rA; row <= rB; ++row) {
         const float v = ((float)row + 0.5f - a.y) * a.w;
-        const float bv = fabsf(fmaf(2.f, v, -1.f));
-        bool in = v >= 0.f && v < 1.f;
-        if (kind == kSprKey) in = in && au + bv < 1.f;
-        else if (kind != kSprGoal) in = in && fmaf(au, au, bv * bv) < 1.f;
-        if (in) {
+        if (v >= 0.f && v < 1.f && fabsf(fmaf(2.f, v, -1.f)) < half) {
           uint8_t* q = px + (row - r0) * rowb;
           q[0] = (uint8_t)(rgbv & 255);
           q[1] = (uint8_t)((rgbv >> 8) & 255);
@@ -884,12 +870,11 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __grid_constant__ Params p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const BlockHead hd = carve_head(smem_raw, p);
-  for (int i = threadIdx.x; i < p.W; i += kThreads) hd.col_k[i] = p.col_k[i];
-  if (threadIdx.x < 16) hd.wall[threadIdx.x] = c_wall[threadIdx.x >> 3][threadIdx.x & 7];
-  if (threadIdx.x < 4) hd.sprite[threadIdx.x] = c_sprite[threadIdx.x];
-  __syncthreads();
-  const WarpSmem ws = carve(smem_raw + block_head_bytes(p) + warp * warp_bytes(p), p);
+  BlockHead hd;
+  const WarpSmem ws = carve(smem_raw + block_head_bytes(p) + warp * warp_bytes(p), p, hd);
+  if (lane < 16) hd.wall[lane] = c_wall[lane >> 3][lane & 7];
+  if (lane < 4) hd.sprite[lane] = c_sprite[lane];
+  __syncwarp();
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
   uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;

@@ -26,7 +26,8 @@ FIELDS = {
     "cell_x": (0, np.int16), "cell_y": (1, np.int16), "frac_x": (2, np.float32), "frac_y": (3, np.float32),
     "theta0": (4, np.float32), "turn": (5, np.int16), "t": (6, np.int32), "episode": (7, np.uint32),
     "flags": (8, np.uint8), "obj": (9, np.int16), "nspr": (10, np.uint8), "spr_x": (11, np.float32),
-    "spr_y": (12, np.float32), "spr_type": (13, np.uint8), "map": (14, np.uint8),
+    "spr_y": (12, np.float32), "spr_type": (13, np.uint8), "map": (14, np.uint8), "cos0": (15, np.float32),
+    "sin0": (16, np.float32),
 }
 
 # Entry points declared in include/jx.h (checked by the ABI test).
