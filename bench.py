@@ -1,11 +1,14 @@
 """Benchmark: batched env step + render (frames/s) on GB300.
 
 Workload: 4096 envs, 32 x 32 random DFS key-door mazes, 64 x 64 RGB frames,
-horizon 500 with auto-reset, uniform random actions (seed 1). A step is one
-fused launch that moves, collides, picks up, rewards, resets and renders all
-envs. Steps are replayed from a CUDA graph of 128 launches; each launch writes
-its frames into slot (step mod 128) of a 6.4 GB rollout buffer, so the frame
-stream never fits the 126 MB L2 and every byte goes to HBM.
+horizon 500 with auto-reset, 10,000 steps of uniform random actions (seed 1).
+A step moves, collides, picks up, rewards, resets and renders all envs. The
+timed path runs the pre-drawn action stream through jx_rollout, 128 steps per
+launch; every step writes its frames into slot (step mod 128) of a 6.4 GB
+rollout buffer, so the frame stream never fits the 126 MB L2 and every byte
+goes to HBM. The single-step entry point (jx_step, CUDA graph of 128
+launches) is timed on the same workload beside it, and its per-call latency
+gives p50 / p99.
 
 Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle on the
 same workload instead (the method's only other implementation here).
@@ -54,17 +57,25 @@ def shard_config(cfg: dict, rank: int) -> dict:
     return out
 
 
+STATE_READ = 2 + 2 + 4 + 4 + 4 + 4 + 2 + 4 + 4 + 1 + 12 + 1  # cells, fracs, cos/sin, turn, t, episode, flags,
+# objects, sprite count (+ the sprite table, K * 9 bytes)
+STATE_WRITE = 2 + 2 + 4 + 4 + 2 + 4 + 1  # cells, fracs, turn, t, flags
+STEP_IO = 1 + 4 + 1  # action, reward, done
+
+
 def algorithmic_bytes_per_env_step(cfg: dict) -> int:
-    """Compulsory HBM bytes of one env-step: the frame written; the state read
-    and written; action, reward and done. The map (re-read from L2 every step)
-    and episode regeneration (once per horizon) are excluded."""
+    """Compulsory HBM bytes of one jx_step per env: the frame written, the state
+    read and written, action, reward and done. The map (re-read from L2 every
+    step) and episode regeneration (once per horizon) are excluded."""
     H, W, K = cfg["frame_h"], cfg["frame_w"], cfg["max_sprites"]
-    frame = 3 * H * W
-    state_read = 2 + 2 + 4 + 4 + 4 + 2 + 4 + 4 + 1 + 12 + 1 + K * (4 + 4 + 1)  # cells, fracs, theta0, turn, t,
-    # episode, flags, objects, sprite count, sprite table
-    state_write = 2 + 2 + 4 + 4 + 2 + 4 + 1  # cells, fracs, turn, t, flags
-    io = 1 + 4 + 1  # action, reward, done
-    return frame + state_read + state_write + io
+    return 3 * H * W + STATE_READ + 9 * K + STATE_WRITE + STEP_IO
+
+
+def rollout_bytes(cfg: dict, n_envs: int, steps: int) -> int:
+    """Compulsory HBM bytes of one jx_rollout launch: per env and step the frame,
+    action, reward and done; per env the state read once and written once."""
+    H, W, K = cfg["frame_h"], cfg["frame_w"], cfg["max_sprites"]
+    return n_envs * steps * (3 * H * W + STEP_IO) + n_envs * (STATE_READ + 9 * K + STATE_WRITE)
 
 
 class ClockSampler:
@@ -228,6 +239,7 @@ def main():
             env.step(acts[s], frames[s % ring], rewards[s % ring], dones[s % ring], stream)
     stream.synchronize()
 
+    # single-step entry point: a CUDA graph of `ring` jx_step launches
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         for i in range(ring):
@@ -235,6 +247,8 @@ def main():
     torch.cuda.synchronize()
     # the capture itself ran nothing; the env state is still after the warm-up
 
+    # timed region: the whole action stream in rollout launches of `ring` steps
+    # (each launch writes one frame per env and step into the rollout buffer)
     n_full, rem = divmod(args.steps, ring)
     launches_before = env.launch_count()
     clocks = ClockSampler(local)
@@ -248,18 +262,16 @@ def main():
         ev0.record(stream)
         s = args.warmup
         for c in range(n_full):
-            ring_acts.copy_(acts[s: s + ring], non_blocking=True)
-            graph.replay()
+            env.rollout(acts[s: s + ring], frames, rewards, dones, stream)
             s += ring
-        for i in range(rem):
-            env.step(acts[s], frames[i], rewards[i], dones[i], stream)
-            s += 1
+        if rem:
+            env.rollout(acts[s: s + rem], frames[:rem], rewards[:rem], dones[:rem], stream)
+            s += rem
         ev1.record(stream)
     stream.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    eager_launches = env.launch_count() - launches_before
-    gpu_launches = n_full * ring + eager_launches
+    gpu_launches = env.launch_count() - launches_before
     t_max = ms
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -268,6 +280,18 @@ def main():
         torch.distributed.barrier()
     ms_per_step = t_max / args.steps
     value = world * N * args.steps / (t_max / 1e3)
+
+    # the single-step entry point on the same workload (graph replays of `ring` launches)
+    n_graph = max(1, min(n_full, 16))
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        g0.record(stream)
+        for c in range(n_graph):
+            ring_acts.copy_(acts[(args.warmup + c * ring) % (total_steps - ring + 1):][:ring], non_blocking=True)
+            graph.replay()
+        g1.record(stream)
+    stream.synchronize()
+    step_ms = g0.elapsed_time(g1) / (n_graph * ring)
 
     # per-step latency (eager launch + kernel, one step at a time)
     lat = []
@@ -299,8 +323,10 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_value = world * N * args.e2e_steps / e2e_s  # every rank runs the same count; host clock per rank
 
-    bytes_per_launch = algorithmic_bytes_per_env_step(cfg) * N
-    achieved = bytes_per_launch / (ms_per_step / 1e3) / 1e9
+    launch_steps = ring if n_full else rem
+    bytes_per_launch = rollout_bytes(cfg, N, launch_steps)
+    launch_ms = t_max / max(1, gpu_launches)
+    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, peak_src = 6800.0, "fallback"
     if os.path.exists(peaks_path):
@@ -334,8 +360,10 @@ def main():
                    "parallelism": f"replicas x{world}",
                    "l2": f"frames written to a {ring}-slot rollout buffer ({ring * N * H * W * 3 / 1e9:.1f} GB) > L2",
                    "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
-                              "cuda_graph_steps": ring}},
+                              "entry": "jx_rollout", "steps_per_launch": ring}},
         "p50_step_ms": p50, "p99_step_ms": p99,
+        "per_step_launch": {"value": world * N / (step_ms / 1e3), "unit": "env-steps/s", "ms_per_step": step_ms,
+                            "how": f"jx_step, CUDA graph of {ring} launches"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_per_launch},

@@ -129,6 +129,18 @@ jx_status jx_reset(jx_env* env, void* stream, uint8_t* d_frames);
 jx_status jx_step(jx_env* env, void* stream, const uint8_t* d_actions, uint8_t* d_frames, float* d_rewards,
                   uint8_t* d_dones);
 
+/* `steps` consecutive calls of jx_step in one kernel launch, for action
+ * streams known in advance (uniform random policies, replayed or scripted
+ * actions): step t reads d_actions + t*N and writes d_frames + t*N*H*W*3,
+ * d_rewards + t*N and d_dones + t*N. The results are identical to the
+ * sequence of jx_step calls.
+ *  d_actions [steps][N] uint8; d_frames [steps][N][H][W][3] uint8;
+ *  d_rewards [steps][N] float32; d_dones [steps][N] uint8.
+ * Each env's pose stays in registers and its map in shared memory across the
+ * steps. Asynchronous on `stream`; allocates nothing. steps >= 1. */
+jx_status jx_rollout(jx_env* env, void* stream, const uint8_t* d_actions, int32_t steps, uint8_t* d_frames,
+                     float* d_rewards, uint8_t* d_dones);
+
 /* Render the current state of all environments into d_frames (no state change). */
 jx_status jx_render(jx_env* env, void* stream, uint8_t* d_frames);
 

@@ -282,7 +282,7 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
                 prop.sharedMemPerBlockOptin);
   }
   int bps = 0;
-  for (int mode = 0; mode < 4; ++mode) {
+  for (int mode = 0; mode < 5; ++mode) {
     int b = 0;
     if ((err = jx::kernel_blocks_per_sm(p, mode, &b)) != cudaSuccess) {
       jx_destroy(env);
@@ -349,6 +349,21 @@ jx_status jx_step(jx_env* env, void* stream, const uint8_t* d_actions, uint8_t* 
   p.rewards = d_rewards;
   p.dones = d_dones;
   return run(env, p, jx::MODE_STEP, stream);
+}
+
+jx_status jx_rollout(jx_env* env, void* stream, const uint8_t* d_actions, int32_t steps, uint8_t* d_frames,
+                     float* d_rewards, uint8_t* d_dones) {
+  if (jx_status st = check_env(env)) return st;
+  if (steps < 1) return fail(JX_EINVAL, "steps must be >= 1 (got %d)", steps);
+  if (!d_actions || !d_rewards || !d_dones) return fail(JX_EINVAL, "NULL device pointer");
+  if (!d_frames || !aligned16(d_frames)) return fail(JX_EINVAL, "d_frames must be a 16-byte aligned device pointer");
+  jx::Params p = env->base;
+  p.actions = d_actions;
+  p.frames = d_frames;
+  p.rewards = d_rewards;
+  p.dones = d_dones;
+  p.steps = steps;
+  return run(env, p, jx::MODE_ROLLOUT, stream);
 }
 
 jx_status jx_render(jx_env* env, void* stream, uint8_t* d_frames) {

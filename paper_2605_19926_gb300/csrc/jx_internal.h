@@ -18,7 +18,7 @@ constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kRingBuffers = 2;  // frame row-block staging buffers per warp
 constexpr int kMinBlocksPerSm = 7; // register budget: 7 blocks of 4 warps resident per SM
 
-enum Mode { MODE_STEP = 0, MODE_RESET = 1, MODE_RENDER = 2, MODE_RAYS = 3 };
+enum Mode { MODE_STEP = 0, MODE_RESET = 1, MODE_RENDER = 2, MODE_RAYS = 3, MODE_ROLLOUT = 4 };
 
 enum Purpose : uint32_t {
   P_WALL = 1,
@@ -65,6 +65,7 @@ struct Params {
   int32_t* dbg_hits;
   float* dbg_perp;
   int32_t n, S, H, W, K, horizon, tpr, task;
+  int32_t steps;  // steps of one rollout launch (actions / outputs are [steps][n][...])
   int32_t rows_per_block;  // rows per staged frame block
   int32_t frame_block_bytes;
   int32_t map_smem_bytes;  // S * S rounded up to 16

@@ -538,9 +538,11 @@ __device__ __forceinline__ void renormalise(int& c, float& f) {
   }
 }
 
-// Returns true when the episode ended (the caller regenerates).
-__device__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, int lane, float& c, float& s) {
-  int a = r.action;
+// One step of env e under action a; the reward and done flag go to output
+// slot `out`. Returns true when the episode ended (the caller regenerates).
+// The pose is written back to the state block only when write_state is set.
+__device__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, int lane, float& c, float& s, int a,
+                         size_t out, bool write_state) {
   if (a > 6) {
     if (lane == 0) atomicOr(p.err, 1u);
     a = 0;
@@ -582,9 +584,9 @@ __device__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, in
   r.t += 1;
   const bool done = (ev & 2) || (p.horizon > 0 && r.t >= p.horizon);
   if (lane == 0) {
-    p.rewards[e] = p.reward_lut[ev];
-    p.dones[e] = done ? 1 : 0;
-    if (!done) {
+    p.rewards[out] = p.reward_lut[ev];
+    p.dones[out] = done ? 1 : 0;
+    if (write_state && !done) {
       const State& st = p.st;
       st.cell_x[e] = (int16_t)r.cx;
       st.cell_y[e] = (int16_t)r.cy;
@@ -836,7 +838,7 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
 
 template <int MODE>
 __device__ void render_env(const Params& p, int e, const Env& r, const SpriteIn& sp, float c, float s,
-                           const WarpSmem& ws, const BlockHead& hd, int lane, int& slot) {
+                           const WarpSmem& ws, const BlockHead& hd, int lane, int& slot, uint8_t* frame) {
   cast_columns<MODE>(p, e, r, c, s, ws, hd, lane);
   if (MODE == MODE_RAYS) return;
   const int nvis = project_sprites(p, r, sp, c, s, ws, hd, lane);  // ends with __syncwarp
@@ -844,7 +846,6 @@ __device__ void render_env(const Params& p, int e, const Env& r, const SpriteIn&
   Group gr;
   const int my_row = lane / groups;
   if (my_row < 32 / groups) load_group(ws, lane - my_row * groups, groups, gr);
-  uint8_t* frame = p.frames + (size_t)e * H * rowb;
   for (int r0 = 0; r0 < H; r0 += p.rows_per_block) {
     const int r1 = r0 + p.rows_per_block < H ? r0 + p.rows_per_block : H;
     uint8_t* buf = ws.ring + slot * p.frame_block_bytes;
@@ -879,10 +880,46 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __
   const int nw = gridDim.x * kWarpsPerBlock;
   uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;
   int slot = 0;
+  const size_t frame_bytes = (size_t)3 * p.H * p.W;
   for (int e = gw; e < p.n; e += nw) {
     Env r;
     SpriteIn sp;
     float c, s;
+    if (MODE == MODE_ROLLOUT) {
+      // the env's pose stays in registers and its map in shared memory for all steps
+      r = load_env<MODE>(p, e);
+      sp = load_sprite(p, e, lane);
+      stage_map(p, e, ws.map, lane);
+      int a_next = p.actions[e];
+      for (int t = 0; t < p.steps; ++t) {
+        const size_t out = (size_t)t * p.n + e;
+        const int a = a_next;
+        if (t + 1 < p.steps) a_next = p.actions[out + p.n];
+        if (step_env(p, e, r, ws.map, lane, c, s, a, out, false)) {
+          const uint32_t ep = r.ep + 1;
+          __syncwarp();
+          generate(p, e, ep, ws, scratch, lane);
+          r = load_env<MODE>(p, e);
+          sp = load_sprite(p, e, lane);
+          heading(p, r, c, s);
+        }
+        open_door(p, r, ws, lane);
+        render_env<MODE>(p, e, r, sp, c, s, ws, hd, lane, slot, p.frames + out * frame_bytes);
+        __syncwarp();
+      }
+      if (lane == 0) {
+        const State& st = p.st;
+        st.cell_x[e] = (int16_t)r.cx;
+        st.cell_y[e] = (int16_t)r.cy;
+        st.frac_x[e] = r.fx;
+        st.frac_y[e] = r.fy;
+        st.turn[e] = (int16_t)r.turn;
+        st.t[e] = r.t;
+        st.flags[e] = (uint8_t)r.has_key;
+      }
+      __syncwarp();
+      continue;
+    }
     if (MODE == MODE_RESET) {
       generate(p, e, 0u, ws, scratch, lane);
       r = load_env<MODE>(p, e);
@@ -893,7 +930,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __
       sp = load_sprite(p, e, lane);
       stage_map(p, e, ws.map, lane);
       if (MODE == MODE_STEP) {
-        if (step_env(p, e, r, ws.map, lane, c, s)) {
+        if (step_env(p, e, r, ws.map, lane, c, s, r.action, (size_t)e, true)) {
           const uint32_t ep = r.ep + 1;
           __syncwarp();
           generate(p, e, ep, ws, scratch, lane);
@@ -906,7 +943,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __
       }
     }
     open_door(p, r, ws, lane);
-    render_env<MODE>(p, e, r, sp, c, s, ws, hd, lane, slot);
+    render_env<MODE>(p, e, r, sp, c, s, ws, hd, lane, slot, p.frames + (size_t)e * frame_bytes);
     __syncwarp();
   }
   // shared memory stays allocated until the bulk stores have read it
@@ -936,6 +973,7 @@ cudaError_t kernel_blocks_per_sm(const Params& p, int mode, int* blocks) {
     case MODE_STEP: return blocks_per_sm_for<MODE_STEP>(p, blocks);
     case MODE_RESET: return blocks_per_sm_for<MODE_RESET>(p, blocks);
     case MODE_RENDER: return blocks_per_sm_for<MODE_RENDER>(p, blocks);
+    case MODE_ROLLOUT: return blocks_per_sm_for<MODE_ROLLOUT>(p, blocks);
     default: return blocks_per_sm_for<MODE_RAYS>(p, blocks);
   }
 }
@@ -946,6 +984,7 @@ cudaError_t launch(const Params& p, int mode, int grid, cudaStream_t stream) {
     case MODE_STEP: env_kernel<MODE_STEP><<<grid, kThreads, smem, stream>>>(p); break;
     case MODE_RESET: env_kernel<MODE_RESET><<<grid, kThreads, smem, stream>>>(p); break;
     case MODE_RENDER: env_kernel<MODE_RENDER><<<grid, kThreads, smem, stream>>>(p); break;
+    case MODE_ROLLOUT: env_kernel<MODE_ROLLOUT><<<grid, kThreads, smem, stream>>>(p); break;
     default: env_kernel<MODE_RAYS><<<grid, kThreads, smem, stream>>>(p); break;
   }
   return cudaGetLastError();

@@ -32,7 +32,7 @@ FIELDS = {
 
 # Entry points declared in include/jx.h (checked by the ABI test).
 SYMBOLS = [
-    "jx_create", "jx_destroy", "jx_reset", "jx_step", "jx_render", "jx_step_host", "jx_debug_rays",
+    "jx_create", "jx_destroy", "jx_reset", "jx_step", "jx_rollout", "jx_render", "jx_step_host", "jx_debug_rays",
     "jx_state_bytes", "jx_state_field", "jx_get_state", "jx_set_state", "jx_sync_status", "jx_launch_count",
     "jx_launch_shape", "jx_last_error",
 ]
@@ -73,6 +73,7 @@ def _load() -> ctypes.CDLL:
         "jx_destroy": [P],
         "jx_reset": [P, P, P],
         "jx_step": [P, P, P, P, P, P],
+        "jx_rollout": [P, P, P, i32, P, P, P],
         "jx_render": [P, P, P],
         "jx_step_host": [P, P, P, P, P, P],
         "jx_debug_rays": [P, P, P, P],
@@ -170,6 +171,12 @@ class Env:
 
     def step(self, actions, frames, rewards, dones, stream=None):
         _check(lib.jx_step(self._h, _stream(stream), _ptr(actions), _ptr(frames), _ptr(rewards), _ptr(dones)))
+
+    def rollout(self, actions, frames, rewards, dones, stream=None):
+        """``actions.shape[0]`` steps in one launch (outputs shaped [steps, N, ...])."""
+        steps = int(actions.shape[0])
+        _check(lib.jx_rollout(self._h, _stream(stream), _ptr(actions), steps, _ptr(frames), _ptr(rewards),
+                              _ptr(dones)))
 
     def render(self, frames, stream=None):
         _check(lib.jx_render(self._h, _stream(stream), _ptr(frames)))

@@ -236,3 +236,45 @@ def test_scripted_goal_reach_and_door_crossing():
     for e in range(1, 32, 2):
         dist = abs(int(after["cell_x"][e]) - int(f["cell_x"][e])) + abs(int(after["cell_y"][e]) - int(f["cell_y"][e]))
         assert (dist >= 1) == opens[e], e
+
+
+def _rollout_vs_steps(cfg, T, seed, warm=0):
+    """jx_rollout over T steps equals T jx_step calls, bit for bit (frames,
+    rewards, dones and the final state); both start from the same state."""
+    N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
+    a, b = Run(cfg), Run(cfg)
+    a.reset()
+    b.reset()
+    for s in range(warm):
+        act = inputs.actions(seed, s, N)
+        a.step(act)
+        b.step(act)
+    acts = torch.from_numpy(inputs.action_stream(seed, T, N, first_step=warm)).to(a.dev)
+    frames = torch.zeros((T, N, H, W, 3), dtype=torch.uint8, device=a.dev)
+    rewards = torch.zeros((T, N), dtype=torch.float32, device=a.dev)
+    dones = torch.zeros((T, N), dtype=torch.uint8, device=a.dev)
+    b.env.rollout(acts, frames, rewards, dones)
+    torch.cuda.synchronize()
+    for t in range(T):
+        a.actions.copy_(acts[t])
+        a.env.step(a.actions, a.frames, a.rewards, a.dones)
+        assert torch.equal(a.frames, frames[t]), t
+        assert torch.equal(a.rewards, rewards[t]) and torch.equal(a.dones, dones[t]), t
+    torch.cuda.synchronize()
+    assert (a.env.get_state() == b.env.get_state()).all()
+    return int(dones.sum().item())
+
+
+@pytest.mark.parametrize("name,T", [("maze32_ragged", 90), ("maze6_events", 150), ("rooms16_sprites_40x48", 40),
+                                    ("maze18_96x128", 45)])
+def test_rollout_matches_step_sequence(name, T):
+    n_done = _rollout_vs_steps(CASES[name], T, seed=13)
+    if name in ("maze32_ragged", "maze18_96x128", "maze6_events"):
+        assert n_done > 0
+
+
+def test_rollout_full_size_across_horizon():
+    """4096 envs, 32 x 32 key-door mazes, in the benchmark's launch shape: a
+    64-step rollout that crosses the 500-step horizon (every env resets)."""
+    n_done = _rollout_vs_steps(inputs.batched_keydoor_mazes(), 64, seed=1, warm=470)
+    assert n_done >= 4096
