@@ -162,8 +162,9 @@ jx_status jx_debug_rays(jx_env* env, void* stream, int32_t* d_hits, float* d_per
  * byte offset and size inside it (fields: JX_F_*). jx_get_state copies the
  * whole block to the host and waits; jx_set_state copies it back and waits.
  * `bytes` must equal jx_state_bytes. jx_set_state checks that every position
- * lies inside the map (cell in [0, S), fraction in [0, 1)) and returns
- * JX_EINVAL otherwise; it recomputes the derived fields (JX_F_COS0, JX_F_SIN0)
+ * lies inside the map (cell in [0, S), fraction in [0, 1)), that turn lies in
+ * [0, turns_per_rev) and the sprite count in [0, K], and returns JX_EINVAL
+ * otherwise; it recomputes the derived fields (JX_F_COS0, JX_F_SIN0)
  * from theta0 and leaves the caller's buffer untouched. */
 enum {
   JX_F_CELL_X = 0,   /* int16  [N]   cell column of the position            */

@@ -268,12 +268,14 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
       jx::Params q = p;
       q.rows_per_block = rows;
       q.frame_block_bytes = rows * rowb;
+      jx::layout_warp_smem(q);
       if ((size_t)(jx::block_smem_bytes(q) + reserved) * jx::kMinBlocksPerSm <= per_sm) {
         p.rows_per_block = rows;
         p.frame_block_bytes = rows * rowb;
         break;
       }
     }
+    jx::layout_warp_smem(p);
   }
   env->smem_block = jx::block_smem_bytes(p);
   if ((size_t)env->smem_block > prop.sharedMemPerBlockOptin) {
@@ -456,6 +458,8 @@ jx_status jx_set_state(jx_env* env, const void* h_buf, size_t bytes) {
   const float* fx = reinterpret_cast<const float*>(fld(JX_F_FRAC_X));
   const float* fy = reinterpret_cast<const float*>(fld(JX_F_FRAC_Y));
   const float* th = reinterpret_cast<const float*>(fld(JX_F_THETA0));
+  const int16_t* turn = reinterpret_cast<const int16_t*>(fld(JX_F_TURN));
+  const uint8_t* nspr = reinterpret_cast<const uint8_t*>(fld(JX_F_NSPR));
   float* c0 = reinterpret_cast<float*>(fld(JX_F_COS0));
   float* s0 = reinterpret_cast<float*>(fld(JX_F_SIN0));
   for (int i = 0; i < N; ++i) {
@@ -463,6 +467,10 @@ jx_status jx_set_state(jx_env* env, const void* h_buf, size_t bytes) {
         !(fy[i] >= 0.f && fy[i] < 1.f))
       return fail(JX_EINVAL, "env %d: position outside the map (cell %d,%d frac %g,%g)", i, cx[i], cy[i], fx[i], fy[i]);
     if (!std::isfinite(th[i])) return fail(JX_EINVAL, "env %d: theta0 is not finite", i);
+    if (turn[i] < 0 || turn[i] >= env->cfg.turns_per_rev)
+      return fail(JX_EINVAL, "env %d: turn %d outside [0, %d)", i, turn[i], env->cfg.turns_per_rev);
+    if (nspr[i] > env->cfg.max_sprites)
+      return fail(JX_EINVAL, "env %d: %d sprites in use, at most %d", i, nspr[i], env->cfg.max_sprites);
     c0[i] = (float)std::cos((double)th[i]);
     s0[i] = (float)std::sin((double)th[i]);
   }

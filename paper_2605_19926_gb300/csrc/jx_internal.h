@@ -13,10 +13,10 @@ constexpr int kMaxSprites = 16;
 constexpr int kMaxSide = 128;
 constexpr int kMaxH = 256;
 constexpr int kMaxW = 256;
-constexpr int kWarpsPerBlock = 4;
+constexpr int kWarpsPerBlock = 1;  // one-warp blocks spread envs evenly over the SMs
 constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kRingBuffers = 2;  // frame row-block staging buffers per warp
-constexpr int kMinBlocksPerSm = 7; // register budget: 7 blocks of 4 warps resident per SM
+constexpr int kMinBlocksPerSm = 28;  // register budget: 28 warps resident per SM
 
 enum Mode { MODE_STEP = 0, MODE_RESET = 1, MODE_RENDER = 2, MODE_RAYS = 3, MODE_ROLLOUT = 4 };
 
@@ -69,12 +69,17 @@ struct Params {
   int32_t rows_per_block;  // rows per staged frame block
   int32_t frame_block_bytes;
   int32_t map_smem_bytes;  // S * S rounded up to 16
+  // per-warp shared memory layout (byte offsets from the warp's base; set by layout_warp_smem)
+  int32_t off_pal, off_map, off_col_rgb, off_col_top, off_col_bot, off_zbuf, off_spr_in, off_spr_a, off_spr_rect,
+      off_spr_ty, off_spr_rgb, off_spr_kind, off_order, off_obj, off_env, warp_bytes;
   float move, radius, tan_half, inv_tan_half;
   float reward_lut[4];
   uint64_t seed;
   uint64_t wall_thr;  // an interior cell is a wall iff (draw >> 11) < wall_thr
 };
 
+// Fill in the per-warp shared memory layout of p (needs W, K, S, frame_block_bytes).
+void layout_warp_smem(Params& p);
 // Dynamic shared memory bytes of one block.
 int block_smem_bytes(const Params& p);
 size_t gen_scratch_bytes(int task, int S);

@@ -90,74 +90,57 @@ __device__ __forceinline__ void bulk_wait_read_all() {
 // ------------------------------------------------------------- warp smem --
 __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; }
 
-// Shared memory of a block: a head shared by its warps (per-column ray
-// coefficients and the palette), then one region per warp.
-struct WarpSmem {
-  uint8_t* ring;      // kRingBuffers * frame_block_bytes (also the maze work space)
-  uint8_t* map;       // map_smem_bytes, row-major cell values
-  uint32_t* col_rgb;  // [W] wall colour, chunk-interleaved (see col_slot)
-  int32_t* col_top;   // [W] first wall row, chunk-interleaved
-  int32_t* col_bot;   // [W] first floor row, chunk-interleaved
-  float* zbuf;        // [W] by column
-  float4* spr_a;      // [K] x0, top, 1 / width, 1 / height (pixels)
-  int4* spr_rect;     // [K] pixel rectangle to test: first/last column, first/last row
-  float* spr_ty;      // [K] depth
-  uint32_t* spr_rgb;  // [K]
-  int32_t* spr_kind;  // [K] type
-  int32_t* order;     // [K] visible sprites, far to near
+// Shared memory of a warp, addressed from one base with the layout offsets
+// of Params (constants), so no pointer lives in a register:
+//   ring      kRingBuffers * frame_block_bytes (also the maze work space)
+//   pal       [2][8] wall colours by face and cell value, then [4] sprite colours by type
+//   map       S * S cell values, row-major
+//   col_rgb   [W] wall colour, chunk-interleaved (see col_slot)
+//   col_top   [W] first wall row, chunk-interleaved
+//   col_bot   [W] first floor row, chunk-interleaved
+//   zbuf      [W] perpendicular distance by column
+//   spr_in    [K] float4 sprite x, y, type (as float)
+//   spr_a     [K] float4 x0, top, 1 / width, 1 / height (pixels)
+//   spr_rect  [K] int4 pixel rectangle to test: first/last column, first/last row
+//   spr_ty    [K] depth;  spr_rgb [K] colour;  spr_kind [K] type
+//   order     [K] visible sprites, far to near
+//   obj       [8] int32 key x, key y, goal x, goal y, door x, door y, sprites in use
+//   env       the scalar state (Env) between the steps of a rollout
+// The lane's place in the frame fill: lanes [0, groups * rows) are laid out
+// as `rows` rows of `groups` 8-pixel groups.
+struct FillLane {
+  int groups, rows, my_row, g;
 };
+__device__ __forceinline__ FillLane fill_lane(const Params& p, int lane) {
+  FillLane f;
+  f.groups = p.W >> 3;
+  f.rows = 32 / f.groups;
+  f.my_row = lane / f.groups;
+  f.g = lane - f.my_row * f.groups;
+  return f;
+}
 
-// Palette copy of each warp: wall colours [face][cell value], then sprite
-// colours by type.
-struct BlockHead {
-  uint32_t* wall;    // [2][8]
-  uint32_t* sprite;  // [4]
+struct WarpSmem {
+  uint8_t* base;
+  FillLane fl;
+  __device__ __forceinline__ uint8_t* ring() const { return base; }
+  __device__ __forceinline__ uint32_t* pal(const Params& p) const { return (uint32_t*)(base + p.off_pal); }
+  __device__ __forceinline__ uint8_t* map(const Params& p) const { return base + p.off_map; }
+  __device__ __forceinline__ uint32_t* col_rgb(const Params& p) const { return (uint32_t*)(base + p.off_col_rgb); }
+  __device__ __forceinline__ int32_t* col_top(const Params& p) const { return (int32_t*)(base + p.off_col_top); }
+  __device__ __forceinline__ int32_t* col_bot(const Params& p) const { return (int32_t*)(base + p.off_col_bot); }
+  __device__ __forceinline__ float* zbuf(const Params& p) const { return (float*)(base + p.off_zbuf); }
+  __device__ __forceinline__ float4* spr_in(const Params& p) const { return (float4*)(base + p.off_spr_in); }
+  __device__ __forceinline__ float4* spr_a(const Params& p) const { return (float4*)(base + p.off_spr_a); }
+  __device__ __forceinline__ int4* spr_rect(const Params& p) const { return (int4*)(base + p.off_spr_rect); }
+  __device__ __forceinline__ float* spr_ty(const Params& p) const { return (float*)(base + p.off_spr_ty); }
+  __device__ __forceinline__ uint32_t* spr_rgb(const Params& p) const { return (uint32_t*)(base + p.off_spr_rgb); }
+  __device__ __forceinline__ int32_t* spr_kind(const Params& p) const { return (int32_t*)(base + p.off_spr_kind); }
+  __device__ __forceinline__ int32_t* order(const Params& p) const { return (int32_t*)(base + p.off_order); }
+  __device__ __forceinline__ int32_t* obj(const Params& p) const { return (int32_t*)(base + p.off_obj); }
 };
 
 constexpr int kPaletteWords = 2 * 8 + 4;
-__host__ __device__ __forceinline__ int block_head_bytes(const Params&) { return 0; }
-
-__host__ __device__ __forceinline__ int warp_bytes(const Params& p) {
-  int b = kRingBuffers * p.frame_block_bytes + align16(4 * kPaletteWords);
-  b += p.map_smem_bytes;
-  b += align16(4 * p.W) * 4;
-  int K = p.K > 0 ? p.K : 1;
-  b += align16(16 * K) * 2 + align16(4 * K) * 4;
-  return align16(b);
-}
-
-__device__ __forceinline__ WarpSmem carve(uint8_t* base, const Params& p, BlockHead& hd) {
-  WarpSmem w;
-  int K = p.K > 0 ? p.K : 1;
-  uint8_t* q = base;
-  w.ring = q;
-  q += kRingBuffers * p.frame_block_bytes;
-  hd.wall = (uint32_t*)q;
-  hd.sprite = hd.wall + 16;
-  q += align16(4 * kPaletteWords);
-  w.map = q;
-  q += p.map_smem_bytes;
-  w.col_rgb = (uint32_t*)q;
-  q += align16(4 * p.W);
-  w.col_top = (int32_t*)q;
-  q += align16(4 * p.W);
-  w.col_bot = (int32_t*)q;
-  q += align16(4 * p.W);
-  w.zbuf = (float*)q;
-  q += align16(4 * p.W);
-  w.spr_a = (float4*)q;
-  q += align16(16 * K);
-  w.spr_rect = (int4*)q;
-  q += align16(16 * K);
-  w.spr_ty = (float*)q;
-  q += align16(4 * K);
-  w.spr_rgb = (uint32_t*)q;
-  q += align16(4 * K);
-  w.spr_kind = (int32_t*)q;
-  q += align16(4 * K);
-  w.order = (int32_t*)q;
-  return w;
-}
 
 // Column data is stored so that the lanes filling one row (8 columns each)
 // read consecutive 16-byte groups: half g (columns 4g..4g+3 of the group) of
@@ -168,25 +151,17 @@ __device__ __forceinline__ int col_slot(int col, int groups) {
 }
 
 // ------------------------------------------------------------ env state ----
+// The scalar state of the env a warp is working on (identical in all lanes).
+// Key, goal and door cells and the sprite table live in the warp's shared
+// memory instead (see load_objects).
 struct Env {
   int cx, cy;    // cell of the position
   float fx, fy;  // position inside the cell, [0, 1)
   float c0, s0;  // cos, sin of theta0
   int turn, t;
-  uint32_t ep;
   int has_key;
-  int key_x, key_y, goal_x, goal_y, door_x, door_y;
-  int nspr;
-  int action;
 };
 
-// Lane j's sprite slot (prefetched with the state).
-struct SpriteIn {
-  float x, y;
-  int type;
-};
-
-template <int MODE>
 __device__ __forceinline__ Env load_env(const Params& p, int e) {
   Env r;
   const State& st = p.st;
@@ -196,33 +171,24 @@ __device__ __forceinline__ Env load_env(const Params& p, int e) {
   r.fy = st.frac_y[e];
   r.c0 = st.cos0[e];
   r.s0 = st.sin0[e];
-  int turn = st.turn[e] % p.tpr;
-  r.turn = turn < 0 ? turn + p.tpr : turn;
+  r.turn = st.turn[e];  // in [0, turns_per_rev): generated so, checked by set_state
   r.t = st.t[e];
-  r.ep = st.episode[e];
   r.has_key = st.flags[e] & 1;
-  const int16_t* o = st.obj + 6 * (size_t)e;
-  r.key_x = o[0];
-  r.key_y = o[1];
-  r.goal_x = o[2];
-  r.goal_y = o[3];
-  r.door_x = o[4];
-  r.door_y = o[5];
-  int ns = st.nspr[e];
-  r.nspr = ns > p.K ? p.K : ns;
-  r.action = MODE == MODE_STEP ? (int)p.actions[e] : 0;
   return r;
 }
 
-__device__ __forceinline__ SpriteIn load_sprite(const Params& p, int e, int lane) {
-  SpriteIn q{0.f, 0.f, 0};
-  if (lane < p.K) {
-    size_t i = (size_t)e * p.K + lane;
-    q.x = p.st.spr_x[i];
-    q.y = p.st.spr_y[i];
-    q.type = p.st.spr_type[i];
+// Key / goal / door cells (lanes 0..5) and sprite slots (lane j: slot j) into
+// the warp's shared memory.
+__device__ __forceinline__ void load_objects(const Params& p, const WarpSmem& ws, int e, int lane) {
+  if (lane < 6) ws.obj(p)[lane] = p.st.obj[6 * (size_t)e + lane];
+  if (lane == 6) {
+    const int ns = p.st.nspr[e];
+    ws.obj(p)[6] = ns > p.K ? p.K : ns;  // sprites in use
   }
-  return q;
+  if (lane < p.K) {
+    const size_t i = (size_t)e * p.K + lane;
+    ws.spr_in(p)[lane] = make_float4(p.st.spr_x[i], p.st.spr_y[i], (float)p.st.spr_type[i], 0.f);
+  }
 }
 
 // heading = theta0 + turn * 2 pi / turns_per_rev: (cos, sin)(theta0), kept in
@@ -488,19 +454,20 @@ __device__ __noinline__ void gen_maze(const Params& p, int e, uint32_t ep, uint8
 
 // The maze work space lives in the warp's frame staging ring when it fits
 // (32 x 32 mazes need 3.4 KB), else in the global per-warp slot.
-__device__ __noinline__ void generate(const Params& p, int e, uint32_t ep, const WarpSmem& ws, uint8_t* scratch,
+__device__ __noinline__ void generate(const Params& p, int e, uint32_t ep, uint8_t* wbase, uint8_t* scratch,
                                       int lane) {
+  const WarpSmem ws{wbase, fill_lane(p, lane)};
   if (p.task == 0) {
-    gen_rooms(p, e, ep, ws.map, lane);
+    gen_rooms(p, e, ep, ws.map(p), lane);
   } else {
     const int nn = (p.S - 2) / 2;
     uint8_t* work = scratch;
     if (maze_scratch_bytes(nn * nn) <= (size_t)(kRingBuffers * p.frame_block_bytes)) {
       if (lane == 0) bulk_wait_read_all();  // the ring's pending frame stores have read it
       __syncwarp();
-      work = ws.ring;
+      work = ws.ring();
     }
-    gen_maze(p, e, ep, ws.map, work, lane);
+    gen_maze(p, e, ep, ws.map(p), work, lane);
   }
 }
 
@@ -541,8 +508,8 @@ __device__ __forceinline__ void renormalise(int& c, float& f) {
 // One step of env e under action a; the reward and done flag go to output
 // slot `out`. Returns true when the episode ended (the caller regenerates).
 // The pose is written back to the state block only when write_state is set.
-__device__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, int lane, float& c, float& s, int a,
-                         size_t out, bool write_state) {
+__device__ __forceinline__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, const int32_t* obj,
+                                         int lane, float& c, float& s, int a, size_t out, bool write_state) {
   if (a > 6) {
     if (lane == 0) atomicOr(p.err, 1u);
     a = 0;
@@ -577,14 +544,15 @@ __device__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, in
     r.fy = nfy;
     renormalise(r.cy, r.fy);
   }
+  const int4 kg = *reinterpret_cast<const int4*>(obj);  // key x, key y, goal x, goal y
   int ev = 0;
-  if (!r.has_key && r.key_x >= 0 && r.cx == r.key_x && r.cy == r.key_y) ev |= 1;
-  if (r.goal_x >= 0 && r.cx == r.goal_x && r.cy == r.goal_y) ev |= 2;
+  if (!r.has_key && kg.x >= 0 && r.cx == kg.x && r.cy == kg.y) ev |= 1;
+  if (kg.z >= 0 && r.cx == kg.z && r.cy == kg.w) ev |= 2;
   if (ev & 1) r.has_key = 1;
   r.t += 1;
   const bool done = (ev & 2) || (p.horizon > 0 && r.t >= p.horizon);
   if (lane == 0) {
-    p.rewards[out] = p.reward_lut[ev];
+    p.rewards[out] = ev == 0 ? p.reward_lut[0] : (ev == 1 ? p.reward_lut[1] : (ev == 2 ? p.reward_lut[2] : p.reward_lut[3]));
     p.dones[out] = done ? 1 : 0;
     if (write_state && !done) {
       const State& st = p.st;
@@ -644,8 +612,7 @@ __device__ __forceinline__ void ray_advance(Ray& q, const uint8_t* smap, int S) 
 
 // Slice of a finished ray: perp, rows and colour into the column arrays.
 template <int MODE>
-__device__ __forceinline__ void finish_column(const Params& p, int e, const Ray& q, int col, const WarpSmem& ws,
-                                              const BlockHead& hd) {
+__device__ __forceinline__ void finish_column(const Params& p, int e, const Ray& q, int col, const WarpSmem& ws) {
   const int S = p.S, H = p.H;
   float perp;
   if (q.side == 0)
@@ -666,12 +633,12 @@ __device__ __forceinline__ void finish_column(const Params& p, int e, const Ray&
   const int bot = top + h;
   int v = 1;
   const bool inside = (unsigned)q.mx < (unsigned)S && (unsigned)q.my < (unsigned)S;
-  if (q.side >= 0 && inside) v = ws.map[q.my * S + q.mx];
+  if (q.side >= 0 && inside) v = ws.map(p)[q.my * S + q.mx];
   const int slot = col_slot(col, p.W >> 3);
-  ws.col_rgb[slot] = hd.wall[(q.side == 1 ? 8 : 0) + (v > 7 ? 7 : v)];
-  ws.col_top[slot] = top < 0 ? 0 : (top > H ? H : top);
-  ws.col_bot[slot] = bot < 0 ? 0 : (bot > H ? H : bot);
-  ws.zbuf[col] = perp;
+  ws.col_rgb(p)[slot] = ws.pal(p)[(q.side == 1 ? 8 : 0) + (v > 7 ? 7 : v)];
+  ws.col_top(p)[slot] = top < 0 ? 0 : (top > H ? H : top);
+  ws.col_bot(p)[slot] = bot < 0 ? 0 : (bot > H ? H : bot);
+  ws.zbuf(p)[col] = perp;
   if (MODE == MODE_RAYS) {
     int4 hv = make_int4(q.side >= 0 ? q.mx : -1, q.side >= 0 ? q.my : -1, q.side, h);
     reinterpret_cast<int4*>(p.dbg_hits)[(size_t)e * p.W + col] = hv;
@@ -679,28 +646,24 @@ __device__ __forceinline__ void finish_column(const Params& p, int e, const Ray&
   }
 }
 
-// Cast every column's ray. Lanes take columns lane and lane + 32 of each 64,
-// both rays advance in the same loop, and the warp leaves the loop when a
-// ballot says every ray has hit.
+// Cast every column's ray: lane l takes columns l, l + 32, ...; in each pass
+// the warp leaves the DDA loop when a ballot says every ray has hit.
 template <int MODE>
-__device__ void cast_columns(const Params& p, int e, const Env& r, float c, float s, const WarpSmem& ws,
-                             const BlockHead& hd, int lane) {
+__device__ __forceinline__ void cast_columns(const Params& p, int e, const Env& r, float c, float s,
+                                             const WarpSmem& ws, int lane) {
   const int W = p.W, S = p.S;
+  const uint8_t* smap = ws.map(p);
   const int max_it = 4 * S + 8;
-  for (int base = 0; base < W; base += 64) {
-    const int c0 = base + lane, c1 = base + 32 + lane;
-    const bool v0 = c0 < W, v1 = c1 < W;
-    const float k0 = __ldg(p.col_k + (v0 ? c0 : 0)), k1 = __ldg(p.col_k + (v1 ? c1 : 0));
-    Ray q0, q1;
-    ray_init(q0, r, fmaf(-k0, s, c), fmaf(k0, c, s), v0);
-    ray_init(q1, r, fmaf(-k1, s, c), fmaf(k1, c, s), v1);
+  for (int col = lane; col - lane < W; col += 32) {
+    const bool valid = col < W;
+    const float k = __ldg(p.col_k + (valid ? col : 0));
+    Ray q;
+    ray_init(q, r, fmaf(-k, s, c), fmaf(k, c, s), valid);
     for (int it = 0; it < max_it; ++it) {
-      if (!q0.done) ray_advance(q0, ws.map, S);
-      if (!q1.done) ray_advance(q1, ws.map, S);
-      if (__all_sync(0xffffffffu, q0.done && q1.done)) break;
+      if (!q.done) ray_advance(q, smap, S);
+      if (__all_sync(0xffffffffu, q.done)) break;
     }
-    if (v0) finish_column<MODE>(p, e, q0, c0, ws, hd);
-    if (v1) finish_column<MODE>(p, e, q1, c1, ws, hd);
+    if (valid) finish_column<MODE>(p, e, q, col, ws);
   }
   __syncwarp();
 }
@@ -709,13 +672,15 @@ __device__ void cast_columns(const Params& p, int e, const Env& r, float c, floa
 // near (equal depths: higher index first, so the lower index is drawn last).
 // A sprite at depth ty is 0.25 W / (tan(fov/2) ty) columns wide, centred on
 // column (W/2)(1 + tx/ty), and (H/2) / ty rows high from row H/2 down.
-__device__ int project_sprites(const Params& p, const Env& r, const SpriteIn& sp, float c, float s,
-                               const WarpSmem& ws, const BlockHead& hd, int lane) {
+__device__ __forceinline__ int project_sprites(const Params& p, const Env& r, float c, float s, const WarpSmem& ws,
+                                               int lane) {
   const int W = p.W, H = p.H;
   bool vis = false;
   float ty = 0.f;
-  if (lane < r.nspr) {
-    const int type = sp.type;
+  const int nspr = ws.obj(p)[6];
+  if (lane < nspr) {
+    const float4 sp = ws.spr_in(p)[lane];
+    const int type = (int)sp.z;
     const float vx = (sp.x - (float)r.cx) - r.fx;
     const float vy = (sp.y - (float)r.cy) - r.fy;
     ty = fmaf(vx, c, vy * s);
@@ -727,27 +692,27 @@ __device__ int project_sprites(const Params& p, const Env& r, const SpriteIn& sp
       const float ht = 0.5f * (float)H * inv_ty;
       const float x0 = fmaf(0.5f * (float)W, fmaf(tx, inv_ty, 1.f), -0.5f * wd);
       const float top = 0.5f * (float)H;
-      ws.spr_a[lane] = make_float4(x0, top, ty * (4.f * p.tan_half / (float)W), ty * (2.f / (float)H));
+      ws.spr_a(p)[lane] = make_float4(x0, top, ty * (4.f * p.tan_half / (float)W), ty * (2.f / (float)H));
       // pixel centres that can fall inside [x0, x0 + wd) x [top, top + ht), one pixel of slack
       const int cA = (int)floorf(fmaxf(x0 - 1.f, -1.f));
       const int cB = (int)floorf(fminf(x0 + wd + 1.f, (float)W));
       const int rA = (int)floorf(fmaxf(top - 1.f, -1.f));
       const int rB = (int)floorf(fminf(top + ht + 1.f, (float)H));
-      ws.spr_rect[lane] =
+      ws.spr_rect(p)[lane] =
           make_int4(cA < 0 ? 0 : cA, cB > W - 1 ? W - 1 : cB, rA < 0 ? 0 : rA, rB > H - 1 ? H - 1 : rB);
-      ws.spr_ty[lane] = ty;
-      ws.spr_rgb[lane] = hd.sprite[type & 3];
-      ws.spr_kind[lane] = type;
+      ws.spr_ty(p)[lane] = ty;
+      ws.spr_rgb(p)[lane] = ws.pal(p)[16 + (type & 3)];
+      ws.spr_kind(p)[lane] = type;
     }
   }
   const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
   int rank = 0;
-  for (int k = 0; k < r.nspr; ++k) {
+  for (int k = 0; k < nspr; ++k) {
     const float tk = __shfl_sync(0xffffffffu, ty, k);
     const bool vk = (vmask >> k) & 1;
     if (vis && vk && (tk > ty || (tk == ty && k > lane))) ++rank;
   }
-  if (vis) ws.order[rank] = lane;
+  if (vis) ws.order(p)[rank] = lane;
   __syncwarp();
   return __popc(vmask);
 }
@@ -768,13 +733,13 @@ struct Group {
   uint32_t rgb[8];
 };
 
-__device__ __forceinline__ void load_group(const WarpSmem& ws, int g, int groups, Group& gr) {
+__device__ __forceinline__ void load_group(const Params& p, const WarpSmem& ws, int g, int groups, Group& gr) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int slot = (h * groups + g) << 2;
-    const int4 t4 = *reinterpret_cast<const int4*>(ws.col_top + slot);
-    const int4 b4 = *reinterpret_cast<const int4*>(ws.col_bot + slot);
-    const uint4 c4 = *reinterpret_cast<const uint4*>(ws.col_rgb + slot);
+    const int4 t4 = *reinterpret_cast<const int4*>(ws.col_top(p) + slot);
+    const int4 b4 = *reinterpret_cast<const int4*>(ws.col_bot(p) + slot);
+    const uint4 c4 = *reinterpret_cast<const uint4*>(ws.col_rgb(p) + slot);
     gr.top[4 * h + 0] = t4.x, gr.top[4 * h + 1] = t4.y, gr.top[4 * h + 2] = t4.z, gr.top[4 * h + 3] = t4.w;
     gr.bot[4 * h + 0] = b4.x, gr.bot[4 * h + 1] = b4.y, gr.bot[4 * h + 2] = b4.z, gr.bot[4 * h + 3] = b4.w;
     gr.rgb[4 * h + 0] = c4.x, gr.rgb[4 * h + 1] = c4.y, gr.rgb[4 * h + 2] = c4.z, gr.rgb[4 * h + 3] = c4.w;
@@ -783,13 +748,15 @@ __device__ __forceinline__ void load_group(const WarpSmem& ws, int g, int groups
 
 // Fill rows [r0, r1) of the frame into `buf` (row-major RGB), then draw the
 // sprites over them.
-__device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, const Group& gr, uint8_t* buf,
-                                          int r0, int r1, int nvis, int lane) {
+__device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, uint8_t* buf, int r0, int r1,
+                                          int nvis, int lane) {
   const int W = p.W, H = p.H, rowb = 3 * W, mid = H >> 1;
-  const int groups = W >> 3;    // lanes per row, 8 pixels (24 bytes) each
-  const int rpp = 32 / groups;  // rows per pass
-  const int my_row = lane / groups, g = lane - my_row * groups;
+  const int groups = ws.fl.groups;  // lanes per row, 8 pixels (24 bytes) each
+  const int rpp = ws.fl.rows;       // rows per pass
+  const int my_row = ws.fl.my_row, g = ws.fl.g;
   if (my_row < rpp) {
+    Group gr;
+    load_group(p, ws, g, groups, gr);
     for (int row = r0 + my_row; row < r1; row += rpp) {
       uint32_t px[8];
       if (row < mid) {
@@ -807,18 +774,18 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
   // are those whose centre has v in [0, 1) with |2v - 1| below the mask's
   // half-height at this u (key: 1 - |2u - 1|, disc: sqrt(1 - (2u - 1)^2)).
   for (int oi = 0; oi < nvis; ++oi) {
-    const int j = ws.order[oi];
-    const int4 rc = ws.spr_rect[j];
+    const int j = ws.order(p)[oi];
+    const int4 rc = ws.spr_rect(p)[j];
     const int rA = rc.z < r0 ? r0 : rc.z;
     const int rB = rc.w > r1 - 1 ? r1 - 1 : rc.w;
     if (rc.x > rc.y || rA > rB) continue;
-    const float4 a = ws.spr_a[j];  // x0, top, 1/width, 1/height
-    const float ty = ws.spr_ty[j];
-    const uint32_t rgbv = ws.spr_rgb[j];
-    const int kind = ws.spr_kind[j];
+    const float4 a = ws.spr_a(p)[j];  // x0, top, 1/width, 1/height
+    const float ty = ws.spr_ty(p)[j];
+    const uint32_t rgbv = ws.spr_rgb(p)[j];
+    const int kind = ws.spr_kind(p)[j];
     for (int col = rc.x + lane; col <= rc.y; col += 32) {
       const float u = ((float)col + 0.5f - a.x) * a.z;
-      if (!(u >= 0.f && u < 1.f && ty < ws.zbuf[col])) continue;
+      if (!(u >= 0.f && u < 1.f && ty < ws.zbuf(p)[col])) continue;
       const float au = fabsf(fmaf(2.f, u, -1.f));
       const float half = kind == kSprKey ? 1.f - au : (kind == kSprGoal ? 2.f : sqrtf(fmaxf(0.f, fmaf(-au, au, 1.f))));
       uint8_t* px = buf + col * 3;
@@ -837,21 +804,18 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
 }
 
 template <int MODE>
-__device__ void render_env(const Params& p, int e, const Env& r, const SpriteIn& sp, float c, float s,
-                           const WarpSmem& ws, const BlockHead& hd, int lane, int& slot, uint8_t* frame) {
-  cast_columns<MODE>(p, e, r, c, s, ws, hd, lane);
+__device__ __forceinline__ void render_env(const Params& p, int e, const Env& r, float c, float s,
+                                           const WarpSmem& ws, int lane, int& slot, uint8_t* frame) {
+  cast_columns<MODE>(p, e, r, c, s, ws, lane);
   if (MODE == MODE_RAYS) return;
-  const int nvis = project_sprites(p, r, sp, c, s, ws, hd, lane);  // ends with __syncwarp
-  const int H = p.H, rowb = 3 * p.W, groups = p.W >> 3;
-  Group gr;
-  const int my_row = lane / groups;
-  if (my_row < 32 / groups) load_group(ws, lane - my_row * groups, groups, gr);
+  const int nvis = project_sprites(p, r, c, s, ws, lane);  // ends with __syncwarp
+  const int H = p.H, rowb = 3 * p.W;
   for (int r0 = 0; r0 < H; r0 += p.rows_per_block) {
     const int r1 = r0 + p.rows_per_block < H ? r0 + p.rows_per_block : H;
-    uint8_t* buf = ws.ring + slot * p.frame_block_bytes;
+    uint8_t* buf = ws.ring() + slot * p.frame_block_bytes;
     if (lane == 0) bulk_wait_read_all_but_one();
     __syncwarp();
-    fill_block(p, ws, gr, buf, r0, r1, nvis, lane);
+    fill_block(p, ws, buf, r0, r1, nvis, lane);
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) bulk_store(frame + (size_t)r0 * rowb, buf, (uint32_t)((r1 - r0) * rowb));
@@ -859,22 +823,52 @@ __device__ void render_env(const Params& p, int e, const Env& r, const SpriteIn&
   }
 }
 
-// The locked door opens (for rays) once the key is held.
+// The locked door opens (for rays and collisions) once the key is held.
 __device__ __forceinline__ void open_door(const Params& p, const Env& r, const WarpSmem& ws, int lane) {
-  if (r.has_key && r.door_x >= 0 && r.door_y >= 0 && r.door_x < p.S && r.door_y < p.S) {
-    if (lane == 0 && ws.map[r.door_y * p.S + r.door_x] == kDoor) ws.map[r.door_y * p.S + r.door_x] = 0;
+  if (r.has_key) {
+    const int2 door = *reinterpret_cast<const int2*>(ws.obj(p) + 4);
+    if (lane == 0 && door.x >= 0 && door.y >= 0 && door.x < p.S && door.y < p.S &&
+        ws.map(p)[door.y * p.S + door.x] == kDoor)
+      ws.map(p)[door.y * p.S + door.x] = 0;
     __syncwarp();
   }
+}
+
+// One step of a rollout for env e (step index t, action a): the scalar state
+// comes from and returns to the warp's shared memory, so the step body gets
+// the whole register budget. Returns the next frame staging slot.
+__device__ __noinline__ int rollout_step(const Params& p, int e, int t, int a, uint8_t* wbase, uint8_t* scratch,
+                                         int lane, int slot) {
+  const WarpSmem ws{wbase, fill_lane(p, lane)};
+  Env* saved = reinterpret_cast<Env*>(wbase + p.off_env);
+  Env r = *saved;
+  float c, s;
+  const size_t out = (size_t)t * p.n + e;
+  if (step_env(p, e, r, ws.map(p), ws.obj(p), lane, c, s, a, out, false)) {
+    const uint32_t ep = p.st.episode[e] + 1;
+    __syncwarp();
+    generate(p, e, ep, wbase, scratch, lane);
+    r = load_env(p, e);
+    load_objects(p, ws, e, lane);
+    __syncwarp();
+    heading(p, r, c, s);
+  }
+  open_door(p, r, ws, lane);
+  render_env<MODE_ROLLOUT>(p, e, r, c, s, ws, lane, slot, p.frames + out * ((size_t)3 * p.H * p.W));
+  __syncwarp();
+  if (lane == 0) *saved = r;
+  __syncwarp();
+  return slot;
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __grid_constant__ Params p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  BlockHead hd;
-  const WarpSmem ws = carve(smem_raw + block_head_bytes(p) + warp * warp_bytes(p), p, hd);
-  if (lane < 16) hd.wall[lane] = c_wall[lane >> 3][lane & 7];
-  if (lane < 4) hd.sprite[lane] = c_sprite[lane];
+  uint8_t* const wbase = smem_raw + warp * p.warp_bytes;
+  const WarpSmem ws{wbase, fill_lane(p, lane)};
+  if (lane < 16) ws.pal(p)[lane] = c_wall[lane >> 3][lane & 7];
+  if (lane < 4) ws.pal(p)[16 + lane] = c_sprite[lane];
   __syncwarp();
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
@@ -883,59 +877,50 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __
   const size_t frame_bytes = (size_t)3 * p.H * p.W;
   for (int e = gw; e < p.n; e += nw) {
     Env r;
-    SpriteIn sp;
     float c, s;
     if (MODE == MODE_ROLLOUT) {
-      // the env's pose stays in registers and its map in shared memory for all steps
-      r = load_env<MODE>(p, e);
-      sp = load_sprite(p, e, lane);
-      stage_map(p, e, ws.map, lane);
+      // the env's scalar state and map stay in shared memory for all steps
+      if (lane == 0) *reinterpret_cast<Env*>(wbase + p.off_env) = load_env(p, e);
+      load_objects(p, ws, e, lane);
+      stage_map(p, e, ws.map(p), lane);  // ends with __syncwarp
       int a_next = p.actions[e];
       for (int t = 0; t < p.steps; ++t) {
-        const size_t out = (size_t)t * p.n + e;
         const int a = a_next;
-        if (t + 1 < p.steps) a_next = p.actions[out + p.n];
-        if (step_env(p, e, r, ws.map, lane, c, s, a, out, false)) {
-          const uint32_t ep = r.ep + 1;
-          __syncwarp();
-          generate(p, e, ep, ws, scratch, lane);
-          r = load_env<MODE>(p, e);
-          sp = load_sprite(p, e, lane);
-          heading(p, r, c, s);
-        }
-        open_door(p, r, ws, lane);
-        render_env<MODE>(p, e, r, sp, c, s, ws, hd, lane, slot, p.frames + out * frame_bytes);
-        __syncwarp();
+        if (t + 1 < p.steps) a_next = p.actions[(size_t)(t + 1) * p.n + e];
+        slot = rollout_step(p, e, t, a, wbase, scratch, lane, slot);
       }
       if (lane == 0) {
+        const Env fin = *reinterpret_cast<const Env*>(wbase + p.off_env);
         const State& st = p.st;
-        st.cell_x[e] = (int16_t)r.cx;
-        st.cell_y[e] = (int16_t)r.cy;
-        st.frac_x[e] = r.fx;
-        st.frac_y[e] = r.fy;
-        st.turn[e] = (int16_t)r.turn;
-        st.t[e] = r.t;
-        st.flags[e] = (uint8_t)r.has_key;
+        st.cell_x[e] = (int16_t)fin.cx;
+        st.cell_y[e] = (int16_t)fin.cy;
+        st.frac_x[e] = fin.fx;
+        st.frac_y[e] = fin.fy;
+        st.turn[e] = (int16_t)fin.turn;
+        st.t[e] = fin.t;
+        st.flags[e] = (uint8_t)fin.has_key;
       }
       __syncwarp();
       continue;
     }
     if (MODE == MODE_RESET) {
-      generate(p, e, 0u, ws, scratch, lane);
-      r = load_env<MODE>(p, e);
-      sp = load_sprite(p, e, lane);
+      generate(p, e, 0u, wbase, scratch, lane);
+      r = load_env(p, e);
+      load_objects(p, ws, e, lane);
+      __syncwarp();
       heading(p, r, c, s);
     } else {
-      r = load_env<MODE>(p, e);
-      sp = load_sprite(p, e, lane);
-      stage_map(p, e, ws.map, lane);
+      r = load_env(p, e);
+      load_objects(p, ws, e, lane);
+      stage_map(p, e, ws.map(p), lane);  // ends with __syncwarp
       if (MODE == MODE_STEP) {
-        if (step_env(p, e, r, ws.map, lane, c, s, r.action, (size_t)e, true)) {
-          const uint32_t ep = r.ep + 1;
+        if (step_env(p, e, r, ws.map(p), ws.obj(p), lane, c, s, (int)p.actions[e], (size_t)e, true)) {
+          const uint32_t ep = p.st.episode[e] + 1;
           __syncwarp();
-          generate(p, e, ep, ws, scratch, lane);
-          r = load_env<MODE>(p, e);
-          sp = load_sprite(p, e, lane);
+          generate(p, e, ep, wbase, scratch, lane);
+          r = load_env(p, e);
+          load_objects(p, ws, e, lane);
+          __syncwarp();
           heading(p, r, c, s);
         }
       } else {
@@ -943,7 +928,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __
       }
     }
     open_door(p, r, ws, lane);
-    render_env<MODE>(p, e, r, sp, c, s, ws, hd, lane, slot, p.frames + (size_t)e * frame_bytes);
+    render_env<MODE>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
     __syncwarp();
   }
   // shared memory stays allocated until the bulk stores have read it
@@ -960,7 +945,33 @@ cudaError_t blocks_per_sm_for(const Params& p, int* blocks) {
 
 }  // namespace
 
-int block_smem_bytes(const Params& p) { return block_head_bytes(p) + warp_bytes(p) * kWarpsPerBlock; }
+void layout_warp_smem(Params& p) {
+  const int K = p.K > 0 ? p.K : 1;
+  int q = kRingBuffers * p.frame_block_bytes;
+  auto take = [&](int bytes) {
+    const int at = q;
+    q += align16(bytes);
+    return at;
+  };
+  p.off_pal = take(4 * kPaletteWords);
+  p.off_map = take(p.map_smem_bytes);
+  p.off_col_rgb = take(4 * p.W);
+  p.off_col_top = take(4 * p.W);
+  p.off_col_bot = take(4 * p.W);
+  p.off_zbuf = take(4 * p.W);
+  p.off_spr_in = take(16 * K);
+  p.off_spr_a = take(16 * K);
+  p.off_spr_rect = take(16 * K);
+  p.off_spr_ty = take(4 * K);
+  p.off_spr_rgb = take(4 * K);
+  p.off_spr_kind = take(4 * K);
+  p.off_order = take(4 * K);
+  p.off_obj = take(4 * 8);
+  p.off_env = take((int)sizeof(Env));
+  p.warp_bytes = align16(q);
+}
+
+int block_smem_bytes(const Params& p) { return p.warp_bytes * kWarpsPerBlock; }
 
 size_t gen_scratch_bytes(int task, int S) {
   if (task != 1) return 0;
