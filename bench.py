@@ -335,7 +335,8 @@ def main():
     if os.path.exists(TRAFFIC_FILE):
         tf = json.load(open(TRAFFIC_FILE))
         if tf.get("kernel_source_sha") == kernel_source_sha() and tf.get("n_envs") == N:
-            traffic = tf.get("dram_bytes_per_launch")
+            # scaled from the captured launch to this one by the env-steps processed
+            traffic = tf["dram_bytes_per_env_step"] * N * launch_steps
 
     if rank != 0:
         if world > 1:
