@@ -151,6 +151,28 @@ jx_status jx_render(jx_env* env, void* stream, uint8_t* d_frames);
 jx_status jx_step_host(jx_env* env, void* stream, const uint8_t* h_actions, uint8_t* h_frames, float* h_rewards,
                        uint8_t* h_dones);
 
+/* jx_step_host for callers that must not allocate device memory, for example
+ * a process whose device memory is already handed out to a framework's
+ * caching allocator, or a loop that may not take the implicit
+ * synchronisation of a first-use cudaMalloc. It behaves like jx_step_host but
+ * stages actions, frames, rewards and dones in a fixed array inside the
+ * library (JX_STATIC_STAGING_BYTES per device, reserved when the library is
+ * loaded and kept until the process exits) instead of buffers allocated on
+ * first use, and it calls no allocating routine. The paper has no counterpart:
+ * this is a deployment convenience of this library.
+ *  - Limit: the batch needs N * (3 H W + 6) bytes plus 256-byte alignment of
+ *    four buffers; larger batches return JX_EINVAL with the sizes.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls on a device share the one array, which keeps the last call's
+ *    contents; every byte a call reads is written earlier in the same call.
+ *    Calls that overlap on the GPU (several envs or threads on different
+ *    streams of one device) race on the array: serialise them.
+ *  - Waits for `stream` before returning, like jx_step_host. */
+#define JX_STATIC_STAGING_BYTES (16u << 20)
+jx_status jx_step_host_static(jx_env* env, void* stream, const uint8_t* h_actions, uint8_t* h_frames,
+                              float* h_rewards, uint8_t* h_dones);
+
 /* Per-column ray results of the current state (test and debug hook):
  *  d_hits [N][W][4] int32: hit cell x, hit cell y, side (0: x face, 1: y face),
  *         slice height h in rows;

@@ -3,6 +3,7 @@
 // constant tables, launch shapes and the checkpoint / test hooks.
 #include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -408,6 +409,68 @@ jx_status jx_step_host(jx_env* env, void* stream, const uint8_t* h_actions, uint
   uint8_t* d_frames = env->stage + env->stage_frames_off;
   float* d_rew = reinterpret_cast<float*>(env->stage + env->stage_rewards_off);
   uint8_t* d_done = env->stage + env->stage_dones_off;
+  cudaError_t err = cudaMemcpyAsync(d_act, h_actions, N, cudaMemcpyHostToDevice, s);
+  if (err != cudaSuccess) return cuda_fail(err, "copy of actions");
+  jx_status st = jx_step(env, stream, d_act, d_frames, d_rew, d_done);
+  if (st != JX_OK) return st;
+  if ((err = cudaMemcpyAsync(h_frames, d_frames, frame_bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(h_rewards, d_rew, 4 * N, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (err = cudaMemcpyAsync(h_dones, d_done, N, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(err, "copy of results");
+  if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "host step");
+  return JX_OK;
+}
+
+// Staging for jx_step_host_static: a fixed array in every device's memory,
+// reserved when the library is loaded and held until the process exits.
+// Host code cannot use the name as a device address; the per-device address
+// comes from cudaGetSymbolAddress.
+static __device__ __align__(256) uint8_t g_static_staging[JX_STATIC_STAGING_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Address of the staging array on the current device (looked up on the first
+// call per device).
+jx_status static_staging(int device, uint8_t** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(JX_EINVAL, "device %d beyond %d", device, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[device]) {
+    void* ptr = nullptr;
+    cudaError_t err = cudaGetSymbolAddress(&ptr, g_static_staging);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress of the static staging array");
+    g_static_ptr[device] = ptr;
+  }
+  *out = static_cast<uint8_t*>(g_static_ptr[device]);
+  return JX_OK;
+}
+}  // namespace
+
+jx_status jx_step_host_static(jx_env* env, void* stream, const uint8_t* h_actions, uint8_t* h_frames,
+                              float* h_rewards, uint8_t* h_dones) {
+  if (jx_status st = check_env(env)) return st;
+  if (!h_actions || !h_frames || !h_rewards || !h_dones) return fail(JX_EINVAL, "NULL host pointer");
+  const size_t N = env->cfg.n_envs;
+  const size_t frame_bytes = N * 3 * (size_t)env->cfg.frame_h * env->cfg.frame_w;
+  const size_t off_frames = align256(N);
+  const size_t off_rewards = off_frames + align256(frame_bytes);
+  const size_t off_dones = off_rewards + align256(4 * N);
+  const size_t need = off_dones + align256(N);
+  if (need > (size_t)JX_STATIC_STAGING_BYTES)
+    return fail(JX_EINVAL, "this batch needs %zu bytes of staging; the static staging array holds %zu", need,
+                (size_t)JX_STATIC_STAGING_BYTES);
+  DeviceGuard g(env->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  uint8_t* base = nullptr;
+  if (jx_status st = static_staging(env->device, &base)) return st;
+  // every byte the step reads is written first in this call: nothing to clear
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint8_t* d_act = base;
+  uint8_t* d_frames = base + off_frames;
+  float* d_rew = reinterpret_cast<float*>(base + off_rewards);
+  uint8_t* d_done = base + off_dones;
   cudaError_t err = cudaMemcpyAsync(d_act, h_actions, N, cudaMemcpyHostToDevice, s);
   if (err != cudaSuccess) return cuda_fail(err, "copy of actions");
   jx_status st = jx_step(env, stream, d_act, d_frames, d_rew, d_done);

@@ -32,7 +32,8 @@ FIELDS = {
 
 # Entry points declared in include/jx.h (checked by the ABI test).
 SYMBOLS = [
-    "jx_create", "jx_destroy", "jx_reset", "jx_step", "jx_rollout", "jx_render", "jx_step_host", "jx_debug_rays",
+    "jx_create", "jx_destroy", "jx_reset", "jx_step", "jx_rollout", "jx_render", "jx_step_host",
+    "jx_step_host_static", "jx_debug_rays",
     "jx_state_bytes", "jx_state_field", "jx_get_state", "jx_set_state", "jx_sync_status", "jx_launch_count",
     "jx_launch_shape", "jx_last_error",
 ]
@@ -76,6 +77,7 @@ def _load() -> ctypes.CDLL:
         "jx_rollout": [P, P, P, i32, P, P, P],
         "jx_render": [P, P, P],
         "jx_step_host": [P, P, P, P, P, P],
+        "jx_step_host_static": [P, P, P, P, P, P],
         "jx_debug_rays": [P, P, P, P],
         "jx_state_bytes": [P, P],
         "jx_state_field": [P, i32, P, P],
@@ -183,6 +185,11 @@ class Env:
 
     def step_host(self, actions, frames, rewards, dones, stream=None):
         _check(lib.jx_step_host(self._h, _stream(stream), _ptr(actions), _ptr(frames), _ptr(rewards), _ptr(dones)))
+
+    def step_host_static(self, actions, frames, rewards, dones, stream=None):
+        """``step_host`` staging through the library's fixed device array (no allocation)."""
+        _check(lib.jx_step_host_static(self._h, _stream(stream), _ptr(actions), _ptr(frames), _ptr(rewards),
+                                       _ptr(dones)))
 
     def debug_rays(self, hits, perp, stream=None):
         _check(lib.jx_debug_rays(self._h, _stream(stream), _ptr(hits), _ptr(perp)))
