@@ -71,7 +71,7 @@ struct Params {
   int32_t map_smem_bytes;  // S * S rounded up to 16
   // per-warp shared memory layout (byte offsets from the warp's base; set by layout_warp_smem)
   int32_t off_pal, off_map, off_col_rgb, off_col_top, off_col_bot, off_zbuf, off_spr_in, off_spr_a, off_spr_rect,
-      off_spr_ty, off_spr_rgb, off_spr_kind, off_order, off_obj, off_env, warp_bytes;
+      off_spr_ty, off_spr_rgb, off_spr_kind, off_order, off_obj, warp_bytes;
   float move, radius, tan_half, inv_tan_half;
   float reward_lut[4];
   uint64_t seed;

@@ -105,7 +105,6 @@ __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; 
 //   spr_ty    [K] depth;  spr_rgb [K] colour;  spr_kind [K] type
 //   order     [K] visible sprites, far to near
 //   obj       [8] int32 key x, key y, goal x, goal y, door x, door y, sprites in use
-//   env       the scalar state (Env) between the steps of a rollout
 // The lane's place in the frame fill: lanes [0, groups * rows) are laid out
 // as `rows` rows of `groups` 8-pixel groups.
 struct FillLane {
@@ -294,7 +293,7 @@ __device__ void write_episode_state(const Params& p, int e, uint32_t ep, int cel
 // Rooms: border walls; interior wall iff a 53-bit uniform draw < wall_prob;
 // wall type 1 + (draw mod 4); spawn and decorative sprites on uniformly
 // chosen free cells (row-major enumeration).
-__device__ __noinline__ void gen_rooms(const Params& p, int e, uint32_t ep, uint8_t* smap, int lane) {
+__device__ __forceinline__ void gen_rooms(const Params& p, int e, uint32_t ep, uint8_t* smap, int lane) {
   const int S = p.S, n = S * S;
   const uint64_t kw = stream_key(p.seed, (uint32_t)e, ep, P_WALL);
   for (int i = lane; i < n; i += 32) {
@@ -366,7 +365,7 @@ __device__ __forceinline__ MazeScratch maze_scratch(uint8_t* q, int n) {
 // the smallest row-major index) and the two path nodes around the door are
 // recorded during the walk. The nodes reachable without crossing the door are
 // those outside the door's subtree (a discovery / finish interval test).
-__device__ __noinline__ void gen_maze(const Params& p, int e, uint32_t ep, uint8_t* smap, uint8_t* scratch, int lane) {
+__device__ __forceinline__ void gen_maze(const Params& p, int e, uint32_t ep, uint8_t* smap, uint8_t* scratch, int lane) {
   const int S = p.S, n_cells = S * S;
   const int nn = (S - 2) / 2, n = nn * nn;
   MazeScratch m = maze_scratch(scratch, n);
@@ -453,8 +452,10 @@ __device__ __noinline__ void gen_maze(const Params& p, int e, uint32_t ep, uint8
 }
 
 // The maze work space lives in the warp's frame staging ring when it fits
-// (32 x 32 mazes need 3.4 KB), else in the global per-warp slot.
-__device__ __noinline__ void generate(const Params& p, int e, uint32_t ep, uint8_t* wbase, uint8_t* scratch,
+// (32 x 32 mazes need 3.4 KB), else in the global per-warp slot. Inlined
+// behind unlikely branches: a call would make every value live across it
+// spill in the hot loop.
+__device__ __forceinline__ void generate(const Params& p, int e, uint32_t ep, uint8_t* wbase, uint8_t* scratch,
                                       int lane) {
   const WarpSmem ws{wbase, fill_lane(p, lane)};
   if (p.task == 0) {
@@ -480,14 +481,21 @@ __device__ __forceinline__ bool solid(const uint8_t* smap, int S, int x, int y, 
 
 // Box of half-size r centred at (cx + fx, cy + fy) overlaps no solid cell
 // (closed intervals).
+// floor(v) for v in [-1, 2): fractions stay in [0, 1) and a move or the box
+// half-size is below 1/2, so every box edge lies in that range.
+__device__ __forceinline__ int floor_small(float v) { return (v >= 1.f ? 1 : 0) - (v < 0.f ? 1 : 0); }
+
 __device__ __forceinline__ bool box_free(const uint8_t* smap, int S, int cx, float fx, int cy, float fy, float r,
                                          int has_key) {
-  int i0 = cx + (int)floorf(fx - r), i1 = cx + (int)floorf(fx + r);
-  int j0 = cy + (int)floorf(fy - r), j1 = cy + (int)floorf(fy + r);
-  for (int j = j0; j <= j1; ++j)
-    for (int i = i0; i <= i1; ++i)
-      if (solid(smap, S, i, j, has_key)) return false;
-  return true;
+  const int i0 = cx + floor_small(fx - r), i1 = cx + floor_small(fx + r);
+  const int j0 = cy + floor_small(fy - r), j1 = cy + floor_small(fy + r);
+  bool hit = solid(smap, S, i0, j0, has_key);
+  if (i1 != i0) hit |= solid(smap, S, i1, j0, has_key);
+  if (j1 != j0) {
+    hit |= solid(smap, S, i0, j1, has_key);
+    if (i1 != i0) hit |= solid(smap, S, i1, j1, has_key);
+  }
+  return !hit;
 }
 
 // keep the position split as an integer cell plus a fraction in [0, 1)
@@ -834,33 +842,6 @@ __device__ __forceinline__ void open_door(const Params& p, const Env& r, const W
   }
 }
 
-// One step of a rollout for env e (step index t, action a): the scalar state
-// comes from and returns to the warp's shared memory, so the step body gets
-// the whole register budget. Returns the next frame staging slot.
-__device__ __noinline__ int rollout_step(const Params& p, int e, int t, int a, uint8_t* wbase, uint8_t* scratch,
-                                         int lane, int slot) {
-  const WarpSmem ws{wbase, fill_lane(p, lane)};
-  Env* saved = reinterpret_cast<Env*>(wbase + p.off_env);
-  Env r = *saved;
-  float c, s;
-  const size_t out = (size_t)t * p.n + e;
-  if (step_env(p, e, r, ws.map(p), ws.obj(p), lane, c, s, a, out, false)) {
-    const uint32_t ep = p.st.episode[e] + 1;
-    __syncwarp();
-    generate(p, e, ep, wbase, scratch, lane);
-    r = load_env(p, e);
-    load_objects(p, ws, e, lane);
-    __syncwarp();
-    heading(p, r, c, s);
-  }
-  open_door(p, r, ws, lane);
-  render_env<MODE_ROLLOUT>(p, e, r, c, s, ws, lane, slot, p.frames + out * ((size_t)3 * p.H * p.W));
-  __syncwarp();
-  if (lane == 0) *saved = r;
-  __syncwarp();
-  return slot;
-}
-
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __grid_constant__ Params p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -879,26 +860,38 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __
     Env r;
     float c, s;
     if (MODE == MODE_ROLLOUT) {
-      // the env's scalar state and map stay in shared memory for all steps
-      if (lane == 0) *reinterpret_cast<Env*>(wbase + p.off_env) = load_env(p, e);
+      // the env's scalar state stays in registers and its map in shared memory for all steps
+      Env r = load_env(p, e);
       load_objects(p, ws, e, lane);
       stage_map(p, e, ws.map(p), lane);  // ends with __syncwarp
       int a_next = p.actions[e];
       for (int t = 0; t < p.steps; ++t) {
         const int a = a_next;
         if (t + 1 < p.steps) a_next = p.actions[(size_t)(t + 1) * p.n + e];
-        slot = rollout_step(p, e, t, a, wbase, scratch, lane, slot);
+        float c, s;
+        const size_t out = (size_t)t * p.n + e;
+        if (__builtin_expect(step_env(p, e, r, ws.map(p), ws.obj(p), lane, c, s, a, out, false), 0)) {
+          const uint32_t ep = p.st.episode[e] + 1;
+          __syncwarp();
+          generate(p, e, ep, wbase, scratch, lane);
+          r = load_env(p, e);
+          load_objects(p, ws, e, lane);
+          __syncwarp();
+          heading(p, r, c, s);
+        }
+        open_door(p, r, ws, lane);
+        render_env<MODE>(p, e, r, c, s, ws, lane, slot, p.frames + out * frame_bytes);
+        __syncwarp();
       }
       if (lane == 0) {
-        const Env fin = *reinterpret_cast<const Env*>(wbase + p.off_env);
         const State& st = p.st;
-        st.cell_x[e] = (int16_t)fin.cx;
-        st.cell_y[e] = (int16_t)fin.cy;
-        st.frac_x[e] = fin.fx;
-        st.frac_y[e] = fin.fy;
-        st.turn[e] = (int16_t)fin.turn;
-        st.t[e] = fin.t;
-        st.flags[e] = (uint8_t)fin.has_key;
+        st.cell_x[e] = (int16_t)r.cx;
+        st.cell_y[e] = (int16_t)r.cy;
+        st.frac_x[e] = r.fx;
+        st.frac_y[e] = r.fy;
+        st.turn[e] = (int16_t)r.turn;
+        st.t[e] = r.t;
+        st.flags[e] = (uint8_t)r.has_key;
       }
       __syncwarp();
       continue;
@@ -914,7 +907,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __
       load_objects(p, ws, e, lane);
       stage_map(p, e, ws.map(p), lane);  // ends with __syncwarp
       if (MODE == MODE_STEP) {
-        if (step_env(p, e, r, ws.map(p), ws.obj(p), lane, c, s, (int)p.actions[e], (size_t)e, true)) {
+        if (__builtin_expect(step_env(p, e, r, ws.map(p), ws.obj(p), lane, c, s, (int)p.actions[e], (size_t)e, true),
+                             0)) {
           const uint32_t ep = p.st.episode[e] + 1;
           __syncwarp();
           generate(p, e, ep, wbase, scratch, lane);
@@ -967,7 +961,6 @@ void layout_warp_smem(Params& p) {
   p.off_spr_kind = take(4 * K);
   p.off_order = take(4 * K);
   p.off_obj = take(4 * 8);
-  p.off_env = take((int)sizeof(Env));
   p.warp_bytes = align16(q);
 }
 
