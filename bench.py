@@ -63,6 +63,23 @@ STATE_WRITE = 2 + 2 + 4 + 4 + 2 + 4 + 1  # cells, fracs, turn, t, flags
 STEP_IO = 1 + 4 + 1  # action, reward, done
 
 
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time: the job is done when every rank is."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, n_envs_per_rank: int, steps: int, t_max_ms: float) -> float:
+    """Whole-job env-steps/s: every rank steps its own n_envs for `steps` steps."""
+    return world * n_envs_per_rank * steps / (t_max_ms / 1e3)
+
+
 def algorithmic_bytes_per_env_step(cfg: dict) -> int:
     """Compulsory HBM bytes of one jx_step per env: the frame written, the state
     read and written, action, reward and done. The map (re-read from L2 every
@@ -189,6 +206,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=600)
     ap.add_argument("--ref-envs", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=1000)
     ap.add_argument("--ring-slots", type=int, default=GRAPH_STEPS,
                     help="rollout buffer slots = launches per CUDA graph (smaller for profiling captures)")
     args = ap.parse_args()
@@ -272,14 +290,11 @@ def main():
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     gpu_launches = env.launch_count() - launches_before
-    t_max = ms
+    t_max = max_over_ranks(ms, world, dev)
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
         torch.distributed.barrier()
     ms_per_step = t_max / args.steps
-    value = world * N * args.steps / (t_max / 1e3)
+    value = job_value(world, N, args.steps, t_max)
 
     # the single-step entry point on the same workload (graph replays of `ring` launches)
     n_graph = max(1, min(n_full, 16))
@@ -307,6 +322,31 @@ def main():
     lat.sort()
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
+
+    # the plain method: one environment, one jx_step launch per step (16 x 16 rooms, 1000 steps)
+    plain = None
+    if rank == 0 and args.plain_steps > 0:
+        pc = inputs.single_env_rooms()
+        penv = jx.Env(pc, local)
+        pa = torch.from_numpy(inputs.action_stream(pc["seed"], args.plain_steps, 1)).to(dev)
+        pf = torch.empty((1, pc["frame_h"], pc["frame_w"], 3), dtype=torch.uint8, device=dev)
+        pr = torch.empty(1, dtype=torch.float32, device=dev)
+        pd = torch.empty(1, dtype=torch.uint8, device=dev)
+        with torch.cuda.stream(stream):
+            penv.reset(pf, stream)
+            for i in range(8):
+                penv.step(pa[i], pf, pr, pd, stream)
+            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            p0.record(stream)
+            for i in range(args.plain_steps):
+                penv.step(pa[i], pf, pr, pd, stream)
+            p1.record(stream)
+        stream.synchronize()
+        pms = p0.elapsed_time(p1)
+        plain = {"value": args.plain_steps / (pms / 1e3), "unit": "env-steps/s", "ms_per_step": pms / args.plain_steps,
+                 "workload": f"1 env, 16x16 random rooms (p = 0.25), 64x64 RGB, {args.plain_steps} uniform random steps, "
+                             "one jx_step launch per step"}
+        penv.close()
 
     # end to end through the public host-buffer entry point
     h_act = torch.empty(N, dtype=torch.uint8).pin_memory()
@@ -365,6 +405,7 @@ def main():
         "p50_step_ms": p50, "p99_step_ms": p99,
         "per_step_launch": {"value": world * N / (step_ms / 1e3), "unit": "env-steps/s", "ms_per_step": step_ms,
                             "how": f"jx_step, CUDA graph of {ring} launches"},
+        "plain_one_env_per_launch": plain,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "algorithmic_bytes_per_launch": bytes_per_launch},

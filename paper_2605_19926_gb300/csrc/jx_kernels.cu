@@ -929,12 +929,18 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __
   if (lane == 0) bulk_wait_read_all();
 }
 
+// The kernel's dynamic shared memory limit is a property of the function, shared
+// by every env in the process: it is raised to the device's opt-in maximum (never
+// lowered), so envs of different sizes can coexist.
 template <int MODE>
 cudaError_t blocks_per_sm_for(const Params& p, int* blocks) {
-  int smem = block_smem_bytes(p);
-  cudaError_t err = cudaFuncSetAttribute(env_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int dev = 0, optin = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (err == cudaSuccess)
+    err = cudaFuncSetAttribute(env_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, env_kernel<MODE>, kThreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, env_kernel<MODE>, kThreads, block_smem_bytes(p));
 }
 
 }  // namespace

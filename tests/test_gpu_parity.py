@@ -278,3 +278,22 @@ def test_rollout_full_size_across_horizon():
     64-step rollout that crosses the 500-step horizon (every env resets)."""
     n_done = _rollout_vs_steps(inputs.batched_keydoor_mazes(), 64, seed=1, warm=470)
     assert n_done >= 4096
+
+
+def test_envs_of_different_sizes_coexist():
+    """Creating a smaller env must not break a larger one's launches (the kernel's
+    shared memory limit is per function, shared by all envs of the process)."""
+    big = Run(inputs.maze_keydoor(n_envs=40, map_side=32, seed=2, horizon=0, frame_h=96, frame_w=128))
+    big.reset()
+    small = Run(inputs.rooms(n_envs=3, map_side=8, seed=1))
+    small.reset()
+    for s in range(5):
+        fb, _, _ = big.step(inputs.actions(1, s, 40))
+        fs, _, _ = small.step(inputs.actions(2, s, 3))
+    stats = Stats()
+    for run in (big, small):
+        ref = oracle.render(run.ocfg, run.state(), nthreads=NTHREADS)
+        run.env.render(run.frames)
+        torch.cuda.synchronize()
+        compare_frames(run.frames.cpu().numpy(), ref, stats)
+    stats.check()
