@@ -193,6 +193,132 @@ def run_reference(args, cfg: dict):
     print(json.dumps(line), flush=True)
 
 
+def uneven_bytes_per_env_step(groups: list) -> float:
+    """Mean compulsory HBM bytes per env-step of an uneven batch (as for one env group)."""
+    tot = sum(g["n_envs"] * algorithmic_bytes_per_env_step(g) for g in groups)
+    return tot / sum(g["n_envs"] for g in groups)
+
+
+def run_uneven(args):
+    """Uneven batching: 16,384 envs of 16 (map side, frame size) groups in one
+    persistent launch per rollout; fixed tiles against autotuned tiles, and the
+    autotuned step sequence replayed as a CUDA graph."""
+    import torch
+
+    from paper_2605_19926_gb300 import build, inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2605_19926_gb300 import jx
+
+    groups = inputs.uneven_groups(seed=2 + rank)
+    envs = [jx.Env(c, local) for c in groups]
+    batch = jx.Batch(envs)
+    N, F = batch.n, batch.frame_bytes
+    dev = torch.device("cuda", local)
+    T = args.uneven_slots
+    K = max(T, (args.steps // T) * T)
+    acts = torch.from_numpy(inputs.action_stream(7 + rank, K + T, N)).to(dev)
+    frames = torch.empty((T, F), dtype=torch.uint8, device=dev)  # T x 0.38 GB > L2
+    rewards = torch.empty((T, N), dtype=torch.float32, device=dev)
+    dones = torch.empty((T, N), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed_rollouts() -> tuple[float, int]:
+        with torch.cuda.stream(stream):
+            batch.reset(frames[0], stream)
+            batch.rollout(acts[:T], frames, rewards, dones, stream)  # warm-up
+        stream.synchronize()
+        n0 = batch.launch_count()
+        if world > 1:
+            torch.distributed.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for c in range(K // T):
+                batch.rollout(acts[T + c * T: T + (c + 1) * T], frames, rewards, dones, stream)
+            e1.record(stream)
+        stream.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), world, dev), batch.launch_count() - n0
+
+    fixed_ms, _ = timed_rollouts()
+    fixed_tiling = batch.tiling
+    t_tune = time.perf_counter()
+    trials = batch.autotune(mode=1, steps=T, max_trials=args.tune_trials, stream=stream)
+    tune_s = time.perf_counter() - t_tune
+    tuned = batch.tiling
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    tuned_ms, launches = timed_rollouts()
+    clk = clocks.stop()
+    # the same steps as a CUDA graph of T single-step launches, replayed
+    graph = batch.capture(acts[T: 2 * T], frames, rewards, dones)
+    with torch.cuda.stream(stream):
+        batch.reset(frames[0], stream)
+        graph.launch(stream)
+    stream.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        g0.record(stream)
+        for c in range(K // T):
+            graph.launch(stream)
+        g1.record(stream)
+    stream.synchronize()
+    graph_ms = max_over_ranks(g0.elapsed_time(g1), world, dev)
+    graph.close()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    bpes = uneven_bytes_per_env_step(groups)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+
+    def leg(ms, tiling):
+        v = world * N * K / (ms / 1e3)
+        gbs = N * K * bpes / (ms / 1e3) / 1e9 / world
+        return {"value": v, "ms_per_step": ms / K, "achieved_gbs": gbs, "frac": gbs / peak,
+                "tiling": dict(zip(("warps_per_block", "cols_per_lane", "bits_min_side", "max_rows_per_block"),
+                                   tiling.as_tuple()))}
+
+    shape = batch.launch_shape()
+    tuned_leg = leg(tuned_ms, tuned)
+    line = {
+        "metric": "env-steps/s incl. render (frames/s), uneven batch", "value": tuned_leg["value"],
+        "unit": "env-steps/s", "n_gpus": world, "steps": K, "warmup": T, "ms_per_step": tuned_ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "16,384 envs per GPU, random-wall rooms p=0.3, map side uniform in {16,32,64,128}, "
+                               "square RGB frames uniform in {32,64,96,128}, 0-8 sprites, uniform random actions",
+                   "groups": len(groups), "n_envs_per_gpu": N, "frame_bytes_per_step": F,
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"frames written to a {T}-slot rollout buffer ({T * F / 1e9:.1f} GB) > L2",
+                   "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
+                              "entry": "jx_batch_rollout", "steps_per_launch": T}},
+        "roofline": {"bound": "hbm", "achieved": tuned_leg["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": tuned_leg["frac"], "traffic": None, "peak_source": peak_src,
+                     "algorithmic_bytes_per_env_step": bpes},
+        "fixed_tiles": leg(fixed_ms, fixed_tiling), "autotuned": tuned_leg,
+        "autotune": {"trials": len(trials), "seconds": tune_s, "mode": "rollout", "steps_per_trial": T},
+        "graph_steps": {"value": world * N * K / (graph_ms / 1e3), "ms_per_step": graph_ms / K,
+                        "how": f"jx_batch_capture of {T} jx_batch_step launches, replayed"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -209,8 +335,17 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1000)
     ap.add_argument("--ring-slots", type=int, default=GRAPH_STEPS,
                     help="rollout buffer slots = launches per CUDA graph (smaller for profiling captures)")
+    ap.add_argument("--workload", default="mazes", choices=["mazes", "uneven"],
+                    help="mazes: 4096 key-door mazes (the headline); uneven: 16,384 envs of mixed sizes")
+    ap.add_argument("--uneven-slots", type=int, default=16, help="steps per rollout launch of the uneven batch")
+    ap.add_argument("--tune-trials", type=int, default=1000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.workload == "uneven" and args.impl == "jx":
+        if args.steps == ap.get_default("steps"):
+            args.steps = 512
+        run_uneven(args)
+        return
 
     from paper_2605_19926_gb300 import inputs
 

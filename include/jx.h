@@ -224,6 +224,102 @@ jx_status jx_launch_count(const jx_env* env, uint64_t* count);
  * dynamic shared memory bytes per block. */
 jx_status jx_launch_shape(const jx_env* env, int32_t* grid, int32_t* block, int32_t* smem_bytes);
 
+/* ------------------------------------------------------------------------
+ * Batches: env groups of different map and frame sizes in one launch.
+ *
+ * A batch ties together G existing envs ("groups"; each is homogeneous, the
+ * groups differ in map side, frame size, sprite count, task, seed, ...) and
+ * steps all of their environments in ONE launch of a persistent kernel:
+ * every warp drains per-group work queues (counters of handed-out envs), the
+ * groups taken largest frames first, so warps that finish early move on to
+ * the remaining envs. Results are bit-identical to stepping each group alone
+ * with jx_step / jx_rollout / jx_reset / jx_render.
+ *
+ * Layout of a batch's arrays (the batch's env order): group g's envs occupy
+ * env indices [env_offset(g), env_offset(g) + n_g) of the action, reward and
+ * done arrays, and bytes [frame_offset(g), frame_offset(g) + n_g*3*H_g*W_g)
+ * of the frame array, groups in the order given to jx_batch_create. Per step
+ * the arrays hold n_envs (jx_batch_info) entries and frame_bytes_per_step
+ * bytes; rollouts stack `steps` such steps.
+ *
+ * The batch references the group envs, it does not own them: they must
+ * outlive it, and while a batch launch is in flight their own calls must not
+ * run on another stream. Launches of one batch must be ordered on one stream
+ * at a time (they share its work-queue counters). */
+typedef struct jx_batch jx_batch;
+typedef struct jx_graph jx_graph;
+
+/* Tile choices of the batched kernel (set by hand or by jx_batch_autotune).
+ *  warps_per_block     envs in flight per thread block: 1, 2 or 4
+ *  cols_per_lane       DDA rays each lane marches together per pass: 1 or 2
+ *  bits_min_side       maps whose side is >= this (and a multiple of 8) are
+ *                      held in shared memory as bit planes (1 bit per cell)
+ *                      instead of byte grids; 0 = byte grids for all
+ *  max_rows_per_block  frame rows per staged shared-memory block (upper
+ *                      bound, 1..16; lowered to fit and to the fill pass) */
+typedef struct {
+  int32_t warps_per_block;
+  int32_t cols_per_lane;
+  int32_t bits_min_side;
+  int32_t max_rows_per_block;
+} jx_tiling;
+
+/* The fixed tiling (what a single env uses): 1 warp per block, 1 ray per
+ * lane, byte maps below side 128, up to 16 rows per block. */
+jx_status jx_tiling_default(jx_tiling* out);
+
+/* Make a batch of n_groups (1..32) distinct envs on one device. tiling NULL
+ * = jx_tiling_default. Allocates the queue counters and the maze work space. */
+jx_status jx_batch_create(jx_env* const* groups, int32_t n_groups, const jx_tiling* tiling, jx_batch** out);
+/* Free the batch (not its groups). NULL is accepted. */
+jx_status jx_batch_destroy(jx_batch* batch);
+/* Total envs and frame bytes of one step of the batch. */
+jx_status jx_batch_info(const jx_batch* batch, int64_t* n_envs, int64_t* frame_bytes_per_step);
+/* Offsets of group g (in the order given) in the env and frame arrays. */
+jx_status jx_batch_group(const jx_batch* batch, int32_t group, int64_t* env_offset, int64_t* frame_offset);
+/* Change / read the tiling. Results do not depend on it, only speed does. */
+jx_status jx_batch_set_tiling(jx_batch* batch, const jx_tiling* tiling);
+jx_status jx_batch_get_tiling(const jx_batch* batch, jx_tiling* tiling);
+/* Launch shape of the batched step kernel: grid, threads per block, dynamic
+ * shared memory per block. */
+jx_status jx_batch_launch_shape(const jx_batch* batch, int32_t* grid, int32_t* block, int32_t* smem_bytes);
+/* Number of batched kernel launches issued since creation (graph replays
+ * count their steps; autotuning trials do not count). */
+jx_status jx_batch_launch_count(const jx_batch* batch, uint64_t* count);
+
+/* jx_reset / jx_step / jx_rollout / jx_render of every env of every group in
+ * one launch each, with the batch's array layout (above). Asynchronous on
+ * `stream`; allocate nothing; capturable in a CUDA graph. */
+jx_status jx_batch_reset(jx_batch* batch, void* stream, uint8_t* d_frames);
+jx_status jx_batch_step(jx_batch* batch, void* stream, const uint8_t* d_actions, uint8_t* d_frames,
+                        float* d_rewards, uint8_t* d_dones);
+jx_status jx_batch_rollout(jx_batch* batch, void* stream, const uint8_t* d_actions, int32_t steps,
+                           uint8_t* d_frames, float* d_rewards, uint8_t* d_dones);
+jx_status jx_batch_render(jx_batch* batch, void* stream, uint8_t* d_frames);
+
+/* Autotuner: times every tiling of the search space (warps_per_block 1, 2,
+ * 4 x cols_per_lane 1, 2 x bits_min_side 0, 128, 64, 32 x max_rows_per_block
+ * 4, 8, 16; the first max_trials of them, the default first) on this batch
+ * and keeps the fastest. mode 0 times `steps` jx_batch_step launches, mode 1
+ * one jx_batch_rollout launch of `steps` steps; each trial starts from
+ * jx_batch_reset and is timed with CUDA events after one untimed launch.
+ * Uses uniform random actions and allocates its own buffers. Every env is
+ * RESET (episode 0) when it returns. trials / ms_per_step (optional, room for
+ * max_trials entries) receive each trial's tiling and time per step;
+ * *n_trials the number run. Waits for `stream`. */
+jx_status jx_batch_autotune(jx_batch* batch, void* stream, int32_t mode, int32_t steps, int32_t max_trials,
+                            int32_t* n_trials, jx_tiling* trials, float* ms_per_step);
+
+/* CUDA graph of `steps` consecutive jx_batch_step launches (step t reads
+ * d_actions + t*n_envs and writes step t's slice of d_frames, d_rewards,
+ * d_dones, laid out as for jx_batch_rollout). jx_graph_launch replays it on
+ * a stream: one submission for all the steps. The graph keeps the batch's
+ * tiling and the pointers of the capture; it must not outlive the batch. */
+jx_status jx_batch_capture(jx_batch* batch, int32_t steps, const uint8_t* d_actions, uint8_t* d_frames,
+                           float* d_rewards, uint8_t* d_dones, jx_graph** out);
+jx_status jx_graph_launch(jx_graph* graph, void* stream);
+jx_status jx_graph_destroy(jx_graph* graph);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* jx_last_error(void);
 

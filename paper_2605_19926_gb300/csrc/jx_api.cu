@@ -10,64 +10,15 @@
 #include <new>
 #include <string>
 
-#include "../../include/jx.h"
-#include "jx_internal.h"
+#include "jx_host.h"
 
-struct jx_env {
-  jx_config cfg;
-  int device = 0;
-  int num_sms = 0;
-  int blocks_per_sm = 0;
-  int grid = 0;
-  int smem_block = 0;
-  jx::Params base{};
-  // struct-of-arrays state block
-  uint8_t* state = nullptr;
-  size_t state_bytes = 0;
-  size_t field_off[JX_F_COUNT] = {};
-  size_t field_size[JX_F_COUNT] = {};
-  // device error word, turn table, column table
-  uint8_t* aux = nullptr;
-  // maze generation work space, one slot per resident warp
-  uint8_t* scratch = nullptr;
-  // staging buffers of jx_step_host
-  uint8_t* stage = nullptr;
-  size_t stage_frames_off = 0, stage_rewards_off = 0, stage_dones_off = 0;
-  std::atomic<uint64_t> launches{0};
-};
+using jx::host::aligned16;
+using jx::host::align256;
+using jx::host::cuda_fail;
+using jx::host::DeviceGuard;
+using jx::host::fail;
 
 namespace {
-
-thread_local std::string g_last_error;
-
-jx_status fail(jx_status st, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  g_last_error = buf;
-  return st;
-}
-
-jx_status cuda_fail(cudaError_t err, const char* what) {
-  return fail(JX_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(err), cudaGetErrorString(err));
-}
-
-// Makes the env's device current for the duration of a call.
-struct DeviceGuard {
-  int prev = -1;
-  cudaError_t err = cudaSuccess;
-  explicit DeviceGuard(int dev) {
-    err = cudaGetDevice(&prev);
-    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 jx_status validate(const jx_config* c) {
   if (!c) return fail(JX_EINVAL, "config is NULL");
@@ -147,13 +98,55 @@ jx_status run(jx_env* env, const jx::Params& p, int mode, void* stream) {
   return JX_OK;
 }
 
-bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
 }  // namespace
+
+namespace jx {
+namespace host {
+
+thread_local std::string g_last_error;
+
+jx_status fail(jx_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+jx_status cuda_fail(cudaError_t err, const char* what) {
+  return fail(JX_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(err), cudaGetErrorString(err));
+}
+
+void choose_rows(Params& p, int max_rows, int warps, int blocks, size_t smem_per_sm, size_t reserved) {
+  const int rowb = 3 * p.W;
+  const int pass_rows = 32 / (p.W / 8) > 0 ? 32 / (p.W / 8) : 1;
+  p.rows_per_block = 1;
+  p.frame_block_bytes = rowb;
+  const int top = p.H < max_rows ? p.H : max_rows;
+  for (int rows = top; rows >= 1; --rows) {
+    if (rows < p.H && rows >= pass_rows && rows % pass_rows != 0) continue;
+    Params q = p;
+    q.rows_per_block = rows;
+    q.frame_block_bytes = rows * rowb;
+    layout_warp_smem(q);
+    const int per_block = q.warp_bytes * warps;
+    if ((size_t)(per_block + reserved) * (size_t)((blocks + warps - 1) / warps) <= smem_per_sm) {
+      p.rows_per_block = rows;
+      p.frame_block_bytes = rows * rowb;
+      break;
+    }
+  }
+  layout_warp_smem(p);
+}
+
+}  // namespace host
+}  // namespace jx
 
 extern "C" {
 
-const char* jx_last_error(void) { return g_last_error.c_str(); }
+const char* jx_last_error(void) { return jx::host::g_last_error.c_str(); }
 
 jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
   if (!out) return fail(JX_EINVAL, "out is NULL");
@@ -236,7 +229,6 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
   p.horizon = c.horizon;
   p.tpr = tpr;
   p.task = c.task;
-  p.map_smem_bytes = (c.map_side * c.map_side + 15) & ~15;
   p.move = (float)c.move_step;
   p.radius = (float)c.radius;
   p.tan_half = (float)std::tan(0.5 * c.fov_deg * 3.14159265358979323846 / 180.0);
@@ -254,30 +246,14 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
     return cuda_fail(err, "cudaGetDeviceProperties");
   }
   env->num_sms = prop.multiProcessorCount;
-  // Frame staging: the largest row block (at most 16 rows, at least 1, a
-  // multiple of the rows one fill pass covers when possible) with which
-  // kMinBlocksPerSm blocks still fit in one SM's shared memory.
-  {
-    const int rowb = 3 * W;
-    const int pass_rows = 32 / (W / 8) > 0 ? 32 / (W / 8) : 1;
-    p.rows_per_block = 1;
-    p.frame_block_bytes = rowb;
-    const size_t per_sm = prop.sharedMemPerMultiprocessor;
-    const size_t reserved = prop.reservedSharedMemPerBlock;
-    for (int rows = c.frame_h < 16 ? c.frame_h : 16; rows >= 1; --rows) {
-      if (rows < c.frame_h && rows >= pass_rows && rows % pass_rows != 0) continue;
-      jx::Params q = p;
-      q.rows_per_block = rows;
-      q.frame_block_bytes = rows * rowb;
-      jx::layout_warp_smem(q);
-      if ((size_t)(jx::block_smem_bytes(q) + reserved) * jx::kMinBlocksPerSm <= per_sm) {
-        p.rows_per_block = rows;
-        p.frame_block_bytes = rows * rowb;
-        break;
-      }
-    }
-    jx::layout_warp_smem(p);
-  }
+  // Frame staging: the largest row block (at most 16 rows) with which
+  // kMinBlocksPerSm one-warp blocks still fit in one SM's shared memory.
+  // Maps of side 128 are staged as bit planes (2 KB instead of 16 KB).
+  p.map_bits = c.map_side >= 128 && c.map_side % 8 == 0;
+  p.out_stride = c.n_envs;
+  p.frame_step = (size_t)c.n_envs * jx::host::frame_bytes(c);
+  jx::host::choose_rows(p, 16, jx::kWarpsPerBlock, jx::kMinBlocksPerSm, prop.sharedMemPerMultiprocessor,
+                        prop.reservedSharedMemPerBlock);
   env->smem_block = jx::block_smem_bytes(p);
   if ((size_t)env->smem_block > prop.sharedMemPerBlockOptin) {
     jx_destroy(env);

@@ -20,6 +20,16 @@ constexpr int kMinBlocksPerSm = 28;  // register budget: 28 warps resident per S
 
 enum Mode { MODE_STEP = 0, MODE_RESET = 1, MODE_RENDER = 2, MODE_RAYS = 3, MODE_ROLLOUT = 4 };
 
+// How a warp holds its env's map in shared memory: one byte per cell, or one
+// bit per cell (wall or closed door) with the wall type read from the state
+// block at a ray's hit. MAP_RUNTIME takes the choice from Params::map_bits.
+enum MapKind { MAP_BYTES = 0, MAP_BITS = 1, MAP_RUNTIME = 2 };
+
+// Batched launches over env groups of different sizes.
+constexpr int kMaxGroups = 32;
+constexpr int kBatchMaxThreads = 128;  // up to 4 warps (envs in flight) per block
+constexpr int kBatchMinBlocks = kMinBlocksPerSm * 32 / kBatchMaxThreads;
+
 enum Purpose : uint32_t {
   P_WALL = 1,
   P_SPAWN = 2,
@@ -65,7 +75,10 @@ struct Params {
   int32_t* dbg_hits;
   float* dbg_perp;
   int32_t n, S, H, W, K, horizon, tpr, task;
-  int32_t steps;  // steps of one rollout launch (actions / outputs are [steps][n][...])
+  int32_t steps;  // steps of one rollout launch (actions / outputs are [steps][out_stride][...])
+  int32_t out_stride;  // envs per step in the action / reward / done arrays (n, or a batch's total)
+  size_t frame_step;   // bytes per step in the frame array (n frames, or a batch's total)
+  int32_t map_bits;    // the map is staged as a bit plane (see MapKind)
   int32_t rows_per_block;  // rows per staged frame block
   int32_t frame_block_bytes;
   int32_t map_smem_bytes;  // S * S rounded up to 16
@@ -78,7 +91,16 @@ struct Params {
   uint64_t wall_thr;  // an interior cell is a wall iff (draw >> 11) < wall_thr
 };
 
-// Fill in the per-warp shared memory layout of p (needs W, K, S, frame_block_bytes).
+// A launch over env groups: warps take envs from per-group work queues, the
+// groups in the order given (largest envs first).
+struct BatchParams {
+  Params g[kMaxGroups];  // per group; actions / outputs already offset to the group's slice
+  uint32_t* queue;       // [kMaxGroups + 1] next env per group, warps finished; zero between launches
+  int32_t n_groups;
+  int32_t warp_bytes;  // per-warp shared memory: the largest group's layout
+};
+
+// Fill in the per-warp shared memory layout of p (needs W, K, S, map_bits, frame_block_bytes).
 void layout_warp_smem(Params& p);
 // Dynamic shared memory bytes of one block.
 int block_smem_bytes(const Params& p);
@@ -88,5 +110,9 @@ size_t gen_scratch_bytes(int task, int S);
 cudaError_t kernel_blocks_per_sm(const Params& p, int mode, int* blocks);
 // Launch the fused kernel for `mode`.
 cudaError_t launch(const Params& p, int mode, int grid, cudaStream_t stream);
+
+// The batched kernel: blocks of `warps` warps, `cols` rays marched together per lane.
+cudaError_t batch_blocks_per_sm(int mode, int cols, int warps, int smem_bytes, int* blocks);
+cudaError_t batch_launch(const BatchParams& bp, int mode, int cols, int warps, int grid, cudaStream_t stream);
 
 }  // namespace jx

@@ -214,6 +214,7 @@ __device__ __forceinline__ void stage_map(const Params& p, int e, uint8_t* smap,
 __device__ __forceinline__ void store_map(const Params& p, int e, const uint8_t* smap, int lane) {
   const int n = p.S * p.S;
   uint8_t* g = p.st.map + (size_t)e * n;
+  if (smap == g) return;  // generated in place
   if ((n & 15) == 0) {
     const uint4* src = reinterpret_cast<const uint4*>(smap);
     uint4* dst = reinterpret_cast<uint4*>(g);
@@ -221,6 +222,47 @@ __device__ __forceinline__ void store_map(const Params& p, int e, const uint8_t*
   } else {
     for (int i = lane; i < n; i += 32) g[i] = smap[i];
   }
+}
+
+// bit k of the result is set iff byte k of x is nonzero
+__device__ __forceinline__ uint32_t nonzero4(uint32_t x) {
+  const uint32_t m = __vcmpne4(x, 0u) & 0x01010101u;
+  return (m * 0x10204080u) >> 28;  // gathers bits 0, 8, 16, 24 into bits 28..31
+}
+
+// The map as a bit plane: bit i of word i / 32 is set iff cell i is nonzero
+// (S * S is a multiple of 32; rows run on across word boundaries).
+__device__ __forceinline__ void stage_map_bits(const Params& p, int e, uint8_t* smap, int lane) {
+  const int words = (p.S * p.S) >> 5;
+  const uint4* g = reinterpret_cast<const uint4*>(p.st.map + (size_t)e * p.S * p.S);
+  uint32_t* w = reinterpret_cast<uint32_t*>(smap);
+  for (int i = lane; i < words; i += 32) {
+    const uint4 a = g[2 * i], b = g[2 * i + 1];
+    w[i] = nonzero4(a.x) | nonzero4(a.y) << 4 | nonzero4(a.z) << 8 | nonzero4(a.w) << 12 | nonzero4(b.x) << 16 |
+           nonzero4(b.y) << 20 | nonzero4(b.z) << 24 | nonzero4(b.w) << 28;
+  }
+  __syncwarp();
+}
+
+template <int MAPK>
+__device__ __forceinline__ bool map_bits(const Params& p) {
+  return MAPK == MAP_BITS || (MAPK == MAP_RUNTIME && p.map_bits != 0);
+}
+
+// cell i of the staged map blocks movement and rays (in bit mode the door's
+// bit is cleared while the key is held, see open_door)
+template <int MAPK>
+__device__ __forceinline__ bool cell_set(const Params& p, const uint8_t* smap, int i) {
+  if (map_bits<MAPK>(p)) return (reinterpret_cast<const uint32_t*>(smap)[i >> 5] >> (i & 31)) & 1u;
+  return smap[i] != 0;
+}
+
+template <int MAPK>
+__device__ __forceinline__ void stage(const Params& p, int e, uint8_t* smap, int lane) {
+  if (map_bits<MAPK>(p))
+    stage_map_bits(p, e, smap, lane);
+  else
+    stage_map(p, e, smap, lane);
 }
 
 // ------------------------------------------------------------ generators --
@@ -454,12 +496,17 @@ __device__ __forceinline__ void gen_maze(const Params& p, int e, uint32_t ep, ui
 // The maze work space lives in the warp's frame staging ring when it fits
 // (32 x 32 mazes need 3.4 KB), else in the global per-warp slot. Inlined
 // behind unlikely branches: a call would make every value live across it
-// spill in the hot loop.
+// spill in the hot loop. A byte map is generated in shared memory and copied
+// out; in bit mode the map is generated in place in the state block and its
+// bit plane staged from there.
+template <int MAPK>
 __device__ __forceinline__ void generate(const Params& p, int e, uint32_t ep, uint8_t* wbase, uint8_t* scratch,
                                       int lane) {
   const WarpSmem ws{wbase, fill_lane(p, lane)};
+  const bool bits = map_bits<MAPK>(p);
+  uint8_t* smap = bits ? p.st.map + (size_t)e * p.S * p.S : ws.map(p);
   if (p.task == 0) {
-    gen_rooms(p, e, ep, ws.map(p), lane);
+    gen_rooms(p, e, ep, smap, lane);
   } else {
     const int nn = (p.S - 2) / 2;
     uint8_t* work = scratch;
@@ -468,13 +515,16 @@ __device__ __forceinline__ void generate(const Params& p, int e, uint32_t ep, ui
       __syncwarp();
       work = ws.ring();
     }
-    gen_maze(p, e, ep, ws.map(p), work, lane);
+    gen_maze(p, e, ep, smap, work, lane);
   }
+  if (bits) stage_map_bits(p, e, ws.map(p), lane);
 }
 
 // ------------------------------------------------------------------ step ----
-__device__ __forceinline__ bool solid(const uint8_t* smap, int S, int x, int y, int has_key) {
+template <int MAPK>
+__device__ __forceinline__ bool solid(const Params& p, const uint8_t* smap, int S, int x, int y, int has_key) {
   if (x < 0 || y < 0 || x >= S || y >= S) return true;
+  if (map_bits<MAPK>(p)) return cell_set<MAPK>(p, smap, y * S + x);
   int v = smap[y * S + x];
   return v != 0 && !(v == kDoor && has_key);
 }
@@ -485,15 +535,16 @@ __device__ __forceinline__ bool solid(const uint8_t* smap, int S, int x, int y, 
 // half-size is below 1/2, so every box edge lies in that range.
 __device__ __forceinline__ int floor_small(float v) { return (v >= 1.f ? 1 : 0) - (v < 0.f ? 1 : 0); }
 
-__device__ __forceinline__ bool box_free(const uint8_t* smap, int S, int cx, float fx, int cy, float fy, float r,
-                                         int has_key) {
+template <int MAPK>
+__device__ __forceinline__ bool box_free(const Params& p, const uint8_t* smap, int S, int cx, float fx, int cy,
+                                         float fy, float r, int has_key) {
   const int i0 = cx + floor_small(fx - r), i1 = cx + floor_small(fx + r);
   const int j0 = cy + floor_small(fy - r), j1 = cy + floor_small(fy + r);
-  bool hit = solid(smap, S, i0, j0, has_key);
-  if (i1 != i0) hit |= solid(smap, S, i1, j0, has_key);
+  bool hit = solid<MAPK>(p, smap, S, i0, j0, has_key);
+  if (i1 != i0) hit |= solid<MAPK>(p, smap, S, i1, j0, has_key);
   if (j1 != j0) {
-    hit |= solid(smap, S, i0, j1, has_key);
-    if (i1 != i0) hit |= solid(smap, S, i1, j1, has_key);
+    hit |= solid<MAPK>(p, smap, S, i0, j1, has_key);
+    if (i1 != i0) hit |= solid<MAPK>(p, smap, S, i1, j1, has_key);
   }
   return !hit;
 }
@@ -516,6 +567,7 @@ __device__ __forceinline__ void renormalise(int& c, float& f) {
 // One step of env e under action a; the reward and done flag go to output
 // slot `out`. Returns true when the episode ended (the caller regenerates).
 // The pose is written back to the state block only when write_state is set.
+template <int MAPK>
 __device__ __forceinline__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, const int32_t* obj,
                                          int lane, float& c, float& s, int a, size_t out, bool write_state) {
   if (a > 6) {
@@ -543,12 +595,12 @@ __device__ __forceinline__ bool step_env(const Params& p, int e, Env& r, const u
   const int S = p.S;
   const float rad = p.radius;
   float nfx = r.fx + dx;
-  if (box_free(smap, S, r.cx, nfx, r.cy, r.fy, rad, r.has_key)) {
+  if (box_free<MAPK>(p, smap, S, r.cx, nfx, r.cy, r.fy, rad, r.has_key)) {
     r.fx = nfx;
     renormalise(r.cx, r.fx);
   }
   float nfy = r.fy + dy;
-  if (box_free(smap, S, r.cx, r.fx, r.cy, nfy, rad, r.has_key)) {
+  if (box_free<MAPK>(p, smap, S, r.cx, r.fx, r.cy, nfy, rad, r.has_key)) {
     r.fy = nfy;
     renormalise(r.cy, r.fy);
   }
@@ -605,7 +657,8 @@ __device__ __forceinline__ void ray_init(Ray& q, const Env& r, float rx, float r
   q.done = !valid;
 }
 
-__device__ __forceinline__ void ray_advance(Ray& q, const uint8_t* smap, int S) {
+template <int MAPK>
+__device__ __forceinline__ void ray_advance(const Params& p, Ray& q, const uint8_t* smap, int S) {
   const float lhs = fmaf(q.kx, q.ay, q.gxay);
   const float rhs = fmaf(q.ky, q.ax, q.gyax);
   const bool tx = lhs < rhs;
@@ -615,11 +668,11 @@ __device__ __forceinline__ void ray_advance(Ray& q, const uint8_t* smap, int S) 
   q.ky += tx ? 0.f : 1.f;
   q.side = tx ? 0 : 1;
   const bool out = (unsigned)q.mx >= (unsigned)S || (unsigned)q.my >= (unsigned)S;
-  q.done = out || smap[q.my * S + q.mx] != 0;
+  q.done = out || cell_set<MAPK>(p, smap, q.my * S + q.mx);
 }
 
 // Slice of a finished ray: perp, rows and colour into the column arrays.
-template <int MODE>
+template <int MODE, int MAPK>
 __device__ __forceinline__ void finish_column(const Params& p, int e, const Ray& q, int col, const WarpSmem& ws) {
   const int S = p.S, H = p.H;
   float perp;
@@ -641,7 +694,8 @@ __device__ __forceinline__ void finish_column(const Params& p, int e, const Ray&
   const int bot = top + h;
   int v = 1;
   const bool inside = (unsigned)q.mx < (unsigned)S && (unsigned)q.my < (unsigned)S;
-  if (q.side >= 0 && inside) v = ws.map(p)[q.my * S + q.mx];
+  if (q.side >= 0 && inside)
+    v = map_bits<MAPK>(p) ? p.st.map[(size_t)e * S * S + q.my * S + q.mx] : ws.map(p)[q.my * S + q.mx];
   const int slot = col_slot(col, p.W >> 3);
   ws.col_rgb(p)[slot] = ws.pal(p)[(q.side == 1 ? 8 : 0) + (v > 7 ? 7 : v)];
   ws.col_top(p)[slot] = top < 0 ? 0 : (top > H ? H : top);
@@ -654,24 +708,36 @@ __device__ __forceinline__ void finish_column(const Params& p, int e, const Ray&
   }
 }
 
-// Cast every column's ray: lane l takes columns l, l + 32, ...; in each pass
-// the warp leaves the DDA loop when a ballot says every ray has hit.
-template <int MODE>
+// Cast every column's ray: in each pass lane l marches the rays of columns
+// l + 32 j (j < COLS) together, and the warp leaves the DDA loop when a
+// ballot says every ray has hit.
+template <int MODE, int MAPK, int COLS>
 __device__ __forceinline__ void cast_columns(const Params& p, int e, const Env& r, float c, float s,
                                              const WarpSmem& ws, int lane) {
   const int W = p.W, S = p.S;
   const uint8_t* smap = ws.map(p);
   const int max_it = 4 * S + 8;
-  for (int col = lane; col - lane < W; col += 32) {
-    const bool valid = col < W;
-    const float k = __ldg(p.col_k + (valid ? col : 0));
-    Ray q;
-    ray_init(q, r, fmaf(-k, s, c), fmaf(k, c, s), valid);
-    for (int it = 0; it < max_it; ++it) {
-      if (!q.done) ray_advance(q, smap, S);
-      if (__all_sync(0xffffffffu, q.done)) break;
+  for (int col0 = lane; col0 - lane < W; col0 += 32 * COLS) {
+    Ray q[COLS];
+#pragma unroll
+    for (int j = 0; j < COLS; ++j) {
+      const int col = col0 + 32 * j;
+      const bool valid = col < W;
+      const float k = __ldg(p.col_k + (valid ? col : 0));
+      ray_init(q[j], r, fmaf(-k, s, c), fmaf(k, c, s), valid);
     }
-    if (valid) finish_column<MODE>(p, e, q, col, ws);
+    for (int it = 0; it < max_it; ++it) {
+      bool all = true;
+#pragma unroll
+      for (int j = 0; j < COLS; ++j) {
+        if (!q[j].done) ray_advance<MAPK>(p, q[j], smap, S);
+        all = all && q[j].done;
+      }
+      if (__all_sync(0xffffffffu, all)) break;
+    }
+#pragma unroll
+    for (int j = 0; j < COLS; ++j)
+      if (col0 + 32 * j < W) finish_column<MODE, MAPK>(p, e, q[j], col0 + 32 * j, ws);
   }
   __syncwarp();
 }
@@ -811,10 +877,10 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
   }
 }
 
-template <int MODE>
+template <int MODE, int MAPK, int COLS>
 __device__ __forceinline__ void render_env(const Params& p, int e, const Env& r, float c, float s,
                                            const WarpSmem& ws, int lane, int& slot, uint8_t* frame) {
-  cast_columns<MODE>(p, e, r, c, s, ws, lane);
+  cast_columns<MODE, MAPK, COLS>(p, e, r, c, s, ws, lane);
   if (MODE == MODE_RAYS) return;
   const int nvis = project_sprites(p, r, c, s, ws, lane);  // ends with __syncwarp
   const int H = p.H, rowb = 3 * p.W;
@@ -831,116 +897,222 @@ __device__ __forceinline__ void render_env(const Params& p, int e, const Env& r,
   }
 }
 
-// The locked door opens (for rays and collisions) once the key is held.
-__device__ __forceinline__ void open_door(const Params& p, const Env& r, const WarpSmem& ws, int lane) {
+// The locked door opens (for rays and collisions) once the key is held. In
+// bit mode it is opened when the map is staged and after the step that picks
+// the key up, so the plane never shows a closed door to a key holder.
+template <int MAPK>
+__device__ __forceinline__ void open_door(const Params& p, int e, const Env& r, const WarpSmem& ws, int lane) {
   if (r.has_key) {
     const int2 door = *reinterpret_cast<const int2*>(ws.obj(p) + 4);
-    if (lane == 0 && door.x >= 0 && door.y >= 0 && door.x < p.S && door.y < p.S &&
-        ws.map(p)[door.y * p.S + door.x] == kDoor)
-      ws.map(p)[door.y * p.S + door.x] = 0;
+    if (lane == 0 && door.x >= 0 && door.y >= 0 && door.x < p.S && door.y < p.S) {
+      const int i = door.y * p.S + door.x;
+      if (map_bits<MAPK>(p)) {
+        if (p.st.map[(size_t)e * p.S * p.S + i] == kDoor)
+          reinterpret_cast<uint32_t*>(ws.map(p))[i >> 5] &= ~(1u << (i & 31));
+      } else if (ws.map(p)[i] == kDoor) {
+        ws.map(p)[i] = 0;
+      }
+    }
     __syncwarp();
   }
 }
 
-template <int MODE>
+// Everything one launch does for env e: MODE_ROLLOUT runs p.steps steps with
+// the env's scalar state in registers and its map in shared memory.
+template <int MODE, int MAPK, int COLS>
+__device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, uint8_t* scratch, int lane,
+                                        int& slot) {
+  const WarpSmem ws{wbase, fill_lane(p, lane)};
+  const size_t frame_bytes = (size_t)3 * p.H * p.W;
+  if (MODE == MODE_ROLLOUT) {
+    Env r = load_env(p, e);
+    load_objects(p, ws, e, lane);
+    stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
+    if (map_bits<MAPK>(p)) open_door<MAPK>(p, e, r, ws, lane);
+    int a_next = p.actions[e];
+    for (int t = 0; t < p.steps; ++t) {
+      const int a = a_next;
+      if (t + 1 < p.steps) a_next = p.actions[(size_t)(t + 1) * p.out_stride + e];
+      float c, s;
+      const size_t out = (size_t)t * p.out_stride + e;
+      if (__builtin_expect(step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), lane, c, s, a, out, false), 0)) {
+        const uint32_t ep = p.st.episode[e] + 1;
+        __syncwarp();
+        generate<MAPK>(p, e, ep, wbase, scratch, lane);
+        r = load_env(p, e);
+        load_objects(p, ws, e, lane);
+        __syncwarp();
+        heading(p, r, c, s);
+      }
+      open_door<MAPK>(p, e, r, ws, lane);
+      render_env<MODE, MAPK, COLS>(p, e, r, c, s, ws, lane, slot,
+                                   p.frames + (size_t)t * p.frame_step + (size_t)e * frame_bytes);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      const State& st = p.st;
+      st.cell_x[e] = (int16_t)r.cx;
+      st.cell_y[e] = (int16_t)r.cy;
+      st.frac_x[e] = r.fx;
+      st.frac_y[e] = r.fy;
+      st.turn[e] = (int16_t)r.turn;
+      st.t[e] = r.t;
+      st.flags[e] = (uint8_t)r.has_key;
+    }
+    __syncwarp();
+    return;
+  }
+  Env r;
+  float c, s;
+  if (MODE == MODE_RESET) {
+    generate<MAPK>(p, e, 0u, wbase, scratch, lane);
+    r = load_env(p, e);
+    load_objects(p, ws, e, lane);
+    __syncwarp();
+    heading(p, r, c, s);
+  } else {
+    r = load_env(p, e);
+    load_objects(p, ws, e, lane);
+    stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
+    if (map_bits<MAPK>(p)) open_door<MAPK>(p, e, r, ws, lane);
+    if (MODE == MODE_STEP) {
+      if (__builtin_expect(
+              step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), lane, c, s, (int)p.actions[e], (size_t)e, true), 0)) {
+        const uint32_t ep = p.st.episode[e] + 1;
+        __syncwarp();
+        generate<MAPK>(p, e, ep, wbase, scratch, lane);
+        r = load_env(p, e);
+        load_objects(p, ws, e, lane);
+        __syncwarp();
+        heading(p, r, c, s);
+      }
+    } else {
+      heading(p, r, c, s);
+    }
+  }
+  open_door<MAPK>(p, e, r, ws, lane);
+  render_env<MODE, MAPK, COLS>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
+  __syncwarp();
+}
+
+__device__ __forceinline__ void write_palette(const Params& p, const WarpSmem& ws, int lane) {
+  if (lane < 16) ws.pal(p)[lane] = c_wall[lane >> 3][lane & 7];
+  if (lane < 4) ws.pal(p)[16 + lane] = c_sprite[lane];
+  __syncwarp();
+}
+
+template <int MODE, int MAPK>
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __grid_constant__ Params p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* const wbase = smem_raw + warp * p.warp_bytes;
-  const WarpSmem ws{wbase, fill_lane(p, lane)};
-  if (lane < 16) ws.pal(p)[lane] = c_wall[lane >> 3][lane & 7];
-  if (lane < 4) ws.pal(p)[16 + lane] = c_sprite[lane];
-  __syncwarp();
+  write_palette(p, WarpSmem{wbase, fill_lane(p, lane)}, lane);
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
   uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;
   int slot = 0;
-  const size_t frame_bytes = (size_t)3 * p.H * p.W;
-  for (int e = gw; e < p.n; e += nw) {
-    Env r;
-    float c, s;
-    if (MODE == MODE_ROLLOUT) {
-      // the env's scalar state stays in registers and its map in shared memory for all steps
-      Env r = load_env(p, e);
-      load_objects(p, ws, e, lane);
-      stage_map(p, e, ws.map(p), lane);  // ends with __syncwarp
-      int a_next = p.actions[e];
-      for (int t = 0; t < p.steps; ++t) {
-        const int a = a_next;
-        if (t + 1 < p.steps) a_next = p.actions[(size_t)(t + 1) * p.n + e];
-        float c, s;
-        const size_t out = (size_t)t * p.n + e;
-        if (__builtin_expect(step_env(p, e, r, ws.map(p), ws.obj(p), lane, c, s, a, out, false), 0)) {
-          const uint32_t ep = p.st.episode[e] + 1;
-          __syncwarp();
-          generate(p, e, ep, wbase, scratch, lane);
-          r = load_env(p, e);
-          load_objects(p, ws, e, lane);
-          __syncwarp();
-          heading(p, r, c, s);
-        }
-        open_door(p, r, ws, lane);
-        render_env<MODE>(p, e, r, c, s, ws, lane, slot, p.frames + out * frame_bytes);
-        __syncwarp();
-      }
-      if (lane == 0) {
-        const State& st = p.st;
-        st.cell_x[e] = (int16_t)r.cx;
-        st.cell_y[e] = (int16_t)r.cy;
-        st.frac_x[e] = r.fx;
-        st.frac_y[e] = r.fy;
-        st.turn[e] = (int16_t)r.turn;
-        st.t[e] = r.t;
-        st.flags[e] = (uint8_t)r.has_key;
-      }
-      __syncwarp();
-      continue;
-    }
-    if (MODE == MODE_RESET) {
-      generate(p, e, 0u, wbase, scratch, lane);
-      r = load_env(p, e);
-      load_objects(p, ws, e, lane);
-      __syncwarp();
-      heading(p, r, c, s);
-    } else {
-      r = load_env(p, e);
-      load_objects(p, ws, e, lane);
-      stage_map(p, e, ws.map(p), lane);  // ends with __syncwarp
-      if (MODE == MODE_STEP) {
-        if (__builtin_expect(step_env(p, e, r, ws.map(p), ws.obj(p), lane, c, s, (int)p.actions[e], (size_t)e, true),
-                             0)) {
-          const uint32_t ep = p.st.episode[e] + 1;
-          __syncwarp();
-          generate(p, e, ep, wbase, scratch, lane);
-          r = load_env(p, e);
-          load_objects(p, ws, e, lane);
-          __syncwarp();
-          heading(p, r, c, s);
-        }
-      } else {
-        heading(p, r, c, s);
-      }
-    }
-    open_door(p, r, ws, lane);
-    render_env<MODE>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
-    __syncwarp();
-  }
+  for (int e = gw; e < p.n; e += nw) run_env<MODE, MAPK, 1>(p, e, wbase, scratch, lane, slot);
   // shared memory stays allocated until the bulk stores have read it
   if (lane == 0) bulk_wait_read_all();
 }
 
-// The kernel's dynamic shared memory limit is a property of the function, shared
+// One launch over the groups of a batch. Each group has a work queue (a
+// counter of handed-out envs); a warp drains the groups' queues in order,
+// one env at a time, fetching its next ticket while it works on the current
+// env. The last warp to finish zeroes the counters for the next launch.
+template <int MODE, int COLS>
+__global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
+    batch_kernel(const __grid_constant__ BatchParams bp) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  uint8_t* const wbase = smem_raw + warp * bp.warp_bytes;
+  const int gw = blockIdx.x * wpb + warp;
+  int slot = 0;
+  bool fresh = true;  // nothing of an earlier group is pending in the ring
+  for (int g = 0; g < bp.n_groups; ++g) {
+    const Params& p = bp.g[g];
+    uint32_t ticket = 0;
+    if (lane == 0) {
+      // a drained queue is skipped without an atomic
+      ticket = *reinterpret_cast<volatile uint32_t*>(bp.queue + g);
+      if (ticket < (uint32_t)p.n) ticket = atomicAdd(bp.queue + g, 1u);
+    }
+    ticket = __shfl_sync(0xffffffffu, ticket, 0);
+    if (ticket >= (uint32_t)p.n) continue;
+    if (!fresh && lane == 0) bulk_wait_read_all();  // the layout changes under the ring
+    __syncwarp();
+    write_palette(p, WarpSmem{wbase, fill_lane(p, lane)}, lane);
+    fresh = false;
+    slot = 0;
+    uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;
+    while (ticket < (uint32_t)p.n) {
+      uint32_t next = 0;
+      if (lane == 0) next = atomicAdd(bp.queue + g, 1u);
+      run_env<MODE, MAP_RUNTIME, COLS>(p, (int)ticket, wbase, scratch, lane, slot);
+      ticket = __shfl_sync(0xffffffffu, next, 0);
+    }
+  }
+  if (lane == 0) {
+    bulk_wait_read_all();
+    __threadfence();
+    const uint32_t nw = gridDim.x * wpb;
+    if (atomicAdd(bp.queue + kMaxGroups, 1u) == nw - 1) {
+      for (int g = 0; g < bp.n_groups; ++g) atomicExch(bp.queue + g, 0u);
+      atomicExch(bp.queue + kMaxGroups, 0u);
+    }
+  }
+}
+
+// A kernel's dynamic shared memory limit is a property of the function, shared
 // by every env in the process: it is raised to the device's opt-in maximum (never
 // lowered), so envs of different sizes can coexist.
-template <int MODE>
-cudaError_t blocks_per_sm_for(const Params& p, int* blocks) {
+template <class Kernel>
+cudaError_t raise_smem_limit(Kernel kernel) {
   int dev = 0, optin = 0;
   cudaError_t err = cudaGetDevice(&dev);
   if (err == cudaSuccess) err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (err == cudaSuccess)
-    err = cudaFuncSetAttribute(env_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (err == cudaSuccess) err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  return err;
+}
+
+template <int MODE, int MAPK>
+cudaError_t blocks_per_sm_for(const Params& p, int* blocks) {
+  cudaError_t err = raise_smem_limit(env_kernel<MODE, MAPK>);
   if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, env_kernel<MODE>, kThreads, block_smem_bytes(p));
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, env_kernel<MODE, MAPK>, kThreads, block_smem_bytes(p));
+}
+
+template <int MODE>
+cudaError_t blocks_per_sm_mode(const Params& p, int* blocks) {
+  return p.map_bits ? blocks_per_sm_for<MODE, MAP_BITS>(p, blocks) : blocks_per_sm_for<MODE, MAP_BYTES>(p, blocks);
+}
+
+template <int MODE, int MAPK>
+void launch_env(const Params& p, int grid, cudaStream_t stream) {
+  env_kernel<MODE, MAPK><<<grid, kThreads, block_smem_bytes(p), stream>>>(p);
+}
+
+template <int MODE>
+void launch_mode(const Params& p, int grid, cudaStream_t stream) {
+  if (p.map_bits)
+    launch_env<MODE, MAP_BITS>(p, grid, stream);
+  else
+    launch_env<MODE, MAP_BYTES>(p, grid, stream);
+}
+
+template <int MODE>
+auto batch_kernel_for(int cols) {
+  return cols == 2 ? batch_kernel<MODE, 2> : batch_kernel<MODE, 1>;
+}
+
+auto batch_kernel_of(int mode, int cols) {
+  switch (mode) {
+    case MODE_RESET: return batch_kernel_for<MODE_RESET>(cols);
+    case MODE_ROLLOUT: return batch_kernel_for<MODE_ROLLOUT>(cols);
+    case MODE_RENDER: return batch_kernel_for<MODE_RENDER>(cols);
+    default: return batch_kernel_for<MODE_STEP>(cols);
+  }
 }
 
 }  // namespace
@@ -953,6 +1125,7 @@ void layout_warp_smem(Params& p) {
     q += align16(bytes);
     return at;
   };
+  p.map_smem_bytes = align16(p.map_bits ? (p.S * p.S + 7) / 8 : p.S * p.S);
   p.off_pal = take(4 * kPaletteWords);
   p.off_map = take(p.map_smem_bytes);
   p.off_col_rgb = take(4 * p.W);
@@ -980,23 +1153,35 @@ size_t gen_scratch_bytes(int task, int S) {
 
 cudaError_t kernel_blocks_per_sm(const Params& p, int mode, int* blocks) {
   switch (mode) {
-    case MODE_STEP: return blocks_per_sm_for<MODE_STEP>(p, blocks);
-    case MODE_RESET: return blocks_per_sm_for<MODE_RESET>(p, blocks);
-    case MODE_RENDER: return blocks_per_sm_for<MODE_RENDER>(p, blocks);
-    case MODE_ROLLOUT: return blocks_per_sm_for<MODE_ROLLOUT>(p, blocks);
-    default: return blocks_per_sm_for<MODE_RAYS>(p, blocks);
+    case MODE_STEP: return blocks_per_sm_mode<MODE_STEP>(p, blocks);
+    case MODE_RESET: return blocks_per_sm_mode<MODE_RESET>(p, blocks);
+    case MODE_RENDER: return blocks_per_sm_mode<MODE_RENDER>(p, blocks);
+    case MODE_ROLLOUT: return blocks_per_sm_mode<MODE_ROLLOUT>(p, blocks);
+    default: return blocks_per_sm_mode<MODE_RAYS>(p, blocks);
   }
 }
 
 cudaError_t launch(const Params& p, int mode, int grid, cudaStream_t stream) {
-  const int smem = block_smem_bytes(p);
   switch (mode) {
-    case MODE_STEP: env_kernel<MODE_STEP><<<grid, kThreads, smem, stream>>>(p); break;
-    case MODE_RESET: env_kernel<MODE_RESET><<<grid, kThreads, smem, stream>>>(p); break;
-    case MODE_RENDER: env_kernel<MODE_RENDER><<<grid, kThreads, smem, stream>>>(p); break;
-    case MODE_ROLLOUT: env_kernel<MODE_ROLLOUT><<<grid, kThreads, smem, stream>>>(p); break;
-    default: env_kernel<MODE_RAYS><<<grid, kThreads, smem, stream>>>(p); break;
+    case MODE_STEP: launch_mode<MODE_STEP>(p, grid, stream); break;
+    case MODE_RESET: launch_mode<MODE_RESET>(p, grid, stream); break;
+    case MODE_RENDER: launch_mode<MODE_RENDER>(p, grid, stream); break;
+    case MODE_ROLLOUT: launch_mode<MODE_ROLLOUT>(p, grid, stream); break;
+    default: launch_mode<MODE_RAYS>(p, grid, stream); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t batch_blocks_per_sm(int mode, int cols, int warps, int smem_bytes, int* blocks) {
+  auto k = batch_kernel_of(mode, cols);
+  cudaError_t err = raise_smem_limit(k);
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, 32 * warps, smem_bytes);
+}
+
+cudaError_t batch_launch(const BatchParams& bp, int mode, int cols, int warps, int grid, cudaStream_t stream) {
+  auto k = batch_kernel_of(mode, cols);
+  k<<<grid, 32 * warps, (size_t)bp.warp_bytes * warps, stream>>>(bp);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,33 @@ def batched_keydoor_mazes(n_envs: int = 4096) -> dict:
     return maze_keydoor(n_envs=n_envs, map_side=32, seed=1, horizon=500)
 
 
+UNEVEN_SIDES = (16, 32, 64, 128)
+UNEVEN_FRAMES = (32, 64, 96, 128)
+
+
+def uneven_groups(n_envs: int = 16384, seed: int = 2, wall_prob: float = 0.3, max_sprites: int = 8,
+                  horizon: int = 0) -> list[dict]:
+    """Uneven batch: ``n_envs`` random-wall rooms (p = 0.3), each env's map side drawn
+    uniformly from {16, 32, 64, 128} and its square RGB frame size uniformly from
+    {32, 64, 96, 128}, 0-8 sprites per env (drawn at each episode start). Envs that
+    share (map side, frame size) form one group, i.e. one env config; the groups
+    come in (side, frame) order and each has its own seed."""
+    rng = np.random.default_rng([int(seed) & 0xFFFFFFFF, 0x4A59])
+    side = rng.integers(0, len(UNEVEN_SIDES), size=n_envs)
+    frame = rng.integers(0, len(UNEVEN_FRAMES), size=n_envs)
+    counts = np.bincount(side * len(UNEVEN_FRAMES) + frame, minlength=len(UNEVEN_SIDES) * len(UNEVEN_FRAMES))
+    groups = []
+    for k, n in enumerate(counts):
+        if n == 0:
+            continue
+        S, F = UNEVEN_SIDES[k // len(UNEVEN_FRAMES)], UNEVEN_FRAMES[k % len(UNEVEN_FRAMES)]
+        g = rooms(n_envs=int(n), map_side=S, wall_prob=wall_prob, seed=int(seed) * 1000 + k, max_sprites=max_sprites,
+                  frame_h=F, frame_w=F)
+        g["horizon"] = horizon
+        groups.append(g)
+    return groups
+
+
 def actions(seed: int, step: int, n_envs: int) -> np.ndarray:
     """Uniform random actions in [0, 7) for one step of ``n_envs`` envs (uint8)."""
     rng = np.random.default_rng([int(seed) & 0xFFFFFFFF, int(step) & 0xFFFFFFFF, 0x4A58])

@@ -36,6 +36,10 @@ SYMBOLS = [
     "jx_step_host_static", "jx_debug_rays",
     "jx_state_bytes", "jx_state_field", "jx_get_state", "jx_set_state", "jx_sync_status", "jx_launch_count",
     "jx_launch_shape", "jx_last_error",
+    "jx_tiling_default", "jx_batch_create", "jx_batch_destroy", "jx_batch_info", "jx_batch_group",
+    "jx_batch_set_tiling", "jx_batch_get_tiling", "jx_batch_launch_shape", "jx_batch_launch_count",
+    "jx_batch_reset", "jx_batch_step", "jx_batch_rollout", "jx_batch_render", "jx_batch_autotune",
+    "jx_batch_capture", "jx_graph_launch", "jx_graph_destroy",
 ]
 
 
@@ -64,6 +68,19 @@ class Config(ctypes.Structure):
         return c
 
 
+class Tiling(ctypes.Structure):
+    """Tile choices of the batched kernel (``jx_tiling``)."""
+
+    _fields_ = [("warps_per_block", ctypes.c_int32), ("cols_per_lane", ctypes.c_int32),
+                ("bits_min_side", ctypes.c_int32), ("max_rows_per_block", ctypes.c_int32)]
+
+    def as_tuple(self) -> tuple[int, int, int, int]:
+        return (self.warps_per_block, self.cols_per_lane, self.bits_min_side, self.max_rows_per_block)
+
+    def __repr__(self):
+        return "Tiling(warps_per_block=%d, cols_per_lane=%d, bits_min_side=%d, max_rows_per_block=%d)" % self.as_tuple()
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_2605_19926_gb300.build.build()")
@@ -86,6 +103,23 @@ def _load() -> ctypes.CDLL:
         "jx_sync_status": [P, P],
         "jx_launch_count": [P, P],
         "jx_launch_shape": [P, P, P, P],
+        "jx_tiling_default": [P],
+        "jx_batch_create": [P, i32, P, P],
+        "jx_batch_destroy": [P],
+        "jx_batch_info": [P, P, P],
+        "jx_batch_group": [P, i32, P, P],
+        "jx_batch_set_tiling": [P, P],
+        "jx_batch_get_tiling": [P, P],
+        "jx_batch_launch_shape": [P, P, P, P],
+        "jx_batch_launch_count": [P, P],
+        "jx_batch_reset": [P, P, P],
+        "jx_batch_step": [P, P, P, P, P, P],
+        "jx_batch_rollout": [P, P, P, i32, P, P, P],
+        "jx_batch_render": [P, P, P],
+        "jx_batch_autotune": [P, P, i32, i32, i32, P, P, P],
+        "jx_batch_capture": [P, i32, P, P, P, P, P],
+        "jx_graph_launch": [P, P],
+        "jx_graph_destroy": [P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -238,6 +272,135 @@ class Env:
         g, b, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(lib.jx_launch_shape(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(s)))
         return Shape(g.value, b.value, s.value)
+
+
+def default_tiling() -> Tiling:
+    t = Tiling()
+    _check(lib.jx_tiling_default(ctypes.byref(t)))
+    return t
+
+
+class Graph:
+    """A captured sequence of batched steps (``jx_batch_capture``)."""
+
+    def __init__(self, handle: ctypes.c_void_p, batch: "Batch"):
+        self._h = handle
+        self._batch = batch  # the graph must not outlive its batch
+
+    def launch(self, stream=None):
+        _check(lib.jx_graph_launch(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.jx_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Env groups of different sizes stepped in one launch (``jx_batch_*``).
+
+    The groups are ``Env`` objects; the batch keeps references to them. The
+    arrays of a batched call hold every group's envs in the order given:
+    ``group_slices`` gives each group's env range and frame byte range.
+    """
+
+    def __init__(self, groups: list, tiling: Tiling | None = None):
+        self.groups = list(groups)
+        arr = (ctypes.c_void_p * len(self.groups))(*[g._h.value for g in self.groups])
+        h = ctypes.c_void_p()
+        _check(lib.jx_batch_create(arr, len(self.groups), ctypes.byref(tiling) if tiling is not None else None,
+                                   ctypes.byref(h)))
+        self._h = h
+        n, f = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.jx_batch_info(self._h, ctypes.byref(n), ctypes.byref(f)))
+        self.n, self.frame_bytes = n.value, f.value
+        self.env_offsets, self.frame_offsets = [], []
+        for i in range(len(self.groups)):
+            eo, fo = ctypes.c_int64(), ctypes.c_int64()
+            _check(lib.jx_batch_group(self._h, i, ctypes.byref(eo), ctypes.byref(fo)))
+            self.env_offsets.append(eo.value)
+            self.frame_offsets.append(fo.value)
+
+    def group_slices(self, i: int) -> tuple[slice, slice]:
+        g = self.groups[i]
+        e0, f0 = self.env_offsets[i], self.frame_offsets[i]
+        return slice(e0, e0 + g.n), slice(f0, f0 + g.n * 3 * g.H * g.W)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.jx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def reset(self, frames, stream=None):
+        _check(lib.jx_batch_reset(self._h, _stream(stream), _ptr(frames)))
+
+    def step(self, actions, frames, rewards, dones, stream=None):
+        _check(lib.jx_batch_step(self._h, _stream(stream), _ptr(actions), _ptr(frames), _ptr(rewards), _ptr(dones)))
+
+    def rollout(self, actions, frames, rewards, dones, stream=None):
+        steps = int(actions.shape[0])
+        _check(lib.jx_batch_rollout(self._h, _stream(stream), _ptr(actions), steps, _ptr(frames), _ptr(rewards),
+                                    _ptr(dones)))
+
+    def render(self, frames, stream=None):
+        _check(lib.jx_batch_render(self._h, _stream(stream), _ptr(frames)))
+
+    @property
+    def tiling(self) -> Tiling:
+        t = Tiling()
+        _check(lib.jx_batch_get_tiling(self._h, ctypes.byref(t)))
+        return t
+
+    @tiling.setter
+    def tiling(self, t: Tiling):
+        _check(lib.jx_batch_set_tiling(self._h, ctypes.byref(t)))
+
+    def autotune(self, mode: int = 0, steps: int = 4, max_trials: int = 1000, stream=None):
+        """Time the tilings of the search space; keeps the fastest and resets every env.
+
+        Returns [(Tiling, ms_per_step)] in trial order (the default tiling first).
+        """
+        cap = max_trials
+        trials = (Tiling * cap)()
+        ms = (ctypes.c_float * cap)()
+        n = ctypes.c_int32()
+        _check(lib.jx_batch_autotune(self._h, _stream(stream), mode, steps, max_trials, ctypes.byref(n), trials, ms))
+        return [(trials[i], float(ms[i])) for i in range(n.value)]
+
+    def capture(self, actions, frames, rewards, dones) -> Graph:
+        steps = int(actions.shape[0])
+        h = ctypes.c_void_p()
+        _check(lib.jx_batch_capture(self._h, steps, _ptr(actions), _ptr(frames), _ptr(rewards), _ptr(dones),
+                                    ctypes.byref(h)))
+        return Graph(h, self)
+
+    def launch_shape(self) -> Shape:
+        g, b, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.jx_batch_launch_shape(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(s)))
+        return Shape(g.value, b.value, s.value)
+
+    def launch_count(self) -> int:
+        n = ctypes.c_uint64()
+        _check(lib.jx_batch_launch_count(self._h, ctypes.byref(n)))
+        return n.value
 
 
 def validate_config(cfg: dict) -> tuple[int, str]:

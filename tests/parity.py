@@ -228,3 +228,132 @@ def lockstep(run: Run, stats: Stats, n_steps: int, seed: int, first_step: int = 
         compare_frames(frames[idx], rr, stats)
         hits, perp = run.rays()
         compare_rays(hits[idx], perp[idx], rr, stats)
+
+
+def place_facing(f, e, cell, target, on_axis_frac):
+    """Put env e's agent in `cell`, facing the adjacent cell `target`."""
+    dx, dy = target[0] - cell[0], target[1] - cell[1]
+    f["cell_x"][e], f["cell_y"][e] = cell
+    f["frac_x"][e] = 0.5 if dx == 0 else (on_axis_frac if dx > 0 else 1.0 - on_axis_frac)
+    f["frac_y"][e] = 0.5 if dy == 0 else (on_axis_frac if dy > 0 else 1.0 - on_axis_frac)
+    f["theta0"][e] = np.float32(np.arctan2(dy, dx) % (2 * np.pi))
+    f["turn"][e] = 0
+
+
+def script_goal_and_door(f: dict, n: int, S: int):
+    """In the state fields f of n maze envs: even envs stand next to their goal
+    (key held) facing it, odd envs in front of their door (key held or not)
+    facing it. Returns (number of goal walkers, {odd env: door will open})."""
+    n_goal, opens = 0, {}
+    for e in range(n):
+        m = f["map"][e]
+        gx, gy, dxc, dyc = (int(v) for v in f["obj"][e][2:6])
+        if e % 2 == 0:
+            target = (gx, gy)
+            f["flags"][e] = 1
+            n_goal += 1
+        else:
+            target = (dxc, dyc)
+            f["flags"][e] = (e // 2) % 2
+        for ox, oy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            nb = (target[0] + ox, target[1] + oy)
+            if 0 <= nb[0] < S and 0 <= nb[1] < S and (m[nb[1], nb[0]] == 0 or
+                                                      (m[nb[1], nb[0]] == 5 and f["flags"][e])):
+                break
+        place_facing(f, e, nb, target, 0.45)
+        if e % 2:
+            key = (int(f["obj"][e][0]), int(f["obj"][e][1]))
+            opens[e] = bool(f["flags"][e]) or nb == key  # standing on the key picks it up at once
+    return n_goal, opens
+
+
+def check_door_crossings(before: dict, after: dict, opens: dict):
+    """A door walker moved at least one cell iff its door was open to it."""
+    for e, will_open in opens.items():
+        dist = abs(int(after["cell_x"][e]) - int(before["cell_x"][e])) + abs(
+            int(after["cell_y"][e]) - int(before["cell_y"][e]))
+        assert (dist >= 1) == will_open, e
+
+
+class BatchRun:
+    """A jx.Batch over fresh envs of the given group configs, with flat torch buffers."""
+
+    def __init__(self, cfgs: list, tiling=None, device: int = 0):
+        self.cfgs = cfgs
+        self.envs = [jx.Env(c, device) for c in cfgs]
+        self.ocfgs = [oracle_cfg(c) for c in cfgs]
+        self.batch = jx.Batch(self.envs, tiling)
+        dev = torch.device("cuda", device)
+        self.dev = dev
+        self.frames = torch.zeros(self.batch.frame_bytes, dtype=torch.uint8, device=dev)
+        self.rewards = torch.zeros(self.batch.n, dtype=torch.float32, device=dev)
+        self.dones = torch.zeros(self.batch.n, dtype=torch.uint8, device=dev)
+        self.actions = torch.zeros(self.batch.n, dtype=torch.uint8, device=dev)
+
+    def group_frames(self, frames: np.ndarray, i: int) -> np.ndarray:
+        """Group i's [n, H, W, 3] frames out of a flat frame array of one step."""
+        env = self.envs[i]
+        _, fs = self.batch.group_slices(i)
+        return frames[fs].reshape(env.n, env.H, env.W, 3)
+
+    def reset(self):
+        self.batch.reset(self.frames)
+        torch.cuda.synchronize()
+        return self.frames.cpu().numpy()
+
+    def step(self, actions: np.ndarray):
+        self.actions.copy_(torch.from_numpy(actions))
+        self.batch.step(self.actions, self.frames, self.rewards, self.dones)
+        torch.cuda.synchronize()
+        return self.frames.cpu().numpy(), self.rewards.cpu().numpy(), self.dones.cpu().numpy()
+
+    def states(self) -> list:
+        return [to_oracle(e, e.get_state()) for e in self.envs]
+
+
+def batch_check_reset(run: BatchRun, stats: Stats):
+    frames = run.reset()
+    for i, env in enumerate(run.envs):
+        gpu = to_oracle(env, env.get_state())
+        ref = oracle.generate(run.ocfgs[i], np.arange(env.n, dtype=np.int32), 0, nthreads=NTHREADS)
+        compare_generated(gpu, ref, env.S, env.K, f"at batch reset, group {i}")
+        compare_frames(run.group_frames(frames, i), oracle.render(run.ocfgs[i], gpu, nthreads=NTHREADS), stats)
+
+
+def batch_lockstep(run: BatchRun, stats: Stats, n_steps: int, seed: int, first_step: int = 0, check_every: int = 1,
+                   action_fn=inputs.actions):
+    """lockstep() for every group of a batch stepped in one launch per step."""
+    N = run.batch.n
+    for s in range(first_step, first_step + n_steps):
+        a = action_fn(seed, s, N)
+        check = (s - first_step) % check_every == 0
+        if check:
+            prev = run.states()
+        frames, rewards, dones = run.step(a)
+        if not check:
+            continue
+        cur = run.states()
+        for i, env in enumerate(run.envs):
+            es, _ = run.batch.group_slices(i)
+            idx = np.arange(env.n, dtype=np.int32)
+            ref = oracle.step(run.ocfgs[i], idx, prev[i], a[es], nthreads=NTHREADS)
+            ev = ref["events"]
+            ok = (ev & oracle.EV_NEAR_TIE) == 0
+            stats.env_steps += env.n
+            stats.near_ties += int((~ok).sum())
+            stats.key_events += int(((ev & oracle.EV_KEY) != 0)[ok].sum())
+            stats.goal_events += int(((ev & oracle.EV_GOAL) != 0)[ok].sum())
+            assert (rewards[es][ok] == ref["rewards"][ok]).all(), f"rewards differ, group {i} step {s}"
+            assert (dones[es][ok] == ref["dones"][ok]).all(), f"dones differ, group {i} step {s}"
+            done = (ref["dones"] == 1) & ok
+            stats.resets += int(done.sum())
+            if done.any():
+                compare_generated(cur[i][done], prev[i][done], env.S, env.K, f"auto-reset, group {i} step {s}")
+            live = ok & ~done
+            for name in ("turn", "t", "episode", "has_key"):
+                assert (cur[i][name][live] == prev[i][name][live]).all(), f"{name}, group {i} step {s}"
+            for name in ("x", "y"):
+                err = np.abs(cur[i][name][live] - prev[i][name][live])
+                assert err.max(initial=0.0) <= TOL_POSE, f"{name} err {err.max()}, group {i} step {s}"
+            rr = oracle.render(run.ocfgs[i], cur[i], nthreads=NTHREADS)
+            compare_frames(run.group_frames(frames, i), rr, stats)

@@ -95,3 +95,37 @@ def test_valid_config_without_gpu_fails_loudly(jx):
     assert st == jx.ECUDA and msg
     with pytest.raises(jx.JxError):
         jx.Env(inputs.single_env_rooms())
+
+
+def test_tiling_struct_and_default(jx):
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct \{([^}]*)\} jx_tiling;", text).group(1)
+    names = re.findall(r"^\s*int32_t\s+(\w+);", body, re.M)
+    assert names == [f[0] for f in jx.Tiling._fields_]
+    assert jx.default_tiling().as_tuple() == (1, 1, 128, 16)
+
+
+def test_batch_arguments_checked_before_cuda(jx):
+    h = ctypes.c_void_p()
+    assert jx.lib.jx_batch_create(None, 1, None, ctypes.byref(h)) == jx.EINVAL
+    arr = (ctypes.c_void_p * 1)(None)
+    assert jx.lib.jx_batch_create(arr, 1, None, ctypes.byref(h)) == jx.EINVAL
+    assert jx.lib.jx_batch_create(arr, 0, None, ctypes.byref(h)) == jx.EINVAL
+    assert jx.lib.jx_batch_create(arr, 33, None, ctypes.byref(h)) == jx.EINVAL
+    assert jx.lib.jx_batch_step(None, None, None, None, None, None) == jx.EINVAL
+    assert jx.lib.jx_graph_launch(None, None) == jx.EINVAL
+    assert jx.lib.jx_batch_destroy(None) == jx.OK and jx.lib.jx_graph_destroy(None) == jx.OK
+
+
+def test_uneven_workload_groups():
+    groups = inputs.uneven_groups()
+    assert sum(g["n_envs"] for g in groups) == 16384
+    assert len(groups) == 16
+    assert {(g["map_side"], g["frame_w"]) for g in groups} == {(s, f) for s in inputs.UNEVEN_SIDES
+                                                               for f in inputs.UNEVEN_FRAMES}
+    for g in groups:
+        assert g["frame_h"] == g["frame_w"] and g["task"] == inputs.TASK_ROOMS
+        assert g["wall_prob"] == 0.3 and g["max_sprites"] == 8
+        assert 800 < g["n_envs"] < 1250  # 1024 expected per (side, frame) pair
+    assert len({g["seed"] for g in groups}) == 16
+    assert inputs.uneven_groups() == groups  # seeded

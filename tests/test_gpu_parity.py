@@ -5,8 +5,8 @@ import torch
 
 import oracle
 from paper_2605_19926_gb300 import inputs
-from parity import (NTHREADS, Run, Stats, check_reset, compare_frames, compare_rays, forward_biased_actions, lockstep,
-                    to_oracle)
+from parity import (NTHREADS, Run, Stats, check_door_crossings, check_reset, compare_frames, compare_rays,
+                    forward_biased_actions, lockstep, script_goal_and_door, to_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -188,16 +188,6 @@ def test_same_seed_same_frames():
         assert (fa == fb).all() and (ra == rb).all() and (da == db).all()
 
 
-def _place_facing(f, e, cell, target, on_axis_frac):
-    """Put env e's agent in `cell`, facing the adjacent cell `target`."""
-    dx, dy = target[0] - cell[0], target[1] - cell[1]
-    f["cell_x"][e], f["cell_y"][e] = cell
-    f["frac_x"][e] = 0.5 if dx == 0 else (on_axis_frac if dx > 0 else 1.0 - on_axis_frac)
-    f["frac_y"][e] = 0.5 if dy == 0 else (on_axis_frac if dy > 0 else 1.0 - on_axis_frac)
-    f["theta0"][e] = np.float32(np.arctan2(dy, dx) % (2 * np.pi))
-    f["turn"][e] = 0
-
-
 def test_scripted_goal_reach_and_door_crossing():
     """Agents placed next to their goal (even envs) or in front of their door
     (odd envs, key held or not) walk forward; checked in lockstep."""
@@ -206,36 +196,13 @@ def test_scripted_goal_reach_and_door_crossing():
     run.reset()
     blob = run.env.get_state()
     f = run.env.fields(blob)
-    S = 16
-    n_goal = 0
-    opens = {}
-    for e in range(32):
-        m = f["map"][e]
-        gx, gy, dxc, dyc = (int(v) for v in f["obj"][e][2:6])
-        if e % 2 == 0:
-            target = (gx, gy)
-            f["flags"][e] = 1
-            n_goal += 1
-        else:
-            target = (dxc, dyc)
-            f["flags"][e] = (e // 2) % 2
-        for ox, oy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
-            nb = (target[0] + ox, target[1] + oy)
-            if 0 <= nb[0] < S and 0 <= nb[1] < S and (m[nb[1], nb[0]] == 0 or
-                                                      (m[nb[1], nb[0]] == 5 and f["flags"][e])):
-                break
-        _place_facing(f, e, nb, target, 0.45)
-        key = (int(f["obj"][e][0]), int(f["obj"][e][1]))
-        opens[e] = bool(f["flags"][e]) or nb == key  # standing on the key picks it up at once
+    n_goal, opens = script_goal_and_door(f, 32, 16)
     run.env.set_state(blob)
     stats = Stats()
     lockstep(run, stats, 20, seed=0, action_fn=lambda seed, step, n: np.ones(n, np.uint8))
     stats.check()
     assert stats.goal_events == n_goal and stats.resets == n_goal, stats
-    after = run.env.fields(run.env.get_state())
-    for e in range(1, 32, 2):
-        dist = abs(int(after["cell_x"][e]) - int(f["cell_x"][e])) + abs(int(after["cell_y"][e]) - int(f["cell_y"][e]))
-        assert (dist >= 1) == opens[e], e
+    check_door_crossings(f, run.env.fields(run.env.get_state()), opens)
 
 
 def _rollout_vs_steps(cfg, T, seed, warm=0):
