@@ -319,6 +319,126 @@ def run_uneven(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serve(args):
+    """Serving: 64 actor groups submit step requests with Poisson arrivals
+    (mean gap 2 ms) to the continuous-batching server. Each group runs
+    sessions of `--session-steps` requests; a session's batch is log-uniform
+    in [16, 4096] envs of 32x32 or 64x64 key-door mazes, 64x64 RGB. Sessions
+    are admitted under a 40 GB state+frame budget. Reports p50 / p99 request
+    latency (submit to completion) and aggregate env-steps/s."""
+    import concurrent.futures as cf
+    import heapq
+
+    import torch
+
+    from paper_2605_19926_gb300 import build, inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2605_19926_gb300 import jx
+
+    seed = 3 + rank
+    n_actors, duration, warm = args.actors, args.serve_seconds, min(2.0, args.serve_seconds / 4)
+    server = jx.Server(budget_bytes=int(args.budget_gb * 1e9), max_sessions=4 * n_actors, max_inflight=4,
+                       max_map_side=64, device=local)
+    pool = cf.ThreadPoolExecutor(max_workers=4)
+    session = [None] * n_actors  # open Session or None
+    opening = [None] * n_actors  # future of a pending open
+    left = [0] * n_actors
+    k_next = [0] * n_actors
+    acts = [None] * n_actors
+    gaps = [inputs.arrival_gaps(seed, a, 1 << 16) for a in range(n_actors)]
+    gi = [0] * n_actors
+    heap = [(float(gaps[a][0]), a) for a in range(n_actors)]
+    heapq.heapify(heap)
+    for a in range(n_actors):
+        gi[a] = 1
+    t0 = time.perf_counter()
+    lat_mark = None
+    stats_mark = None
+    submitted = 0
+    while heap:
+        t_rel, a = heapq.heappop(heap)
+        if t_rel > duration:
+            break
+        while time.perf_counter() - t0 < t_rel:
+            pass
+        if lat_mark is None and t_rel >= warm:
+            server.latencies()  # drop the warm-up requests
+            stats_mark = (time.perf_counter(), server.stats())
+            lat_mark = True
+        if session[a] is None and opening[a] is not None and opening[a].done():
+            session[a] = opening[a].result()
+            opening[a] = None
+            if session[a] is not None:
+                left[a] = args.session_steps
+                n = session[a].n
+                acts[a] = np.random.default_rng([seed, a, k_next[a]]).integers(0, 7, size=(8, n), dtype=np.uint8)
+        if session[a] is not None:
+            session[a].submit(acts[a][left[a] % 8])
+            submitted += 1
+            left[a] -= 1
+            if left[a] == 0:
+                session[a].close()
+                session[a] = None
+        elif opening[a] is None:
+            cfg = inputs.serving_session(seed, a, k_next[a])
+            k_next[a] += 1
+            opening[a] = pool.submit(server.try_open, cfg)
+        heapq.heappush(heap, (t_rel + float(gaps[a][gi[a] % len(gaps[a])]), a))
+        gi[a] += 1
+    t_end = time.perf_counter()
+    st_end = server.stats()
+    lat = server.latencies()
+    pool.shutdown(wait=True)
+    t_stats0, st0 = stats_mark
+    window = t_end - t_stats0
+    env_steps = st_end["env_steps"] - st0["env_steps"]
+    reqs = st_end["requests_done"] - st0["requests_done"]
+    launches = st_end["launches"] - st0["launches"]
+    groups = st_end["groups_launched"] - st0["groups_launched"]
+    server.close()
+    value = env_steps / window
+    p50 = float(np.percentile(lat, 50)) * 1e3 if len(lat) else None
+    p99 = float(np.percentile(lat, 99)) * 1e3 if len(lat) else None
+    tot = max_over_ranks(window * 1e3, world, torch.device("cuda", local))
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {
+        "metric": "env-steps/s incl. render (frames/s), served requests", "value": value * world,
+        "unit": "env-steps/s", "n_gpus": world, "steps": int(reqs), "warmup": 0,
+        "ms_per_step": tot / max(1, reqs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"{n_actors} actor groups, Poisson arrivals (mean gap 2 ms), sessions of "
+                               f"{args.session_steps} requests, batch log-uniform in [16, 4096] envs, 32x32 or 64x64 "
+                               "key-door mazes, 64x64 RGB, continuous batching",
+                   "budget_gb": args.budget_gb, "seconds": duration, "measured_seconds": window,
+                   "max_inflight_launches": 4},
+        "p50_step_ms": p50, "p99_step_ms": p99,
+        "requests_per_s": reqs / window, "submitted_per_s": submitted / (t_end - t0),
+        "mean_sessions_per_launch": groups / max(1, launches), "launches": int(launches),
+        "server": {k: st_end[k] for k in ("peak_bytes_in_use", "budget_bytes", "peak_sessions",
+                                          "peak_inflight_launches", "rejected_opens")},
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": value * world, "unit": "env-steps/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": 0,
+                "how": "host actions submitted per request through jx_server_submit; results stay on the device"},
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,12 +455,20 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1000)
     ap.add_argument("--ring-slots", type=int, default=GRAPH_STEPS,
                     help="rollout buffer slots = launches per CUDA graph (smaller for profiling captures)")
-    ap.add_argument("--workload", default="mazes", choices=["mazes", "uneven"],
-                    help="mazes: 4096 key-door mazes (the headline); uneven: 16,384 envs of mixed sizes")
+    ap.add_argument("--workload", default="mazes", choices=["mazes", "uneven", "serve"],
+                    help="mazes: 4096 key-door mazes (the headline); uneven: 16,384 envs of mixed sizes; "
+                         "serve: the continuous-batching step server under Poisson request arrivals")
+    ap.add_argument("--actors", type=int, default=64)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--session-steps", type=int, default=250)
+    ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--uneven-slots", type=int, default=16, help="steps per rollout launch of the uneven batch")
     ap.add_argument("--tune-trials", type=int, default=1000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.workload == "serve" and args.impl == "jx":
+        run_serve(args)
+        return
     if args.workload == "uneven" and args.impl == "jx":
         if args.steps == ap.get_default("steps"):
             args.steps = 512

@@ -108,8 +108,21 @@ typedef struct {
  * the handle, owned by the caller until jx_destroy. */
 jx_status jx_create(const jx_config* cfg, int device, jx_env** out);
 
+/* Device bytes jx_create allocates for cfg on `device`: one block holding
+ * the state, the per-env tables and the maze work space. Validates cfg like
+ * jx_create. */
+jx_status jx_env_bytes(const jx_config* cfg, int device, size_t* bytes);
+
+/* jx_create with the env's device block placed in caller memory d_mem
+ * (256-byte aligned, at least jx_env_bytes bytes, on `device`) instead of
+ * allocated: for callers that manage device memory themselves (the step
+ * server's arena). The env never frees d_mem. */
+jx_status jx_create_in(const jx_config* cfg, int device, void* d_mem, size_t bytes, jx_env** out);
+
 /* Free the env's device memory and the handle. NULL is accepted. Waits for
- * the env's outstanding work on the device first. */
+ * the env's outstanding work on the device first, unless the env lives in
+ * caller memory (jx_create_in) and has no host-step staging, in which case
+ * it touches the device not at all. */
 jx_status jx_destroy(jx_env* env);
 
 /* Start episode 0 of every environment: generate its map, spawn, heading and
@@ -319,6 +332,81 @@ jx_status jx_batch_capture(jx_batch* batch, int32_t steps, const uint8_t* d_acti
                            float* d_rewards, uint8_t* d_dones, jx_graph** out);
 jx_status jx_graph_launch(jx_graph* graph, void* stream);
 jx_status jx_graph_destroy(jx_graph* graph);
+
+/* ------------------------------------------------------------------------
+ * Step server: continuous batching of step requests.
+ *
+ * Clients (actor groups) open sessions: a session is a group of envs with one
+ * config whose state, frames, rewards and dones stay in device memory for the
+ * session's life. They submit step requests (one step of all the session's
+ * envs, actions from host memory) as they arrive. A dispatcher thread inside
+ * the server merges the oldest pending request of every idle session (up to
+ * 32 sessions and 2^20 envs per launch) into one launch of the batched
+ * persistent kernel (see jx_batch_*), on one of `max_inflight` launch slots,
+ * each with its own stream; requests that arrive while launches run go into
+ * the next launch on a free slot, so their work overlaps on the device. A
+ * session has at most one request on the device; its later requests wait in
+ * its FIFO. Results equal those of stepping the session's env alone with
+ * jx_step, bit for bit.
+ *
+ * Admission: sessions live in one device arena of budget_bytes (allocated at
+ * creation). jx_server_open returns JX_EBUDGET when the session's block does
+ * not fit in the free arena or all max_sessions slots are taken; the block
+ * returns to the arena when the session is closed and drained, so a later
+ * open succeeds. The server's own launch slots (streams, maze work space,
+ * action staging) are allocated outside the budget. */
+typedef struct jx_server jx_server;
+
+typedef struct {
+  uint64_t requests_submitted;
+  uint64_t requests_done;
+  uint64_t launches;         /* batched kernel launches */
+  uint64_t env_steps;        /* env steps of all launches */
+  uint64_t groups_launched;  /* sum over launches of the sessions in the launch */
+  uint64_t rejected_opens;   /* JX_EBUDGET answers of jx_server_open */
+  uint64_t budget_bytes;
+  uint64_t bytes_in_use;
+  uint64_t peak_bytes_in_use;
+  int32_t sessions_open;
+  int32_t peak_sessions;
+  int32_t inflight_launches;
+  int32_t peak_inflight_launches;
+} jx_server_counters;
+
+/* Create a server on `device`: a budget_bytes session arena, max_sessions
+ * session slots, max_inflight (1..16) launch slots, maps up to max_map_side,
+ * the batched kernel's tiling (NULL = jx_tiling_default). Starts the
+ * dispatcher thread. */
+jx_status jx_server_create(int device, uint64_t budget_bytes, int32_t max_sessions, int32_t max_inflight,
+                           int32_t max_map_side, const jx_tiling* tiling, jx_server** out);
+/* Stop the dispatcher, wait for the device, free every session and the arena. */
+jx_status jx_server_destroy(jx_server* server);
+/* Admit a session of cfg.n_envs envs: create them in the arena and reset
+ * them (episode 0; the first frames are in the session's frame buffer when
+ * this returns). JX_EBUDGET: no room now (retry after a close). */
+jx_status jx_server_open(jx_server* server, const jx_config* cfg, int32_t* session);
+/* Close a session: no further submits; its memory returns to the arena once
+ * its queued requests have run. */
+jx_status jx_server_close(jx_server* server, int32_t session);
+/* The session's env handle and its device output buffers (frames
+ * [n][H][W][3], rewards [n], dones [n]), valid until close. After a request's
+ * wait returns they hold that step's results, until the session's next
+ * request runs. */
+jx_status jx_server_session(jx_server* server, int32_t session, jx_env** env, uint8_t** d_frames,
+                            float** d_rewards, uint8_t** d_dones);
+/* Queue one step request: h_actions [n] (copied before returning). *ticket
+ * identifies it for jx_server_wait. Never blocks on the device. */
+jx_status jx_server_submit(jx_server* server, int32_t session, const uint8_t* h_actions, uint64_t* ticket);
+/* Wait (at most timeout_s seconds: JX_ETIMEOUT) until the request's step has
+ * completed on the device. */
+jx_status jx_server_wait(jx_server* server, uint64_t ticket, double timeout_s);
+/* Hold (paused != 0) or resume the dispatcher: while held, submitted
+ * requests queue and launches already on the device complete. */
+jx_status jx_server_pause(jx_server* server, int32_t paused);
+jx_status jx_server_stats(jx_server* server, jx_server_counters* out);
+/* Move up to `capacity` latencies (seconds from submit to completion seen
+ * by the dispatcher) of completed requests, oldest first, into out. */
+jx_status jx_server_latencies(jx_server* server, double* out, uint64_t capacity, uint64_t* count);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* jx_last_error(void);

@@ -148,9 +148,17 @@ extern "C" {
 
 const char* jx_last_error(void) { return jx::host::g_last_error.c_str(); }
 
-jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
-  if (!out) return fail(JX_EINVAL, "out is NULL");
-  *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// jx_create / jx_env_bytes / jx_create_in. Everything that does not need
+// device memory is decided first (layout, tables, launch shape); then the
+// env's one device block (state | aux | maze scratch) is allocated, or placed
+// in the caller's memory `ext`. With `bytes_only` the block size is returned
+// in *bytes and nothing is kept.
+jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_bytes, bool bytes_only, size_t* bytes,
+                      jx_env** out) {
   jx_status st = validate(cfg);
   if (st != JX_OK) return st;
   int ndev = 0;
@@ -174,53 +182,8 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
   // aux block: error word | turn table | column table
   const size_t aux_err = 0, aux_turn = 256, aux_col = align256(aux_turn + 8 * (size_t)tpr);
   const size_t aux_bytes = align256(aux_col + 4 * (size_t)W);
-  if ((err = cudaMalloc(&env->state, env->state_bytes)) != cudaSuccess ||
-      (err = cudaMalloc(&env->aux, aux_bytes)) != cudaSuccess) {
-    jx_destroy(env);
-    return fail(JX_ENOMEM, "cudaMalloc of %zu state bytes failed: %s", env->state_bytes, cudaGetErrorString(err));
-  }
-  cudaMemset(env->state, 0, env->state_bytes);
-  {
-    // per-env constant tables, computed in double and rounded once
-    std::string host(aux_bytes, '\0');
-    const double two_pi = 2.0 * 3.14159265358979323846;
-    float* turn = reinterpret_cast<float*>(&host[aux_turn]);
-    for (int k = 0; k < tpr; ++k) {
-      double a = two_pi * (double)k / (double)tpr;
-      turn[2 * k] = (float)std::cos(a);
-      turn[2 * k + 1] = (float)std::sin(a);
-    }
-    float* colk = reinterpret_cast<float*>(&host[aux_col]);
-    const double t = std::tan(0.5 * c.fov_deg * 3.14159265358979323846 / 180.0);
-    for (int col = 0; col < W; ++col) colk[col] = (float)((2.0 * (col + 0.5) / W - 1.0) * t);
-    err = cudaMemcpy(env->aux, host.data(), aux_bytes, cudaMemcpyHostToDevice);
-    if (err != cudaSuccess) {
-      jx_destroy(env);
-      return cuda_fail(err, "cudaMemcpy of tables");
-    }
-  }
 
   jx::Params& p = env->base;
-  p.st.cell_x = field_ptr<int16_t>(env, JX_F_CELL_X);
-  p.st.cell_y = field_ptr<int16_t>(env, JX_F_CELL_Y);
-  p.st.frac_x = field_ptr<float>(env, JX_F_FRAC_X);
-  p.st.frac_y = field_ptr<float>(env, JX_F_FRAC_Y);
-  p.st.theta0 = field_ptr<float>(env, JX_F_THETA0);
-  p.st.turn = field_ptr<int16_t>(env, JX_F_TURN);
-  p.st.t = field_ptr<int32_t>(env, JX_F_T);
-  p.st.episode = field_ptr<uint32_t>(env, JX_F_EPISODE);
-  p.st.flags = field_ptr<uint8_t>(env, JX_F_FLAGS);
-  p.st.obj = field_ptr<int16_t>(env, JX_F_OBJ);
-  p.st.nspr = field_ptr<uint8_t>(env, JX_F_NSPR);
-  p.st.spr_x = field_ptr<float>(env, JX_F_SPR_X);
-  p.st.spr_y = field_ptr<float>(env, JX_F_SPR_Y);
-  p.st.spr_type = field_ptr<uint8_t>(env, JX_F_SPR_TYPE);
-  p.st.map = field_ptr<uint8_t>(env, JX_F_MAP);
-  p.st.cos0 = field_ptr<float>(env, JX_F_COS0);
-  p.st.sin0 = field_ptr<float>(env, JX_F_SIN0);
-  p.err = reinterpret_cast<uint32_t*>(env->aux + aux_err);
-  p.turn_cs = reinterpret_cast<const float2*>(env->aux + aux_turn);
-  p.col_k = reinterpret_cast<const float*>(env->aux + aux_col);
   p.n = c.n_envs;
   p.S = c.map_side;
   p.H = c.frame_h;
@@ -242,7 +205,7 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
 
   cudaDeviceProp prop;
   if ((err = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) {
-    jx_destroy(env);
+    delete env;
     return cuda_fail(err, "cudaGetDeviceProperties");
   }
   env->num_sms = prop.multiProcessorCount;
@@ -255,23 +218,24 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
   jx::host::choose_rows(p, 16, jx::kWarpsPerBlock, jx::kMinBlocksPerSm, prop.sharedMemPerMultiprocessor,
                         prop.reservedSharedMemPerBlock);
   env->smem_block = jx::block_smem_bytes(p);
-  if ((size_t)env->smem_block > prop.sharedMemPerBlockOptin) {
-    jx_destroy(env);
-    return fail(JX_EINVAL, "configuration needs %d bytes of shared memory per block (limit %zu)", env->smem_block,
+  const int smem_block = env->smem_block;
+  if ((size_t)smem_block > prop.sharedMemPerBlockOptin) {
+    delete env;
+    return fail(JX_EINVAL, "configuration needs %d bytes of shared memory per block (limit %zu)", smem_block,
                 prop.sharedMemPerBlockOptin);
   }
   int bps = 0;
   for (int mode = 0; mode < 5; ++mode) {
     int b = 0;
     if ((err = jx::kernel_blocks_per_sm(p, mode, &b)) != cudaSuccess) {
-      jx_destroy(env);
+      delete env;
       return cuda_fail(err, "occupancy query");
     }
     bps = mode == 0 || b < bps ? b : bps;
   }
   if (bps < 1) {
-    jx_destroy(env);
-    return fail(JX_EINVAL, "kernel cannot be resident with %d bytes of shared memory", env->smem_block);
+    delete env;
+    return fail(JX_EINVAL, "kernel cannot be resident with %d bytes of shared memory", smem_block);
   }
   env->blocks_per_sm = bps;
   const long need = (c.n_envs + jx::kWarpsPerBlock - 1) / jx::kWarpsPerBlock;
@@ -279,15 +243,81 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
   env->grid = (int)(need < cap ? need : cap);
   // maze work space: one slot per warp of the grid
   p.gen_scratch_stride = jx::gen_scratch_bytes(c.task, c.map_side);
-  if (p.gen_scratch_stride > 0) {
-    size_t bytes = p.gen_scratch_stride * (size_t)env->grid * jx::kWarpsPerBlock;
-    if ((err = cudaMalloc(&env->scratch, bytes)) != cudaSuccess) {
+  const size_t scratch_bytes = p.gen_scratch_stride * (size_t)env->grid * jx::kWarpsPerBlock;
+
+  // the device block: state | aux | scratch
+  const size_t off_aux = align256(env->state_bytes), off_scratch = off_aux + aux_bytes;
+  const size_t total = off_scratch + align256(scratch_bytes);
+  if (bytes) *bytes = total;
+  if (bytes_only) {
+    delete env;
+    return JX_OK;
+  }
+  if (ext) {
+    if (ext_bytes < total || (reinterpret_cast<uintptr_t>(ext) & 255u)) {
+      delete env;
+      return fail(JX_EINVAL, "external block must be 256-byte aligned and hold %zu bytes (got %zu)", total, ext_bytes);
+    }
+    env->mem = static_cast<uint8_t*>(ext);
+    env->owns_mem = false;
+  } else {
+    if ((err = cudaMalloc(&env->mem, total)) != cudaSuccess) {
+      env->mem = nullptr;
+      delete env;
+      return fail(JX_ENOMEM, "cudaMalloc of %zu env bytes failed: %s", total, cudaGetErrorString(err));
+    }
+    env->owns_mem = true;
+  }
+  env->mem_bytes = total;
+  env->state = env->mem;
+  env->aux = env->mem + off_aux;
+  env->scratch = scratch_bytes ? env->mem + off_scratch : nullptr;
+  if ((err = cudaMemset(env->state, 0, env->state_bytes)) != cudaSuccess) {
+    jx_destroy(env);
+    return cuda_fail(err, "cudaMemset of the state");
+  }
+  {
+    // per-env constant tables, computed in double and rounded once
+    std::string host(aux_bytes, '\0');
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    float* turn = reinterpret_cast<float*>(&host[aux_turn]);
+    for (int k = 0; k < tpr; ++k) {
+      double a = two_pi * (double)k / (double)tpr;
+      turn[2 * k] = (float)std::cos(a);
+      turn[2 * k + 1] = (float)std::sin(a);
+    }
+    float* colk = reinterpret_cast<float*>(&host[aux_col]);
+    const double t = std::tan(0.5 * c.fov_deg * 3.14159265358979323846 / 180.0);
+    for (int col = 0; col < W; ++col) colk[col] = (float)((2.0 * (col + 0.5) / W - 1.0) * t);
+    err = cudaMemcpy(env->aux, host.data(), aux_bytes, cudaMemcpyHostToDevice);
+    if (err != cudaSuccess) {
       jx_destroy(env);
-      return fail(JX_ENOMEM, "cudaMalloc of %zu scratch bytes failed", bytes);
+      return cuda_fail(err, "cudaMemcpy of tables");
     }
   }
+  p.st.cell_x = field_ptr<int16_t>(env, JX_F_CELL_X);
+  p.st.cell_y = field_ptr<int16_t>(env, JX_F_CELL_Y);
+  p.st.frac_x = field_ptr<float>(env, JX_F_FRAC_X);
+  p.st.frac_y = field_ptr<float>(env, JX_F_FRAC_Y);
+  p.st.theta0 = field_ptr<float>(env, JX_F_THETA0);
+  p.st.turn = field_ptr<int16_t>(env, JX_F_TURN);
+  p.st.t = field_ptr<int32_t>(env, JX_F_T);
+  p.st.episode = field_ptr<uint32_t>(env, JX_F_EPISODE);
+  p.st.flags = field_ptr<uint8_t>(env, JX_F_FLAGS);
+  p.st.obj = field_ptr<int16_t>(env, JX_F_OBJ);
+  p.st.nspr = field_ptr<uint8_t>(env, JX_F_NSPR);
+  p.st.spr_x = field_ptr<float>(env, JX_F_SPR_X);
+  p.st.spr_y = field_ptr<float>(env, JX_F_SPR_Y);
+  p.st.spr_type = field_ptr<uint8_t>(env, JX_F_SPR_TYPE);
+  p.st.map = field_ptr<uint8_t>(env, JX_F_MAP);
+  p.st.cos0 = field_ptr<float>(env, JX_F_COS0);
+  p.st.sin0 = field_ptr<float>(env, JX_F_SIN0);
+  p.err = reinterpret_cast<uint32_t*>(env->aux + aux_err);
+  p.turn_cs = reinterpret_cast<const float2*>(env->aux + aux_turn);
+  p.col_k = reinterpret_cast<const float*>(env->aux + aux_col);
   p.gen_scratch = env->scratch;
-  if ((err = cudaDeviceSynchronize()) != cudaSuccess) {
+  // the memset and the table copy are done before the handle is returned
+  if ((err = cudaStreamSynchronize(0)) != cudaSuccess) {
     jx_destroy(env);
     return cuda_fail(err, "create");
   }
@@ -295,14 +325,36 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
   return JX_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
+  if (!out) return fail(JX_EINVAL, "out is NULL");
+  *out = nullptr;
+  return create_impl(cfg, device, nullptr, 0, false, nullptr, out);
+}
+
+jx_status jx_env_bytes(const jx_config* cfg, int device, size_t* bytes) {
+  if (!bytes) return fail(JX_EINVAL, "bytes is NULL");
+  *bytes = 0;
+  return create_impl(cfg, device, nullptr, 0, true, bytes, nullptr);
+}
+
+jx_status jx_create_in(const jx_config* cfg, int device, void* d_mem, size_t bytes, jx_env** out) {
+  if (!out) return fail(JX_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d_mem) return fail(JX_EINVAL, "d_mem is NULL");
+  return create_impl(cfg, device, d_mem, bytes, false, nullptr, out);
+}
+
 jx_status jx_destroy(jx_env* env) {
   if (!env) return JX_OK;
   {
     DeviceGuard g(env->device);
-    cudaDeviceSynchronize();
-    if (env->state) cudaFree(env->state);
-    if (env->aux) cudaFree(env->aux);
-    if (env->scratch) cudaFree(env->scratch);
+    // an env in caller memory frees nothing on the device: no synchronisation
+    if (env->owns_mem || env->stage) cudaDeviceSynchronize();
+    if (env->owns_mem && env->mem) cudaFree(env->mem);
     if (env->stage) cudaFree(env->stage);
   }
   delete env;

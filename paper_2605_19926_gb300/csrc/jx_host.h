@@ -18,6 +18,10 @@ struct jx_env {
   int grid = 0;
   int smem_block = 0;
   jx::Params base{};
+  // one device block: state | aux | scratch (owned, or in the caller's memory)
+  uint8_t* mem = nullptr;
+  size_t mem_bytes = 0;
+  bool owns_mem = true;
   // struct-of-arrays state block
   uint8_t* state = nullptr;
   size_t state_bytes = 0;

@@ -81,6 +81,22 @@ def uneven_groups(n_envs: int = 16384, seed: int = 2, wall_prob: float = 0.3, ma
     return groups
 
 
+def serving_session(seed: int, actor: int, k: int) -> dict:
+    """Session k of actor group `actor` in the serving workload: a batch of envs
+    log-uniform in [16, 4096], 32 x 32 or 64 x 64 key-door mazes (even), 64 x 64
+    RGB frames, its own seed."""
+    rng = np.random.default_rng([int(seed) & 0xFFFFFFFF, int(actor), int(k), 0x4A5A])
+    n = int(round(float(np.exp(rng.uniform(np.log(16.0), np.log(4096.0))))))
+    side = int(rng.choice([32, 64]))
+    return maze_keydoor(n_envs=n, map_side=side, seed=int(seed) * 1_000_003 + actor * 10_007 + k, horizon=500)
+
+
+def arrival_gaps(seed: int, actor: int, n: int, mean_s: float = 2e-3) -> np.ndarray:
+    """Exponential gaps (a Poisson process of mean gap `mean_s`) between one actor group's step requests."""
+    rng = np.random.default_rng([int(seed) & 0xFFFFFFFF, int(actor), 0x4A5B])
+    return rng.exponential(mean_s, size=n)
+
+
 def actions(seed: int, step: int, n_envs: int) -> np.ndarray:
     """Uniform random actions in [0, 7) for one step of ``n_envs`` envs (uint8)."""
     rng = np.random.default_rng([int(seed) & 0xFFFFFFFF, int(step) & 0xFFFFFFFF, 0x4A58])

@@ -40,6 +40,9 @@ SYMBOLS = [
     "jx_batch_set_tiling", "jx_batch_get_tiling", "jx_batch_launch_shape", "jx_batch_launch_count",
     "jx_batch_reset", "jx_batch_step", "jx_batch_rollout", "jx_batch_render", "jx_batch_autotune",
     "jx_batch_capture", "jx_graph_launch", "jx_graph_destroy",
+    "jx_env_bytes", "jx_create_in",
+    "jx_server_create", "jx_server_destroy", "jx_server_open", "jx_server_close", "jx_server_session",
+    "jx_server_submit", "jx_server_wait", "jx_server_pause", "jx_server_stats", "jx_server_latencies",
 ]
 
 
@@ -81,6 +84,20 @@ class Tiling(ctypes.Structure):
         return "Tiling(warps_per_block=%d, cols_per_lane=%d, bits_min_side=%d, max_rows_per_block=%d)" % self.as_tuple()
 
 
+class ServerCounters(ctypes.Structure):
+    """Counters of a step server (``jx_server_counters``)."""
+
+    _fields_ = [("requests_submitted", ctypes.c_uint64), ("requests_done", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("env_steps", ctypes.c_uint64), ("groups_launched", ctypes.c_uint64),
+                ("rejected_opens", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64),
+                ("bytes_in_use", ctypes.c_uint64), ("peak_bytes_in_use", ctypes.c_uint64),
+                ("sessions_open", ctypes.c_int32), ("peak_sessions", ctypes.c_int32),
+                ("inflight_launches", ctypes.c_int32), ("peak_inflight_launches", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with paper_2605_19926_gb300.build.build()")
@@ -120,6 +137,18 @@ def _load() -> ctypes.CDLL:
         "jx_batch_capture": [P, i32, P, P, P, P, P],
         "jx_graph_launch": [P, P],
         "jx_graph_destroy": [P],
+        "jx_env_bytes": [P, ctypes.c_int, P],
+        "jx_create_in": [P, ctypes.c_int, P, sz, P],
+        "jx_server_create": [ctypes.c_int, ctypes.c_uint64, i32, i32, i32, P, P],
+        "jx_server_destroy": [P],
+        "jx_server_open": [P, P, P],
+        "jx_server_close": [P, i32],
+        "jx_server_session": [P, i32, P, P, P, P],
+        "jx_server_submit": [P, i32, P, P],
+        "jx_server_wait": [P, ctypes.c_uint64, ctypes.c_double],
+        "jx_server_pause": [P, i32],
+        "jx_server_stats": [P, P],
+        "jx_server_latencies": [P, P, ctypes.c_uint64, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -184,10 +213,25 @@ class Env:
         self.H, self.W, self.S, self.K = int(cfg["frame_h"]), int(cfg["frame_w"]), int(cfg["map_side"]), int(
             cfg["max_sprites"])
 
+    @classmethod
+    def view(cls, handle: int, cfg: dict, device: int = 0) -> "Env":
+        """An Env over a handle owned elsewhere (a server session): state access
+        and launches, never destroyed by this object."""
+        self = cls.__new__(cls)
+        self.cfg = dict(cfg)
+        self._c = Config.from_dict(cfg)
+        self._h = ctypes.c_void_p(handle)
+        self._owned = False
+        self.device = device
+        self.n = int(cfg["n_envs"])
+        self.H, self.W, self.S, self.K = int(cfg["frame_h"]), int(cfg["frame_w"]), int(cfg["map_side"]), int(
+            cfg["max_sprites"])
+        return self
+
     def close(self):
-        if getattr(self, "_h", None) is not None and self._h.value:
+        if getattr(self, "_h", None) is not None and self._h.value and getattr(self, "_owned", True):
             lib.jx_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
@@ -401,6 +445,117 @@ class Batch:
         n = ctypes.c_uint64()
         _check(lib.jx_batch_launch_count(self._h, ctypes.byref(n)))
         return n.value
+
+
+class _DeviceArray:
+    """A view of library-owned device memory for ``torch.as_tensor``."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str, device: int):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3,
+                                         "strides": None, "stream": None}
+        self.device = device
+
+
+def device_view(ptr: int, shape: tuple, dtype, device: int):
+    """torch tensor aliasing `ptr` (no copy); valid while the owner keeps the memory."""
+    import torch
+
+    typestr = {np.uint8: "|u1", np.float32: "<f4"}[dtype]
+    with torch.cuda.device(device):
+        return torch.as_tensor(_DeviceArray(ptr, shape, typestr, device), device=torch.device("cuda", device))
+
+
+class Session:
+    """An open server session: its config and views of its device outputs."""
+
+    def __init__(self, server: "Server", sid: int, cfg: dict):
+        self.server, self.id, self.cfg = server, sid, dict(cfg)
+        self.n = int(cfg["n_envs"])
+        env, fr, rw, dn = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib.jx_server_session(server._h, sid, ctypes.byref(env), ctypes.byref(fr), ctypes.byref(rw),
+                                     ctypes.byref(dn)))
+        self.env_handle = env.value
+        self.env = Env.view(env.value, cfg, server.device)
+        H, W = int(cfg["frame_h"]), int(cfg["frame_w"])
+        d = server.device
+        self.frames = device_view(fr.value, (self.n, H, W, 3), np.uint8, d)
+        self.rewards = device_view(rw.value, (self.n,), np.float32, d)
+        self.dones = device_view(dn.value, (self.n,), np.uint8, d)
+
+    def submit(self, actions: np.ndarray) -> int:
+        a = np.ascontiguousarray(actions, dtype=np.uint8)
+        assert a.shape == (self.n,)
+        t = ctypes.c_uint64()
+        _check(lib.jx_server_submit(self.server._h, self.id, a.ctypes.data, ctypes.byref(t)))
+        return t.value
+
+    def close(self):
+        _check(lib.jx_server_close(self.server._h, self.id))
+
+
+class Server:
+    """Continuous-batching step server (``jx_server_*``)."""
+
+    def __init__(self, budget_bytes: int, max_sessions: int = 256, max_inflight: int = 4, max_map_side: int = 64,
+                 tiling: Tiling | None = None, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib.jx_server_create(device, int(budget_bytes), max_sessions, max_inflight, max_map_side,
+                                    ctypes.byref(tiling) if tiling is not None else None, ctypes.byref(h)))
+        self._h = h
+        self.device = device
+
+    def open(self, cfg: dict) -> Session:
+        """Admit a session; raises JxError (status EBUDGET) when it does not fit now."""
+        c = Config.from_dict(cfg)
+        sid = ctypes.c_int32()
+        _check(lib.jx_server_open(self._h, ctypes.byref(c), ctypes.byref(sid)))
+        return Session(self, sid.value, cfg)
+
+    def try_open(self, cfg: dict) -> Session | None:
+        try:
+            return self.open(cfg)
+        except JxError as e:
+            if e.status == EBUDGET:
+                return None
+            raise
+
+    def wait(self, ticket: int, timeout: float = 10.0):
+        _check(lib.jx_server_wait(self._h, ticket, timeout))
+
+    def pause(self, paused: bool = True):
+        _check(lib.jx_server_pause(self._h, int(paused)))
+
+    def stats(self) -> dict:
+        c = ServerCounters()
+        _check(lib.jx_server_stats(self._h, ctypes.byref(c)))
+        return c.as_dict()
+
+    def latencies(self) -> np.ndarray:
+        out, chunk = [], 1 << 16
+        buf = np.empty(chunk, np.float64)
+        while True:
+            n = ctypes.c_uint64()
+            _check(lib.jx_server_latencies(self._h, buf.ctypes.data, chunk, ctypes.byref(n)))
+            out.append(buf[: n.value].copy())
+            if n.value < chunk:
+                return np.concatenate(out)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.jx_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def validate_config(cfg: dict) -> tuple[int, str]:

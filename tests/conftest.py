@@ -10,6 +10,12 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    # test modules load libjx.so when they are collected: rebuild it first if
+    # a source is newer (nvcc cross-compiles without a GPU)
+    from paper_2605_19926_gb300 import build
+
+    if build.needs_build():
+        build.build()
 
 
 @pytest.fixture(scope="session")

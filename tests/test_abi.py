@@ -129,3 +129,22 @@ def test_uneven_workload_groups():
         assert 800 < g["n_envs"] < 1250  # 1024 expected per (side, frame) pair
     assert len({g["seed"] for g in groups}) == 16
     assert inputs.uneven_groups() == groups  # seeded
+
+
+def test_server_arguments_checked_before_cuda(jx):
+    h = ctypes.c_void_p()
+    assert jx.lib.jx_server_create(0, 0, 4, 2, 64, None, ctypes.byref(h)) == jx.EINVAL  # budget
+    assert jx.lib.jx_server_create(0, 1 << 20, 0, 2, 64, None, ctypes.byref(h)) == jx.EINVAL  # sessions
+    assert jx.lib.jx_server_create(0, 1 << 20, 4, 0, 64, None, ctypes.byref(h)) == jx.EINVAL  # in flight
+    assert jx.lib.jx_server_create(0, 1 << 20, 4, 17, 64, None, ctypes.byref(h)) == jx.EINVAL
+    assert jx.lib.jx_server_create(0, 1 << 20, 4, 2, 129, None, ctypes.byref(h)) == jx.EINVAL  # map side
+    assert jx.lib.jx_server_submit(None, 1, None, None) == jx.EINVAL
+    assert jx.lib.jx_server_wait(None, 0, 0.0) == jx.EINVAL
+    assert jx.lib.jx_server_destroy(None) == jx.OK
+
+
+def test_server_counters_struct_matches_header(jx):
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct \{([^}]*)\} jx_server_counters;", text).group(1)
+    names = re.findall(r"^\s*(?:u?int\d+_t)\s+(\w+);", body, re.M)
+    assert names == [f[0] for f in jx.ServerCounters._fields_]
