@@ -32,6 +32,7 @@ MAX_SPRITES = 16
 
 TASK_ROOMS = 0
 TASK_MAZE_KEYDOOR = 1
+TASK_MAZE_ROOMS = 2
 
 EV_KEY = 1
 EV_GOAL = 2
@@ -134,6 +135,8 @@ def lib() -> ctypes.CDLL:
         L.jxo_step_render_batch.argtypes = [P, P, P, i32, P, P, P, P, P, P, P, i32]
         L.jxo_render_batch.argtypes = [P, P, i32, P, P, P, i32]
         L.jxo_generate_batch.argtypes = [P, P, P, P, i32, i32]
+        L.jxo_gray.argtypes = [P, ctypes.c_int64, P]
+        L.jxo_gray.restype = None
         assert L.jxo_sizeof_env() == ENV_DTYPE.itemsize, "oracle env layout mismatch"
         assert L.jxo_sizeof_config() == CONFIG_DTYPE.itemsize, "oracle config layout mismatch"
         assert L.jxo_sizeof_ray() == RAY_DTYPE.itemsize, "oracle ray layout mismatch"
@@ -231,6 +234,14 @@ def cast(cfg: np.ndarray, env: np.ndarray, ox: float, oy: float, rx: float, ry: 
     e = np.ascontiguousarray(env.reshape(1))
     lib().jxo_cast(_ptr(cfg), _ptr(e), ox, oy, rx, ry, bias, _ptr(out))
     return out[0]
+
+
+def gray(rgb: np.ndarray) -> np.ndarray:
+    """Integer BT.601 luma of an [..., 3] uint8 array: (77 R + 150 G + 29 B + 128) >> 8."""
+    rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+    out = np.empty(rgb.shape[:-1], np.uint8)
+    lib().jxo_gray(_ptr(rgb), out.size, _ptr(out))
+    return out
 
 
 def map_view(cfg: np.ndarray, env) -> np.ndarray:

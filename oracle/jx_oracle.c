@@ -96,7 +96,7 @@ static int config_ok(const jxo_config* cfg) {
   if (cfg->frame_h < 1 || cfg->frame_w < 1) return 0;
   if (cfg->max_sprites < 0 || cfg->max_sprites > JXO_MAX_SPRITES) return 0;
   if (cfg->turns_per_rev < 1) return 0;
-  if (cfg->task == JXO_TASK_MAZE_KEYDOOR) {
+  if (cfg->task == JXO_TASK_MAZE_KEYDOOR || cfg->task == JXO_TASK_MAZE_ROOMS) {
     if (S < 6 || (S % 2) != 0 || cfg->max_sprites < 2) return 0;
   } else if (cfg->task != JXO_TASK_ROOMS) {
     return 0;
@@ -336,6 +336,52 @@ static int gen_maze(const jxo_config* cfg, int32_t env, uint32_t ep, jxo_env* e)
   return 0;
 }
 
+/* Maze with rooms (the large-scale workload): the key-door maze above, then
+ * S*S/1024 open rooms of 8 x 8 cells, room r with its top-left cell at
+ * (1 + u mod (S - 9), 1 + u' mod (S - 9)) from draws 2r and 2r+1 of the room
+ * stream, every cell inside turned to floor except the locked door; then a
+ * uniform number in [0, K-2] of distractor sprites after the key and the goal,
+ * each on a uniformly chosen floor cell (row-major enumeration of the final
+ * map). Rooms only add floor, so every floor cell stays reachable; they may
+ * open a way around the door. */
+static void gen_maze_rooms(const jxo_config* cfg, int32_t env, uint32_t ep, jxo_env* e) {
+  int S = cfg->map_side;
+  uint64_t seed = cfg->seed;
+  gen_maze(cfg, env, ep, e);
+  int n_rooms = (S * S) / 1024;
+  for (int r = 0; r < n_rooms; ++r) {
+    int x0 = 1 + (int)uniform_below(jxo_draw(seed, (uint32_t)env, ep, JXO_P_ROOM, (uint32_t)(2 * r)), (uint32_t)(S - 9));
+    int y0 = 1 + (int)uniform_below(jxo_draw(seed, (uint32_t)env, ep, JXO_P_ROOM, (uint32_t)(2 * r + 1)),
+                                    (uint32_t)(S - 9));
+    for (int y = y0; y < y0 + 8; ++y)
+      for (int x = x0; x < x0 + 8; ++x)
+        if (e->map[y * S + x] != JXO_DOOR) e->map[y * S + x] = JXO_FLOOR;
+  }
+  int n_free = 0;
+  for (int i = 0; i < S * S; ++i) n_free += e->map[i] == JXO_FLOOR;
+  uint32_t n = uniform_below(jxo_draw(seed, (uint32_t)env, ep, JXO_P_NSPRITES, 0), (uint32_t)cfg->max_sprites - 1);
+  for (uint32_t k = 0; k < n; ++k) {
+    uint32_t c = uniform_below(jxo_draw(seed, (uint32_t)env, ep, JXO_P_SPRITE_CELL, k), (uint32_t)n_free);
+    int seen = 0;
+    for (int i = 0; i < S * S; ++i) {
+      if (e->map[i] != JXO_FLOOR) continue;
+      if ((uint32_t)seen == c) {
+        e->spr_x[2 + k] = (i % S) + 0.5;
+        e->spr_y[2 + k] = (i / S) + 0.5;
+        e->spr_type[2 + k] = JXO_SPR_DISTRACTOR;
+        break;
+      }
+      ++seen;
+    }
+  }
+  e->n_sprites = 2 + (int32_t)n;
+}
+
+void jxo_gray(const uint8_t* rgb, int64_t n, uint8_t* out) {
+  for (int64_t i = 0; i < n; ++i)
+    out[i] = (uint8_t)((77 * (int)rgb[3 * i] + 150 * (int)rgb[3 * i + 1] + 29 * (int)rgb[3 * i + 2] + 128) >> 8);
+}
+
 int jxo_generate(const jxo_config* cfg, int32_t env_index, uint32_t episode, jxo_env* out) {
   if (!config_ok(cfg)) return -1;
   memset(out, 0, sizeof(*out));
@@ -345,6 +391,8 @@ int jxo_generate(const jxo_config* cfg, int32_t env_index, uint32_t episode, jxo
   out->has_key = 0;
   if (cfg->task == JXO_TASK_ROOMS)
     gen_rooms(cfg, env_index, episode, out);
+  else if (cfg->task == JXO_TASK_MAZE_ROOMS)
+    gen_maze_rooms(cfg, env_index, episode, out);
   else
     gen_maze(cfg, env_index, episode, out);
   out->theta0 = heading_from_draw(jxo_draw(cfg->seed, (uint32_t)env_index, episode, JXO_P_HEADING, 0));

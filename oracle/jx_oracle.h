@@ -34,6 +34,7 @@ extern "C" {
 /* Tasks */
 #define JXO_TASK_ROOMS 0        /* border walls + random interior walls       */
 #define JXO_TASK_MAZE_KEYDOOR 1 /* DFS maze, one key, one locked door, a goal */
+#define JXO_TASK_MAZE_ROOMS 2   /* the key-door maze with 8 x 8 open rooms carved in and distractor sprites */
 
 /* Map cell values */
 #define JXO_FLOOR 0
@@ -62,6 +63,7 @@ extern "C" {
 #define JXO_P_KEY 5
 #define JXO_P_NSPRITES 6
 #define JXO_P_SPRITE_CELL 7
+#define JXO_P_ROOM 8
 
 /* Tolerances the oracle uses to flag decisions that finite precision may flip. */
 #define JXO_EPS_CELL 1e-5   /* cells: DDA ties, hit near a lattice point, collision boundaries */
@@ -125,6 +127,9 @@ int jxo_sizeof_ray(void);
 
 /* Build episode `episode` of environment `env_index`. Returns 0, or -1 on an invalid config. */
 int jxo_generate(const jxo_config* cfg, int32_t env_index, uint32_t episode, jxo_env* out);
+
+/* Grayscale of n RGB pixels: the integer BT.601 luma (77 R + 150 G + 29 B + 128) >> 8. */
+void jxo_gray(const uint8_t* rgb, int64_t n, uint8_t* out);
 
 /* One environment step with auto-reset. Returns 0 or -1. */
 int jxo_step(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t action,

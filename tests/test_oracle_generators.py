@@ -148,3 +148,68 @@ def test_generation_is_deterministic_per_episode(orc):
     c = orc.generate(cfg, np.arange(4), 6)
     assert a.tobytes() == b.tobytes()
     assert (a["map"] != c["map"]).any(axis=1).all()
+
+
+@pytest.mark.parametrize("S,K", [(32, 4), (64, 16), (128, 16)])
+def test_maze_with_rooms_extends_the_keydoor_maze(orc, S, K):
+    """The maze-with-rooms task is the key-door maze of the same seed with open
+    8 x 8 squares added: the maze's floor, spawn, key, door and goal are kept;
+    every added floor cell lies in an 8 x 8 window of floor (or the door) inside
+    the border; all floor stays connected; sprites are key, goal, then up to
+    K - 2 distractors on floor cells."""
+    base = dict(inputs.maze_keydoor(n_envs=6, map_side=S, seed=17), max_sprites=K)
+    c1 = orc.make_config(**base)
+    c2 = orc.make_config(**dict(base, task=orc.TASK_MAZE_ROOMS))
+    idx, eps = np.arange(6), np.array([0, 1, 2, 0, 5, 9])
+    maze, rooms = orc.generate(c1, idx, eps), orc.generate(c2, idx, eps)
+    n_added = 0
+    for a, b in zip(maze, rooms):
+        m1, m2 = orc.map_view(c1, a).astype(int), orc.map_view(c2, b).astype(int)
+        for name in ("x", "y", "theta0", "key_x", "key_y", "goal_x", "goal_y", "door_x", "door_y"):
+            assert a[name] == b[name], name
+        assert (m2[m1 == 0] == 0).all(), "the maze's floor is kept"
+        assert (m2 == 5).sum() == 1 and m2[a["door_y"], a["door_x"]] == 5
+        added = (m2 == 0) & (m1 != 0)
+        n_added += int(added.sum())
+        open8 = (m2 == 0) | (m2 == 5)
+        # windows of 8 x 8 entirely open, by 2-D prefix sums
+        ps = np.pad(open8.astype(int).cumsum(0).cumsum(1), ((1, 0), (1, 0)))
+        win = ps[8:, 8:] - ps[:-8, 8:] - ps[8:, :-8] + ps[:-8, :-8] == 64
+        cover = np.zeros_like(open8)
+        for y0, x0 in zip(*np.nonzero(win)):
+            cover[y0:y0 + 8, x0:x0 + 8] = True
+        assert cover[added].all(), "added floor lies in open 8 x 8 squares"
+        assert (m2[0] != 0).all() and (m2[-1] != 0).all() and (m2[:, 0] != 0).all() and (m2[:, -1] != 0).all()
+        g = _grid_graph(open8)
+        _, lab = connected_components(g, directed=False)
+        assert len(set(lab[np.flatnonzero(open8.reshape(-1))])) == 1, "connected with the door open"
+        ns = int(b["n_sprites"])
+        assert 2 <= ns <= K
+        assert b["spr_type"][0] == 1 and b["spr_type"][1] == 2 and (b["spr_type"][2:ns] == 3).all()
+        assert (b["spr_x"][0], b["spr_y"][0]) == (b["key_x"] + 0.5, b["key_y"] + 0.5)
+        for k in range(2, ns):
+            assert m2[int(b["spr_y"][k]), int(b["spr_x"][k])] == 0
+    if S >= 32:
+        assert n_added > 0
+
+
+def test_maze_with_rooms_distractor_count_is_uniform(orc):
+    K = 6
+    c = orc.make_config(**dict(inputs.maze_keydoor(n_envs=1, map_side=32, seed=23), max_sprites=K,
+                               task=orc.TASK_MAZE_ROOMS))
+    envs = orc.generate(c, np.arange(700))
+    counts = np.bincount(envs["n_sprites"] - 2, minlength=K - 1)
+    assert len(counts) == K - 1 and counts.min() > 0.6 * 700 / (K - 1), counts
+
+
+def test_gray_is_bt601_luma(orc):
+    """Integer luma: exact at black and white, and within one level of the
+    real-valued BT.601 weights 0.299, 0.587, 0.114 for every RGB triple drawn."""
+    rng = np.random.default_rng(3)
+    rgb = rng.integers(0, 256, size=(20000, 3), dtype=np.uint8)
+    rgb[:4] = [[0, 0, 0], [255, 255, 255], [255, 0, 0], [0, 255, 0]]
+    g = orc.gray(rgb).astype(int)
+    ref = rgb.astype(float) @ np.array([0.299, 0.587, 0.114])
+    assert g[0] == 0 and g[1] == 255
+    assert np.abs(g - ref).max() <= 1.0
+    assert (np.diff(orc.gray(np.stack([np.arange(256)] * 3, 1).astype(np.uint8)).astype(int)) >= 0).all()
