@@ -193,6 +193,14 @@ def run_reference(args, cfg: dict):
     print(json.dumps(line), flush=True)
 
 
+def tiling_dict(t) -> dict:
+    """A launch choice as JSON: all zero means the env's own kernel."""
+    names = ("warps_per_block", "cols_per_lane", "bits_min_side", "max_rows_per_block")
+    d = dict(zip(names, t.as_tuple()))
+    d["kernel"] = "env kernel" if not any(t.as_tuple()) else "batched kernel"
+    return d
+
+
 def uneven_bytes_per_env_step(groups: list) -> float:
     """Mean compulsory HBM bytes per env-step of an uneven batch (as for one env group)."""
     tot = sum(g["n_envs"] * algorithmic_bytes_per_env_step(g) for g in groups)
@@ -312,6 +320,102 @@ def run_uneven(args):
         "autotune": {"trials": len(trials), "seconds": tune_s, "mode": "rollout", "steps_per_trial": T},
         "graph_steps": {"value": world * N * K / (graph_ms / 1e3), "ms_per_step": graph_ms / K,
                         "how": f"jx_batch_capture of {T} jx_batch_step launches, replayed"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_large(args):
+    """Large scale: 65,536 envs of 128 x 128 mazes with 8 x 8 rooms, 16 sprite
+    slots, 128 x 128 RGB frames plus the 4-frame grayscale stack written in the
+    same pass, horizon 500, `--steps` (1000) steps of uniform random actions in
+    rollout launches of `--large-slots` steps."""
+    import torch
+
+    from paper_2605_19926_gb300 import build, inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2605_19926_gb300 import jx
+
+    cfg = shard_config(inputs.large_scale(args.large_envs), rank)
+    N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
+    dev = torch.device("cuda", local)
+    env = jx.Env(cfg, local)
+    tuned = None
+    if not args.no_autotune:
+        # the env's own kernel against the batched kernel's tilings, before timing
+        tuned = env.autotune(mode=1, steps=args.large_slots, max_trials=args.tune_trials)
+    T = args.large_slots
+    K = max(T, (args.steps // T) * T)
+    acts = torch.from_numpy(inputs.action_stream(cfg["seed"], K + T, N)).to(dev)
+    frames = torch.empty((T, N, H, W, 3), dtype=torch.uint8, device=dev)
+    rewards = torch.empty((T, N), dtype=torch.float32, device=dev)
+    dones = torch.empty((T, N), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    t_reset = time.perf_counter()
+    with torch.cuda.stream(stream):
+        env.reset(frames[0], stream)
+    stream.synchronize()
+    reset_s = time.perf_counter() - t_reset
+    with torch.cuda.stream(stream):
+        env.rollout(acts[:T], frames, rewards, dones, stream)  # warm-up
+    stream.synchronize()
+    n0 = env.launch_count()
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for c in range(K // T):
+            env.rollout(acts[T + c * T: T + (c + 1) * T], frames, rewards, dones, stream)
+        e1.record(stream)
+    stream.synchronize()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    launches = env.launch_count() - n0
+    n_done = int(dones.sum().item())
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    gray = H * W  # one plane per env-step (all four at an episode start)
+    bpes = algorithmic_bytes_per_env_step(cfg) + gray
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    gbs = N * K * bpes / (ms / 1e3) / 1e9
+    shape = env.launch_shape()
+    line = {
+        "metric": "env-steps/s incl. render (frames/s), 128x128 RGB + gray stack", "value": world * N * K / (ms / 1e3),
+        "unit": "env-steps/s", "n_gpus": world, "steps": K, "warmup": T, "ms_per_step": ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"{N} envs per GPU, 128x128 DFS mazes with 8x8 open rooms, 16 sprite slots (key, goal, "
+                               "0-14 distractors), 128x128 RGB + 4-frame grayscale stack in the same pass, horizon 500, "
+                               "uniform random actions",
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"frames written to a {T}-slot rollout buffer ({T * N * H * W * 3 / 1e9:.1f} GB) > L2",
+                   "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
+                              "entry": "jx_rollout", "steps_per_launch": T}},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                     "traffic": None, "peak_source": peak_src, "algorithmic_bytes_per_env_step": bpes},
+        "reset_seconds": reset_s, "episode_ends_in_last_launch": n_done,
+        "tiling": tiling_dict(env.tiling),
+        "autotune_trials": len(tuned) if tuned else 0,
         "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -455,17 +559,26 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1000)
     ap.add_argument("--ring-slots", type=int, default=GRAPH_STEPS,
                     help="rollout buffer slots = launches per CUDA graph (smaller for profiling captures)")
-    ap.add_argument("--workload", default="mazes", choices=["mazes", "uneven", "serve"],
+    ap.add_argument("--workload", default="mazes", choices=["mazes", "uneven", "serve", "large"],
                     help="mazes: 4096 key-door mazes (the headline); uneven: 16,384 envs of mixed sizes; "
                          "serve: the continuous-batching step server under Poisson request arrivals")
     ap.add_argument("--actors", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--session-steps", type=int, default=250)
     ap.add_argument("--budget-gb", type=float, default=40.0)
+    ap.add_argument("--large-envs", type=int, default=65536)
+    ap.add_argument("--large-slots", type=int, default=8, help="steps per rollout launch of the large workload")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip jx_autotune before timing (the env's own kernel with its fixed tiles)")
     ap.add_argument("--uneven-slots", type=int, default=16, help="steps per rollout launch of the uneven batch")
     ap.add_argument("--tune-trials", type=int, default=1000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.workload == "large" and args.impl == "jx":
+        if args.steps == ap.get_default("steps"):
+            args.steps = 1000
+        run_large(args)
+        return
     if args.workload == "serve" and args.impl == "jx":
         run_serve(args)
         return
@@ -503,6 +616,10 @@ def main():
     dev = torch.device("cuda", local)
     env = jx.Env(cfg, local)
     ring = args.ring_slots
+    tuned = None
+    if not args.no_autotune:
+        # the env's own kernel against the batched kernel's tilings, before timing
+        tuned = env.autotune(mode=1, steps=ring, max_trials=args.tune_trials)
     total_steps = args.warmup + args.steps
     # inputs resident in HBM before timing: the whole action stream
     acts_host = inputs.action_stream(cfg["seed"], total_steps, N)
@@ -664,7 +781,8 @@ def main():
                    "parallelism": f"replicas x{world}",
                    "l2": f"frames written to a {ring}-slot rollout buffer ({ring * N * H * W * 3 / 1e9:.1f} GB) > L2",
                    "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
-                              "entry": "jx_rollout", "steps_per_launch": ring}},
+                              "entry": "jx_rollout", "steps_per_launch": ring,
+                              "tiling": tiling_dict(env.tiling), "autotune_trials": len(tuned) if tuned else 0}},
         "p50_step_ms": p50, "p99_step_ms": p99,
         "per_step_launch": {"value": world * N / (step_ms / 1e3), "unit": "env-steps/s", "ms_per_step": step_ms,
                             "how": f"jx_step, CUDA graph of {ring} launches"},

@@ -51,7 +51,7 @@ typedef enum {
   JX_EDEVICE = 6   /* the device error word was set by a kernel */
 } jx_status;
 
-enum { JX_TASK_ROOMS = 0, JX_TASK_MAZE_KEYDOOR = 1 };
+enum { JX_TASK_ROOMS = 0, JX_TASK_MAZE_KEYDOOR = 1, JX_TASK_MAZE_ROOMS = 2 };
 
 enum {
   JX_ACT_NOOP = 0,
@@ -68,7 +68,10 @@ enum {
  *  task          JX_TASK_ROOMS: border walls, interior walls with probability
  *                wall_prob, optional decorative sprites; JX_TASK_MAZE_KEYDOOR:
  *                random DFS maze with one key, one locked door and a goal at
- *                the cell farthest from the spawn (Table 1 "key-door")
+ *                the cell farthest from the spawn (Table 1 "key-door");
+ *                JX_TASK_MAZE_ROOMS: that maze with S*S/1024 open 8 x 8 rooms
+ *                carved in (the door kept) and 0..K-2 distractor sprites after
+ *                the key and the goal
  *  map_side      S, the map is S x S cells; rooms: 3..128; mazes: even, 6..128
  *  frame_h       H rows, 1..256
  *  frame_w       W columns, a multiple of 16, 16..256
@@ -82,7 +85,15 @@ enum {
  *  step_reward, key_reward, goal_reward: reward of a step is
  *                step_reward + key_reward [key picked] + goal_reward [goal reached],
  *                rounded once to float32
- *  seed          master seed of all map, spawn and heading draws */
+ *  seed          master seed of all map, spawn and heading draws
+ *  gray_stack    nonzero: keep a 4-frame grayscale stack per env in the state
+ *                (field JX_F_GRAY, [N][4][H][W] uint8), written in the same
+ *                pass as the RGB frame: the frame of episode step t goes to
+ *                plane t mod 4 (integer BT.601 luma (77 R + 150 G + 29 B +
+ *                128) >> 8 of each pixel), and an episode's first frame to all
+ *                four planes. So after step t the planes t, t-1, t-2, t-3
+ *                (mod 4) hold the last four frames, the first one repeated
+ *                early in an episode. */
 typedef struct {
   int32_t n_envs;
   int32_t task;
@@ -100,6 +111,7 @@ typedef struct {
   double key_reward;
   double goal_reward;
   uint64_t seed;
+  int32_t gray_stack;
 } jx_config;
 
 /* Create N environments on CUDA device `device` and allocate their state in
@@ -219,7 +231,8 @@ enum {
   JX_F_MAP = 14,     /* uint8  [N][S][S] 0 floor, 1..4 wall types, 5 locked door */
   JX_F_COS0 = 15,    /* float  [N]   cos(theta0), derived: jx_set_state recomputes it */
   JX_F_SIN0 = 16,    /* float  [N]   sin(theta0), derived: jx_set_state recomputes it */
-  JX_F_COUNT = 17
+  JX_F_GRAY = 17,    /* uint8  [N][4][H][W] grayscale frame stack (0 bytes unless gray_stack) */
+  JX_F_COUNT = 18
 };
 jx_status jx_state_bytes(const jx_env* env, size_t* bytes);
 jx_status jx_state_field(const jx_env* env, int32_t field, size_t* offset, size_t* bytes);
@@ -322,6 +335,21 @@ jx_status jx_batch_render(jx_batch* batch, void* stream, uint8_t* d_frames);
  * *n_trials the number run. Waits for `stream`. */
 jx_status jx_batch_autotune(jx_batch* batch, void* stream, int32_t mode, int32_t steps, int32_t max_trials,
                             int32_t* n_trials, jx_tiling* trials, float* ms_per_step);
+
+/* Autotuner of a single env: times the env's own kernel (trial 0, reported as
+ * the all-zero tiling) and the batched kernel over this env alone under every
+ * tiling of jx_batch_autotune's search space (the first max_trials - 1), with
+ * jx_batch_autotune's protocol, and keeps the fastest: afterwards jx_reset,
+ * jx_step, jx_rollout and jx_render of the env launch the chosen kernel
+ * (results are identical either way; jx_debug_rays always uses the env's own
+ * kernel). Every env is RESET (episode 0) when it returns. Waits for `stream`. */
+jx_status jx_autotune(jx_env* env, void* stream, int32_t mode, int32_t steps, int32_t max_trials,
+                      int32_t* n_trials, jx_tiling* trials, float* ms_per_step);
+/* The env's launch choice: the all-zero tiling for its own kernel, else the
+ * batched kernel's tiling. jx_env_set_tiling pins it (all zero: the env's own
+ * kernel); a bad tiling returns JX_EINVAL and changes nothing. */
+jx_status jx_env_tiling(const jx_env* env, jx_tiling* tiling);
+jx_status jx_env_set_tiling(jx_env* env, const jx_tiling* tiling);
 
 /* CUDA graph of `steps` consecutive jx_batch_step launches (step t reads
  * d_actions + t*n_envs and writes step t's slice of d_frames, d_rewards,

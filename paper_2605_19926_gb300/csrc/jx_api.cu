@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "jx_host.h"
 
@@ -23,11 +24,12 @@ namespace {
 jx_status validate(const jx_config* c) {
   if (!c) return fail(JX_EINVAL, "config is NULL");
   if (c->n_envs < 1) return fail(JX_EINVAL, "n_envs must be >= 1 (got %d)", c->n_envs);
-  if (c->task != JX_TASK_ROOMS && c->task != JX_TASK_MAZE_KEYDOOR)
+  if (c->task != JX_TASK_ROOMS && c->task != JX_TASK_MAZE_KEYDOOR && c->task != JX_TASK_MAZE_ROOMS)
     return fail(JX_EINVAL, "unknown task %d", c->task);
+  const bool maze = c->task == JX_TASK_MAZE_KEYDOOR || c->task == JX_TASK_MAZE_ROOMS;
   if (c->map_side < 3 || c->map_side > jx::kMaxSide)
     return fail(JX_EINVAL, "map_side must be in [3, %d] (got %d)", jx::kMaxSide, c->map_side);
-  if (c->task == JX_TASK_MAZE_KEYDOOR && (c->map_side < 6 || c->map_side % 2 != 0))
+  if (maze && (c->map_side < 6 || c->map_side % 2 != 0))
     return fail(JX_EINVAL, "maze map_side must be even and >= 6 (got %d)", c->map_side);
   if (c->frame_h < 1 || c->frame_h > jx::kMaxH)
     return fail(JX_EINVAL, "frame_h must be in [1, %d] (got %d)", jx::kMaxH, c->frame_h);
@@ -35,7 +37,7 @@ jx_status validate(const jx_config* c) {
     return fail(JX_EINVAL, "frame_w must be a multiple of 16 in [16, %d] (got %d)", jx::kMaxW, c->frame_w);
   if (c->max_sprites < 0 || c->max_sprites > jx::kMaxSprites)
     return fail(JX_EINVAL, "max_sprites must be in [0, %d] (got %d)", jx::kMaxSprites, c->max_sprites);
-  if (c->task == JX_TASK_MAZE_KEYDOOR && c->max_sprites < 2)
+  if (maze && c->max_sprites < 2)
     return fail(JX_EINVAL, "the maze task needs max_sprites >= 2 (key and goal)");
   if (c->horizon < 0) return fail(JX_EINVAL, "horizon must be >= 0");
   if (c->turns_per_rev < 1 || c->turns_per_rev > 32767) return fail(JX_EINVAL, "turns_per_rev must be in [1, 32767]");
@@ -69,6 +71,7 @@ void layout(jx_env* env) {
       N * S * S,  // map
       4 * N,      // cos0
       4 * N,      // sin0
+      env->cfg.gray_stack ? 4 * N * (size_t)env->cfg.frame_h * env->cfg.frame_w : 0,  // gray
   };
   size_t off = 0;
   for (int f = 0; f < JX_F_COUNT; ++f) {
@@ -122,22 +125,25 @@ jx_status cuda_fail(cudaError_t err, const char* what) {
 void choose_rows(Params& p, int max_rows, int warps, int blocks, size_t smem_per_sm, size_t reserved) {
   const int rowb = 3 * p.W;
   const int pass_rows = 32 / (p.W / 8) > 0 ? 32 / (p.W / 8) : 1;
-  p.rows_per_block = 1;
-  p.frame_block_bytes = rowb;
+  // candidates: whole fill passes up to max_rows (or the whole frame when it is
+  // shorter); the largest with which `blocks` warps fit, else the smallest
   const int top = p.H < max_rows ? p.H : max_rows;
+  int best = 0, smallest = 0;
   for (int rows = top; rows >= 1; --rows) {
-    if (rows < p.H && rows >= pass_rows && rows % pass_rows != 0) continue;
+    if (rows < p.H && rows % pass_rows != 0 && rows != top) continue;
+    smallest = rows;
     Params q = p;
     q.rows_per_block = rows;
     q.frame_block_bytes = rows * rowb;
+    q.gray_block_bytes = q.gray ? rows * p.W : 0;
     layout_warp_smem(q);
     const int per_block = q.warp_bytes * warps;
-    if ((size_t)(per_block + reserved) * (size_t)((blocks + warps - 1) / warps) <= smem_per_sm) {
-      p.rows_per_block = rows;
-      p.frame_block_bytes = rows * rowb;
-      break;
-    }
+    if (!best && (size_t)(per_block + reserved) * (size_t)((blocks + warps - 1) / warps) <= smem_per_sm) best = rows;
   }
+  const int rows = best ? best : (smallest ? smallest : 1);
+  p.rows_per_block = rows;
+  p.frame_block_bytes = rows * rowb;
+  p.gray_block_bytes = p.gray ? rows * p.W : 0;
   layout_warp_smem(p);
 }
 
@@ -213,6 +219,7 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
   // kMinBlocksPerSm one-warp blocks still fit in one SM's shared memory.
   // Maps of side 128 are staged as bit planes (2 KB instead of 16 KB).
   p.map_bits = c.map_side >= 128 && c.map_side % 8 == 0;
+  p.gray = c.gray_stack != 0;
   p.out_stride = c.n_envs;
   p.frame_step = (size_t)c.n_envs * jx::host::frame_bytes(c);
   jx::host::choose_rows(p, 16, jx::kWarpsPerBlock, jx::kMinBlocksPerSm, prop.sharedMemPerMultiprocessor,
@@ -312,6 +319,7 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
   p.st.map = field_ptr<uint8_t>(env, JX_F_MAP);
   p.st.cos0 = field_ptr<float>(env, JX_F_COS0);
   p.st.sin0 = field_ptr<float>(env, JX_F_SIN0);
+  p.st.gray = c.gray_stack ? field_ptr<uint8_t>(env, JX_F_GRAY) : nullptr;
   p.err = reinterpret_cast<uint32_t*>(env->aux + aux_err);
   p.turn_cs = reinterpret_cast<const float2*>(env->aux + aux_turn);
   p.col_k = reinterpret_cast<const float*>(env->aux + aux_col);
@@ -350,6 +358,7 @@ jx_status jx_create_in(const jx_config* cfg, int device, void* d_mem, size_t byt
 
 jx_status jx_destroy(jx_env* env) {
   if (!env) return JX_OK;
+  if (env->tuned) jx_batch_destroy(env->tuned);
   {
     DeviceGuard g(env->device);
     // an env in caller memory frees nothing on the device: no synchronisation
@@ -363,6 +372,7 @@ jx_status jx_destroy(jx_env* env) {
 
 jx_status jx_reset(jx_env* env, void* stream, uint8_t* d_frames) {
   if (jx_status st = check_env(env)) return st;
+  if (env->use_batch) return jx_batch_reset(env->tuned, stream, d_frames);
   if (!d_frames || !aligned16(d_frames)) return fail(JX_EINVAL, "d_frames must be a 16-byte aligned device pointer");
   jx::Params p = env->base;
   p.frames = d_frames;
@@ -372,6 +382,7 @@ jx_status jx_reset(jx_env* env, void* stream, uint8_t* d_frames) {
 jx_status jx_step(jx_env* env, void* stream, const uint8_t* d_actions, uint8_t* d_frames, float* d_rewards,
                   uint8_t* d_dones) {
   if (jx_status st = check_env(env)) return st;
+  if (env->use_batch) return jx_batch_step(env->tuned, stream, d_actions, d_frames, d_rewards, d_dones);
   if (!d_actions || !d_rewards || !d_dones) return fail(JX_EINVAL, "NULL device pointer");
   if (!d_frames || !aligned16(d_frames)) return fail(JX_EINVAL, "d_frames must be a 16-byte aligned device pointer");
   jx::Params p = env->base;
@@ -385,6 +396,7 @@ jx_status jx_step(jx_env* env, void* stream, const uint8_t* d_actions, uint8_t* 
 jx_status jx_rollout(jx_env* env, void* stream, const uint8_t* d_actions, int32_t steps, uint8_t* d_frames,
                      float* d_rewards, uint8_t* d_dones) {
   if (jx_status st = check_env(env)) return st;
+  if (env->use_batch) return jx_batch_rollout(env->tuned, stream, d_actions, steps, d_frames, d_rewards, d_dones);
   if (steps < 1) return fail(JX_EINVAL, "steps must be >= 1 (got %d)", steps);
   if (!d_actions || !d_rewards || !d_dones) return fail(JX_EINVAL, "NULL device pointer");
   if (!d_frames || !aligned16(d_frames)) return fail(JX_EINVAL, "d_frames must be a 16-byte aligned device pointer");
@@ -399,6 +411,7 @@ jx_status jx_rollout(jx_env* env, void* stream, const uint8_t* d_actions, int32_
 
 jx_status jx_render(jx_env* env, void* stream, uint8_t* d_frames) {
   if (jx_status st = check_env(env)) return st;
+  if (env->use_batch) return jx_batch_render(env->tuned, stream, d_frames);
   if (!d_frames || !aligned16(d_frames)) return fail(JX_EINVAL, "d_frames must be a 16-byte aligned device pointer");
   jx::Params p = env->base;
   p.frames = d_frames;
@@ -511,6 +524,138 @@ jx_status jx_step_host_static(jx_env* env, void* stream, const uint8_t* h_action
   return JX_OK;
 }
 
+jx_status jx_autotune(jx_env* env, void* stream, int32_t mode, int32_t steps, int32_t max_trials, int32_t* n_trials,
+                      jx_tiling* trials, float* ms_per_step) {
+  if (jx_status st = check_env(env)) return st;
+  if (mode != 0 && mode != 1) return fail(JX_EINVAL, "mode must be 0 (steps) or 1 (rollout) (got %d)", mode);
+  if (steps < 1 || steps > 1024) return fail(JX_EINVAL, "steps must be in [1, 1024] (got %d)", steps);
+  if (max_trials < 1) return fail(JX_EINVAL, "max_trials must be >= 1 (got %d)", max_trials);
+  if (n_trials) *n_trials = 0;
+  DeviceGuard g(env->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  if (!env->tuned) {
+    jx_env* self = env;
+    if (jx_status st = jx_batch_create(&self, 1, nullptr, &env->tuned)) return st;
+  }
+  env->use_batch = false;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t N = env->cfg.n_envs, T = steps, F = N * jx::host::frame_bytes(env->cfg);
+  // trial 0: the env's own kernel, under the batched trials' protocol
+  float env_ms = 0.f;
+  {
+    uint8_t* base = nullptr;
+    const size_t off_frames = align256(T * N), off_rewards = off_frames + align256(T * F);
+    const size_t off_dones = off_rewards + align256(4 * T * N);
+    cudaError_t err = cudaMalloc(&base, off_dones + align256(T * N));
+    if (err != cudaSuccess) return fail(JX_ENOMEM, "cudaMalloc of the autotuning buffers failed");
+    std::string act(T * N, '\0');
+    for (size_t i = 0; i < act.size(); ++i) act[i] = (char)jx::host::tune_action(i);
+    uint8_t* frames = base + off_frames;
+    float* rewards = reinterpret_cast<float*>(base + off_rewards);
+    uint8_t* dones = base + off_dones;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    jx_status st = JX_OK;
+    if ((err = cudaMemcpy(base, act.data(), act.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (err = cudaEventCreate(&e0)) != cudaSuccess || (err = cudaEventCreate(&e1)) != cudaSuccess)
+      st = cuda_fail(err, "autotuning setup");
+    auto run_steps = [&]() -> jx_status {
+      jx::Params p = env->base;
+      p.rewards = rewards;
+      p.dones = dones;
+      if (mode == 1) {
+        p.actions = base;
+        p.frames = frames;
+        p.steps = steps;
+        return run(env, p, jx::MODE_ROLLOUT, s);
+      }
+      for (size_t k = 0; k < T; ++k) {
+        p.actions = base + k * N;
+        p.frames = frames + k * F;
+        p.rewards = rewards + k * N;
+        p.dones = dones + k * N;
+        if (jx_status r = run(env, p, jx::MODE_STEP, s)) return r;
+      }
+      return JX_OK;
+    };
+    if (st == JX_OK) {
+      jx::Params p = env->base;
+      p.frames = frames;
+      st = run(env, p, jx::MODE_RESET, s);
+    }
+    if (st == JX_OK) st = run_steps();
+    if (st == JX_OK && (err = cudaEventRecord(e0, s)) != cudaSuccess) st = cuda_fail(err, "cudaEventRecord");
+    if (st == JX_OK) st = run_steps();
+    if (st == JX_OK && (err = cudaEventRecord(e1, s)) != cudaSuccess) st = cuda_fail(err, "cudaEventRecord");
+    if (st == JX_OK && (err = cudaEventSynchronize(e1)) != cudaSuccess) st = cuda_fail(err, "autotuning trial");
+    if (st == JX_OK) cudaEventElapsedTime(&env_ms, e0, e1);
+    env_ms /= (float)T;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(base);
+    if (st != JX_OK) return st;
+  }
+  std::vector<jx_tiling> bt(max_trials > 1 ? max_trials - 1 : 0);
+  std::vector<float> bms(bt.size());
+  int32_t nb = 0;
+  if (!bt.empty()) {
+    if (jx_status st = jx_batch_autotune(env->tuned, stream, mode, steps, (int32_t)bt.size(), &nb, bt.data(),
+                                         bms.data()))
+      return st;
+  } else {
+    // no batched trial: leave every env reset as promised
+    jx::Params p = env->base;
+    uint8_t* frames = nullptr;
+    cudaError_t err = cudaMalloc(&frames, F);
+    if (err != cudaSuccess) return fail(JX_ENOMEM, "cudaMalloc of a reset frame buffer failed");
+    p.frames = frames;
+    jx_status st = run(env, p, jx::MODE_RESET, s);
+    if (st == JX_OK && (err = cudaStreamSynchronize(s)) != cudaSuccess) st = cuda_fail(err, "autotuning reset");
+    cudaFree(frames);
+    if (st != JX_OK) return st;
+  }
+  float best = env_ms;
+  for (int i = 0; i < nb; ++i) best = bms[i] < best ? bms[i] : best;
+  env->use_batch = best < env_ms;
+  if (trials) {
+    trials[0] = jx_tiling{0, 0, 0, 0};
+    for (int i = 0; i < nb; ++i) trials[1 + i] = bt[i];
+  }
+  if (ms_per_step) {
+    ms_per_step[0] = env_ms;
+    for (int i = 0; i < nb; ++i) ms_per_step[1 + i] = bms[i];
+  }
+  if (n_trials) *n_trials = 1 + nb;
+  return JX_OK;
+}
+
+jx_status jx_env_set_tiling(jx_env* env, const jx_tiling* tiling) {
+  if (jx_status st = check_env(env)) return st;
+  if (!tiling) return fail(JX_EINVAL, "tiling is NULL");
+  const jx_tiling t = *tiling;
+  if (t.warps_per_block == 0 && t.cols_per_lane == 0 && t.bits_min_side == 0 && t.max_rows_per_block == 0) {
+    env->use_batch = false;
+    return JX_OK;
+  }
+  DeviceGuard g(env->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  if (!env->tuned) {
+    jx_env* self = env;
+    if (jx_status st = jx_batch_create(&self, 1, &t, &env->tuned)) return st;
+  } else if (jx_status st = jx_batch_set_tiling(env->tuned, &t)) {
+    return st;
+  }
+  env->use_batch = true;
+  return JX_OK;
+}
+
+jx_status jx_env_tiling(const jx_env* env, jx_tiling* tiling) {
+  if (jx_status st = check_env(env)) return st;
+  if (!tiling) return fail(JX_EINVAL, "tiling is NULL");
+  if (env->use_batch) return jx_batch_get_tiling(env->tuned, tiling);
+  *tiling = jx_tiling{0, 0, 0, 0};
+  return JX_OK;
+}
+
 jx_status jx_state_bytes(const jx_env* env, size_t* bytes) {
   if (jx_status st = check_env(env)) return st;
   if (!bytes) return fail(JX_EINVAL, "bytes is NULL");
@@ -590,12 +735,15 @@ jx_status jx_sync_status(jx_env* env, void* stream) {
 jx_status jx_launch_count(const jx_env* env, uint64_t* count) {
   if (jx_status st = check_env(env)) return st;
   if (!count) return fail(JX_EINVAL, "count is NULL");
-  *count = env->launches.load(std::memory_order_relaxed);
+  uint64_t batched = 0;
+  if (env->tuned) jx_batch_launch_count(env->tuned, &batched);
+  *count = env->launches.load(std::memory_order_relaxed) + batched;
   return JX_OK;
 }
 
 jx_status jx_launch_shape(const jx_env* env, int32_t* grid, int32_t* block, int32_t* smem_bytes) {
   if (jx_status st = check_env(env)) return st;
+  if (env->use_batch) return jx_batch_launch_shape(env->tuned, grid, block, smem_bytes);
   if (grid) *grid = env->grid;
   if (block) *block = jx::kThreads;
   if (smem_bytes) *smem_bytes = env->smem_block;

@@ -149,13 +149,6 @@ jx_status check_outputs(const uint8_t* actions, const uint8_t* frames, const flo
   return JX_OK;
 }
 
-uint64_t splitmix_host(uint64_t x) {
-  x += 0x9E3779B97F4A7C15ull;
-  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-  return x ^ (x >> 31);
-}
-
 // The autotuner's search space, the default tiling first.
 std::vector<jx_tiling> search_space() {
   jx_tiling def;
@@ -382,7 +375,7 @@ jx_status jx_batch_autotune(jx_batch* batch, void* stream, int32_t mode, int32_t
   buf.dones = buf.base + off_dones;
   {
     std::vector<uint8_t> act(T * N);
-    for (size_t i = 0; i < act.size(); ++i) act[i] = (uint8_t)(((splitmix_host(i) >> 32) * 7) >> 32);
+    for (size_t i = 0; i < act.size(); ++i) act[i] = jx::host::tune_action(i);
     if ((err = cudaMemcpy(buf.actions, act.data(), act.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_fail(err, "copy of autotuning actions");
   }

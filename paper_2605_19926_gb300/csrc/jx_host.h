@@ -35,6 +35,10 @@ struct jx_env {
   uint8_t* stage = nullptr;
   size_t stage_frames_off = 0, stage_rewards_off = 0, stage_dones_off = 0;
   std::atomic<uint64_t> launches{0};
+  // jx_autotune: a private one-group batch over this env, and whether the
+  // env's launches go through it (the batched kernel with tuned tiles)
+  jx_batch* tuned = nullptr;
+  bool use_batch = false;
 };
 
 namespace jx {
@@ -60,6 +64,15 @@ struct DeviceGuard {
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Uniform random actions of the autotuners: action i = (SplitMix64 output i) * 7 >> 64.
+inline uint8_t tune_action(uint64_t i) {
+  uint64_t x = i + 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (uint8_t)(((x >> 32) * 7) >> 32);
+}
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Bytes of one env's RGB frame.

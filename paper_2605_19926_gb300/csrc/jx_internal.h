@@ -37,7 +37,8 @@ enum Purpose : uint32_t {
   P_DFS = 4,
   P_KEY = 5,
   P_NSPRITES = 6,
-  P_SPRITE_CELL = 7
+  P_SPRITE_CELL = 7,
+  P_ROOM = 8
 };
 
 // Device pointers into the struct-of-arrays state block.
@@ -59,6 +60,7 @@ struct State {
   uint8_t* map;  // [N][S][S]
   float* cos0;   // [N] cos(theta0), derived
   float* sin0;   // [N] sin(theta0), derived
+  uint8_t* gray; // [N][4][H][W] grayscale frame stack, or null
 };
 
 struct Params {
@@ -79,12 +81,14 @@ struct Params {
   int32_t out_stride;  // envs per step in the action / reward / done arrays (n, or a batch's total)
   size_t frame_step;   // bytes per step in the frame array (n frames, or a batch's total)
   int32_t map_bits;    // the map is staged as a bit plane (see MapKind)
+  int32_t gray;        // the env keeps a grayscale frame stack (st.gray)
+  int32_t gray_block_bytes;  // rows_per_block * W when gray, else 0
   int32_t rows_per_block;  // rows per staged frame block
   int32_t frame_block_bytes;
   int32_t map_smem_bytes;  // S * S rounded up to 16
   // per-warp shared memory layout (byte offsets from the warp's base; set by layout_warp_smem)
-  int32_t off_pal, off_map, off_col_rgb, off_col_top, off_col_bot, off_zbuf, off_spr_in, off_spr_a, off_spr_rect,
-      off_spr_ty, off_spr_rgb, off_spr_kind, off_order, off_obj, warp_bytes;
+  int32_t off_gray, off_pal, off_map, off_col_rgb, off_col_top, off_col_bot, off_zbuf, off_spr_in, off_spr_a, off_spr_rect,
+      off_spr_ty, off_spr_rgb, off_spr_kind, off_order, off_spr_span, off_obj, warp_bytes;
   float move, radius, tan_half, inv_tan_half;
   float reward_lut[4];
   uint64_t seed;

@@ -28,9 +28,12 @@ constexpr int kSprGoal = 2;
 static_assert(kRingBuffers == 2, "bulk wait depth below assumes two staging buffers");
 
 // ------------------------------------------------------------- palette ----
-// Colours packed as 0x00BBGGRR so that the low three bytes are R, G, B.
-constexpr uint32_t rgb(uint32_t r, uint32_t g, uint32_t b) { return r | (g << 8) | (b << 16); }
-constexpr uint32_t shade34(uint32_t c) {  // y faces: each channel scaled by 3/4 (floor)
+// Colours packed as 0xYYBBGGRR: the low three bytes are R, G, B and the top
+// byte is the colour's integer BT.601 luma (77 R + 150 G + 29 B + 128) >> 8,
+// the pixel's value in the grayscale frame stack.
+constexpr uint32_t luma(uint32_t r, uint32_t g, uint32_t b) { return (77 * r + 150 * g + 29 * b + 128) >> 8; }
+constexpr uint32_t rgb(uint32_t r, uint32_t g, uint32_t b) { return r | (g << 8) | (b << 16) | (luma(r, g, b) << 24); }
+constexpr uint32_t shade34(uint32_t c) {  // y faces: each channel scaled by 3/4 (floor), luma of the result
   return rgb((((c >> 0) & 255) * 3) >> 2, (((c >> 8) & 255) * 3) >> 2, (((c >> 16) & 255) * 3) >> 2);
 }
 constexpr uint32_t kWall1 = rgb(160, 160, 160);
@@ -73,12 +76,12 @@ __device__ __forceinline__ uint32_t below(uint64_t d, uint32_t n) { return below
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
-__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+__device__ __forceinline__ void bulk_copy(void* gdst, const void* ssrc, uint32_t bytes) {
   uint32_t s = (uint32_t)__cvta_generic_to_shared(ssrc);
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(s), "r"(bytes)
                : "memory");
-  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
 }
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 // all but the newest group have finished reading shared memory
 __device__ __forceinline__ void bulk_wait_read_all_but_one() {
   asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
@@ -93,6 +96,7 @@ __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; 
 // Shared memory of a warp, addressed from one base with the layout offsets
 // of Params (constants), so no pointer lives in a register:
 //   ring      kRingBuffers * frame_block_bytes (also the maze work space)
+//   gray      kRingBuffers * gray_block_bytes: the row blocks of the grayscale frame
 //   pal       [2][8] wall colours by face and cell value, then [4] sprite colours by type
 //   map       S * S cell values, row-major
 //   col_rgb   [W] wall colour, chunk-interleaved (see col_slot)
@@ -104,6 +108,7 @@ __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; 
 //   spr_rect  [K] int4 pixel rectangle to test: first/last column, first/last row
 //   spr_ty    [K] depth;  spr_rgb [K] colour;  spr_kind [K] type
 //   order     [K] visible sprites, far to near
+//   spr_span  [K] first row << 16 | last row the oi-th sprite of that order can cover
 //   obj       [8] int32 key x, key y, goal x, goal y, door x, door y, sprites in use
 // The lane's place in the frame fill: lanes [0, groups * rows) are laid out
 // as `rows` rows of `groups` 8-pixel groups.
@@ -123,6 +128,7 @@ struct WarpSmem {
   uint8_t* base;
   FillLane fl;
   __device__ __forceinline__ uint8_t* ring() const { return base; }
+  __device__ __forceinline__ uint8_t* gray_ring(const Params& p) const { return base + p.off_gray; }
   __device__ __forceinline__ uint32_t* pal(const Params& p) const { return (uint32_t*)(base + p.off_pal); }
   __device__ __forceinline__ uint8_t* map(const Params& p) const { return base + p.off_map; }
   __device__ __forceinline__ uint32_t* col_rgb(const Params& p) const { return (uint32_t*)(base + p.off_col_rgb); }
@@ -136,6 +142,7 @@ struct WarpSmem {
   __device__ __forceinline__ uint32_t* spr_rgb(const Params& p) const { return (uint32_t*)(base + p.off_spr_rgb); }
   __device__ __forceinline__ int32_t* spr_kind(const Params& p) const { return (int32_t*)(base + p.off_spr_kind); }
   __device__ __forceinline__ int32_t* order(const Params& p) const { return (int32_t*)(base + p.off_order); }
+  __device__ __forceinline__ uint32_t* spr_span(const Params& p) const { return (uint32_t*)(base + p.off_spr_span); }
   __device__ __forceinline__ int32_t* obj(const Params& p) const { return (int32_t*)(base + p.off_obj); }
 };
 
@@ -485,10 +492,39 @@ __device__ __forceinline__ void gen_maze(const Params& p, int e, uint32_t ep, ui
   auto cell_of = [&](int v) { return (2 * (v / nn) + 1) * S + 2 * (v % nn) + 1; };
   const int kc = cell_of(key), gc = cell_of(goal);
   const int obj[6] = {kc % S, kc / S, gc % S, gc / S, dxc, dyc};
-  const int spr_cell[2] = {kc, gc};
-  const int spr_type[2] = {kSprKey, kSprGoal};
+  int spr_cell[kMaxSprites], spr_type[kMaxSprites];
+  spr_cell[0] = kc;
+  spr_type[0] = kSprKey;
+  spr_cell[1] = gc;
+  spr_type[1] = kSprGoal;
+  int nspr = 2;
+  if (p.task == 2) {
+    // open 8 x 8 rooms (the door kept), then distractors on floor cells
+    __syncwarp();
+    const uint64_t kr = stream_key(p.seed, (uint32_t)e, ep, P_ROOM);
+    const int n_rooms = n_cells / 1024;
+    for (int r = 0; r < n_rooms; ++r) {
+      const int x0 = 1 + (int)below(draw_at(kr, (uint32_t)(2 * r)), (uint32_t)(S - 9));
+      const int y0 = 1 + (int)below(draw_at(kr, (uint32_t)(2 * r + 1)), (uint32_t)(S - 9));
+      for (int j = lane; j < 64; j += 32) {
+        const int i = (y0 + (j >> 3)) * S + x0 + (j & 7);
+        if (smap[i] != kDoor) smap[i] = 0;
+      }
+    }
+    __syncwarp();
+    auto is_free = [&](int i) { return smap[i] == 0; };
+    const int n_free = count_cells(n_cells, lane, is_free);
+    const int nd = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_NSPRITES), 0), (uint32_t)(p.K - 1));
+    const uint64_t ks = stream_key(p.seed, (uint32_t)e, ep, P_SPRITE_CELL);
+    for (int k = 0; k < nd; ++k) {
+      const uint32_t c = below(draw_at(ks, (uint32_t)k), (uint32_t)n_free);
+      spr_cell[2 + k] = nth_cell(n_cells, c, lane, is_free);
+      spr_type[2 + k] = 3;
+    }
+    nspr = 2 + nd;
+  }
   __syncwarp();
-  write_episode_state(p, e, ep, cell_of(start), obj, 2, spr_cell, spr_type, lane);
+  write_episode_state(p, e, ep, cell_of(start), obj, nspr, spr_cell, spr_type, lane);
   store_map(p, e, smap, lane);
   __syncwarp();
 }
@@ -822,9 +858,10 @@ __device__ __forceinline__ void load_group(const Params& p, const WarpSmem& ws, 
 
 // Fill rows [r0, r1) of the frame into `buf` (row-major RGB), then draw the
 // sprites over them.
-__device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, uint8_t* buf, int r0, int r1,
-                                          int nvis, int lane) {
+__device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, uint8_t* buf, uint8_t* gbuf, int r0,
+                                          int r1, int nvis, int lane) {
   const int W = p.W, H = p.H, rowb = 3 * W, mid = H >> 1;
+  const bool gray = gbuf != nullptr;
   const int groups = ws.fl.groups;  // lanes per row, 8 pixels (24 bytes) each
   const int rpp = ws.fl.rows;       // rows per pass
   const int my_row = ws.fl.my_row, g = ws.fl.g;
@@ -841,13 +878,23 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
         for (int k = 0; k < 8; ++k) px[k] = row < gr.bot[k] ? gr.rgb[k] : kFloor;
       }
       store24(buf + (row - r0) * rowb + g * 24, px);
+      if (gray) {  // the luma bytes (top byte of each colour) of the 8 pixels
+        const uint32_t lo = __byte_perm(__byte_perm(px[0], px[1], 0x0073), __byte_perm(px[2], px[3], 0x0073), 0x5410);
+        const uint32_t hi = __byte_perm(__byte_perm(px[4], px[5], 0x0073), __byte_perm(px[6], px[7], 0x0073), 0x5410);
+        *reinterpret_cast<uint2*>(gbuf + (row - r0) * W + g * 8) = make_uint2(lo, hi);
+      }
     }
   }
   __syncwarp();
   // sprites, far to near; lanes take columns. For a column, the covered rows
   // are those whose centre has v in [0, 1) with |2v - 1| below the mask's
   // half-height at this u (key: 1 - |2u - 1|, disc: sqrt(1 - (2u - 1)^2)).
-  for (int oi = 0; oi < nvis; ++oi) {
+  // the sprites whose rows meet this block, far to near
+  const uint32_t span = lane < nvis ? ws.spr_span(p)[lane] : 0xFFFF0000u;
+  uint32_t hits = __ballot_sync(0xffffffffu, (int)(span >> 16) < r1 && (int)(span & 0xffffu) >= r0);
+  while (hits) {
+    const int oi = __ffs(hits) - 1;
+    hits &= hits - 1;
     const int j = ws.order(p)[oi];
     const int4 rc = ws.spr_rect(p)[j];
     const int rA = rc.z < r0 ? r0 : rc.z;
@@ -870,6 +917,7 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
           q[0] = (uint8_t)(rgbv & 255);
           q[1] = (uint8_t)((rgbv >> 8) & 255);
           q[2] = (uint8_t)((rgbv >> 16) & 255);
+          if (gray) gbuf[(row - r0) * W + col] = (uint8_t)(rgbv >> 24);
         }
       }
     }
@@ -877,22 +925,44 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
   }
 }
 
-template <int MODE, int MAPK, int COLS>
+// GRAY: 0 no grayscale stack, 1 a stack, 2 as p.st.gray says (batched kernel).
+template <int MODE, int MAPK, int COLS, int GRAY>
 __device__ __forceinline__ void render_env(const Params& p, int e, const Env& r, float c, float s,
                                            const WarpSmem& ws, int lane, int& slot, uint8_t* frame) {
   cast_columns<MODE, MAPK, COLS>(p, e, r, c, s, ws, lane);
   if (MODE == MODE_RAYS) return;
   const int nvis = project_sprites(p, r, c, s, ws, lane);  // ends with __syncwarp
-  const int H = p.H, rowb = 3 * p.W;
+  const int H = p.H, W = p.W, rowb = 3 * W;
+  if (lane < nvis) {  // rows each sprite of the far-to-near order can cover
+    const int4 rc = ws.spr_rect(p)[ws.order(p)[lane]];
+    ws.spr_span(p)[lane] = rc.x <= rc.y ? ((uint32_t)rc.z << 16) | (uint32_t)rc.w : 0xFFFF0000u;
+  }
+  __syncwarp();
+  const bool gray_on = GRAY == 1 || (GRAY == 2 && p.st.gray != nullptr);
   for (int r0 = 0; r0 < H; r0 += p.rows_per_block) {
     const int r1 = r0 + p.rows_per_block < H ? r0 + p.rows_per_block : H;
     uint8_t* buf = ws.ring() + slot * p.frame_block_bytes;
+    uint8_t* gbuf = gray_on ? ws.gray_ring(p) + slot * p.gray_block_bytes : nullptr;
     if (lane == 0) bulk_wait_read_all_but_one();
     __syncwarp();
-    fill_block(p, ws, buf, r0, r1, nvis, lane);
+    fill_block(p, ws, buf, gbuf, r0, r1, nvis, lane);
     fence_proxy_async_smem();
     __syncwarp();
-    if (lane == 0) bulk_store(frame + (size_t)r0 * rowb, buf, (uint32_t)((r1 - r0) * rowb));
+    if (lane == 0) {
+      bulk_copy(frame + (size_t)r0 * rowb, buf, (uint32_t)((r1 - r0) * rowb));
+      if (gray_on) {
+        // grayscale stack: plane t mod 4, or all four planes for an episode's first frame
+        const size_t plane = (size_t)H * W;
+        uint8_t* g0 = p.st.gray + (size_t)e * 4 * plane + (size_t)r0 * W;
+        const uint32_t gbytes = (uint32_t)((r1 - r0) * W);
+        if (r.t == 0) {
+          for (int k = 0; k < 4; ++k) bulk_copy(g0 + k * plane, gbuf, gbytes);
+        } else {
+          bulk_copy(g0 + (size_t)(r.t & 3) * plane, gbuf, gbytes);
+        }
+      }
+      bulk_commit();
+    }
     slot ^= 1;
   }
 }
@@ -919,7 +989,7 @@ __device__ __forceinline__ void open_door(const Params& p, int e, const Env& r, 
 
 // Everything one launch does for env e: MODE_ROLLOUT runs p.steps steps with
 // the env's scalar state in registers and its map in shared memory.
-template <int MODE, int MAPK, int COLS>
+template <int MODE, int MAPK, int COLS, int GRAY>
 __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, uint8_t* scratch, int lane,
                                         int& slot) {
   const WarpSmem ws{wbase, fill_lane(p, lane)};
@@ -945,8 +1015,8 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
         heading(p, r, c, s);
       }
       open_door<MAPK>(p, e, r, ws, lane);
-      render_env<MODE, MAPK, COLS>(p, e, r, c, s, ws, lane, slot,
-                                   p.frames + (size_t)t * p.frame_step + (size_t)e * frame_bytes);
+      render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot,
+                                         p.frames + (size_t)t * p.frame_step + (size_t)e * frame_bytes);
       __syncwarp();
     }
     if (lane == 0) {
@@ -991,7 +1061,7 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
     }
   }
   open_door<MAPK>(p, e, r, ws, lane);
-  render_env<MODE, MAPK, COLS>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
+  render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
   __syncwarp();
 }
 
@@ -1001,7 +1071,7 @@ __device__ __forceinline__ void write_palette(const Params& p, const WarpSmem& w
   __syncwarp();
 }
 
-template <int MODE, int MAPK>
+template <int MODE, int MAPK, int GRAY>
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __grid_constant__ Params p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1011,7 +1081,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __
   const int nw = gridDim.x * kWarpsPerBlock;
   uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;
   int slot = 0;
-  for (int e = gw; e < p.n; e += nw) run_env<MODE, MAPK, 1>(p, e, wbase, scratch, lane, slot);
+  for (int e = gw; e < p.n; e += nw) run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot);
   // shared memory stays allocated until the bulk stores have read it
   if (lane == 0) bulk_wait_read_all();
 }
@@ -1049,7 +1119,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
     while (ticket < (uint32_t)p.n) {
       uint32_t next = 0;
       if (lane == 0) next = atomicAdd(bp.queue + g, 1u);
-      run_env<MODE, MAP_RUNTIME, COLS>(p, (int)ticket, wbase, scratch, lane, slot);
+      run_env<MODE, MAP_RUNTIME, COLS, 2>(p, (int)ticket, wbase, scratch, lane, slot);
       ticket = __shfl_sync(0xffffffffu, next, 0);
     }
   }
@@ -1076,29 +1146,24 @@ cudaError_t raise_smem_limit(Kernel kernel) {
   return err;
 }
 
-template <int MODE, int MAPK>
-cudaError_t blocks_per_sm_for(const Params& p, int* blocks) {
-  cudaError_t err = raise_smem_limit(env_kernel<MODE, MAPK>);
-  if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, env_kernel<MODE, MAPK>, kThreads, block_smem_bytes(p));
+// The env kernel of a mode for p's map kind and grayscale stack.
+template <int MODE>
+auto env_kernel_of(const Params& p) {
+  if (p.map_bits) return p.gray ? env_kernel<MODE, MAP_BITS, 1> : env_kernel<MODE, MAP_BITS, 0>;
+  return p.gray ? env_kernel<MODE, MAP_BYTES, 1> : env_kernel<MODE, MAP_BYTES, 0>;
 }
 
 template <int MODE>
 cudaError_t blocks_per_sm_mode(const Params& p, int* blocks) {
-  return p.map_bits ? blocks_per_sm_for<MODE, MAP_BITS>(p, blocks) : blocks_per_sm_for<MODE, MAP_BYTES>(p, blocks);
-}
-
-template <int MODE, int MAPK>
-void launch_env(const Params& p, int grid, cudaStream_t stream) {
-  env_kernel<MODE, MAPK><<<grid, kThreads, block_smem_bytes(p), stream>>>(p);
+  auto k = env_kernel_of<MODE>(p);
+  cudaError_t err = raise_smem_limit(k);
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kThreads, block_smem_bytes(p));
 }
 
 template <int MODE>
 void launch_mode(const Params& p, int grid, cudaStream_t stream) {
-  if (p.map_bits)
-    launch_env<MODE, MAP_BITS>(p, grid, stream);
-  else
-    launch_env<MODE, MAP_BYTES>(p, grid, stream);
+  env_kernel_of<MODE>(p)<<<grid, kThreads, block_smem_bytes(p), stream>>>(p);
 }
 
 template <int MODE>
@@ -1126,6 +1191,7 @@ void layout_warp_smem(Params& p) {
     return at;
   };
   p.map_smem_bytes = align16(p.map_bits ? (p.S * p.S + 7) / 8 : p.S * p.S);
+  p.off_gray = take(kRingBuffers * p.gray_block_bytes);
   p.off_pal = take(4 * kPaletteWords);
   p.off_map = take(p.map_smem_bytes);
   p.off_col_rgb = take(4 * p.W);
@@ -1139,6 +1205,7 @@ void layout_warp_smem(Params& p) {
   p.off_spr_rgb = take(4 * K);
   p.off_spr_kind = take(4 * K);
   p.off_order = take(4 * K);
+  p.off_spr_span = take(4 * K);
   p.off_obj = take(4 * 8);
   p.warp_bytes = align16(q);
 }
@@ -1146,7 +1213,7 @@ void layout_warp_smem(Params& p) {
 int block_smem_bytes(const Params& p) { return p.warp_bytes * kWarpsPerBlock; }
 
 size_t gen_scratch_bytes(int task, int S) {
-  if (task != 1) return 0;
+  if (task != 1 && task != 2) return 0;
   int nn = (S - 2) / 2;
   return (maze_scratch_bytes(nn * nn) + 255) & ~(size_t)255;
 }

@@ -14,6 +14,7 @@ N_ACTIONS = 7  # noop, forward, back, strafe-left, strafe-right, turn-left, turn
 
 TASK_ROOMS = 0
 TASK_MAZE_KEYDOOR = 1
+TASK_MAZE_ROOMS = 2
 
 _COMMON = dict(
     frame_h=64,
@@ -52,6 +53,20 @@ def single_env_rooms() -> dict:
 def batched_keydoor_mazes(n_envs: int = 4096) -> dict:
     """4096 envs, 32 x 32 DFS key-door mazes, 64 x 64 RGB, horizon 500, 10,000 random steps, seed 1."""
     return maze_keydoor(n_envs=n_envs, map_side=32, seed=1, horizon=500)
+
+
+def maze_rooms(n_envs: int = 65536, map_side: int = 128, seed: int = 4, horizon: int = 500, max_sprites: int = 16,
+               frame_h: int = 128, frame_w: int = 128, gray_stack: int = 1) -> dict:
+    """Key-door mazes with S*S/1024 open 8 x 8 rooms and up to K - 2 distractor sprites
+    (rewards as the key-door maze), RGB frames plus the 4-frame grayscale stack."""
+    return dict(maze_keydoor(n_envs=n_envs, map_side=map_side, seed=seed, horizon=horizon, frame_h=frame_h,
+                             frame_w=frame_w), task=TASK_MAZE_ROOMS, max_sprites=max_sprites, gray_stack=gray_stack)
+
+
+def large_scale(n_envs: int = 65536) -> dict:
+    """65,536 envs, 128 x 128 mazes with 8 x 8 rooms, 16 sprite slots, 128 x 128 RGB and
+    the grayscale stack, horizon 500, 1000-step random-action rollouts, seed 4."""
+    return maze_rooms(n_envs=n_envs)
 
 
 UNEVEN_SIDES = (16, 32, 64, 128)

@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libjx.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, EDEVICE = range(7)
-TASK_ROOMS, TASK_MAZE_KEYDOOR = 0, 1
+TASK_ROOMS, TASK_MAZE_KEYDOOR, TASK_MAZE_ROOMS = 0, 1, 2
 
 # State fields (JX_F_*), name -> (index, numpy dtype, per-env shape builder)
 FIELDS = {
@@ -27,7 +27,7 @@ FIELDS = {
     "theta0": (4, np.float32), "turn": (5, np.int16), "t": (6, np.int32), "episode": (7, np.uint32),
     "flags": (8, np.uint8), "obj": (9, np.int16), "nspr": (10, np.uint8), "spr_x": (11, np.float32),
     "spr_y": (12, np.float32), "spr_type": (13, np.uint8), "map": (14, np.uint8), "cos0": (15, np.float32),
-    "sin0": (16, np.float32),
+    "sin0": (16, np.float32), "gray": (17, np.uint8),
 }
 
 # Entry points declared in include/jx.h (checked by the ABI test).
@@ -40,7 +40,7 @@ SYMBOLS = [
     "jx_batch_set_tiling", "jx_batch_get_tiling", "jx_batch_launch_shape", "jx_batch_launch_count",
     "jx_batch_reset", "jx_batch_step", "jx_batch_rollout", "jx_batch_render", "jx_batch_autotune",
     "jx_batch_capture", "jx_graph_launch", "jx_graph_destroy",
-    "jx_env_bytes", "jx_create_in",
+    "jx_env_bytes", "jx_create_in", "jx_autotune", "jx_env_tiling", "jx_env_set_tiling",
     "jx_server_create", "jx_server_destroy", "jx_server_open", "jx_server_close", "jx_server_session",
     "jx_server_submit", "jx_server_wait", "jx_server_pause", "jx_server_stats", "jx_server_latencies",
 ]
@@ -59,7 +59,7 @@ class Config(ctypes.Structure):
         ("horizon", ctypes.c_int32), ("turns_per_rev", ctypes.c_int32), ("wall_prob", ctypes.c_double),
         ("fov_deg", ctypes.c_double), ("move_step", ctypes.c_double), ("radius", ctypes.c_double),
         ("step_reward", ctypes.c_double), ("key_reward", ctypes.c_double), ("goal_reward", ctypes.c_double),
-        ("seed", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64), ("gray_stack", ctypes.c_int32),
     ]
 
     @classmethod
@@ -138,6 +138,9 @@ def _load() -> ctypes.CDLL:
         "jx_graph_launch": [P, P],
         "jx_graph_destroy": [P],
         "jx_env_bytes": [P, ctypes.c_int, P],
+        "jx_autotune": [P, P, i32, i32, i32, P, P, P],
+        "jx_env_tiling": [P, P],
+        "jx_env_set_tiling": [P, P],
         "jx_create_in": [P, ctypes.c_int, P, sz, P],
         "jx_server_create": [ctypes.c_int, ctypes.c_uint64, i32, i32, i32, P, P],
         "jx_server_destroy": [P],
@@ -299,7 +302,8 @@ class Env:
         """Views of every state field inside a ``get_state`` blob."""
         out = {}
         N, K, S = self.n, self.K, self.S
-        shapes = {"obj": (N, 6), "spr_x": (N, K), "spr_y": (N, K), "spr_type": (N, K), "map": (N, S, S)}
+        shapes = {"obj": (N, 6), "spr_x": (N, K), "spr_y": (N, K), "spr_type": (N, K), "map": (N, S, S),
+                  "gray": (N, 4, self.H, self.W) if self.cfg.get("gray_stack") else (0,)}
         for name, (_, dt) in FIELDS.items():
             off, nb = self.field(name)
             a = blob[off: off + nb].view(dt)
@@ -316,6 +320,26 @@ class Env:
         g, b, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(lib.jx_launch_shape(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(s)))
         return Shape(g.value, b.value, s.value)
+
+    def autotune(self, mode: int = 1, steps: int = 8, max_trials: int = 1000, stream=None):
+        """Time the env's own kernel (trial 0) against the batched kernel's tilings; keep
+        the fastest; every env is reset. Returns [(Tiling, ms_per_step)]."""
+        trials = (Tiling * max_trials)()
+        ms = (ctypes.c_float * max_trials)()
+        n = ctypes.c_int32()
+        _check(lib.jx_autotune(self._h, _stream(stream), mode, steps, max_trials, ctypes.byref(n), trials, ms))
+        return [(trials[i], float(ms[i])) for i in range(n.value)]
+
+    @property
+    def tiling(self) -> "Tiling":
+        """All zero while the env's own kernel runs, else the batched kernel's tiling."""
+        t = Tiling()
+        _check(lib.jx_env_tiling(self._h, ctypes.byref(t)))
+        return t
+
+    @tiling.setter
+    def tiling(self, t: "Tiling | None"):
+        _check(lib.jx_env_set_tiling(self._h, ctypes.byref(t if t is not None else Tiling())))
 
 
 def default_tiling() -> Tiling:

@@ -144,6 +144,7 @@ class Run:
         self.perp = torch.zeros((N, W), dtype=torch.float32, device=dev)
         self.actions = torch.zeros(N, dtype=torch.uint8, device=dev)
         self.dev = dev
+        self.gray = GrayModel(N, H, W) if cfg.get("gray_stack") else None
 
     def state(self, idx=None) -> np.ndarray:
         return to_oracle(self.env, self.env.get_state(), idx)
@@ -164,10 +165,36 @@ class Run:
         return self.frames.cpu().numpy(), self.rewards.cpu().numpy(), self.dones.cpu().numpy()
 
 
+class GrayModel:
+    """The grayscale stack a Run's envs should hold, rebuilt on the host from the
+    GPU's RGB frames and step counters: the frame of episode step t in plane
+    t mod 4, an episode's first frame in all four planes."""
+
+    def __init__(self, n: int, H: int, W: int):
+        self.planes = np.zeros((n, 4, H, W), np.uint8)
+
+    def update(self, frames: np.ndarray, t: np.ndarray):
+        g = oracle.gray(frames)
+        for e in range(len(t)):
+            if t[e] == 0:
+                self.planes[e, :] = g[e]
+            else:
+                self.planes[e, t[e] % 4] = g[e]
+
+    def check(self, env: jx.Env, idx=None):
+        f = env.fields(env.get_state())
+        got = f["gray"] if idx is None else f["gray"][idx]
+        want = self.planes if idx is None else self.planes[idx]
+        assert (got == want).all(), "grayscale stack differs"
+
+
 def check_reset(run: Run, stats: Stats, idx=None):
     N = run.cfg["n_envs"]
     idx = np.arange(N) if idx is None else np.asarray(idx)
     run.reset()
+    if run.gray is not None:
+        run.gray.update(run.frames.cpu().numpy(), run.env.fields(run.env.get_state())["t"])
+        run.gray.check(run.env)
     gpu = run.state(idx)
     ref = oracle.generate(run.ocfg, idx.astype(np.int32), 0, nthreads=NTHREADS)
     compare_generated(gpu, ref, run.env.S, run.env.K, "at reset")
@@ -200,8 +227,12 @@ def lockstep(run: Run, stats: Stats, n_steps: int, seed: int, first_step: int = 
         if check:
             prev = run.state(idx)
         frames, rewards, dones = run.step(a)
+        if run.gray is not None:
+            run.gray.update(frames, run.env.fields(run.env.get_state())["t"])
         if not check:
             continue
+        if run.gray is not None:
+            run.gray.check(run.env)
         cur = run.state(idx)
         ref = oracle.step(run.ocfg, idx.astype(np.int32), prev, a[idx], nthreads=NTHREADS)
         ev = ref["events"]

@@ -234,3 +234,29 @@ def test_full_size_uneven_batch_sampled():
     rf, _, _ = _rollout(run, torch.from_numpy(acts).to(run.dev))
     for s in range(T):
         assert (rf[s].cpu().numpy() == step_frames[s]).all(), s
+
+
+@pytest.mark.parametrize("cfg", [inputs.maze_keydoor(n_envs=40, map_side=32, seed=101, horizon=30),
+                                 inputs.maze_rooms(n_envs=9, map_side=64, seed=102, horizon=20, frame_h=96,
+                                                   frame_w=96)])
+def test_env_autotune_and_pinned_tilings_give_identical_results(cfg):
+    """jx_autotune times the env's own kernel (trial 0) against batched tilings and
+    resets every env; whichever kernel an env is pinned to, its frames, rewards,
+    dones and state (grayscale stack included) are the same."""
+    ref, tuned = Run(cfg), Run(cfg)
+    trials = tuned.env.autotune(mode=1, steps=3, max_trials=6)
+    assert len(trials) == 6 and trials[0][0].as_tuple() == (0, 0, 0, 0)
+    best = min(trials, key=lambda x: x[1])[0].as_tuple()
+    assert tuned.env.tiling.as_tuple() == best
+    ref.reset()
+    assert (ref.env.get_state() == tuned.env.get_state()).all()
+    pins = [tiling(4, 2, 8, 4), None, tiling(1, 1, 0, 16)]
+    tuned.reset()
+    for s in range(36):
+        if s % 12 == 0:
+            tuned.env.tiling = pins[s // 12]
+        act = forward_biased_actions(103, s, cfg["n_envs"])
+        fa, ra, da = ref.step(act)
+        fb, rb, db = tuned.step(act)
+        assert (fa == fb).all() and (ra == rb).all() and (da == db).all(), s
+    assert (ref.env.get_state() == tuned.env.get_state()).all()

@@ -5,8 +5,8 @@ import torch
 
 import oracle
 from paper_2605_19926_gb300 import inputs
-from parity import (NTHREADS, Run, Stats, check_door_crossings, check_reset, compare_frames, compare_rays,
-                    forward_biased_actions, lockstep, script_goal_and_door, to_oracle)
+from parity import (NTHREADS, Run, Stats, check_door_crossings, check_reset, compare_frames, compare_generated,
+                    compare_rays, forward_biased_actions, lockstep, script_goal_and_door, to_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -27,6 +27,11 @@ CASES = {
     "maze8_events": inputs.maze_keydoor(n_envs=64, map_side=8, seed=3, horizon=120),
     "maze6_events": inputs.maze_keydoor(n_envs=64, map_side=6, seed=5, horizon=120),
     "maze18_96x128": inputs.maze_keydoor(n_envs=9, map_side=18, seed=7, horizon=30, frame_h=96, frame_w=128),
+    "mazerooms64_gray": inputs.maze_rooms(n_envs=12, map_side=64, seed=8, horizon=25, max_sprites=16, frame_h=64,
+                                          frame_w=64),
+    "mazerooms128_gray_128x128": inputs.maze_rooms(n_envs=5, map_side=128, seed=9, horizon=20),
+    "mazerooms32_gray_48x80": inputs.maze_rooms(n_envs=21, map_side=32, seed=10, horizon=15, max_sprites=6,
+                                                frame_h=48, frame_w=80),
 }
 
 
@@ -49,7 +54,9 @@ def test_single_env_rooms_1000_steps():
 
 
 @pytest.mark.parametrize("name,steps", [("maze32_ragged", 150), ("maze8_events", 300), ("maze6_events", 300),
-                                        ("rooms16_sprites_40x48", 120), ("maze18_96x128", 70)])
+                                        ("rooms16_sprites_40x48", 120), ("maze18_96x128", 70),
+                                        ("mazerooms64_gray", 60), ("mazerooms128_gray_128x128", 45),
+                                        ("mazerooms32_gray_48x80", 40)])
 def test_lockstep(name, steps):
     run = Run(CASES[name])
     stats = Stats()
@@ -59,7 +66,7 @@ def test_lockstep(name, steps):
     stats.check()
     if events:
         assert stats.key_events > 0 and stats.resets > 0, stats
-    if name in ("maze32_ragged", "maze18_96x128"):
+    if name in ("maze32_ragged", "maze18_96x128") or name.startswith("mazerooms"):
         assert stats.resets > 0
 
 
@@ -263,4 +270,61 @@ def test_envs_of_different_sizes_coexist():
         run.env.render(run.frames)
         torch.cuda.synchronize()
         compare_frames(run.frames.cpu().numpy(), ref, stats)
+    stats.check()
+
+
+@pytest.mark.parametrize("name,T", [("mazerooms64_gray", 60), ("mazerooms128_gray_128x128", 30)])
+def test_rollout_with_gray_stack_matches_step_sequence(name, T):
+    """Rollouts write the grayscale stack exactly as the step sequence does."""
+    cfg = CASES[name]
+    a, b = Run(cfg), Run(cfg)
+    a.reset()
+    b.reset()
+    acts = torch.from_numpy(inputs.action_stream(19, T, cfg["n_envs"])).to(a.dev)
+    N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
+    frames = torch.zeros((T, N, H, W, 3), dtype=torch.uint8, device=a.dev)
+    rewards = torch.zeros((T, N), dtype=torch.float32, device=a.dev)
+    dones = torch.zeros((T, N), dtype=torch.uint8, device=a.dev)
+    b.env.rollout(acts, frames, rewards, dones)
+    for t in range(T):
+        a.actions.copy_(acts[t])
+        a.env.step(a.actions, a.frames, a.rewards, a.dones)
+        assert torch.equal(a.frames, frames[t]), t
+    torch.cuda.synchronize()
+    assert (a.env.get_state() == b.env.get_state()).all()  # gray planes included
+    assert int(dones.sum().item()) > 0
+
+
+def test_large_scale_mazes_with_rooms_sampled():
+    """65,536 envs of 128 x 128 mazes with rooms, 16 sprite slots, 128 x 128 RGB and
+    the grayscale stack: 24 sampled envs against the oracle at reset and over
+    4 steps; their grayscale stacks against the host model."""
+    cfg = inputs.large_scale()
+    run = Run(cfg)
+    stats = Stats()
+    rng = np.random.default_rng(12)
+    idx = np.sort(rng.choice(cfg["n_envs"], 24, replace=False))
+    idx[-1] = cfg["n_envs"] - 1
+    run.reset()
+    gpu = run.state(idx)
+    ref = oracle.generate(run.ocfg, idx.astype(np.int32), 0, nthreads=NTHREADS)
+    compare_generated(gpu, ref, run.env.S, run.env.K, "at reset")
+    compare_frames(run.frames.cpu().numpy()[idx], oracle.render(run.ocfg, gpu, nthreads=NTHREADS), stats)
+    g = oracle.gray(run.frames.cpu().numpy()[idx])
+    f = run.env.fields(run.env.get_state())
+    assert (f["gray"][idx] == g[:, None]).all()
+    for s in range(4):
+        prev = run.state(idx)
+        a = inputs.actions(4, s, cfg["n_envs"])
+        frames, rewards, dones = run.step(a)
+        cur = run.state(idx)
+        r = oracle.step(run.ocfg, idx.astype(np.int32), prev, a[idx], nthreads=NTHREADS)
+        ok = (r["events"] & oracle.EV_NEAR_TIE) == 0
+        assert (rewards[idx][ok] == r["rewards"][ok]).all() and (dones[idx][ok] == r["dones"][ok]).all()
+        assert np.abs(cur["x"][ok] - prev["x"][ok]).max(initial=0.0) <= 1e-5
+        compare_frames(frames[idx], oracle.render(run.ocfg, cur, nthreads=NTHREADS), stats)
+        f = run.env.fields(run.env.get_state())
+        t = f["t"][idx]
+        planes = f["gray"][idx][np.arange(len(idx)), t % 4]
+        assert (planes == oracle.gray(frames[idx])).all()
     stats.check()
