@@ -33,6 +33,13 @@ MAX_SPRITES = 16
 TASK_ROOMS = 0
 TASK_MAZE_KEYDOOR = 1
 TASK_MAZE_ROOMS = 2
+TASK_ASCII = 3
+
+FLOOR = 0
+LOCKED = 16  # + colour (0 red, 1 blue, 2 yellow)
+UNLOCKED = 20  # + colour
+DOOR = LOCKED  # the red locked door of the generated key-door mazes
+SPR_KEY, SPR_GOAL, SPR_DISTRACTOR, SPR_KEY_BLUE, SPR_KEY_YELLOW = 1, 2, 3, 4, 5
 
 EV_KEY = 1
 EV_GOAL = 2
@@ -47,7 +54,7 @@ CONFIG_DTYPE = np.dtype(
         ("max_sprites", np.int32),
         ("horizon", np.int32),
         ("turns_per_rev", np.int32),
-        ("pad0", np.int32),
+        ("shading", np.int32),
         ("wall_prob", np.float64),
         ("fov_deg", np.float64),
         ("move_step", np.float64),
@@ -56,6 +63,7 @@ CONFIG_DTYPE = np.dtype(
         ("key_reward", np.float64),
         ("goal_reward", np.float64),
         ("seed", np.uint64),
+        ("ascii", np.uint64),
     ],
     align=True,
 )
@@ -68,7 +76,7 @@ ENV_DTYPE = np.dtype(
         ("turn", np.int32),
         ("t", np.int32),
         ("episode", np.uint32),
-        ("has_key", np.int32),
+        ("keys", np.int32),
         ("key_x", np.int32),
         ("key_y", np.int32),
         ("goal_x", np.int32),
@@ -137,6 +145,8 @@ def lib() -> ctypes.CDLL:
         L.jxo_generate_batch.argtypes = [P, P, P, P, i32, i32]
         L.jxo_gray.argtypes = [P, ctypes.c_int64, P]
         L.jxo_gray.restype = None
+        L.jxo_parse_ascii.argtypes = [ctypes.c_char_p, i32, P]
+        L.jxo_sizeof_ascii.restype = ctypes.c_int
         assert L.jxo_sizeof_env() == ENV_DTYPE.itemsize, "oracle env layout mismatch"
         assert L.jxo_sizeof_config() == CONFIG_DTYPE.itemsize, "oracle config layout mismatch"
         assert L.jxo_sizeof_ray() == RAY_DTYPE.itemsize, "oracle ray layout mismatch"
@@ -151,12 +161,27 @@ def _ptr(a: np.ndarray | None):
     return a.ctypes.data
 
 
+_ascii_maps = []  # parsed maps referenced by configs (kept alive for the process)
+
+
+def parse_ascii(text: str, side: int) -> np.ndarray:
+    """The oracle's parse of an ASCII map (Table 2 symbols) laid out in an S x S grid."""
+    buf = np.zeros(lib().jxo_sizeof_ascii(), np.uint8)
+    if lib().jxo_parse_ascii(text.encode("ascii"), side, _ptr(buf)) != 0:
+        raise ValueError("oracle: ASCII map does not parse")
+    _ascii_maps.append(buf)
+    return buf
+
+
 def make_config(**params) -> np.ndarray:
-    """A one-element CONFIG_DTYPE record; unknown keys (e.g. ``n_envs``) are ignored."""
+    """A one-element CONFIG_DTYPE record; unknown keys (e.g. ``n_envs``) are ignored.
+    ``ascii_map`` (text) is parsed by the oracle for the ASCII task."""
     cfg = np.zeros(1, dtype=CONFIG_DTYPE)
     for name in CONFIG_DTYPE.names:
-        if name in params:
+        if name in params and name != "ascii":
             cfg[name] = params[name]
+    if params.get("ascii_map") is not None:
+        cfg["ascii"] = parse_ascii(params["ascii_map"], int(params["map_side"])).ctypes.data
     return cfg
 
 

@@ -70,23 +70,44 @@ int jxo_sizeof_ray(void) { return (int)sizeof(jxo_ray); }
  * The paper renders untextured walls, a red key, a red locked door and a
  * yellow goal (Table 1, Table 2). The exact RGB values are this
  * implementation's choice; they are fixed. */
+static void set_rgb(uint8_t rgb[3], int r, int g, int b) {
+  rgb[0] = (uint8_t)r;
+  rgb[1] = (uint8_t)g;
+  rgb[2] = (uint8_t)b;
+}
 static void wall_rgb(int v, uint8_t rgb[3]) {
   switch (v) {
-    case 2: rgb[0] = 64; rgb[1] = 160; rgb[2] = 64; break;
-    case 3: rgb[0] = 64; rgb[1] = 96; rgb[2] = 192; break;
-    case 4: rgb[0] = 176; rgb[1] = 144; rgb[2] = 80; break;
-    case JXO_DOOR: rgb[0] = 200; rgb[1] = 32; rgb[2] = 32; break;
-    default: rgb[0] = 160; rgb[1] = 160; rgb[2] = 160; break; /* type 1 and anything else */
+    case 2: set_rgb(rgb, 64, 160, 64); break;
+    case 3: set_rgb(rgb, 64, 96, 192); break;
+    case 4: set_rgb(rgb, 176, 144, 80); break;
+    case 5: set_rgb(rgb, 200, 100, 40); break;
+    case 6: set_rgb(rgb, 112, 64, 160); break;
+    case 7: set_rgb(rgb, 40, 160, 160); break;
+    case 8: set_rgb(rgb, 128, 128, 48); break;
+    case 9: set_rgb(rgb, 216, 216, 216); break;
+    case JXO_LOCKED + 0: set_rgb(rgb, 200, 32, 32); break;
+    case JXO_LOCKED + 1: set_rgb(rgb, 32, 64, 200); break;
+    case JXO_LOCKED + 2: set_rgb(rgb, 208, 184, 32); break;
+    case JXO_UNLOCKED + 0: set_rgb(rgb, 232, 120, 120); break;
+    case JXO_UNLOCKED + 1: set_rgb(rgb, 120, 150, 232); break;
+    case JXO_UNLOCKED + 2: set_rgb(rgb, 236, 222, 128); break;
+    default: set_rgb(rgb, 160, 160, 160); break; /* type 1 and anything else */
   }
 }
 static const uint8_t CEIL_RGB[3] = {48, 48, 56};
 static const uint8_t FLOOR_RGB[3] = {104, 96, 88};
 static void sprite_rgb(int type, uint8_t rgb[3]) {
   switch (type) {
-    case JXO_SPR_KEY: rgb[0] = 224; rgb[1] = 40; rgb[2] = 40; break;
-    case JXO_SPR_GOAL: rgb[0] = 240; rgb[1] = 208; rgb[2] = 32; break;
-    default: rgb[0] = 144; rgb[1] = 64; rgb[2] = 192; break;
+    case JXO_SPR_KEY: set_rgb(rgb, 224, 40, 40); break;
+    case JXO_SPR_GOAL: set_rgb(rgb, 240, 208, 32); break;
+    case JXO_SPR_KEY_BLUE: set_rgb(rgb, 40, 80, 224); break;
+    case JXO_SPR_KEY_YELLOW: set_rgb(rgb, 232, 200, 40); break;
+    default: set_rgb(rgb, 144, 64, 192); break;
   }
+}
+/* colour of a key sprite type, -1 for other types */
+static int key_colour(int type) {
+  return type == JXO_SPR_KEY ? 0 : (type == JXO_SPR_KEY_BLUE ? 1 : (type == JXO_SPR_KEY_YELLOW ? 2 : -1));
 }
 
 /* ---------------------------------------------------------------- map ---- */
@@ -98,6 +119,9 @@ static int config_ok(const jxo_config* cfg) {
   if (cfg->turns_per_rev < 1) return 0;
   if (cfg->task == JXO_TASK_MAZE_KEYDOOR || cfg->task == JXO_TASK_MAZE_ROOMS) {
     if (S < 6 || (S % 2) != 0 || cfg->max_sprites < 2) return 0;
+  } else if (cfg->task == JXO_TASK_ASCII) {
+    const jxo_ascii* a = (const jxo_ascii*)(uintptr_t)cfg->ascii;
+    if (!a || a->side != S || cfg->max_sprites < a->n_keys + (a->n_goal > 0)) return 0;
   } else if (cfg->task != JXO_TASK_ROOMS) {
     return 0;
   }
@@ -111,11 +135,12 @@ static int cell_value(const jxo_config* cfg, const jxo_env* e, int x, int y) {
   return e->map[y * S + x];
 }
 
-/* Walls are solid; the locked door is solid while the key is not held. */
+/* Walls and closed doors are solid; a locked door is open (floor) while the
+ * key of its colour is held (Table 2: locked doors open with their key). */
 static int is_solid(const jxo_config* cfg, const jxo_env* e, int x, int y) {
   int v = cell_value(cfg, e, x, y);
   if (v == JXO_FLOOR) return 0;
-  if (v == JXO_DOOR && e->has_key) return 0;
+  if (v >= JXO_LOCKED && v < JXO_LOCKED + 3 && ((e->keys >> (v - JXO_LOCKED)) & 1)) return 0;
   return 1;
 }
 
@@ -377,6 +402,107 @@ static void gen_maze_rooms(const jxo_config* cfg, int32_t env, uint32_t ep, jxo_
   e->n_sprites = 2 + (int32_t)n;
 }
 
+/* ASCII maps (Table 2): each episode starts from the parsed map: the spawn
+ * uniform over the 'S' cells (over all floor cells when there is none), the
+ * goal sprite on one 'G' cell drawn uniformly each episode (DMLab's random
+ * goal; the only one when there is one), the keys as sprites on their cells
+ * in row-major order, then the goal. Doors start as written. */
+static void gen_ascii(const jxo_config* cfg, int32_t env, uint32_t ep, jxo_env* e) {
+  const jxo_ascii* a = (const jxo_ascii*)(uintptr_t)cfg->ascii;
+  int S = cfg->map_side;
+  uint64_t seed = cfg->seed;
+  memcpy(e->map, a->map, (size_t)S * S);
+  uint64_t d = jxo_draw(seed, (uint32_t)env, ep, JXO_P_SPAWN, 0);
+  int cell = 0;
+  if (a->n_spawn > 0) {
+    cell = a->spawn[uniform_below(d, (uint32_t)a->n_spawn)];
+  } else {
+    int n_free = 0;
+    for (int i = 0; i < S * S; ++i) n_free += e->map[i] == JXO_FLOOR;
+    uint32_t pick = uniform_below(d, (uint32_t)n_free);
+    for (int i = 0, seen = 0; i < S * S; ++i) {
+      if (e->map[i] != JXO_FLOOR) continue;
+      if ((uint32_t)seen++ == pick) {
+        cell = i;
+        break;
+      }
+    }
+  }
+  e->x = (cell % S) + 0.5;
+  e->y = (cell / S) + 0.5;
+  int k = 0;
+  const int key_type[3] = {JXO_SPR_KEY, JXO_SPR_KEY_BLUE, JXO_SPR_KEY_YELLOW};
+  for (int i = 0; i < a->n_keys; ++i, ++k) {
+    e->spr_x[k] = (a->key_cell[i] % S) + 0.5;
+    e->spr_y[k] = (a->key_cell[i] / S) + 0.5;
+    e->spr_type[k] = key_type[a->key_colour[i]];
+  }
+  e->key_x = a->n_keys ? a->key_cell[0] % S : -1;
+  e->key_y = a->n_keys ? a->key_cell[0] / S : -1;
+  e->goal_x = e->goal_y = -1;
+  if (a->n_goal > 0) {
+    int g = a->goal[uniform_below(jxo_draw(seed, (uint32_t)env, ep, JXO_P_GOAL, 0), (uint32_t)a->n_goal)];
+    e->spr_x[k] = (g % S) + 0.5;
+    e->spr_y[k] = (g / S) + 0.5;
+    e->spr_type[k] = JXO_SPR_GOAL;
+    ++k;
+    e->goal_x = g % S;
+    e->goal_y = g / S;
+  }
+  e->door_x = e->door_y = -1;
+  for (int i = 0; i < S * S; ++i)
+    if (e->map[i] >= JXO_LOCKED && e->map[i] < JXO_LOCKED + 3) {
+      e->door_x = i % S;
+      e->door_y = i / S;
+      break;
+    }
+  e->n_sprites = k;
+}
+
+int jxo_sizeof_ascii(void) { return (int)sizeof(jxo_ascii); }
+
+int jxo_parse_ascii(const char* text, int32_t side, jxo_ascii* a) {
+  if (!text || !a || side < 3 || side > JXO_MAX_SIDE) return -1;
+  memset(a, 0, sizeof(*a));
+  a->side = side;
+  for (int i = 0; i < side * side; ++i) a->map[i] = 1;
+  int row = 0, col = 0, n_floor = 0;
+  for (const char* q = text; *q; ++q) {
+    char ch = *q;
+    if (ch == '\n') {
+      ++row;
+      col = 0;
+      continue;
+    }
+    if (ch == '\r') continue;
+    if ((unsigned char)ch < 32 || (unsigned char)ch > 126) return -1;
+    if (row >= side || col >= side) return -1;
+    int cell = row * side + col, v;
+    switch (ch) {
+      case '#': v = 1; break;
+      case '.': case ' ': v = JXO_FLOOR; break;
+      case 'S': v = JXO_FLOOR; a->spawn[a->n_spawn++] = cell; break;
+      case 'G': v = JXO_FLOOR; a->goal[a->n_goal++] = cell; break;
+      case 'r': case 'b': case 'y':
+        if (a->n_keys == JXO_MAX_SPRITES) return -1;
+        v = JXO_FLOOR;
+        a->key_cell[a->n_keys] = cell;
+        a->key_colour[a->n_keys++] = ch == 'r' ? 0 : (ch == 'b' ? 1 : 2);
+        break;
+      case '"': v = JXO_UNLOCKED + 1; break;
+      case '\\': v = JXO_UNLOCKED + 2; break;
+      case 'R': v = JXO_LOCKED + 0; break;
+      case 'B': v = JXO_LOCKED + 1; break;
+      case 'Y': v = JXO_LOCKED + 2; break;
+      default: v = (ch >= '1' && ch <= '9') ? ch - '0' : 1 + ((unsigned char)ch % 9); break;
+    }
+    a->map[cell] = (uint8_t)v;
+    n_floor += v == JXO_FLOOR;
+    ++col;
+  }
+  return n_floor > 0 ? 0 : -1;
+}
+
 void jxo_gray(const uint8_t* rgb, int64_t n, uint8_t* out) {
   for (int64_t i = 0; i < n; ++i)
     out[i] = (uint8_t)((77 * (int)rgb[3 * i] + 150 * (int)rgb[3 * i + 1] + 29 * (int)rgb[3 * i + 2] + 128) >> 8);
@@ -388,9 +514,11 @@ int jxo_generate(const jxo_config* cfg, int32_t env_index, uint32_t episode, jxo
   out->episode = episode;
   out->t = 0;
   out->turn = 0;
-  out->has_key = 0;
+  out->keys = 0;
   if (cfg->task == JXO_TASK_ROOMS)
     gen_rooms(cfg, env_index, episode, out);
+  else if (cfg->task == JXO_TASK_ASCII)
+    gen_ascii(cfg, env_index, episode, out);
   else if (cfg->task == JXO_TASK_MAZE_ROOMS)
     gen_maze_rooms(cfg, env_index, episode, out);
   else
@@ -426,11 +554,38 @@ static int box_near_tie(const jxo_config* cfg, const jxo_env* e, double px, doub
   return box_free_margin(cfg, e, px, py, JXO_EPS_CELL) != box_free_margin(cfg, e, px, py, -JXO_EPS_CELL);
 }
 
-static int pickup_events(const jxo_env* e, double px, double py, int has_key) {
+/* An unlocked door opens when the agent walks into it (there is no separate
+ * toggle action): every unlocked door cell the rejected box overlaps becomes
+ * floor. */
+static void open_unlocked(const jxo_config* cfg, jxo_env* e, double px, double py) {
+  int S = cfg->map_side;
+  double r = cfg->radius;
+  int x0 = (int)floor(px - r), x1 = (int)floor(px + r);
+  int y0 = (int)floor(py - r), y1 = (int)floor(py + r);
+  for (int j = y0; j <= y1; ++j)
+    for (int i = x0; i <= x1; ++i) {
+      if (i < 0 || j < 0 || i >= S || j >= S) continue;
+      int v = e->map[j * S + i];
+      if (v >= JXO_UNLOCKED && v < JXO_UNLOCKED + 3) e->map[j * S + i] = JXO_FLOOR;
+    }
+}
+
+/* Key and goal events at position (px, py): a key sprite whose cell is the
+ * agent's cell and whose colour is not held yet is picked up (its colour
+ * bit into *picked); a goal sprite there is reached. */
+static int pickup_events(const jxo_env* e, double px, double py, int* picked) {
   int cx = (int)floor(px), cy = (int)floor(py);
-  int ev = 0;
-  if (!has_key && e->key_x >= 0 && cx == e->key_x && cy == e->key_y) ev |= JXO_EV_KEY;
-  if (e->goal_x >= 0 && cx == e->goal_x && cy == e->goal_y) ev |= JXO_EV_GOAL;
+  int ev = 0, bits = 0;
+  for (int j = 0; j < e->n_sprites; ++j) {
+    if ((int)floor(e->spr_x[j]) != cx || (int)floor(e->spr_y[j]) != cy) continue;
+    int c = key_colour(e->spr_type[j]);
+    if (c >= 0 && !((e->keys >> c) & 1)) {
+      ev |= JXO_EV_KEY;
+      bits |= 1 << c;
+    }
+    if (e->spr_type[j] == JXO_SPR_GOAL) ev |= JXO_EV_GOAL;
+  }
+  if (picked) *picked = bits;
   return ev;
 }
 
@@ -453,21 +608,28 @@ int jxo_step(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t actio
   int near = 0;
   double nx = e->x + dx;
   near |= box_near_tie(cfg, e, nx, e->y);
-  if (!box_free(cfg, e, nx, e->y)) nx = e->x;
+  if (!box_free(cfg, e, nx, e->y)) {
+    open_unlocked(cfg, e, nx, e->y);
+    nx = e->x;
+  }
   double ny = e->y + dy;
   near |= box_near_tie(cfg, e, nx, ny);
-  if (!box_free(cfg, e, nx, ny)) ny = e->y;
+  if (!box_free(cfg, e, nx, ny)) {
+    open_unlocked(cfg, e, nx, ny);
+    ny = e->y;
+  }
   e->x = nx;
   e->y = ny;
 
-  int ev = pickup_events(e, nx, ny, e->has_key);
+  int picked = 0;
+  int ev = pickup_events(e, nx, ny, &picked);
   /* a key or goal event that moving the position by JXO_EPS_CELL could flip */
   for (int k = 0; k < 4; ++k) {
     double px = nx + ((k & 1) ? JXO_EPS_CELL : -JXO_EPS_CELL);
     double py = ny + ((k & 2) ? JXO_EPS_CELL : -JXO_EPS_CELL);
-    if (pickup_events(e, px, py, e->has_key) != ev) near = 1;
+    if (pickup_events(e, px, py, NULL) != ev) near = 1;
   }
-  if (ev & JXO_EV_KEY) e->has_key = 1;
+  e->keys |= picked;
   *reward = cfg->step_reward + ((ev & JXO_EV_KEY) ? cfg->key_reward : 0.0) +
             ((ev & JXO_EV_GOAL) ? cfg->goal_reward : 0.0);
   e->t += 1;
@@ -552,10 +714,12 @@ static void slice_rows(int H, double perp, jxo_ray* r) {
   }
 }
 
+/* a key whose colour is held is no longer drawn */
 static int sprite_visible(const jxo_env* e, int j) {
   int type = e->spr_type[j];
   if (type == JXO_SPR_NONE) return 0;
-  if (type == JXO_SPR_KEY && e->has_key) return 0;
+  int c = key_colour(type);
+  if (c >= 0 && ((e->keys >> c) & 1)) return 0;
   return 1;
 }
 
@@ -564,7 +728,7 @@ static int sprite_visible(const jxo_env* e, int j) {
  * signed margin (> 0 inside); the rectangle's own edges are tested apart. */
 static double mask_margin(int type, double u, double v) {
   double a = 2.0 * u - 1.0, b = 2.0 * v - 1.0;
-  if (type == JXO_SPR_KEY) return 1.0 - (fabs(a) + fabs(b));
+  if (key_colour(type) >= 0) return 1.0 - (fabs(a) + fabs(b));
   if (type == JXO_SPR_GOAL) return 1.0;
   return 1.0 - (a * a + b * b);
 }
@@ -628,13 +792,20 @@ int jxo_render(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray*
     }
   }
 
-  /* walls, ceiling and floor; the wall colour is scaled by 3/4 on y faces */
+  /* walls, ceiling and floor; the wall colour is scaled by 3/4 on y faces
+   * and, with distance shading (Sec. 2.1: shading from the distance), by
+   * q / 256 with q = 64 + floor(192 min(h, H) / H): full colour for a slice
+   * of the whole frame height or more, a quarter of it far away */
   for (int col = 0; col < W; ++col) {
     const jxo_ray* r = &col_rays[col];
     uint8_t wall[3];
     wall_rgb(r->side >= 0 ? cell_value(cfg, e, r->cell_x, r->cell_y) : 1, wall);
     if (r->side == 1)
       for (int k = 0; k < 3; ++k) wall[k] = (uint8_t)((wall[k] * 3) >> 2);
+    if (cfg->shading) {
+      int q = 64 + (192 * (r->h < H ? r->h : H)) / H;
+      for (int k = 0; k < 3; ++k) wall[k] = (uint8_t)((wall[k] * q) >> 8);
+    }
     for (int row = 0; row < H; ++row) {
       const uint8_t* rgb = row < r->top ? CEIL_RGB : (row < r->bot ? wall : FLOOR_RGB);
       uint8_t* px = frame + ((size_t)row * W + col) * 3;
@@ -645,6 +816,10 @@ int jxo_render(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray*
     if (ambiguous) {
       if (r->corner) {
         for (int row = 0; row < H; ++row) ambiguous[row * W + col] = 1;
+      } else if (r->h_ambiguous && cfg->shading) {
+        /* a one-row change of h recolours the whole slice */
+        for (int row = r->top - 1; row <= r->bot; ++row)
+          if (row >= 0 && row < H) ambiguous[row * W + col] = 1;
       } else if (r->h_ambiguous) {
         int rows[4] = {r->top - 1, r->top, r->bot - 1, r->bot};
         for (int k = 0; k < 4; ++k)

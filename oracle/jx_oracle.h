@@ -35,18 +35,25 @@ extern "C" {
 #define JXO_TASK_ROOMS 0        /* border walls + random interior walls       */
 #define JXO_TASK_MAZE_KEYDOOR 1 /* DFS maze, one key, one locked door, a goal */
 #define JXO_TASK_MAZE_ROOMS 2   /* the key-door maze with 8 x 8 open rooms carved in and distractor sprites */
+#define JXO_TASK_ASCII 3        /* a map given as ASCII text (Table 2 symbols) */
 
 /* Map cell values */
 #define JXO_FLOOR 0
-#define JXO_DOOR 5              /* 1..4 are wall types */
+/* cell values: 1..9 static walls (colour by value); locked doors 16 + c and
+ * unlocked doors 20 + c for colour c = 0 red, 1 blue, 2 yellow */
+#define JXO_LOCKED 16
+#define JXO_UNLOCKED 20
+#define JXO_DOOR JXO_LOCKED /* the red locked door of the generated key-door mazes */
 
-/* Sprite types */
+/* sprite types; keys of colour c: red 1, blue 4, yellow 5 */
 #define JXO_SPR_NONE 0
 #define JXO_SPR_KEY 1
 #define JXO_SPR_GOAL 2
 #define JXO_SPR_DISTRACTOR 3
+#define JXO_SPR_KEY_BLUE 4
+#define JXO_SPR_KEY_YELLOW 5
 
-/* Actions */
+/* actions */
 #define JXO_NOOP 0
 #define JXO_FWD 1
 #define JXO_BACK 2
@@ -64,6 +71,7 @@ extern "C" {
 #define JXO_P_NSPRITES 6
 #define JXO_P_SPRITE_CELL 7
 #define JXO_P_ROOM 8
+#define JXO_P_GOAL 9
 
 /* Tolerances the oracle uses to flag decisions that finite precision may flip. */
 #define JXO_EPS_CELL 1e-5   /* cells: DDA ties, hit near a lattice point, collision boundaries */
@@ -82,13 +90,14 @@ typedef struct {
   int32_t max_sprites;
   int32_t horizon;       /* episode length limit in steps; 0 = none */
   int32_t turns_per_rev; /* a turn action rotates by 2*pi / turns_per_rev */
-  int32_t pad0;
+  int32_t shading;       /* 1: wall colours also scaled by the slice height (distance shading) */
   double wall_prob;      /* interior wall probability (rooms task) */
   double fov_deg;        /* horizontal field of view */
   double move_step;      /* cells per move action */
   double radius;         /* half-size of the agent's collision box */
   double step_reward, key_reward, goal_reward;
   uint64_t seed;
+  uint64_t ascii;        /* JXO_TASK_ASCII: address of the parsed jxo_ascii map */
 } jxo_config;
 
 typedef struct {
@@ -97,7 +106,7 @@ typedef struct {
   int32_t turn;          /* heading = theta0 + turn * 2*pi/turns_per_rev */
   int32_t t;             /* steps taken in this episode */
   uint32_t episode;
-  int32_t has_key;
+  int32_t keys;          /* keys held: bit c for colour c (0 red, 1 blue, 2 yellow) */
   int32_t key_x, key_y, goal_x, goal_y, door_x, door_y; /* -1 when absent */
   int32_t n_sprites;
   int32_t pad0;
@@ -127,6 +136,27 @@ int jxo_sizeof_ray(void);
 
 /* Build episode `episode` of environment `env_index`. Returns 0, or -1 on an invalid config. */
 int jxo_generate(const jxo_config* cfg, int32_t env_index, uint32_t episode, jxo_env* out);
+
+/* An ASCII map (Table 2) laid out in the top-left corner of an S x S grid of
+ * walls: '#' wall 1; '1'..'9' wall of that colour; '.' and ' ' floor; 'S'
+ * spawn candidate; 'G' goal candidate; 'r', 'b', 'y' red, blue, yellow keys;
+ * '"', '\\' blue and yellow unlocked doors; 'R', 'B', 'Y' locked doors; any
+ * other printable character a static wall of colour 1 + (code mod 9) (the
+ * generated DMLab symbols). Candidates and keys in row-major order. */
+typedef struct {
+  int32_t side;
+  int32_t n_spawn, n_goal, n_keys;
+  uint8_t map[JXO_MAX_SIDE * JXO_MAX_SIDE];
+  int32_t spawn[JXO_MAX_SIDE * JXO_MAX_SIDE];
+  int32_t goal[JXO_MAX_SIDE * JXO_MAX_SIDE];
+  int32_t key_cell[JXO_MAX_SPRITES];
+  int32_t key_colour[JXO_MAX_SPRITES];
+} jxo_ascii;
+
+/* 0 on success; -1 when the text does not fit S x S, holds a control
+ * character, or more than JXO_MAX_SPRITES keys. */
+int jxo_parse_ascii(const char* text, int32_t side, jxo_ascii* out);
+int jxo_sizeof_ascii(void);
 
 /* Grayscale of n RGB pixels: the integer BT.601 luma (77 R + 150 G + 29 B + 128) >> 8. */
 void jxo_gray(const uint8_t* rgb, int64_t n, uint8_t* out);

@@ -20,7 +20,7 @@ def empty_room(S=16, wall=1):
 
 
 def env_from(S, grid, x, y, theta0=0.0, turn=0, sprites=(), key=(-1, -1), goal=(-1, -1), door=(-1, -1),
-             has_key=0):
+             keys=0):
     e = np.zeros(1, oracle.ENV_DTYPE)
     e["x"], e["y"], e["theta0"], e["turn"] = x, y, theta0, turn
     flat = np.zeros(oracle.MAX_SIDE * oracle.MAX_SIDE, np.uint8)
@@ -29,7 +29,7 @@ def env_from(S, grid, x, y, theta0=0.0, turn=0, sprites=(), key=(-1, -1), goal=(
     e["key_x"], e["key_y"] = key
     e["goal_x"], e["goal_y"] = goal
     e["door_x"], e["door_y"] = door
-    e["has_key"] = has_key
+    e["keys"] = keys
     e["n_sprites"] = len(sprites)
     for i, (sx, sy, st) in enumerate(sprites):
         e["spr_x"][0, i], e["spr_y"][0, i], e["spr_type"][0, i] = sx, sy, st

@@ -49,7 +49,7 @@ def to_oracle(env: jx.Env, blob: np.ndarray, idx=None) -> np.ndarray:
     o["turn"] = f["turn"][idx]
     o["t"] = f["t"][idx]
     o["episode"] = f["episode"][idx]
-    o["has_key"] = f["flags"][idx] & 1
+    o["keys"] = f["flags"][idx] & 7
     obj = f["obj"][idx].astype(np.int32)
     for k, name in enumerate(("key_x", "key_y", "goal_x", "goal_y", "door_x", "door_y")):
         o[name] = obj[:, k]
@@ -86,7 +86,7 @@ def compare_generated(gpu: np.ndarray, ref: np.ndarray, S: int, K: int, where: s
     n = S * S
     assert (gpu["map"][:, :n] == ref["map"][:, :n]).all(), f"maps differ {where}"
     for name in ("key_x", "key_y", "goal_x", "goal_y", "door_x", "door_y", "n_sprites", "turn", "t", "episode",
-                 "has_key"):
+                 "keys"):
         assert (gpu[name] == ref[name]).all(), f"{name} differs {where}"
     assert (gpu["x"] == ref["x"]).all() and (gpu["y"] == ref["y"]).all(), f"spawn differs {where}"
     assert (gpu["theta0"].astype(np.float32) == ref["theta0"].astype(np.float32)).all(), f"theta0 differs {where}"
@@ -249,7 +249,7 @@ def lockstep(run: Run, stats: Stats, n_steps: int, seed: int, first_step: int = 
         if done.any():
             compare_generated(cur[done], prev[done], run.env.S, run.env.K, f"after auto-reset at step {s}")
         live = ok & ~done
-        for name in ("turn", "t", "episode", "has_key"):
+        for name in ("turn", "t", "episode", "keys"):
             assert (cur[name][live] == prev[name][live]).all(), f"{name} differs at step {s}"
         for name in ("x", "y"):
             err = np.abs(cur[name][live] - prev[name][live])
@@ -289,7 +289,7 @@ def script_goal_and_door(f: dict, n: int, S: int):
         for ox, oy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
             nb = (target[0] + ox, target[1] + oy)
             if 0 <= nb[0] < S and 0 <= nb[1] < S and (m[nb[1], nb[0]] == 0 or
-                                                      (m[nb[1], nb[0]] == 5 and f["flags"][e])):
+                                                      (m[nb[1], nb[0]] == oracle.DOOR and f["flags"][e])):
                 break
         place_facing(f, e, nb, target, 0.45)
         if e % 2:
@@ -381,7 +381,7 @@ def batch_lockstep(run: BatchRun, stats: Stats, n_steps: int, seed: int, first_s
             if done.any():
                 compare_generated(cur[i][done], prev[i][done], env.S, env.K, f"auto-reset, group {i} step {s}")
             live = ok & ~done
-            for name in ("turn", "t", "episode", "has_key"):
+            for name in ("turn", "t", "episode", "keys"):
                 assert (cur[i][name][live] == prev[i][name][live]).all(), f"{name}, group {i} step {s}"
             for name in ("x", "y"):
                 err = np.abs(cur[i][name][live] - prev[i][name][live])

@@ -34,8 +34,8 @@ def test_maze_is_a_spanning_tree_with_keydoor_layout(orc, S):
     assert np.abs(types / types.sum() - 0.25).max() < 0.05, "wall types uniform over 1..4"
     for e in envs:
         m = orc.map_view(cfg, e).astype(int)
-        assert set(np.unique(m)) <= {0, 1, 2, 3, 4, 5}
-        assert (m == 5).sum() == 1
+        assert set(np.unique(m)) <= {0, 1, 2, 3, 4, orc.DOOR}
+        assert (m == orc.DOOR).sum() == 1
         assert (m[0] != 0).all() and (m[:, 0] != 0).all() and (m[S - 2:] != 0).all() and (m[:, S - 2:] != 0).all()
         open_ = m != 1
         open_ &= m != 2
@@ -72,7 +72,7 @@ def test_maze_is_a_spanning_tree_with_keydoor_layout(orc, S):
         mm = (len(path) - 1) // 2
         door = path[2 * ((mm + 1) // 2) - 1]
         assert (e["door_x"], e["door_y"]) == (door % S, door // S)
-        assert m.reshape(-1)[door] == 5
+        assert m.reshape(-1)[door] == orc.DOOR
         # with the door closed: goal unreachable, key reachable
         closed = open_.copy()
         closed.reshape(-1)[door] = False
@@ -168,10 +168,10 @@ def test_maze_with_rooms_extends_the_keydoor_maze(orc, S, K):
         for name in ("x", "y", "theta0", "key_x", "key_y", "goal_x", "goal_y", "door_x", "door_y"):
             assert a[name] == b[name], name
         assert (m2[m1 == 0] == 0).all(), "the maze's floor is kept"
-        assert (m2 == 5).sum() == 1 and m2[a["door_y"], a["door_x"]] == 5
+        assert (m2 == orc.DOOR).sum() == 1 and m2[a["door_y"], a["door_x"]] == orc.DOOR
         added = (m2 == 0) & (m1 != 0)
         n_added += int(added.sum())
-        open8 = (m2 == 0) | (m2 == 5)
+        open8 = (m2 == 0) | (m2 == orc.DOOR)
         # windows of 8 x 8 entirely open, by 2-D prefix sums
         ps = np.pad(open8.astype(int).cumsum(0).cumsum(1), ((1, 0), (1, 0)))
         win = ps[8:, 8:] - ps[:-8, 8:] - ps[8:, :-8] + ps[:-8, :-8] == 64

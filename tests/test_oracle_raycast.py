@@ -197,11 +197,11 @@ def test_locked_door_blocks_rays_until_key(orc):
     cfg = config(task=1, S=S)
     grid = empty_room(S)
     grid[:, 8] = 2
-    grid[8, 8] = 5
+    grid[8, 8] = orc.DOOR
     e = env_from(S, grid, 4.5, 8.5, 0.0)
     r = orc.render(cfg, e)["rays"][0][W // 2]
     assert (r["cell_x"], r["cell_y"]) == (8, 8)
-    e["has_key"] = 1
+    e["keys"] = 1
     r = orc.render(cfg, e)["rays"][0][W // 2]
     assert r["cell_x"] == 15
 
@@ -217,3 +217,40 @@ def test_screen_handedness(orc):
     rays = orc.render(cfg, e)["rays"][0]
     assert (rays[0]["cell_y"], rays[0]["side"]) == (0, 1)
     assert (rays[W - 1]["cell_x"], rays[W - 1]["side"]) == (15, 0)
+
+
+@pytest.mark.parametrize("d", [0.8, 1.0, 2.0, 4.0, 7.5, 13.0])
+def test_distance_shading_closed_form(orc, d):
+    """Distance shading facing a wall at distance d (x face, type-1 wall of RGB
+    (160, 160, 160)): the slice of h = min(H, round(H/d)) rows is drawn at
+    160 q / 256 per channel, q = 64 + floor(192 min(h, H) / H) -- full colour
+    at d <= 1, 160 * 160 / 256 = 100 at d = 2, tending to a quarter far away --
+    and the unshaded frame differs only in the wall's colour."""
+    S = 16
+    x0, y0 = 15.0 - d, 8.2
+    plain = orc.render(config(S=S), env_from(S, empty_room(S), x0, y0, theta0=0.0))["frames"][0]
+    shaded = orc.render(config(S=S, shading=1), env_from(S, empty_room(S), x0, y0, theta0=0.0))["frames"][0]
+    h = min(H, math.floor(H / d + 0.5))
+    q = 64 + (192 * h) // H
+    c = W // 2
+    col_p, col_s = plain[:, c], shaded[:, c]
+    wall = (col_p == np.array([160, 160, 160], np.uint8)).all(axis=1)
+    assert wall.sum() == h
+    assert (col_s[wall] == (160 * q) >> 8).all()
+    assert (col_s[~wall] == col_p[~wall]).all()
+    if d <= 1.0:
+        assert (col_s[wall] == 160).all()
+    if d == 2.0:
+        assert (col_s[wall] == 100).all()
+    assert (col_s[wall] >= 40).all()
+
+
+def test_distance_shading_is_monotone(orc):
+    """Nearer walls are never darker than farther ones."""
+    S = 16
+    vals = []
+    for d in (0.6, 1.5, 2.5, 3.5, 5.0, 8.0, 12.0):
+        f = orc.render(config(S=S, shading=1), env_from(S, empty_room(S), 15.0 - d, 8.2, theta0=0.0))["frames"][0]
+        vals.append(int(f[H // 2, W // 2, 0]))
+    assert all(a >= b for a, b in zip(vals, vals[1:])), vals
+    assert vals[0] == 160 and vals[-1] < 160

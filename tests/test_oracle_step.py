@@ -30,11 +30,18 @@ def _step(orc, cfg, e, a, env_index=0):
 def test_hand_worked_keydoor_trace(orc, trace):
     g = json.load(open(GOLDEN))
     cfg = orc.make_config(**g["config"])
-    grid = np.array([[ord(ch) - ord("0") if ch.isdigit() else (0 if ch == "." else 1) for ch in row]
-                     for row in trace["map"]], np.uint8)
+    # the trace's map notation: '#' wall, '.' floor, '5' the red locked door;
+    # its key and goal are the key and goal sprites on those cells
+    grid = np.array([[orc.DOOR if ch == "5" else (0 if ch == "." else 1) for ch in row] for row in trace["map"]],
+                    np.uint8)
     S = grid.shape[0]
     st = trace["start"]
-    e = env_from(S, grid, st["x"], st["y"], st["theta0"], st["turn"], key=tuple(trace["key"]),
+    sprites = []
+    if trace["key"][0] >= 0:
+        sprites.append((trace["key"][0] + 0.5, trace["key"][1] + 0.5, orc.SPR_KEY))
+    if trace["goal"][0] >= 0:
+        sprites.append((trace["goal"][0] + 0.5, trace["goal"][1] + 0.5, orc.SPR_GOAL))
+    e = env_from(S, grid, st["x"], st["y"], st["theta0"], st["turn"], sprites=sprites, key=tuple(trace["key"]),
                  goal=tuple(trace["goal"]), door=tuple(trace["door"]))
     ex = trace["expect"]
     keys, goals, dones = [], [], []
@@ -98,13 +105,13 @@ def test_turns_are_inverse_and_periodic(orc):
     assert e["turn"][0] == 70
 
 
-def _box_overlaps_wall(grid, x, y, r, has_key):
+def _box_overlaps_wall(grid, x, y, r, keys):
     """Open-box overlap with any solid cell (the invariant: never inside a wall)."""
     S = grid.shape[0]
     for j in range(S):
         for i in range(S):
             v = grid[j, i]
-            if v == 0 or (v == 5 and has_key):
+            if v == 0 or (v == 16 and keys & 1):
                 continue
             if x + r > i and x - r < i + 1 and y + r > j and y - r < j + 1:
                 return True
@@ -130,7 +137,7 @@ def test_agent_never_inside_a_wall(orc, task, S):
         if s % 10 == 0:
             for i in range(n):
                 grid = orc.map_view(cfg, envs[i])
-                assert not _box_overlaps_wall(grid, envs["x"][i], envs["y"][i], 0.2, envs["has_key"][i])
+                assert not _box_overlaps_wall(grid, envs["x"][i], envs["y"][i], 0.2, envs["keys"][i])
     assert moved > 100
 
 
