@@ -51,7 +51,16 @@ typedef enum {
   JX_EDEVICE = 6   /* the device error word was set by a kernel */
 } jx_status;
 
-enum { JX_TASK_ROOMS = 0, JX_TASK_MAZE_KEYDOOR = 1, JX_TASK_MAZE_ROOMS = 2 };
+enum { JX_TASK_ROOMS = 0, JX_TASK_MAZE_KEYDOOR = 1, JX_TASK_MAZE_ROOMS = 2, JX_TASK_ASCII = 3 };
+
+/* Map cell values (JX_F_MAP): 0 floor; 1..9 static walls of colour 1..9;
+ * JX_LOCKED + c a locked door and JX_UNLOCKED + c an unlocked door of colour
+ * c (0 red, 1 blue, 2 yellow); any other value draws and blocks as wall 1.
+ * A locked door is open while the key of its colour is held (Table 2); an
+ * unlocked door opens (turns to floor) when the agent walks into it.
+ * Sprite types (JX_F_SPR_TYPE): 0 none, 1 red key, 2 goal, 3 distractor,
+ * 4 blue key, 5 yellow key. */
+enum { JX_LOCKED = 16, JX_UNLOCKED = 20 };
 
 enum {
   JX_ACT_NOOP = 0,
@@ -71,7 +80,8 @@ enum {
  *                the cell farthest from the spawn (Table 1 "key-door");
  *                JX_TASK_MAZE_ROOMS: that maze with S*S/1024 open 8 x 8 rooms
  *                carved in (the door kept) and 0..K-2 distractor sprites after
- *                the key and the goal
+ *                the key and the goal; JX_TASK_ASCII: a map given as text,
+ *                see jx_create_ascii
  *  map_side      S, the map is S x S cells; rooms: 3..128; mazes: even, 6..128
  *  frame_h       H rows, 1..256
  *  frame_w       W columns, a multiple of 16, 16..256
@@ -93,7 +103,11 @@ enum {
  *                128) >> 8 of each pixel), and an episode's first frame to all
  *                four planes. So after step t the planes t, t-1, t-2, t-3
  *                (mod 4) hold the last four frames, the first one repeated
- *                early in an episode. */
+ *                early in an episode.
+ *  shading       nonzero: distance shading of walls (Sec. 2.1): each channel
+ *                of the wall colour (after the 3/4 of y faces) is scaled by
+ *                q / 256, q = 64 + floor(192 min(h, H) / H), h the slice
+ *                height in rows. */
 typedef struct {
   int32_t n_envs;
   int32_t task;
@@ -112,6 +126,7 @@ typedef struct {
   double goal_reward;
   uint64_t seed;
   int32_t gray_stack;
+  int32_t shading;
 } jx_config;
 
 /* Create N environments on CUDA device `device` and allocate their state in
@@ -119,6 +134,21 @@ typedef struct {
  * validated before any CUDA call, so JX_EINVAL needs no GPU. *out receives
  * the handle, owned by the caller until jx_destroy. */
 jx_status jx_create(const jx_config* cfg, int device, jx_env** out);
+
+/* jx_create for the ASCII task (cfg->task == JX_TASK_ASCII): the map is the
+ * text `ascii` (rows separated by '\n', '\r' ignored) in the top-left corner
+ * of an S x S grid of walls, S = cfg->map_side. Symbols (Table 2): '#' wall
+ * 1; '1'..'9' wall of that colour; '.' and ' ' floor; 'S' spawn candidate;
+ * 'G' goal candidate; 'r', 'b', 'y' red, blue and yellow keys; '"' and '\\'
+ * blue and yellow unlocked doors; 'R', 'B', 'Y' red, blue and yellow locked
+ * doors; any other printable character a wall of colour 1 + (code mod 9).
+ * Every episode starts from this map: spawn uniform over the 'S' cells (over
+ * all floor cells when there is none), the keys as sprites on their cells in
+ * row-major order, then a goal sprite on one 'G' cell drawn uniformly per
+ * episode (none without 'G'). Needs max_sprites >= keys + (1 if any 'G').
+ * JX_EINVAL when the text does not fit, holds a control character, more than
+ * 16 keys, or no floor. */
+jx_status jx_create_ascii(const jx_config* cfg, const char* ascii, int device, jx_env** out);
 
 /* Device bytes jx_create allocates for cfg on `device`: one block holding
  * the state, the per-env tables and the maze work space. Validates cfg like
@@ -222,13 +252,13 @@ enum {
   JX_F_TURN = 5,     /* int16  [N]   heading = theta0 + turn * 2pi/turns_per_rev */
   JX_F_T = 6,        /* int32  [N]   steps taken in the episode             */
   JX_F_EPISODE = 7,  /* uint32 [N]   episode counter                        */
-  JX_F_FLAGS = 8,    /* uint8  [N]   bit 0: key held                        */
+  JX_F_FLAGS = 8,    /* uint8  [N]   keys held: bit 0 red, bit 1 blue, bit 2 yellow */
   JX_F_OBJ = 9,      /* int16  [N][6] key x, key y, goal x, goal y, door x, door y (-1: none) */
   JX_F_NSPR = 10,    /* uint8  [N]   sprites in use                         */
   JX_F_SPR_X = 11,   /* float  [N][K] sprite x (absolute map coordinate)    */
   JX_F_SPR_Y = 12,   /* float  [N][K] sprite y                              */
-  JX_F_SPR_TYPE = 13, /* uint8 [N][K] 0 none, 1 key, 2 goal, 3 distractor   */
-  JX_F_MAP = 14,     /* uint8  [N][S][S] 0 floor, 1..4 wall types, 5 locked door */
+  JX_F_SPR_TYPE = 13, /* uint8 [N][K] sprite types (above)                 */
+  JX_F_MAP = 14,     /* uint8  [N][S][S] cell values (JX_LOCKED, JX_UNLOCKED above) */
   JX_F_COS0 = 15,    /* float  [N]   cos(theta0), derived: jx_set_state recomputes it */
   JX_F_SIN0 = 16,    /* float  [N]   sin(theta0), derived: jx_set_state recomputes it */
   JX_F_GRAY = 17,    /* uint8  [N][4][H][W] grayscale frame stack (0 bytes unless gray_stack) */

@@ -21,11 +21,68 @@ using jx::host::fail;
 
 namespace {
 
-jx_status validate(const jx_config* c) {
+// The ASCII task's map, parsed on the host: the S x S cells, then the spawn
+// candidates, the goal candidates and the keys (cell * 4 + colour), each in
+// row-major order.
+struct AsciiMap {
+  std::vector<uint8_t> cells;
+  std::vector<int32_t> spawn, goal, keys;
+};
+
+jx_status parse_ascii(const char* text, int S, AsciiMap& m) {
+  if (!text) return fail(JX_EINVAL, "ascii is NULL");
+  m.cells.assign((size_t)S * S, 1);
+  int row = 0, col = 0, n_floor = 0;
+  for (const char* q = text; *q; ++q) {
+    const unsigned char ch = (unsigned char)*q;
+    if (ch == '\n') {
+      ++row;
+      col = 0;
+      continue;
+    }
+    if (ch == '\r') continue;
+    if (ch < 32 || ch > 126) return fail(JX_EINVAL, "ascii map: character %d at row %d is not printable", ch, row);
+    if (row >= S || col >= S) return fail(JX_EINVAL, "ascii map: cell (%d, %d) outside the %d x %d map", col, row, S, S);
+    const int32_t cell = row * S + col;
+    int v;
+    if (ch == '#') {
+      v = 1;
+    } else if (ch == '.' || ch == ' ') {
+      v = 0;
+    } else if (ch == 'S' || ch == 'G') {
+      v = 0;
+      (ch == 'S' ? m.spawn : m.goal).push_back(cell);
+    } else if (ch == 'r' || ch == 'b' || ch == 'y') {
+      v = 0;
+      m.keys.push_back(cell * 4 + (ch == 'r' ? 0 : (ch == 'b' ? 1 : 2)));
+    } else if (ch == '"' || ch == '\\') {
+      v = JX_UNLOCKED + (ch == '"' ? 1 : 2);
+    } else if (ch == 'R' || ch == 'B' || ch == 'Y') {
+      v = JX_LOCKED + (ch == 'R' ? 0 : (ch == 'B' ? 1 : 2));
+    } else if (ch >= '1' && ch <= '9') {
+      v = ch - '0';
+    } else {
+      v = 1 + ch % 9;  // other symbols (generated DMLab maps): coloured static walls
+    }
+    m.cells[cell] = (uint8_t)v;
+    n_floor += v == 0;
+    ++col;
+  }
+  if (m.keys.size() > (size_t)jx::kMaxSprites)
+    return fail(JX_EINVAL, "ascii map: %zu keys, at most %d", m.keys.size(), jx::kMaxSprites);
+  if (n_floor == 0) return fail(JX_EINVAL, "ascii map: no floor cell");
+  return JX_OK;
+}
+
+jx_status validate(const jx_config* c, const AsciiMap* am = nullptr) {
   if (!c) return fail(JX_EINVAL, "config is NULL");
   if (c->n_envs < 1) return fail(JX_EINVAL, "n_envs must be >= 1 (got %d)", c->n_envs);
-  if (c->task != JX_TASK_ROOMS && c->task != JX_TASK_MAZE_KEYDOOR && c->task != JX_TASK_MAZE_ROOMS)
+  if (c->task != JX_TASK_ROOMS && c->task != JX_TASK_MAZE_KEYDOOR && c->task != JX_TASK_MAZE_ROOMS &&
+      c->task != JX_TASK_ASCII)
     return fail(JX_EINVAL, "unknown task %d", c->task);
+  if ((c->task == JX_TASK_ASCII) != (am != nullptr))
+    return fail(JX_EINVAL, c->task == JX_TASK_ASCII ? "the ASCII task needs jx_create_ascii and its map"
+                                                     : "a map text needs task JX_TASK_ASCII");
   const bool maze = c->task == JX_TASK_MAZE_KEYDOOR || c->task == JX_TASK_MAZE_ROOMS;
   if (c->map_side < 3 || c->map_side > jx::kMaxSide)
     return fail(JX_EINVAL, "map_side must be in [3, %d] (got %d)", jx::kMaxSide, c->map_side);
@@ -47,6 +104,9 @@ jx_status validate(const jx_config* c) {
   if (!(c->radius >= 0.0 && c->radius <= 0.49)) return fail(JX_EINVAL, "radius must be in [0, 0.49]");
   if (!std::isfinite(c->step_reward) || !std::isfinite(c->key_reward) || !std::isfinite(c->goal_reward))
     return fail(JX_EINVAL, "rewards must be finite");
+  if (am && c->max_sprites < (int)am->keys.size() + (am->goal.empty() ? 0 : 1))
+    return fail(JX_EINVAL, "the map has %zu keys%s: max_sprites must be at least %zu", am->keys.size(),
+                am->goal.empty() ? "" : " and a goal", am->keys.size() + (am->goal.empty() ? 0 : 1));
   return JX_OK;
 }
 
@@ -164,8 +224,8 @@ namespace {
 // in the caller's memory `ext`. With `bytes_only` the block size is returned
 // in *bytes and nothing is kept.
 jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_bytes, bool bytes_only, size_t* bytes,
-                      jx_env** out) {
-  jx_status st = validate(cfg);
+                      jx_env** out, const AsciiMap* am = nullptr) {
+  jx_status st = validate(cfg, am);
   if (st != JX_OK) return st;
   int ndev = 0;
   cudaError_t err = cudaGetDeviceCount(&ndev);
@@ -185,9 +245,12 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
 
   const jx_config& c = *cfg;
   const int W = c.frame_w, tpr = c.turns_per_rev;
-  // aux block: error word | turn table | column table
+  // aux block: error word | turn table | column table | ASCII map and candidates
   const size_t aux_err = 0, aux_turn = 256, aux_col = align256(aux_turn + 8 * (size_t)tpr);
-  const size_t aux_bytes = align256(aux_col + 4 * (size_t)W);
+  const size_t aux_tmpl = align256(aux_col + 4 * (size_t)W);
+  const size_t n_cand = am ? am->spawn.size() + am->goal.size() + am->keys.size() : 0;
+  const size_t aux_cand = align256(aux_tmpl + (am ? am->cells.size() : 0));
+  const size_t aux_bytes = align256(aux_cand + 4 * n_cand);
 
   jx::Params& p = env->base;
   p.n = c.n_envs;
@@ -220,6 +283,7 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
   // Maps of side 128 are staged as bit planes (2 KB instead of 16 KB).
   p.map_bits = c.map_side >= 128 && c.map_side % 8 == 0;
   p.gray = c.gray_stack != 0;
+  p.shading = c.shading != 0;
   p.out_stride = c.n_envs;
   p.frame_step = (size_t)c.n_envs * jx::host::frame_bytes(c);
   jx::host::choose_rows(p, 16, jx::kWarpsPerBlock, jx::kMinBlocksPerSm, prop.sharedMemPerMultiprocessor,
@@ -296,6 +360,13 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
     float* colk = reinterpret_cast<float*>(&host[aux_col]);
     const double t = std::tan(0.5 * c.fov_deg * 3.14159265358979323846 / 180.0);
     for (int col = 0; col < W; ++col) colk[col] = (float)((2.0 * (col + 0.5) / W - 1.0) * t);
+    if (am) {
+      std::memcpy(&host[aux_tmpl], am->cells.data(), am->cells.size());
+      int32_t* cand = reinterpret_cast<int32_t*>(&host[aux_cand]);
+      for (int32_t v : am->spawn) *cand++ = v;
+      for (int32_t v : am->goal) *cand++ = v;
+      for (int32_t v : am->keys) *cand++ = v;
+    }
     err = cudaMemcpy(env->aux, host.data(), aux_bytes, cudaMemcpyHostToDevice);
     if (err != cudaSuccess) {
       jx_destroy(env);
@@ -323,6 +394,13 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
   p.err = reinterpret_cast<uint32_t*>(env->aux + aux_err);
   p.turn_cs = reinterpret_cast<const float2*>(env->aux + aux_turn);
   p.col_k = reinterpret_cast<const float*>(env->aux + aux_col);
+  if (am) {
+    p.tmpl = env->aux + aux_tmpl;
+    p.cand = reinterpret_cast<const int32_t*>(env->aux + aux_cand);
+    p.n_spawn = (int32_t)am->spawn.size();
+    p.n_goal = (int32_t)am->goal.size();
+    p.n_keys = (int32_t)am->keys.size();
+  }
   p.gen_scratch = env->scratch;
   // the memset and the table copy are done before the handle is returned
   if ((err = cudaStreamSynchronize(0)) != cudaSuccess) {
@@ -341,6 +419,17 @@ jx_status jx_create(const jx_config* cfg, int device, jx_env** out) {
   if (!out) return fail(JX_EINVAL, "out is NULL");
   *out = nullptr;
   return create_impl(cfg, device, nullptr, 0, false, nullptr, out);
+}
+
+jx_status jx_create_ascii(const jx_config* cfg, const char* ascii, int device, jx_env** out) {
+  if (!out) return fail(JX_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(JX_EINVAL, "config is NULL");
+  if (cfg->map_side < 3 || cfg->map_side > jx::kMaxSide)
+    return fail(JX_EINVAL, "map_side must be in [3, %d] (got %d)", jx::kMaxSide, cfg->map_side);
+  AsciiMap am;
+  if (jx_status st = parse_ascii(ascii, cfg->map_side, am)) return st;
+  return create_impl(cfg, device, nullptr, 0, false, nullptr, out, &am);
 }
 
 jx_status jx_env_bytes(const jx_config* cfg, int device, size_t* bytes) {

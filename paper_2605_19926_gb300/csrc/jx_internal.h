@@ -38,7 +38,8 @@ enum Purpose : uint32_t {
   P_KEY = 5,
   P_NSPRITES = 6,
   P_SPRITE_CELL = 7,
-  P_ROOM = 8
+  P_ROOM = 8,
+  P_GOAL = 9
 };
 
 // Device pointers into the struct-of-arrays state block.
@@ -82,6 +83,12 @@ struct Params {
   size_t frame_step;   // bytes per step in the frame array (n frames, or a batch's total)
   int32_t map_bits;    // the map is staged as a bit plane (see MapKind)
   int32_t gray;        // the env keeps a grayscale frame stack (st.gray)
+  int32_t shading;     // distance shading of wall colours
+  // ASCII task: the parsed map [S*S] and its candidate cells: n_spawn spawn
+  // cells, n_goal goal cells, n_keys keys (cell * 4 + colour), in that order
+  const uint8_t* tmpl;
+  const int32_t* cand;
+  int32_t n_spawn, n_goal, n_keys;
   int32_t gray_block_bytes;  // rows_per_block * W when gray, else 0
   int32_t rows_per_block;  // rows per staged frame block
   int32_t frame_block_bytes;

@@ -22,35 +22,68 @@ namespace {
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 constexpr double kHeadingScale = (2.0 * 3.14159265358979323846) / 16777216.0;  // 2 pi / 2^24
 constexpr int kHMax = 1 << 20;
-constexpr int kDoor = 5;
+constexpr int kLocked = 16;    // + colour (0 red, 1 blue, 2 yellow): locked doors
+constexpr int kUnlocked = 20;  // + colour: unlocked doors
+constexpr int kDoor = kLocked;  // the red locked door of the generated mazes
+constexpr int kTaskAscii = 3;
 constexpr int kSprKey = 1;
 constexpr int kSprGoal = 2;
+constexpr int kSprKeyBlue = 4;
+constexpr int kSprKeyYellow = 5;
+// colour of a key sprite type, -1 for other types
+__host__ __device__ constexpr int key_colour(int type) {
+  return type == kSprKey ? 0 : (type == kSprKeyBlue ? 1 : (type == kSprKeyYellow ? 2 : -1));
+}
+__device__ __forceinline__ bool is_locked(int v) { return (unsigned)(v - kLocked) < 3u; }
+__device__ __forceinline__ bool is_unlocked(int v) { return (unsigned)(v - kUnlocked) < 3u; }
 static_assert(kRingBuffers == 2, "bulk wait depth below assumes two staging buffers");
 
 // ------------------------------------------------------------- palette ----
 // Colours packed as 0xYYBBGGRR: the low three bytes are R, G, B and the top
 // byte is the colour's integer BT.601 luma (77 R + 150 G + 29 B + 128) >> 8,
 // the pixel's value in the grayscale frame stack.
-constexpr uint32_t luma(uint32_t r, uint32_t g, uint32_t b) { return (77 * r + 150 * g + 29 * b + 128) >> 8; }
+__host__ __device__ constexpr uint32_t luma(uint32_t r, uint32_t g, uint32_t b) { return (77 * r + 150 * g + 29 * b + 128) >> 8; }
 constexpr uint32_t rgb(uint32_t r, uint32_t g, uint32_t b) { return r | (g << 8) | (b << 16) | (luma(r, g, b) << 24); }
 constexpr uint32_t shade34(uint32_t c) {  // y faces: each channel scaled by 3/4 (floor), luma of the result
   return rgb((((c >> 0) & 255) * 3) >> 2, (((c >> 8) & 255) * 3) >> 2, (((c >> 16) & 255) * 3) >> 2);
 }
 constexpr uint32_t kWall1 = rgb(160, 160, 160);
-constexpr uint32_t kWall2 = rgb(64, 160, 64);
-constexpr uint32_t kWall3 = rgb(64, 96, 192);
-constexpr uint32_t kWall4 = rgb(176, 144, 80);
-constexpr uint32_t kDoorRgb = rgb(200, 32, 32);
 constexpr uint32_t kCeil = rgb(48, 48, 56);
 constexpr uint32_t kFloor = rgb(104, 96, 88);
 
-// [side][cell value]; values above 5 draw as wall type 1
-__constant__ uint32_t c_wall[2][8] = {
-    {kWall1, kWall1, kWall2, kWall3, kWall4, kDoorRgb, kWall1, kWall1},
-    {shade34(kWall1), shade34(kWall1), shade34(kWall2), shade34(kWall3), shade34(kWall4), shade34(kDoorRgb),
-     shade34(kWall1), shade34(kWall1)}};
-// by sprite type: 1 key, 2 goal, 3 distractor
-__constant__ uint32_t c_sprite[4] = {rgb(144, 64, 192), rgb(224, 40, 40), rgb(240, 208, 32), rgb(144, 64, 192)};
+// Colour of a cell value: walls 1..9, locked and unlocked doors by colour,
+// anything else as wall 1.
+constexpr uint32_t cell_rgb(int v) {
+  return v == 2 ? rgb(64, 160, 64)
+       : v == 3 ? rgb(64, 96, 192)
+       : v == 4 ? rgb(176, 144, 80)
+       : v == 5 ? rgb(200, 100, 40)
+       : v == 6 ? rgb(112, 64, 160)
+       : v == 7 ? rgb(40, 160, 160)
+       : v == 8 ? rgb(128, 128, 48)
+       : v == 9 ? rgb(216, 216, 216)
+       : v == kLocked + 0 ? rgb(200, 32, 32)
+       : v == kLocked + 1 ? rgb(32, 64, 200)
+       : v == kLocked + 2 ? rgb(208, 184, 32)
+       : v == kUnlocked + 0 ? rgb(232, 120, 120)
+       : v == kUnlocked + 1 ? rgb(120, 150, 232)
+       : v == kUnlocked + 2 ? rgb(236, 222, 128)
+       : kWall1;
+}
+constexpr int kCellColours = 32;  // palette entries per face; values above draw as wall 1
+
+// [face][cell value]: x faces, then y faces (3/4)
+#define JX_CELLS(f) f(0), f(1), f(2), f(3), f(4), f(5), f(6), f(7), f(8), f(9), f(10), f(11), f(12), f(13), f(14), \
+    f(15), f(16), f(17), f(18), f(19), f(20), f(21), f(22), f(23), f(24), f(25), f(26), f(27), f(28), f(29), f(30), f(31)
+#define JX_X_FACE(v) cell_rgb(v)
+#define JX_Y_FACE(v) shade34(cell_rgb(v))
+__constant__ uint32_t c_wall[2 * kCellColours] = {JX_CELLS(JX_X_FACE), JX_CELLS(JX_Y_FACE)};
+#undef JX_X_FACE
+#undef JX_Y_FACE
+#undef JX_CELLS
+// by sprite type: 1 red key, 2 goal, 3 distractor, 4 blue key, 5 yellow key (others as distractor)
+__constant__ uint32_t c_sprite[8] = {rgb(144, 64, 192), rgb(224, 40, 40), rgb(240, 208, 32), rgb(144, 64, 192),
+                                     rgb(40, 80, 224),  rgb(232, 200, 40), rgb(144, 64, 192), rgb(144, 64, 192)};
 
 // ------------------------------------------------------------ SplitMix64 --
 // Steele, Lea & Flood (OOPSLA 2014): output n of the generator seeded with s
@@ -97,7 +130,7 @@ __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; 
 // of Params (constants), so no pointer lives in a register:
 //   ring      kRingBuffers * frame_block_bytes (also the maze work space)
 //   gray      kRingBuffers * gray_block_bytes: the row blocks of the grayscale frame
-//   pal       [2][8] wall colours by face and cell value, then [4] sprite colours by type
+//   pal       [2][32] wall colours by face and cell value, then [8] sprite colours by type
 //   map       S * S cell values, row-major
 //   col_rgb   [W] wall colour, chunk-interleaved (see col_slot)
 //   col_top   [W] first wall row, chunk-interleaved
@@ -146,7 +179,7 @@ struct WarpSmem {
   __device__ __forceinline__ int32_t* obj(const Params& p) const { return (int32_t*)(base + p.off_obj); }
 };
 
-constexpr int kPaletteWords = 2 * 8 + 4;
+constexpr int kPaletteWords = 2 * kCellColours + 8;
 
 // Column data is stored so that the lanes filling one row (8 columns each)
 // read consecutive 16-byte groups: half g (columns 4g..4g+3 of the group) of
@@ -165,7 +198,7 @@ struct Env {
   float fx, fy;  // position inside the cell, [0, 1)
   float c0, s0;  // cos, sin of theta0
   int turn, t;
-  int has_key;
+  int keys;  // keys held: bit c for colour c
 };
 
 __device__ __forceinline__ Env load_env(const Params& p, int e) {
@@ -179,7 +212,7 @@ __device__ __forceinline__ Env load_env(const Params& p, int e) {
   r.s0 = st.sin0[e];
   r.turn = st.turn[e];  // in [0, turns_per_rev): generated so, checked by set_state
   r.t = st.t[e];
-  r.has_key = st.flags[e] & 1;
+  r.keys = st.flags[e] & 7;
   return r;
 }
 
@@ -529,6 +562,61 @@ __device__ __forceinline__ void gen_maze(const Params& p, int e, uint32_t ep, ui
   __syncwarp();
 }
 
+// ASCII maps (Table 2): each episode copies the parsed map; the spawn is
+// uniform over the 'S' cells (over all floor cells when there is none), the
+// keys become sprites on their cells in row-major order, and a goal sprite
+// goes on one 'G' cell drawn uniformly per episode.
+__device__ __forceinline__ void gen_ascii(const Params& p, int e, uint32_t ep, uint8_t* smap, int lane) {
+  const int S = p.S, n = S * S;
+  for (int i = lane; i < n; i += 32) smap[i] = p.tmpl[i];
+  __syncwarp();
+  const uint64_t d = draw_at(stream_key(p.seed, (uint32_t)e, ep, P_SPAWN), 0);
+  auto is_free = [&](int i) { return smap[i] == 0; };
+  int cell;
+  if (p.n_spawn > 0) {
+    cell = p.cand[below(d, (uint32_t)p.n_spawn)];
+  } else {
+    const int n_free = count_cells(n, lane, is_free);
+    cell = nth_cell(n, below(d, (uint32_t)n_free), lane, is_free);
+  }
+  int spr_cell[kMaxSprites], spr_type[kMaxSprites];
+  int obj[6] = {-1, -1, -1, -1, -1, -1};
+  const int32_t* keys = p.cand + p.n_spawn + p.n_goal;
+  int k = 0;
+  for (int i = 0; i < p.n_keys; ++i, ++k) {
+    const int colour = keys[i] & 3;
+    spr_cell[k] = keys[i] >> 2;
+    spr_type[k] = colour == 0 ? kSprKey : (colour == 1 ? kSprKeyBlue : kSprKeyYellow);
+  }
+  if (p.n_keys > 0) {
+    obj[0] = (keys[0] >> 2) % S;
+    obj[1] = (keys[0] >> 2) / S;
+  }
+  if (p.n_goal > 0) {
+    const int g = p.cand[p.n_spawn + below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_GOAL), 0),
+                                           (uint32_t)p.n_goal)];
+    spr_cell[k] = g;
+    spr_type[k] = kSprGoal;
+    ++k;
+    obj[2] = g % S;
+    obj[3] = g / S;
+  }
+  // the first locked door in row-major order
+  for (int base = 0; base < n; base += 32) {
+    const uint32_t b = __ballot_sync(0xffffffffu, base + lane < n && is_locked(smap[base + lane]));
+    if (b) {
+      const int c = base + __ffs(b) - 1;
+      obj[4] = c % S;
+      obj[5] = c / S;
+      break;
+    }
+  }
+  write_episode_state(p, e, ep, cell, obj, k, spr_cell, spr_type, lane);
+  __syncwarp();
+  store_map(p, e, smap, lane);
+  __syncwarp();
+}
+
 // The maze work space lives in the warp's frame staging ring when it fits
 // (32 x 32 mazes need 3.4 KB), else in the global per-warp slot. Inlined
 // behind unlikely branches: a call would make every value live across it
@@ -543,6 +631,8 @@ __device__ __forceinline__ void generate(const Params& p, int e, uint32_t ep, ui
   uint8_t* smap = bits ? p.st.map + (size_t)e * p.S * p.S : ws.map(p);
   if (p.task == 0) {
     gen_rooms(p, e, ep, smap, lane);
+  } else if (p.task == kTaskAscii) {
+    gen_ascii(p, e, ep, smap, lane);
   } else {
     const int nn = (p.S - 2) / 2;
     uint8_t* work = scratch;
@@ -558,11 +648,11 @@ __device__ __forceinline__ void generate(const Params& p, int e, uint32_t ep, ui
 
 // ------------------------------------------------------------------ step ----
 template <int MAPK>
-__device__ __forceinline__ bool solid(const Params& p, const uint8_t* smap, int S, int x, int y, int has_key) {
+__device__ __forceinline__ bool solid(const Params& p, const uint8_t* smap, int S, int x, int y, int keys) {
   if (x < 0 || y < 0 || x >= S || y >= S) return true;
   if (map_bits<MAPK>(p)) return cell_set<MAPK>(p, smap, y * S + x);
   int v = smap[y * S + x];
-  return v != 0 && !(v == kDoor && has_key);
+  return v != 0 && !(is_locked(v) && ((keys >> (v - kLocked)) & 1));
 }
 
 // Box of half-size r centred at (cx + fx, cy + fy) overlaps no solid cell
@@ -573,16 +663,43 @@ __device__ __forceinline__ int floor_small(float v) { return (v >= 1.f ? 1 : 0) 
 
 template <int MAPK>
 __device__ __forceinline__ bool box_free(const Params& p, const uint8_t* smap, int S, int cx, float fx, int cy,
-                                         float fy, float r, int has_key) {
+                                         float fy, float r, int keys) {
   const int i0 = cx + floor_small(fx - r), i1 = cx + floor_small(fx + r);
   const int j0 = cy + floor_small(fy - r), j1 = cy + floor_small(fy + r);
-  bool hit = solid<MAPK>(p, smap, S, i0, j0, has_key);
-  if (i1 != i0) hit |= solid<MAPK>(p, smap, S, i1, j0, has_key);
+  bool hit = solid<MAPK>(p, smap, S, i0, j0, keys);
+  if (i1 != i0) hit |= solid<MAPK>(p, smap, S, i1, j0, keys);
   if (j1 != j0) {
-    hit |= solid<MAPK>(p, smap, S, i0, j1, has_key);
-    if (i1 != i0) hit |= solid<MAPK>(p, smap, S, i1, j1, has_key);
+    hit |= solid<MAPK>(p, smap, S, i0, j1, keys);
+    if (i1 != i0) hit |= solid<MAPK>(p, smap, S, i1, j1, keys);
   }
   return !hit;
+}
+
+// An unlocked door opens when the agent walks into it: after a rejected axis
+// move, every unlocked door cell under the box at (cx + fx, cy + fy) turns
+// to floor, in the staged map and in the state block.
+template <int MAPK>
+__device__ __noinline__ void open_unlocked(const Params& p, int e, uint8_t* smap, int cx, float fx, int cy, float fy,
+                                           int lane) {
+  const int S = p.S;
+  const float r = p.radius;
+  const int i0 = cx + floor_small(fx - r), i1 = cx + floor_small(fx + r);
+  const int j0 = cy + floor_small(fy - r), j1 = cy + floor_small(fy + r);
+  uint8_t* g = p.st.map + (size_t)e * S * S;
+  for (int j = j0; j <= j1; ++j)
+    for (int i = i0; i <= i1; ++i) {
+      if (i < 0 || j < 0 || i >= S || j >= S) continue;
+      const int c = j * S + i;
+      if (!is_unlocked(map_bits<MAPK>(p) ? g[c] : smap[c])) continue;
+      if (lane == 0) {
+        g[c] = 0;
+        if (map_bits<MAPK>(p))
+          reinterpret_cast<uint32_t*>(smap)[c >> 5] &= ~(1u << (c & 31));
+        else
+          smap[c] = 0;
+      }
+    }
+  __syncwarp();
 }
 
 // keep the position split as an integer cell plus a fraction in [0, 1)
@@ -605,6 +722,7 @@ __device__ __forceinline__ void renormalise(int& c, float& f) {
 // The pose is written back to the state block only when write_state is set.
 template <int MAPK>
 __device__ __forceinline__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, const int32_t* obj,
+                                         const float4* spr_in,
                                          int lane, float& c, float& s, int a, size_t out, bool write_state) {
   if (a > 6) {
     if (lane == 0) atomicOr(p.err, 1u);
@@ -630,21 +748,38 @@ __device__ __forceinline__ bool step_env(const Params& p, int e, Env& r, const u
   }
   const int S = p.S;
   const float rad = p.radius;
+  const bool doors = p.task == kTaskAscii;  // maps with unlocked doors
   float nfx = r.fx + dx;
-  if (box_free<MAPK>(p, smap, S, r.cx, nfx, r.cy, r.fy, rad, r.has_key)) {
+  if (box_free<MAPK>(p, smap, S, r.cx, nfx, r.cy, r.fy, rad, r.keys)) {
     r.fx = nfx;
     renormalise(r.cx, r.fx);
+  } else if (__builtin_expect(doors, 0)) {
+    open_unlocked<MAPK>(p, e, const_cast<uint8_t*>(smap), r.cx, nfx, r.cy, r.fy, lane);
   }
   float nfy = r.fy + dy;
-  if (box_free<MAPK>(p, smap, S, r.cx, r.fx, r.cy, nfy, rad, r.has_key)) {
+  if (box_free<MAPK>(p, smap, S, r.cx, r.fx, r.cy, nfy, rad, r.keys)) {
     r.fy = nfy;
     renormalise(r.cy, r.fy);
+  } else if (__builtin_expect(doors, 0)) {
+    open_unlocked<MAPK>(p, e, const_cast<uint8_t*>(smap), r.cx, r.fx, r.cy, nfy, lane);
   }
-  const int4 kg = *reinterpret_cast<const int4*>(obj);  // key x, key y, goal x, goal y
-  int ev = 0;
-  if (!r.has_key && kg.x >= 0 && r.cx == kg.x && r.cy == kg.y) ev |= 1;
-  if (kg.z >= 0 && r.cx == kg.z && r.cy == kg.w) ev |= 2;
-  if (ev & 1) r.has_key = 1;
+  // key and goal events from the sprite table (lane j looks at slot j): a key
+  // of a colour not held yet on the agent's cell is picked up; a goal there
+  // is reached
+  uint32_t kbit = 0;
+  bool goal = false;
+  if (lane < obj[6]) {
+    const float4 sp = spr_in[lane];
+    if ((int)floorf(sp.x) == r.cx && (int)floorf(sp.y) == r.cy) {
+      const int type = (int)sp.z;
+      const int kc = key_colour(type);
+      if (kc >= 0 && !((r.keys >> kc) & 1)) kbit = 1u << kc;
+      goal = type == kSprGoal;
+    }
+  }
+  const uint32_t picked = __reduce_or_sync(0xffffffffu, kbit);
+  int ev = (picked ? 1 : 0) | (__any_sync(0xffffffffu, goal) ? 2 : 0);
+  r.keys |= (int)picked;
   r.t += 1;
   const bool done = (ev & 2) || (p.horizon > 0 && r.t >= p.horizon);
   if (lane == 0) {
@@ -658,7 +793,7 @@ __device__ __forceinline__ bool step_env(const Params& p, int e, Env& r, const u
       st.frac_y[e] = r.fy;
       st.turn[e] = (int16_t)r.turn;
       st.t[e] = r.t;
-      st.flags[e] = (uint8_t)r.has_key;
+      st.flags[e] = (uint8_t)r.keys;
     }
   }
   return done;
@@ -733,7 +868,14 @@ __device__ __forceinline__ void finish_column(const Params& p, int e, const Ray&
   if (q.side >= 0 && inside)
     v = map_bits<MAPK>(p) ? p.st.map[(size_t)e * S * S + q.my * S + q.mx] : ws.map(p)[q.my * S + q.mx];
   const int slot = col_slot(col, p.W >> 3);
-  ws.col_rgb(p)[slot] = ws.pal(p)[(q.side == 1 ? 8 : 0) + (v > 7 ? 7 : v)];
+  uint32_t colour = ws.pal(p)[(q.side == 1 ? kCellColours : 0) + (v < kCellColours ? v : 1)];
+  if (p.shading) {  // distance shading: channels scaled by q / 256, q = 64 + 192 min(h, H) / H
+    const uint32_t qq = 64u + (uint32_t)(192 * (h < H ? h : H)) / (uint32_t)H;
+    const uint32_t R = ((colour & 255u) * qq) >> 8, G = (((colour >> 8) & 255u) * qq) >> 8,
+                   B = (((colour >> 16) & 255u) * qq) >> 8;
+    colour = R | (G << 8) | (B << 16) | (luma(R, G, B) << 24);
+  }
+  ws.col_rgb(p)[slot] = colour;
   ws.col_top(p)[slot] = top < 0 ? 0 : (top > H ? H : top);
   ws.col_bot(p)[slot] = bot < 0 ? 0 : (bot > H ? H : bot);
   ws.zbuf(p)[col] = perp;
@@ -794,7 +936,8 @@ __device__ __forceinline__ int project_sprites(const Params& p, const Env& r, fl
     const float vx = (sp.x - (float)r.cx) - r.fx;
     const float vy = (sp.y - (float)r.cy) - r.fy;
     ty = fmaf(vx, c, vy * s);
-    vis = type != 0 && !(type == kSprKey && r.has_key) && ty > 0.1f;
+    const int kc = key_colour(type);
+    vis = type != 0 && !(kc >= 0 && ((r.keys >> kc) & 1)) && ty > 0.1f;
     if (vis) {
       const float inv_ty = __frcp_rn(ty);
       const float tx = fmaf(-vx, s, vy * c) * p.inv_tan_half;
@@ -811,8 +954,8 @@ __device__ __forceinline__ int project_sprites(const Params& p, const Env& r, fl
       ws.spr_rect(p)[lane] =
           make_int4(cA < 0 ? 0 : cA, cB > W - 1 ? W - 1 : cB, rA < 0 ? 0 : rA, rB > H - 1 ? H - 1 : rB);
       ws.spr_ty(p)[lane] = ty;
-      ws.spr_rgb(p)[lane] = ws.pal(p)[16 + (type & 3)];
-      ws.spr_kind(p)[lane] = type;
+      ws.spr_rgb(p)[lane] = ws.pal(p)[2 * kCellColours + (type & 7)];
+      ws.spr_kind(p)[lane] = kc >= 0 ? 1 : (type == kSprGoal ? 2 : 3);  // mask: diamond, rectangle, disc
     }
   }
   const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
@@ -908,7 +1051,7 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
       const float u = ((float)col + 0.5f - a.x) * a.z;
       if (!(u >= 0.f && u < 1.f && ty < ws.zbuf(p)[col])) continue;
       const float au = fabsf(fmaf(2.f, u, -1.f));
-      const float half = kind == kSprKey ? 1.f - au : (kind == kSprGoal ? 2.f : sqrtf(fmaxf(0.f, fmaf(-au, au, 1.f))));
+      const float half = kind == 1 ? 1.f - au : (kind == 2 ? 2.f : sqrtf(fmaxf(0.f, fmaf(-au, au, 1.f))));
       uint8_t* px = buf + col * 3;
       for (int row = rA; row <= rB; ++row) {
         const float v = ((float)row + 0.5f - a.y) * a.w;
@@ -967,24 +1110,38 @@ __device__ __forceinline__ void render_env(const Params& p, int e, const Env& r,
   }
 }
 
-// The locked door opens (for rays and collisions) once the key is held. In
-// bit mode it is opened when the map is staged and after the step that picks
-// the key up, so the plane never shows a closed door to a key holder.
+// Locked doors of the colours held open for rays (and, in bit mode, for
+// collisions): their cells are cleared in the staged map, which the state
+// block keeps as written. Run after staging and whenever the keys change.
+// Generated mazes have one red door (the door cell of the state); ASCII maps
+// are scanned.
 template <int MAPK>
-__device__ __forceinline__ void open_door(const Params& p, int e, const Env& r, const WarpSmem& ws, int lane) {
-  if (r.has_key) {
+__device__ __noinline__ void open_doors(const Params& p, int e, int keys, const WarpSmem& ws, int lane) {
+  if (keys == 0) return;
+  const int S = p.S, n = S * S;
+  const uint8_t* g = p.st.map + (size_t)e * n;
+  uint8_t* smap = ws.map(p);
+  if (p.task == kTaskAscii) {
+    for (int i = lane; i < n; i += 32) {
+      const int v = map_bits<MAPK>(p) ? g[i] : smap[i];
+      if (!(is_locked(v) && ((keys >> (v - kLocked)) & 1))) continue;
+      if (map_bits<MAPK>(p))
+        atomicAnd(reinterpret_cast<uint32_t*>(smap) + (i >> 5), ~(1u << (i & 31)));
+      else
+        smap[i] = 0;
+    }
+  } else if (keys & 1) {
     const int2 door = *reinterpret_cast<const int2*>(ws.obj(p) + 4);
-    if (lane == 0 && door.x >= 0 && door.y >= 0 && door.x < p.S && door.y < p.S) {
-      const int i = door.y * p.S + door.x;
+    if (lane == 0 && door.x >= 0 && door.y >= 0 && door.x < S && door.y < S) {
+      const int i = door.y * S + door.x;
       if (map_bits<MAPK>(p)) {
-        if (p.st.map[(size_t)e * p.S * p.S + i] == kDoor)
-          reinterpret_cast<uint32_t*>(ws.map(p))[i >> 5] &= ~(1u << (i & 31));
-      } else if (ws.map(p)[i] == kDoor) {
-        ws.map(p)[i] = 0;
+        if (g[i] == kDoor) reinterpret_cast<uint32_t*>(smap)[i >> 5] &= ~(1u << (i & 31));
+      } else if (smap[i] == kDoor) {
+        smap[i] = 0;
       }
     }
-    __syncwarp();
   }
+  __syncwarp();
 }
 
 // Everything one launch does for env e: MODE_ROLLOUT runs p.steps steps with
@@ -998,14 +1155,15 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
     Env r = load_env(p, e);
     load_objects(p, ws, e, lane);
     stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
-    if (map_bits<MAPK>(p)) open_door<MAPK>(p, e, r, ws, lane);
+    open_doors<MAPK>(p, e, r.keys, ws, lane);
     int a_next = p.actions[e];
     for (int t = 0; t < p.steps; ++t) {
       const int a = a_next;
       if (t + 1 < p.steps) a_next = p.actions[(size_t)(t + 1) * p.out_stride + e];
       float c, s;
       const size_t out = (size_t)t * p.out_stride + e;
-      if (__builtin_expect(step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), lane, c, s, a, out, false), 0)) {
+      const int keys0 = r.keys;
+      if (__builtin_expect(step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), ws.spr_in(p), lane, c, s, a, out, false), 0)) {
         const uint32_t ep = p.st.episode[e] + 1;
         __syncwarp();
         generate<MAPK>(p, e, ep, wbase, scratch, lane);
@@ -1014,7 +1172,7 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
         __syncwarp();
         heading(p, r, c, s);
       }
-      open_door<MAPK>(p, e, r, ws, lane);
+      if (__builtin_expect(r.keys != keys0, 0)) open_doors<MAPK>(p, e, r.keys, ws, lane);
       render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot,
                                          p.frames + (size_t)t * p.frame_step + (size_t)e * frame_bytes);
       __syncwarp();
@@ -1027,7 +1185,7 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
       st.frac_y[e] = r.fy;
       st.turn[e] = (int16_t)r.turn;
       st.t[e] = r.t;
-      st.flags[e] = (uint8_t)r.has_key;
+      st.flags[e] = (uint8_t)r.keys;
     }
     __syncwarp();
     return;
@@ -1044,10 +1202,12 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
     r = load_env(p, e);
     load_objects(p, ws, e, lane);
     stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
-    if (map_bits<MAPK>(p)) open_door<MAPK>(p, e, r, ws, lane);
+    open_doors<MAPK>(p, e, r.keys, ws, lane);
     if (MODE == MODE_STEP) {
+      const int keys0 = r.keys;
       if (__builtin_expect(
-              step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), lane, c, s, (int)p.actions[e], (size_t)e, true), 0)) {
+              step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), ws.spr_in(p), lane, c, s, (int)p.actions[e], (size_t)e,
+                             true), 0)) {
         const uint32_t ep = p.st.episode[e] + 1;
         __syncwarp();
         generate<MAPK>(p, e, ep, wbase, scratch, lane);
@@ -1055,19 +1215,21 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
         load_objects(p, ws, e, lane);
         __syncwarp();
         heading(p, r, c, s);
+      } else if (r.keys != keys0) {
+        open_doors<MAPK>(p, e, r.keys, ws, lane);
       }
     } else {
       heading(p, r, c, s);
     }
   }
-  open_door<MAPK>(p, e, r, ws, lane);
   render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
   __syncwarp();
 }
 
 __device__ __forceinline__ void write_palette(const Params& p, const WarpSmem& ws, int lane) {
-  if (lane < 16) ws.pal(p)[lane] = c_wall[lane >> 3][lane & 7];
-  if (lane < 4) ws.pal(p)[16 + lane] = c_sprite[lane];
+  ws.pal(p)[lane] = c_wall[lane];
+  ws.pal(p)[32 + lane] = c_wall[32 + lane];
+  if (lane < 8) ws.pal(p)[64 + lane] = c_sprite[lane];
   __syncwarp();
 }
 

@@ -15,6 +15,7 @@ N_ACTIONS = 7  # noop, forward, back, strafe-left, strafe-right, turn-left, turn
 TASK_ROOMS = 0
 TASK_MAZE_KEYDOOR = 1
 TASK_MAZE_ROOMS = 2
+TASK_ASCII = 3
 
 _COMMON = dict(
     frame_h=64,
@@ -67,6 +68,46 @@ def large_scale(n_envs: int = 65536) -> dict:
     """65,536 envs, 128 x 128 mazes with 8 x 8 rooms, 16 sprite slots, 128 x 128 RGB and
     the grayscale stack, horizon 500, 1000-step random-action rollouts, seed 4."""
     return maze_rooms(n_envs=n_envs)
+
+
+# ASCII maps (Table 2 symbols) of this repository's own design: the paper names
+# its ASCII domains (simple, key-door, key-corridor) but prints none of them.
+ASCII_MAPS = {
+    "simple": "\n".join([
+        "############",
+        "#S.........#",
+        "#..####....#",
+        "#.....#....#",
+        "#.....#..G.#",
+        "############",
+    ]),
+    "key-door": "\n".join([
+        "##########",
+        "#S...#...#",
+        "#....#.G.#",
+        "#.r..R...#",
+        "#....#...#",
+        "##########",
+    ]),
+    "coloured-rooms": "\n".join([
+        "#################",
+        "#S..#...#.....#.#",
+        "#...B...\".....Y.#",
+        "#.b.#...#..y..#G#",
+        "##R###\\#######.#",
+        "#...#...#.......#",
+        "#.r.#S..1...2..S#",
+        "#################",
+    ]),
+}
+
+
+def ascii_env(name: str, n_envs: int = 16, map_side: int = 24, seed: int = 6, horizon: int = 200,
+              max_sprites: int = 4, frame_h: int = 64, frame_w: int = 64, shading: int = 0) -> dict:
+    """An ASCII map of ASCII_MAPS as an env config (+1 per key, +10 at the goal, -0.001 per step)."""
+    return dict(_COMMON, task=TASK_ASCII, n_envs=n_envs, map_side=map_side, wall_prob=0.0, max_sprites=max_sprites,
+                horizon=horizon, step_reward=-0.001, key_reward=1.0, goal_reward=10.0, seed=seed, frame_h=frame_h,
+                frame_w=frame_w, shading=shading, ascii_map=ASCII_MAPS[name])
 
 
 UNEVEN_SIDES = (16, 32, 64, 128)

@@ -19,7 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libjx.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, EDEVICE = range(7)
-TASK_ROOMS, TASK_MAZE_KEYDOOR, TASK_MAZE_ROOMS = 0, 1, 2
+TASK_ROOMS, TASK_MAZE_KEYDOOR, TASK_MAZE_ROOMS, TASK_ASCII = 0, 1, 2, 3
+LOCKED, UNLOCKED = 16, 20
 
 # State fields (JX_F_*), name -> (index, numpy dtype, per-env shape builder)
 FIELDS = {
@@ -32,7 +33,7 @@ FIELDS = {
 
 # Entry points declared in include/jx.h (checked by the ABI test).
 SYMBOLS = [
-    "jx_create", "jx_destroy", "jx_reset", "jx_step", "jx_rollout", "jx_render", "jx_step_host",
+    "jx_create", "jx_create_ascii", "jx_destroy", "jx_reset", "jx_step", "jx_rollout", "jx_render", "jx_step_host",
     "jx_step_host_static", "jx_debug_rays",
     "jx_state_bytes", "jx_state_field", "jx_get_state", "jx_set_state", "jx_sync_status", "jx_launch_count",
     "jx_launch_shape", "jx_last_error",
@@ -59,7 +60,7 @@ class Config(ctypes.Structure):
         ("horizon", ctypes.c_int32), ("turns_per_rev", ctypes.c_int32), ("wall_prob", ctypes.c_double),
         ("fov_deg", ctypes.c_double), ("move_step", ctypes.c_double), ("radius", ctypes.c_double),
         ("step_reward", ctypes.c_double), ("key_reward", ctypes.c_double), ("goal_reward", ctypes.c_double),
-        ("seed", ctypes.c_uint64), ("gray_stack", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("gray_stack", ctypes.c_int32), ("shading", ctypes.c_int32),
     ]
 
     @classmethod
@@ -105,6 +106,7 @@ def _load() -> ctypes.CDLL:
     P, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
     sig = {
         "jx_create": [P, ctypes.c_int, P],
+        "jx_create_ascii": [P, ctypes.c_char_p, ctypes.c_int, P],
         "jx_destroy": [P],
         "jx_reset": [P, P, P],
         "jx_step": [P, P, P, P, P, P],
@@ -206,10 +208,15 @@ class Env:
     """N environments on one GPU (``jx_create`` ... ``jx_destroy``)."""
 
     def __init__(self, cfg: dict, device: int = 0):
+        """``cfg["ascii_map"]`` (text) is the map of the ASCII task."""
         self.cfg = dict(cfg)
         self._c = Config.from_dict(cfg)
         h = ctypes.c_void_p()
-        _check(lib.jx_create(ctypes.byref(self._c), device, ctypes.byref(h)))
+        if cfg.get("ascii_map") is not None:
+            _check(lib.jx_create_ascii(ctypes.byref(self._c), cfg["ascii_map"].encode("ascii"), device,
+                                       ctypes.byref(h)))
+        else:
+            _check(lib.jx_create(ctypes.byref(self._c), device, ctypes.byref(h)))
         self._h = h
         self.device = device
         self.n = int(cfg["n_envs"])

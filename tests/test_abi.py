@@ -54,7 +54,7 @@ def test_config_struct_matches_header(jx):
     for decl in re.findall(r"^\s*(?:int32_t|double|uint64_t)\s+([^;]+);", body, re.M):
         names += [n.strip() for n in decl.split(",")]
     assert names == [f[0] for f in jx.Config._fields_]
-    assert ctypes.sizeof(jx.Config) == 8 * 4 + 7 * 8 + 8 + 8  # gray_stack padded to 8
+    assert ctypes.sizeof(jx.Config) == 8 * 4 + 7 * 8 + 8 + 8  # gray_stack and shading
 
 
 BAD = [

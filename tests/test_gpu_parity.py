@@ -4,7 +4,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2605_19926_gb300 import inputs
+from paper_2605_19926_gb300 import inputs, jx
 from parity import (NTHREADS, Run, Stats, check_door_crossings, check_reset, compare_frames, compare_generated,
                     compare_rays, forward_biased_actions, lockstep, script_goal_and_door, to_oracle)
 
@@ -32,6 +32,14 @@ CASES = {
     "mazerooms128_gray_128x128": inputs.maze_rooms(n_envs=5, map_side=128, seed=9, horizon=20),
     "mazerooms32_gray_48x80": inputs.maze_rooms(n_envs=21, map_side=32, seed=10, horizon=15, max_sprites=6,
                                                 frame_h=48, frame_w=80),
+    "ascii_simple_shaded": inputs.ascii_env("simple", n_envs=24, map_side=16, shading=1, horizon=80),
+    "ascii_keydoor": inputs.ascii_env("key-door", n_envs=40, map_side=16, horizon=120),
+    "ascii_coloured_rooms_shaded": inputs.ascii_env("coloured-rooms", n_envs=48, map_side=24, seed=9, horizon=150,
+                                                    shading=1, frame_h=48, frame_w=80),
+    "maze32_shaded_gray": dict(inputs.maze_keydoor(n_envs=20, map_side=32, seed=11, horizon=40), shading=1,
+                               gray_stack=1),
+    "ascii_coloured_rooms_128": dict(inputs.ascii_env("coloured-rooms", n_envs=6, map_side=128, seed=3, horizon=60),
+                                     gray_stack=1),
 }
 
 
@@ -56,17 +64,20 @@ def test_single_env_rooms_1000_steps():
 @pytest.mark.parametrize("name,steps", [("maze32_ragged", 150), ("maze8_events", 300), ("maze6_events", 300),
                                         ("rooms16_sprites_40x48", 120), ("maze18_96x128", 70),
                                         ("mazerooms64_gray", 60), ("mazerooms128_gray_128x128", 45),
-                                        ("mazerooms32_gray_48x80", 40)])
+                                        ("mazerooms32_gray_48x80", 40), ("ascii_simple_shaded", 120),
+                                        ("ascii_keydoor", 200), ("ascii_coloured_rooms_shaded", 200),
+                                        ("maze32_shaded_gray", 60), ("ascii_coloured_rooms_128", 80)])
 def test_lockstep(name, steps):
     run = Run(CASES[name])
     stats = Stats()
     check_reset(run, stats)
-    events = name.endswith("_events")
-    lockstep(run, stats, steps, seed=11, action_fn=forward_biased_actions if events else inputs.actions)
+    events = name.endswith("_events") or name in ("ascii_keydoor", "ascii_coloured_rooms_shaded")
+    walk = events or name.startswith("ascii")
+    lockstep(run, stats, steps, seed=11, action_fn=forward_biased_actions if walk else inputs.actions)
     stats.check()
     if events:
         assert stats.key_events > 0 and stats.resets > 0, stats
-    if name in ("maze32_ragged", "maze18_96x128") or name.startswith("mazerooms"):
+    if name in ("maze32_ragged", "maze18_96x128", "maze32_shaded_gray") or name.startswith("mazerooms"):
         assert stats.resets > 0
 
 
@@ -327,4 +338,47 @@ def test_large_scale_mazes_with_rooms_sampled():
         t = f["t"][idx]
         planes = f["gray"][idx][np.arange(len(idx)), t % 4]
         assert (planes == oracle.gray(frames[idx])).all()
+    stats.check()
+
+
+def _corridor(text, n=8):
+    cfg = dict(inputs.ascii_env("simple", n_envs=n, map_side=16, horizon=0), ascii_map=text)
+    run = Run(cfg)
+    run.reset()
+    blob = run.env.get_state()
+    f = run.env.fields(blob)
+    f["theta0"][:] = 0.0
+    f["turn"][:] = 0
+    f["cell_x"][:], f["frac_x"][:] = 1, 0.45
+    f["cell_y"][:], f["frac_y"][:] = 1, 0.5
+    run.env.set_state(blob)
+    return run
+
+
+@pytest.mark.parametrize("door,passes", [("R", False), ("B", True)])
+def test_coloured_key_corridor(door, passes):
+    """The blue key is picked up after 16 forward moves; a red locked door then
+    stops the agent at x = 4.75, a blue one lets it reach the goal after 56."""
+    run = _corridor(f"#########\n#S.b.{door}.G#\n#########")
+    stats = Stats()
+    lockstep(run, stats, 60, seed=0, action_fn=lambda seed, step, n: np.ones(n, np.uint8))
+    stats.check()
+    assert stats.key_events == run.env.n
+    assert stats.goal_events == (run.env.n if passes else 0)
+
+
+def test_unlocked_door_opens_when_bumped():
+    """Move 24 from x = 1.45 bumps the blue unlocked door at x = 4: it opens in
+    the state's map; the agents then walk through, in lockstep with the oracle."""
+    run = _corridor("########\n#S..\"..#\n########")
+    stats = Stats()
+    lockstep(run, stats, 23, seed=0, action_fn=lambda seed, step, n: np.ones(n, np.uint8))
+    f = run.env.fields(run.env.get_state())
+    assert (f["map"][:, 1, 4] == jx.UNLOCKED + 1).all()
+    lockstep(run, stats, 1, seed=0, first_step=23, action_fn=lambda seed, step, n: np.ones(n, np.uint8))
+    f = run.env.fields(run.env.get_state())
+    assert (f["map"][:, 1, 4] == 0).all() and (np.abs(f["frac_x"] - 0.75) < 1e-4).all()
+    lockstep(run, stats, 3, seed=0, first_step=24, action_fn=lambda seed, step, n: np.ones(n, np.uint8))
+    f = run.env.fields(run.env.get_state())
+    assert (f["cell_x"] == 4).all()
     stats.check()

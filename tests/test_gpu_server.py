@@ -1,6 +1,8 @@
 """The continuous-batching step server (jx_server_*): results are the same
 alone and in the mix, admission follows the byte budget, launches overlap,
 waits are bounded, and the frames match the oracle."""
+import time
+
 import numpy as np
 import pytest
 import torch
@@ -99,25 +101,33 @@ def test_admission_follows_the_budget():
 
 
 def test_launches_overlap_and_stay_exact():
-    """A large session's launch runs while a second session's request arrives:
-    the second goes to another launch slot and both results match jx_step."""
-    big = inputs.rooms(n_envs=4096, map_side=64, wall_prob=0.3, seed=81, max_sprites=8, frame_h=128, frame_w=128)
+    """A long launch (16,384 envs, 128 x 128 frames) is on the device when a
+    second session's request arrives: the second goes out on another launch
+    slot at once, and both sessions' results match each env stepped alone."""
+    big = inputs.rooms(n_envs=16384, map_side=64, wall_prob=0.3, seed=81, max_sprites=8, frame_h=128, frame_w=128)
     small = inputs.maze_keydoor(n_envs=64, map_side=32, seed=82, horizon=50)
-    with jx.Server(budget_bytes=2 << 30, max_inflight=4) as server:
+    with jx.Server(budget_bytes=4 << 30, max_inflight=4) as server:
         sb, ss = server.open(big), server.open(small)
         rb, rs = Run(big), Run(small)
         rb.reset()
         rs.reset()
-        for r in range(12):
+        for r in range(6):
             ab, as_ = inputs.actions(83, r, big["n_envs"]), inputs.actions(84, r, small["n_envs"])
+            n0 = server.stats()["launches"]
             tb = sb.submit(ab)
+            t0 = time.perf_counter()
+            while server.stats()["launches"] == n0 and time.perf_counter() - t0 < 5.0:
+                pass  # the big request is on the device
             ts = ss.submit(as_)
             server.wait(tb, timeout=30.0)
             server.wait(ts, timeout=30.0)
+            torch.cuda.synchronize()
             for sess, run, act in ((sb, rb, ab), (ss, rs, as_)):
-                f, rw, d = _copy(sess)
-                fa, ra, da = run.step(act)
-                assert (f.cpu().numpy() == fa).all() and (rw.cpu().numpy() == ra).all() and (d.cpu().numpy() == da).all()
+                run.actions.copy_(torch.from_numpy(act))
+                run.env.step(run.actions, run.frames, run.rewards, run.dones)
+                torch.cuda.synchronize()
+                assert torch.equal(sess.frames, run.frames), r
+                assert torch.equal(sess.rewards, run.rewards) and torch.equal(sess.dones, run.dones), r
         assert server.stats()["peak_inflight_launches"] >= 2
         sb.close()
         ss.close()
