@@ -227,9 +227,14 @@ def run_uneven(args):
         torch.distributed.barrier()
     from paper_2605_19926_gb300 import jx
 
-    groups = inputs.uneven_groups(seed=2 + rank)
+    groups = inputs.uneven_groups(n_envs=args.uneven_envs, seed=2 + rank)
     envs = [jx.Env(c, local) for c in groups]
-    batch = jx.Batch(envs)
+    pinned = None
+    if args.tiling:
+        pinned = jx.Tiling()
+        (pinned.warps_per_block, pinned.cols_per_lane, pinned.bits_min_side,
+         pinned.max_rows_per_block) = (int(v) for v in args.tiling.split(","))
+    batch = jx.Batch(envs, pinned)
     N, F = batch.n, batch.frame_bytes
     dev = torch.device("cuda", local)
     T = args.uneven_slots
@@ -260,7 +265,8 @@ def run_uneven(args):
     fixed_ms, _ = timed_rollouts()
     fixed_tiling = batch.tiling
     t_tune = time.perf_counter()
-    trials = batch.autotune(mode=1, steps=T, max_trials=args.tune_trials, stream=stream)
+    trials = [] if pinned is not None else batch.autotune(mode=1, steps=T, max_trials=args.tune_trials,
+                                                          stream=stream)
     tune_s = time.perf_counter() - t_tune
     tuned = batch.tiling
     clocks = ClockSampler(local)
@@ -571,6 +577,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip jx_autotune before timing (the env's own kernel with its fixed tiles)")
     ap.add_argument("--uneven-slots", type=int, default=16, help="steps per rollout launch of the uneven batch")
+    ap.add_argument("--uneven-envs", type=int, default=16384)
+    ap.add_argument("--tiling", default="", help="uneven batch: w,c,b,r tiling to use instead of autotuning")
     ap.add_argument("--tune-trials", type=int, default=1000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
