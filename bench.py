@@ -195,7 +195,7 @@ def run_reference(args, cfg: dict):
 
 def tiling_dict(t) -> dict:
     """A launch choice as JSON: all zero means the env's own kernel."""
-    names = ("warps_per_block", "cols_per_lane", "bits_min_side", "max_rows_per_block")
+    names = ("warps_per_block", "cols_per_lane", "bits_min_side", "max_rows_per_block", "staging_buffers")
     d = dict(zip(names, t.as_tuple()))
     d["kernel"] = "env kernel" if not any(t.as_tuple()) else "batched kernel"
     return d
@@ -232,8 +232,9 @@ def run_uneven(args):
     pinned = None
     if args.tiling:
         pinned = jx.Tiling()
-        (pinned.warps_per_block, pinned.cols_per_lane, pinned.bits_min_side,
-         pinned.max_rows_per_block) = (int(v) for v in args.tiling.split(","))
+        vals = [int(v) for v in args.tiling.split(",")] + [1]
+        (pinned.warps_per_block, pinned.cols_per_lane, pinned.bits_min_side, pinned.max_rows_per_block,
+         pinned.staging_buffers) = vals[:5]
     batch = jx.Batch(envs, pinned)
     N, F = batch.n, batch.frame_bytes
     dev = torch.device("cuda", local)
@@ -303,8 +304,7 @@ def run_uneven(args):
         v = world * N * K / (ms / 1e3)
         gbs = N * K * bpes / (ms / 1e3) / 1e9 / world
         return {"value": v, "ms_per_step": ms / K, "achieved_gbs": gbs, "frac": gbs / peak,
-                "tiling": dict(zip(("warps_per_block", "cols_per_lane", "bits_min_side", "max_rows_per_block"),
-                                   tiling.as_tuple()))}
+                "tiling": tiling_dict(tiling)}
 
     shape = batch.launch_shape()
     tuned_leg = leg(tuned_ms, tuned)

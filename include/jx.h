@@ -312,16 +312,21 @@ typedef struct jx_graph jx_graph;
  *                      held in shared memory as bit planes (1 bit per cell)
  *                      instead of byte grids; 0 = byte grids for all
  *  max_rows_per_block  frame rows per staged shared-memory block (upper
- *                      bound, 1..16; lowered to fit and to the fill pass) */
+ *                      bound, 1..64; lowered to fit 28 warps per SM and to
+ *                      whole fill passes)
+ *  staging_buffers     row-block staging buffers per warp: 1 (a block waits
+ *                      for the copy-out of the one before; larger blocks fit)
+ *                      or 2 (fill one while the other drains) */
 typedef struct {
   int32_t warps_per_block;
   int32_t cols_per_lane;
   int32_t bits_min_side;
   int32_t max_rows_per_block;
+  int32_t staging_buffers;
 } jx_tiling;
 
 /* The fixed tiling (what a single env uses): 1 warp per block, 1 ray per
- * lane, byte maps below side 128, up to 16 rows per block. */
+ * lane, byte maps below side 128, up to 32 rows per block, one staging buffer. */
 jx_status jx_tiling_default(jx_tiling* out);
 
 /* Make a batch of n_groups (1..32) distinct envs on one device. tiling NULL
@@ -355,7 +360,8 @@ jx_status jx_batch_render(jx_batch* batch, void* stream, uint8_t* d_frames);
 
 /* Autotuner: times every tiling of the search space (warps_per_block 1, 2,
  * 4 x cols_per_lane 1, 2 x bits_min_side 0, 128, 64, 32 x max_rows_per_block
- * 4, 8, 16; the first max_trials of them, the default first) on this batch
+ * 8, 16, 32 x staging_buffers 1, 2; the first max_trials of them, the
+ * default first) on this batch
  * and keeps the fastest. mode 0 times `steps` jx_batch_step launches, mode 1
  * one jx_batch_rollout launch of `steps` steps; each trial starts from
  * jx_batch_reset and is timed with CUDA events after one untimed launch.

@@ -278,15 +278,18 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
     return cuda_fail(err, "cudaGetDeviceProperties");
   }
   env->num_sms = prop.multiProcessorCount;
-  // Frame staging: the largest row block (at most 16 rows) with which
-  // kMinBlocksPerSm one-warp blocks still fit in one SM's shared memory.
+  // Frame staging: one buffer per warp (each row block waits for the copy-out
+  // of the one before), the largest row block (at most 32 rows) with which
+  // kMinBlocksPerSm one-warp blocks still fit in one SM's shared memory:
+  // fewer, larger blocks beat double buffering at the same shared memory.
   // Maps of side 128 are staged as bit planes (2 KB instead of 16 KB).
   p.map_bits = c.map_side >= 128 && c.map_side % 8 == 0;
   p.gray = c.gray_stack != 0;
   p.shading = c.shading != 0;
   p.out_stride = c.n_envs;
   p.frame_step = (size_t)c.n_envs * jx::host::frame_bytes(c);
-  jx::host::choose_rows(p, 16, jx::kWarpsPerBlock, jx::kMinBlocksPerSm, prop.sharedMemPerMultiprocessor,
+  p.staging = 1;
+  jx::host::choose_rows(p, 32, jx::kWarpsPerBlock, jx::kMinBlocksPerSm, prop.sharedMemPerMultiprocessor,
                         prop.reservedSharedMemPerBlock);
   env->smem_block = jx::block_smem_bytes(p);
   const int smem_block = env->smem_block;
@@ -706,7 +709,7 @@ jx_status jx_autotune(jx_env* env, void* stream, int32_t mode, int32_t steps, in
   for (int i = 0; i < nb; ++i) best = bms[i] < best ? bms[i] : best;
   env->use_batch = best < env_ms;
   if (trials) {
-    trials[0] = jx_tiling{0, 0, 0, 0};
+    trials[0] = jx_tiling{0, 0, 0, 0, 0};
     for (int i = 0; i < nb; ++i) trials[1 + i] = bt[i];
   }
   if (ms_per_step) {
@@ -721,7 +724,8 @@ jx_status jx_env_set_tiling(jx_env* env, const jx_tiling* tiling) {
   if (jx_status st = check_env(env)) return st;
   if (!tiling) return fail(JX_EINVAL, "tiling is NULL");
   const jx_tiling t = *tiling;
-  if (t.warps_per_block == 0 && t.cols_per_lane == 0 && t.bits_min_side == 0 && t.max_rows_per_block == 0) {
+  if (t.warps_per_block == 0 && t.cols_per_lane == 0 && t.bits_min_side == 0 && t.max_rows_per_block == 0 &&
+      t.staging_buffers == 0) {
     env->use_batch = false;
     return JX_OK;
   }
@@ -741,7 +745,7 @@ jx_status jx_env_tiling(const jx_env* env, jx_tiling* tiling) {
   if (jx_status st = check_env(env)) return st;
   if (!tiling) return fail(JX_EINVAL, "tiling is NULL");
   if (env->use_batch) return jx_batch_get_tiling(env->tuned, tiling);
-  *tiling = jx_tiling{0, 0, 0, 0};
+  *tiling = jx_tiling{0, 0, 0, 0, 0};
   return JX_OK;
 }
 

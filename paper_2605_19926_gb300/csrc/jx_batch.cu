@@ -50,8 +50,10 @@ jx_status check_tiling(const jx_tiling& t) {
   if (t.cols_per_lane != 1 && t.cols_per_lane != 2)
     return fail(JX_EINVAL, "cols_per_lane must be 1 or 2 (got %d)", t.cols_per_lane);
   if (t.bits_min_side < 0) return fail(JX_EINVAL, "bits_min_side must be >= 0 (got %d)", t.bits_min_side);
-  if (t.max_rows_per_block < 1 || t.max_rows_per_block > 16)
-    return fail(JX_EINVAL, "max_rows_per_block must be in [1, 16] (got %d)", t.max_rows_per_block);
+  if (t.max_rows_per_block < 1 || t.max_rows_per_block > 64)
+    return fail(JX_EINVAL, "max_rows_per_block must be in [1, 64] (got %d)", t.max_rows_per_block);
+  if (t.staging_buffers != 1 && t.staging_buffers != 2)
+    return fail(JX_EINVAL, "staging_buffers must be 1 or 2 (got %d)", t.staging_buffers);
   return JX_OK;
 }
 
@@ -68,6 +70,7 @@ jx_status apply_tiling(jx_batch* b, const jx_tiling& t) {
     jx::Params p = env->base;
     const int S = env->cfg.map_side;
     p.map_bits = t.bits_min_side > 0 && S >= t.bits_min_side && S % 8 == 0;
+    p.staging = t.staging_buffers;
     jx::host::choose_rows(p, t.max_rows_per_block, t.warps_per_block, jx::kMinBlocksPerSm, b->smem_per_sm,
                           b->reserved);
     p.out_stride = (int32_t)b->n_total;
@@ -157,10 +160,11 @@ std::vector<jx_tiling> search_space() {
   for (int w : {1, 2, 4})
     for (int c : {1, 2})
       for (int bits : {0, 128, 64, 32})
-        for (int rows : {4, 8, 16}) {
-          jx_tiling t{w, c, bits, rows};
-          if (std::memcmp(&t, &def, sizeof(t)) != 0) out.push_back(t);
-        }
+        for (int rows : {8, 16, 32})
+          for (int staging : {1, 2}) {
+            jx_tiling t{w, c, bits, rows, staging};
+            if (std::memcmp(&t, &def, sizeof(t)) != 0) out.push_back(t);
+          }
   return out;
 }
 
@@ -183,7 +187,8 @@ jx_status jx_tiling_default(jx_tiling* out) {
   out->warps_per_block = 1;
   out->cols_per_lane = 1;
   out->bits_min_side = 128;
-  out->max_rows_per_block = 16;
+  out->max_rows_per_block = 32;
+  out->staging_buffers = 1;
   return JX_OK;
 }
 

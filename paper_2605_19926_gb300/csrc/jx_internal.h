@@ -15,7 +15,7 @@ constexpr int kMaxH = 256;
 constexpr int kMaxW = 256;
 constexpr int kWarpsPerBlock = 1;  // one-warp blocks spread envs evenly over the SMs
 constexpr int kThreads = kWarpsPerBlock * 32;
-constexpr int kRingBuffers = 2;  // frame row-block staging buffers per warp
+constexpr int kMaxStaging = 2;  // frame row-block staging buffers per warp: 1 or 2
 constexpr int kMinBlocksPerSm = 28;  // register budget: 28 warps resident per SM
 
 enum Mode { MODE_STEP = 0, MODE_RESET = 1, MODE_RENDER = 2, MODE_RAYS = 3, MODE_ROLLOUT = 4 };
@@ -91,6 +91,7 @@ struct Params {
   int32_t n_spawn, n_goal, n_keys;
   int32_t gray_block_bytes;  // rows_per_block * W when gray, else 0
   int32_t rows_per_block;  // rows per staged frame block
+  int32_t staging;         // staging buffers per warp (1: each block waits for the last one's copy-out)
   int32_t frame_block_bytes;
   int32_t map_smem_bytes;  // S * S rounded up to 16
   // per-warp shared memory layout (byte offsets from the warp's base; set by layout_warp_smem)

@@ -36,7 +36,6 @@ __host__ __device__ constexpr int key_colour(int type) {
 }
 __device__ __forceinline__ bool is_locked(int v) { return (unsigned)(v - kLocked) < 3u; }
 __device__ __forceinline__ bool is_unlocked(int v) { return (unsigned)(v - kUnlocked) < 3u; }
-static_assert(kRingBuffers == 2, "bulk wait depth below assumes two staging buffers");
 
 // ------------------------------------------------------------- palette ----
 // Colours packed as 0xYYBBGGRR: the low three bytes are R, G, B and the top
@@ -115,9 +114,13 @@ __device__ __forceinline__ void bulk_copy(void* gdst, const void* ssrc, uint32_t
                : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-// all but the newest group have finished reading shared memory
-__device__ __forceinline__ void bulk_wait_read_all_but_one() {
-  asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+// the staging buffer about to be filled has been read out: with two buffers
+// the other one may still be draining, with one every earlier copy is done
+__device__ __forceinline__ void bulk_wait_staging(int staging) {
+  if (staging == 1)
+    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+  else
+    asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
 }
 __device__ __forceinline__ void bulk_wait_read_all() {
   asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
@@ -128,8 +131,8 @@ __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; 
 
 // Shared memory of a warp, addressed from one base with the layout offsets
 // of Params (constants), so no pointer lives in a register:
-//   ring      kRingBuffers * frame_block_bytes (also the maze work space)
-//   gray      kRingBuffers * gray_block_bytes: the row blocks of the grayscale frame
+//   ring      staging * frame_block_bytes (also the maze work space)
+//   gray      staging * gray_block_bytes: the row blocks of the grayscale frame
 //   pal       [2][32] wall colours by face and cell value, then [8] sprite colours by type
 //   map       S * S cell values, row-major
 //   col_rgb   [W] wall colour, chunk-interleaved (see col_slot)
@@ -636,7 +639,7 @@ __device__ __forceinline__ void generate(const Params& p, int e, uint32_t ep, ui
   } else {
     const int nn = (p.S - 2) / 2;
     uint8_t* work = scratch;
-    if (maze_scratch_bytes(nn * nn) <= (size_t)(kRingBuffers * p.frame_block_bytes)) {
+    if (maze_scratch_bytes(nn * nn) <= (size_t)(p.staging * p.frame_block_bytes)) {
       if (lane == 0) bulk_wait_read_all();  // the ring's pending frame stores have read it
       __syncwarp();
       work = ws.ring();
@@ -1086,7 +1089,7 @@ __device__ __forceinline__ void render_env(const Params& p, int e, const Env& r,
     const int r1 = r0 + p.rows_per_block < H ? r0 + p.rows_per_block : H;
     uint8_t* buf = ws.ring() + slot * p.frame_block_bytes;
     uint8_t* gbuf = gray_on ? ws.gray_ring(p) + slot * p.gray_block_bytes : nullptr;
-    if (lane == 0) bulk_wait_read_all_but_one();
+    if (lane == 0) bulk_wait_staging(p.staging);
     __syncwarp();
     fill_block(p, ws, buf, gbuf, r0, r1, nvis, lane);
     fence_proxy_async_smem();
@@ -1106,7 +1109,7 @@ __device__ __forceinline__ void render_env(const Params& p, int e, const Env& r,
       }
       bulk_commit();
     }
-    slot ^= 1;
+    slot = slot + 1 == p.staging ? 0 : slot + 1;
   }
 }
 
@@ -1346,14 +1349,14 @@ auto batch_kernel_of(int mode, int cols) {
 
 void layout_warp_smem(Params& p) {
   const int K = p.K > 0 ? p.K : 1;
-  int q = kRingBuffers * p.frame_block_bytes;
+  int q = p.staging * p.frame_block_bytes;
   auto take = [&](int bytes) {
     const int at = q;
     q += align16(bytes);
     return at;
   };
   p.map_smem_bytes = align16(p.map_bits ? (p.S * p.S + 7) / 8 : p.S * p.S);
-  p.off_gray = take(kRingBuffers * p.gray_block_bytes);
+  p.off_gray = take(p.staging * p.gray_block_bytes);
   p.off_pal = take(4 * kPaletteWords);
   p.off_map = take(p.map_smem_bytes);
   p.off_col_rgb = take(4 * p.W);

@@ -338,7 +338,8 @@ jx_status jx_server_create(int device, uint64_t budget_bytes, int32_t max_sessio
   if (t.warps_per_block != 1 && t.warps_per_block != 2 && t.warps_per_block != 4)
     return fail(JX_EINVAL, "warps_per_block must be 1, 2 or 4");
   if (t.cols_per_lane != 1 && t.cols_per_lane != 2) return fail(JX_EINVAL, "cols_per_lane must be 1 or 2");
-  if (t.bits_min_side < 0 || t.max_rows_per_block < 1 || t.max_rows_per_block > 16)
+  if (t.bits_min_side < 0 || t.max_rows_per_block < 1 || t.max_rows_per_block > 64 ||
+      (t.staging_buffers != 1 && t.staging_buffers != 2))
     return fail(JX_EINVAL, "bad tiling");
   int ndev = 0;
   cudaError_t err = cudaGetDeviceCount(&ndev);
@@ -476,6 +477,7 @@ jx_status jx_server_open(jx_server* sv, const jx_config* cfg, int32_t* session) 
   }
   jx::Params p = s->env->base;
   p.map_bits = sv->tiling.bits_min_side > 0 && cfg->map_side >= sv->tiling.bits_min_side && cfg->map_side % 8 == 0;
+  p.staging = sv->tiling.staging_buffers;
   jx::host::choose_rows(p, sv->tiling.max_rows_per_block, sv->tiling.warps_per_block, jx::kMinBlocksPerSm,
                         sv->smem_per_sm, sv->reserved);
   p.frames = s->d_frames;

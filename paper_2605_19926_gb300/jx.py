@@ -76,13 +76,16 @@ class Tiling(ctypes.Structure):
     """Tile choices of the batched kernel (``jx_tiling``)."""
 
     _fields_ = [("warps_per_block", ctypes.c_int32), ("cols_per_lane", ctypes.c_int32),
-                ("bits_min_side", ctypes.c_int32), ("max_rows_per_block", ctypes.c_int32)]
+                ("bits_min_side", ctypes.c_int32), ("max_rows_per_block", ctypes.c_int32),
+                ("staging_buffers", ctypes.c_int32)]
 
-    def as_tuple(self) -> tuple[int, int, int, int]:
-        return (self.warps_per_block, self.cols_per_lane, self.bits_min_side, self.max_rows_per_block)
+    def as_tuple(self) -> tuple[int, int, int, int, int]:
+        return (self.warps_per_block, self.cols_per_lane, self.bits_min_side, self.max_rows_per_block,
+                self.staging_buffers)
 
     def __repr__(self):
-        return "Tiling(warps_per_block=%d, cols_per_lane=%d, bits_min_side=%d, max_rows_per_block=%d)" % self.as_tuple()
+        return ("Tiling(warps_per_block=%d, cols_per_lane=%d, bits_min_side=%d, max_rows_per_block=%d, "
+                "staging_buffers=%d)" % self.as_tuple())
 
 
 class ServerCounters(ctypes.Structure):

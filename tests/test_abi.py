@@ -102,7 +102,7 @@ def test_tiling_struct_and_default(jx):
     body = re.search(r"typedef struct \{([^}]*)\} jx_tiling;", text).group(1)
     names = re.findall(r"^\s*int32_t\s+(\w+);", body, re.M)
     assert names == [f[0] for f in jx.Tiling._fields_]
-    assert jx.default_tiling().as_tuple() == (1, 1, 128, 16)
+    assert jx.default_tiling().as_tuple() == (1, 1, 128, 32, 1)
 
 
 def test_batch_arguments_checked_before_cuda(jx):

@@ -34,16 +34,17 @@ def mixed():
     ]
 
 
-def tiling(w, c, bits, rows):
+def tiling(w, c, bits, rows, staging=1):
     t = jx.Tiling()
-    t.warps_per_block, t.cols_per_lane, t.bits_min_side, t.max_rows_per_block = w, c, bits, rows
+    t.warps_per_block, t.cols_per_lane, t.bits_min_side, t.max_rows_per_block, t.staging_buffers = (w, c, bits, rows,
+                                                                                                   staging)
     return t
 
 
 TILINGS = {
     "default": None,
     "bits_everywhere_2w_2c_4rows": tiling(2, 2, 8, 4),
-    "bytes_everywhere_4w_8rows": tiling(4, 1, 0, 8),
+    "bytes_everywhere_4w_8rows_2buffers": tiling(4, 1, 0, 8, 2),
 }
 
 
@@ -86,7 +87,7 @@ def test_batch_equals_groups_alone():
     """Each group's frames, rewards, dones and state are the same stepped alone
     (jx_step of that env) and in the mix (one batched launch)."""
     cfgs = mixed()
-    run = BatchRun(cfgs, tiling(2, 2, 32, 8))
+    run = BatchRun(cfgs, tiling(2, 2, 32, 8, 2))
     alone = [Run(c) for c in cfgs]
     frames = run.reset()
     for i, a in enumerate(alone):
@@ -183,7 +184,8 @@ def test_autotune_keeps_fastest_and_resets(mode):
 
 def test_tiling_validation():
     run = BatchRun(mixed()[:1])
-    for bad in (tiling(3, 1, 0, 8), tiling(1, 3, 0, 8), tiling(1, 1, -1, 8), tiling(1, 1, 0, 0), tiling(1, 1, 0, 17)):
+    for bad in (tiling(3, 1, 0, 8), tiling(1, 3, 0, 8), tiling(1, 1, -1, 8), tiling(1, 1, 0, 0), tiling(1, 1, 0, 65),
+                tiling(1, 1, 0, 8, 3), tiling(1, 1, 0, 8, 0)):
         with pytest.raises(jx.JxError) as ei:
             run.batch.tiling = bad
         assert ei.value.status == jx.EINVAL
@@ -245,12 +247,12 @@ def test_env_autotune_and_pinned_tilings_give_identical_results(cfg):
     dones and state (grayscale stack included) are the same."""
     ref, tuned = Run(cfg), Run(cfg)
     trials = tuned.env.autotune(mode=1, steps=3, max_trials=6)
-    assert len(trials) == 6 and trials[0][0].as_tuple() == (0, 0, 0, 0)
+    assert len(trials) == 6 and trials[0][0].as_tuple() == (0, 0, 0, 0, 0)
     best = min(trials, key=lambda x: x[1])[0].as_tuple()
     assert tuned.env.tiling.as_tuple() == best
     ref.reset()
     assert (ref.env.get_state() == tuned.env.get_state()).all()
-    pins = [tiling(4, 2, 8, 4), None, tiling(1, 1, 0, 16)]
+    pins = [tiling(4, 2, 8, 4), None, tiling(1, 1, 0, 16, 2)]
     tuned.reset()
     for s in range(36):
         if s % 12 == 0:
