@@ -280,17 +280,30 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
   env->num_sms = prop.multiProcessorCount;
   // Frame staging: one buffer per warp (each row block waits for the copy-out
   // of the one before), the largest row block (at most 32 rows) with which
-  // kMinBlocksPerSm one-warp blocks still fit in one SM's shared memory:
-  // fewer, larger blocks beat double buffering at the same shared memory.
-  // Maps of side 128 are staged as bit planes (2 KB instead of 16 KB).
-  p.map_bits = c.map_side >= 128 && c.map_side % 8 == 0;
+  // kMinBlocksPerSm warps still fit in one SM's shared memory: fewer, larger
+  // blocks beat double buffering at the same shared memory. The map is held
+  // as a bit plane when that buys fewer row blocks per frame (the smaller map
+  // leaves room for more rows), and always at side 128 (2 KB instead of 16 KB).
   p.gray = c.gray_stack != 0;
   p.shading = c.shading != 0;
   p.out_stride = c.n_envs;
   p.frame_step = (size_t)c.n_envs * jx::host::frame_bytes(c);
   p.staging = 1;
-  jx::host::choose_rows(p, 32, jx::kWarpsPerBlock, jx::kMinBlocksPerSm, prop.sharedMemPerMultiprocessor,
-                        prop.reservedSharedMemPerBlock);
+  {
+    auto rows_with = [&](bool bits) {
+      jx::Params q = p;
+      q.map_bits = bits;
+      jx::host::choose_rows(q, 32, jx::kWarpsPerBlock, jx::kMinBlocksPerSm, prop.sharedMemPerMultiprocessor,
+                            prop.reservedSharedMemPerBlock);
+      return q;
+    };
+    const bool bits_ok = c.map_side % 8 == 0;
+    const jx::Params with_bytes = rows_with(false);
+    const jx::Params with_bits = bits_ok ? rows_with(true) : with_bytes;
+    auto blocks = [&](const jx::Params& q) { return (c.frame_h + q.rows_per_block - 1) / q.rows_per_block; };
+    const bool bits = bits_ok && (c.map_side >= 128 || blocks(with_bits) < blocks(with_bytes));
+    p = bits ? with_bits : with_bytes;
+  }
   env->smem_block = jx::block_smem_bytes(p);
   const int smem_block = env->smem_block;
   if ((size_t)smem_block > prop.sharedMemPerBlockOptin) {

@@ -13,7 +13,7 @@ constexpr int kMaxSprites = 16;
 constexpr int kMaxSide = 128;
 constexpr int kMaxH = 256;
 constexpr int kMaxW = 256;
-constexpr int kWarpsPerBlock = 1;  // one-warp blocks spread envs evenly over the SMs
+constexpr int kWarpsPerBlock = 2;  // envs in flight per block of the env kernel (shares the per-block smem reserve)
 constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kMaxStaging = 2;  // frame row-block staging buffers per warp: 1 or 2
 constexpr int kMinBlocksPerSm = 28;  // register budget: 28 warps resident per SM

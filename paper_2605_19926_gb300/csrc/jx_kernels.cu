@@ -1237,7 +1237,8 @@ __device__ __forceinline__ void write_palette(const Params& p, const WarpSmem& w
 }
 
 template <int MODE, int MAPK, int GRAY>
-__global__ void __launch_bounds__(kThreads, kMinBlocksPerSm) env_kernel(const __grid_constant__ Params p) {
+__global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
+    env_kernel(const __grid_constant__ Params p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* const wbase = smem_raw + warp * p.warp_bytes;
