@@ -833,7 +833,8 @@ jx_status jx_sync_status(jx_env* env, void* stream) {
     return cuda_fail(err, "error word");
   if (word) {
     cudaMemset(env->base.err, 0, 4);
-    return fail(JX_EDEVICE, "device error word 0x%x (1: action outside 0..6)", word);
+    return fail(JX_EDEVICE, "device error word 0x%x (1: action outside 0..6; 2: a bulk map copy did not complete "
+                            "in time and the map was loaded with plain loads)", word);
   }
   return JX_OK;
 }

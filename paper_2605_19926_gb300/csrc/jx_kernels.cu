@@ -114,6 +114,61 @@ __device__ __forceinline__ void bulk_copy(void* gdst, const void* ssrc, uint32_t
                : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+
+// Every warp's shared memory starts with a 16-byte header: the mbarrier that
+// bulk global->shared map copies complete on (bytes 0..7), the phase parity
+// the next copy waits for (8..11), and 1 once a copy has timed out (12..15;
+// later copies then use plain loads).
+constexpr int kWarpHeader = 16;
+constexpr int kBulkWaitLimit = 1 << 16;  // try_wait rounds before a copy counts as lost
+
+__device__ __forceinline__ void init_warp_header(uint8_t* wbase, int lane) {
+  if (lane == 0) {
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(wbase);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+    reinterpret_cast<uint32_t*>(wbase)[2] = 0;
+    reinterpret_cast<uint32_t*>(wbase)[3] = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncwarp();
+}
+
+// n bytes (a multiple of 16, both addresses 16-byte aligned) from global
+// memory to shared memory with one bulk copy issued by lane 0 and completed
+// on the warp's mbarrier; every lane waits, at most kBulkWaitLimit rounds.
+// Returns false (after recording it in the header) when the copy did not
+// complete in time.
+__device__ __forceinline__ bool bulk_load(uint8_t* wbase, uint8_t* sdst, const uint8_t* gsrc, uint32_t n, int lane) {
+  volatile uint32_t* hdr = reinterpret_cast<volatile uint32_t*>(wbase);
+  const uint32_t phase = hdr[2];
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(wbase);
+  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(sdst);
+  __syncwarp();
+  if (lane == 0) {
+    // earlier generic-proxy accesses of the destination and the source come first
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
+                 "r"(n)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+                 "l"(gsrc), "r"(n), "r"(bar)
+                 : "memory");
+  }
+  uint32_t done = 0;
+  for (int it = 0; it < kBulkWaitLimit && !done; ++it)
+    asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(done)
+                 : "r"(bar), "r"(phase)
+                 : "memory");
+  const bool ok = __all_sync(0xffffffffu, done != 0);
+  if (lane == 0) {
+    hdr[2] = phase ^ 1u;
+    if (!ok) hdr[3] = 1u;
+  }
+  __syncwarp();
+  return ok;
+}
 // the staging buffer about to be filled has been read out: with two buffers
 // the other one may still be draining, with one every earlier copy is done
 __device__ __forceinline__ void bulk_wait_staging(int staging) {
@@ -131,6 +186,7 @@ __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; 
 
 // Shared memory of a warp, addressed from one base with the layout offsets
 // of Params (constants), so no pointer lives in a register:
+//   header    16 bytes: the map-copy mbarrier and its phase (see kWarpHeader)
 //   ring      staging * frame_block_bytes (also the maze work space)
 //   gray      staging * gray_block_bytes: the row blocks of the grayscale frame
 //   pal       [2][32] wall colours by face and cell value, then [8] sprite colours by type
@@ -163,7 +219,7 @@ __device__ __forceinline__ FillLane fill_lane(const Params& p, int lane) {
 struct WarpSmem {
   uint8_t* base;
   FillLane fl;
-  __device__ __forceinline__ uint8_t* ring() const { return base; }
+  __device__ __forceinline__ uint8_t* ring() const { return base + kWarpHeader; }
   __device__ __forceinline__ uint8_t* gray_ring(const Params& p) const { return base + p.off_gray; }
   __device__ __forceinline__ uint32_t* pal(const Params& p) const { return (uint32_t*)(base + p.off_pal); }
   __device__ __forceinline__ uint8_t* map(const Params& p) const { return base + p.off_map; }
@@ -241,9 +297,16 @@ __device__ __forceinline__ void heading(const Params& p, const Env& r, float& c,
   s = fmaf(r.s0, cs.x, r.c0 * cs.y);
 }
 
+// Byte maps of 4 KB or more (side >= 64) are copied by one bulk copy, smaller
+// ones by 16-byte loads of all lanes.
 __device__ __forceinline__ void stage_map(const Params& p, int e, uint8_t* smap, int lane) {
   const int n = p.S * p.S;
   const uint8_t* g = p.st.map + (size_t)e * n;
+  uint8_t* wbase = smap - p.off_map;
+  if (n >= 4096 && (n & 15) == 0 && reinterpret_cast<volatile uint32_t*>(wbase)[3] == 0) {
+    if (bulk_load(wbase, smap, g, (uint32_t)n, lane)) return;
+    if (lane == 0) atomicOr(p.err, 2u);  // the copy was lost: load the map below
+  }
   if ((n & 15) == 0) {
     const uint4* src = reinterpret_cast<const uint4*>(g);
     uint4* dst = reinterpret_cast<uint4*>(smap);
@@ -1242,6 +1305,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* const wbase = smem_raw + warp * p.warp_bytes;
+  init_warp_header(wbase, lane);
   write_palette(p, WarpSmem{wbase, fill_lane(p, lane)}, lane);
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
@@ -1263,6 +1327,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   uint8_t* const wbase = smem_raw + warp * bp.warp_bytes;
+  init_warp_header(wbase, lane);
   const int gw = blockIdx.x * wpb + warp;
   int slot = 0;
   bool fresh = true;  // nothing of an earlier group is pending in the ring
@@ -1350,7 +1415,7 @@ auto batch_kernel_of(int mode, int cols) {
 
 void layout_warp_smem(Params& p) {
   const int K = p.K > 0 ? p.K : 1;
-  int q = p.staging * p.frame_block_bytes;
+  int q = kWarpHeader + p.staging * p.frame_block_bytes;
   auto take = [&](int bytes) {
     const int at = q;
     q += align16(bytes);

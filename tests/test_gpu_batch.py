@@ -103,6 +103,7 @@ def test_batch_equals_groups_alone():
             assert (rewards[es] == ra).all() and (dones[es] == da).all(), (s, i)
     for env, a in zip(run.envs, alone):
         assert (env.get_state() == a.env.get_state()).all()
+        env.sync_status()  # no bulk map copy (side-64 byte maps) timed out
 
 
 def _rollout(run: BatchRun, acts: torch.Tensor):
@@ -134,6 +135,8 @@ def test_batch_rollout_matches_step_sequence(name):
     torch.cuda.synchronize()
     for a, b in zip(ref.envs, run.envs):
         assert (a.get_state() == b.get_state()).all()
+        a.sync_status()
+        b.sync_status()
     assert int(dones.sum().item()) > 0
 
 
