@@ -449,6 +449,9 @@ jx_status jx_server_destroy(jx_server* server);
  * them (episode 0; the first frames are in the session's frame buffer when
  * this returns). JX_EBUDGET: no room now (retry after a close). */
 jx_status jx_server_open(jx_server* server, const jx_config* cfg, int32_t* session);
+/* jx_server_open for the ASCII task: the session's envs play the map `ascii`
+ * (see jx_create_ascii). */
+jx_status jx_server_open_ascii(jx_server* server, const jx_config* cfg, const char* ascii, int32_t* session);
 /* Close a session: no further submits; its memory returns to the arena once
  * its queued requests have run. */
 jx_status jx_server_close(jx_server* server, int32_t session);

@@ -448,6 +448,41 @@ jx_status jx_create_ascii(const jx_config* cfg, const char* ascii, int device, j
   return create_impl(cfg, device, nullptr, 0, false, nullptr, out, &am);
 }
 
+}  // extern "C"
+
+namespace jx {
+namespace host {
+
+jx_status env_bytes(const jx_config* cfg, const char* ascii, int device, size_t* bytes) {
+  if (!bytes) return fail(JX_EINVAL, "bytes is NULL");
+  *bytes = 0;
+  if (!ascii) return create_impl(cfg, device, nullptr, 0, true, bytes, nullptr);
+  if (!cfg) return fail(JX_EINVAL, "config is NULL");
+  if (cfg->map_side < 3 || cfg->map_side > jx::kMaxSide)
+    return fail(JX_EINVAL, "map_side must be in [3, %d] (got %d)", jx::kMaxSide, cfg->map_side);
+  AsciiMap am;
+  if (jx_status st = parse_ascii(ascii, cfg->map_side, am)) return st;
+  return create_impl(cfg, device, nullptr, 0, true, bytes, nullptr, &am);
+}
+
+jx_status create_in(const jx_config* cfg, const char* ascii, int device, void* d_mem, size_t bytes, jx_env** out) {
+  if (!out) return fail(JX_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d_mem) return fail(JX_EINVAL, "d_mem is NULL");
+  if (!ascii) return create_impl(cfg, device, d_mem, bytes, false, nullptr, out);
+  if (!cfg) return fail(JX_EINVAL, "config is NULL");
+  if (cfg->map_side < 3 || cfg->map_side > jx::kMaxSide)
+    return fail(JX_EINVAL, "map_side must be in [3, %d] (got %d)", jx::kMaxSide, cfg->map_side);
+  AsciiMap am;
+  if (jx_status st = parse_ascii(ascii, cfg->map_side, am)) return st;
+  return create_impl(cfg, device, d_mem, bytes, false, nullptr, out, &am);
+}
+
+}  // namespace host
+}  // namespace jx
+
+extern "C" {
+
 jx_status jx_env_bytes(const jx_config* cfg, int device, size_t* bytes) {
   if (!bytes) return fail(JX_EINVAL, "bytes is NULL");
   *bytes = 0;

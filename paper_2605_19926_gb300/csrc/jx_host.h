@@ -84,5 +84,9 @@ inline size_t frame_bytes(const jx_config& c) { return (size_t)3 * c.frame_h * c
 // `reserved` bytes. Sets rows_per_block, frame_block_bytes and the layout.
 void choose_rows(Params& p, int max_rows, int warps, int blocks, size_t smem_per_sm, size_t reserved);
 
+// jx_env_bytes / jx_create_in, for the ASCII task too (ascii: the map text, or null).
+jx_status env_bytes(const jx_config* cfg, const char* ascii, int device, size_t* bytes);
+jx_status create_in(const jx_config* cfg, const char* ascii, int device, void* d_mem, size_t bytes, jx_env** out);
+
 }  // namespace host
 }  // namespace jx

@@ -421,12 +421,16 @@ jx_status jx_server_destroy(jx_server* sv) {
   return JX_OK;
 }
 
-jx_status jx_server_open(jx_server* sv, const jx_config* cfg, int32_t* session) {
+}  // extern "C"
+
+namespace {
+
+jx_status open_session(jx_server* sv, const jx_config* cfg, const char* ascii, int32_t* session) {
   if (jx_status st = check_server(sv)) return st;
   if (!session) return fail(JX_EINVAL, "session is NULL");
   *session = 0;
   size_t env_bytes = 0;
-  if (jx_status st = jx_env_bytes(cfg, sv->device, &env_bytes)) return st;
+  if (jx_status st = jx::host::env_bytes(cfg, ascii, sv->device, &env_bytes)) return st;
   if (cfg->map_side > sv->max_map_side)
     return fail(JX_EINVAL, "map_side %d above the server's max_map_side %d", cfg->map_side, sv->max_map_side);
   if (cfg->n_envs > sv->max_launch_envs)
@@ -458,7 +462,7 @@ jx_status jx_server_open(jx_server* sv, const jx_config* cfg, int32_t* session) 
     sv->peak_sessions = std::max(sv->peak_sessions, (int)sv->sessions.size());
   }
   DeviceGuard dg(sv->device);
-  jx_status st = jx_create_in(cfg, sv->device, s->block, env_bytes, &s->env);
+  jx_status st = jx::host::create_in(cfg, ascii, sv->device, s->block, env_bytes, &s->env);
   s->d_frames = s->block + off_frames;
   s->d_rewards = reinterpret_cast<float*>(s->block + off_rewards);
   s->d_dones = s->block + off_dones;
@@ -488,6 +492,19 @@ jx_status jx_server_open(jx_server* sv, const jx_config* cfg, int32_t* session) 
   s->ready = true;
   *session = s->id;
   return JX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+jx_status jx_server_open(jx_server* sv, const jx_config* cfg, int32_t* session) {
+  return open_session(sv, cfg, nullptr, session);
+}
+
+jx_status jx_server_open_ascii(jx_server* sv, const jx_config* cfg, const char* ascii, int32_t* session) {
+  if (!ascii) return fail(JX_EINVAL, "ascii is NULL");
+  return open_session(sv, cfg, ascii, session);
 }
 
 jx_status jx_server_close(jx_server* sv, int32_t session) {

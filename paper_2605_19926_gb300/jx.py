@@ -42,7 +42,8 @@ SYMBOLS = [
     "jx_batch_reset", "jx_batch_step", "jx_batch_rollout", "jx_batch_render", "jx_batch_autotune",
     "jx_batch_capture", "jx_graph_launch", "jx_graph_destroy",
     "jx_env_bytes", "jx_create_in", "jx_autotune", "jx_env_tiling", "jx_env_set_tiling",
-    "jx_server_create", "jx_server_destroy", "jx_server_open", "jx_server_close", "jx_server_session",
+    "jx_server_create", "jx_server_destroy", "jx_server_open", "jx_server_open_ascii", "jx_server_close",
+    "jx_server_session",
     "jx_server_submit", "jx_server_wait", "jx_server_pause", "jx_server_stats", "jx_server_latencies",
 ]
 
@@ -150,6 +151,7 @@ def _load() -> ctypes.CDLL:
         "jx_server_create": [ctypes.c_int, ctypes.c_uint64, i32, i32, i32, P, P],
         "jx_server_destroy": [P],
         "jx_server_open": [P, P, P],
+        "jx_server_open_ascii": [P, P, ctypes.c_char_p, P],
         "jx_server_close": [P, i32],
         "jx_server_session": [P, i32, P, P, P, P],
         "jx_server_submit": [P, i32, P, P],
@@ -542,7 +544,11 @@ class Server:
         """Admit a session; raises JxError (status EBUDGET) when it does not fit now."""
         c = Config.from_dict(cfg)
         sid = ctypes.c_int32()
-        _check(lib.jx_server_open(self._h, ctypes.byref(c), ctypes.byref(sid)))
+        if cfg.get("ascii_map") is not None:
+            _check(lib.jx_server_open_ascii(self._h, ctypes.byref(c), cfg["ascii_map"].encode("ascii"),
+                                            ctypes.byref(sid)))
+        else:
+            _check(lib.jx_server_open(self._h, ctypes.byref(c), ctypes.byref(sid)))
         return Session(self, sid.value, cfg)
 
     def try_open(self, cfg: dict) -> Session | None:

@@ -22,8 +22,9 @@ def _built():
 
 
 def mixed():
-    """Five groups: every map side and frame size of the uneven workload, both
-    tasks, sprites, episode ends by horizon and by goal."""
+    """Six groups: every map side and frame size of the uneven workload, the
+    room, maze and ASCII tasks, sprites, coloured keys and doors, distance
+    shading, episode ends by horizon and by goal."""
     return [
         inputs.rooms(n_envs=7, map_side=16, wall_prob=0.3, seed=21, max_sprites=8, frame_h=32, frame_w=32),
         dict(inputs.rooms(n_envs=3, map_side=128, wall_prob=0.3, seed=22, max_sprites=8, frame_h=128, frame_w=128),
@@ -31,6 +32,8 @@ def mixed():
         inputs.maze_keydoor(n_envs=9, map_side=32, seed=23, horizon=40),
         inputs.rooms(n_envs=5, map_side=64, wall_prob=0.3, seed=24, max_sprites=8, frame_h=96, frame_w=96),
         inputs.maze_keydoor(n_envs=33, map_side=8, seed=25, horizon=60),
+        inputs.ascii_env("coloured-rooms", n_envs=11, map_side=24, seed=26, horizon=70, shading=1, frame_h=48,
+                         frame_w=80),
     ]
 
 

@@ -28,6 +28,7 @@ def configs():
         inputs.maze_keydoor(n_envs=300, map_side=64, seed=52, horizon=40),
         dict(inputs.rooms(n_envs=1000, map_side=32, wall_prob=0.3, seed=53, max_sprites=8), horizon=25),
         inputs.maze_keydoor(n_envs=4096, map_side=32, seed=54, horizon=500),
+        inputs.ascii_env("key-door", n_envs=40, map_side=16, seed=55, horizon=60, shading=1),
     ]
 
 
