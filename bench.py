@@ -32,7 +32,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/s incl. render (frames/s) at 64x64 RGB"
 GRAPH_STEPS = 128  # default launches per CUDA graph = rollout buffer slots
-KERNEL_SOURCES = ["paper_2605_19926_gb300/csrc/jx_kernels.cu", "paper_2605_19926_gb300/csrc/jx_internal.h"]
+KERNEL_SOURCES = ["paper_2605_19926_gb300/csrc/jx_device.cuh", "paper_2605_19926_gb300/csrc/jx_kernels.cu",
+                  "paper_2605_19926_gb300/csrc/jx_internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 

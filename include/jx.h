@@ -359,7 +359,7 @@ jx_status jx_batch_rollout(jx_batch* batch, void* stream, const uint8_t* d_actio
 jx_status jx_batch_render(jx_batch* batch, void* stream, uint8_t* d_frames);
 
 /* Autotuner: times every tiling of the search space (warps_per_block 1, 2,
- * 4 x cols_per_lane 1, 2 x bits_min_side 0, 128, 64, 32 x max_rows_per_block
+ * 4 x cols_per_lane 1, 2 x bits_min_side 0, 128, 64, 32, 8 x max_rows_per_block
  * 8, 16, 32 x staging_buffers 1, 2; the first max_trials of them, the
  * default first) on this batch
  * and keeps the fastest. mode 0 times `steps` jx_batch_step launches, mode 1

@@ -35,7 +35,8 @@ def sources() -> list[str]:
 
 
 def _inputs() -> list[str]:
-    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "jx.h"), __file__]
+    return (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            [os.path.join(ROOT, "include", "jx.h"), __file__])
 
 
 def needs_build() -> bool:

@@ -87,7 +87,7 @@ jx_status apply_tiling(jx_batch* b, const jx_tiling& t) {
   int max_grid = 0;
   for (int mode : kModes) {
     int bps = 0;
-    cudaError_t err = jx::batch_blocks_per_sm(mode, t.cols_per_lane, t.warps_per_block, smem, &bps);
+    cudaError_t err = jx::batch_blocks_per_sm(mode, t.cols_per_lane, jx::batch_spec(bp), t.warps_per_block, smem, &bps);
     if (err != cudaSuccess) return cuda_fail(err, "occupancy query");
     if (bps < 1) return fail(JX_EINVAL, "batched kernel cannot be resident with %d bytes of shared memory", smem);
     const int64_t need = (b->n_total + t.warps_per_block - 1) / t.warps_per_block;
@@ -159,7 +159,7 @@ std::vector<jx_tiling> search_space() {
   std::vector<jx_tiling> out{def};
   for (int w : {1, 2, 4})
     for (int c : {1, 2})
-      for (int bits : {0, 128, 64, 32})
+      for (int bits : {0, 128, 64, 32, 8})
         for (int rows : {8, 16, 32})
           for (int staging : {1, 2}) {
             jx_tiling t{w, c, bits, rows, staging};

@@ -123,8 +123,11 @@ cudaError_t kernel_blocks_per_sm(const Params& p, int mode, int* blocks);
 // Launch the fused kernel for `mode`.
 cudaError_t launch(const Params& p, int mode, int grid, cudaStream_t stream);
 
-// The batched kernel: blocks of `warps` warps, `cols` rays marched together per lane.
-cudaError_t batch_blocks_per_sm(int mode, int cols, int warps, int smem_bytes, int* blocks);
+// The batched kernel: blocks of `warps` warps, `cols` rays marched together per lane;
+// spec 1 (every group with bit-plane maps and no grayscale stack) selects a
+// specialised instance, 0 the general one (batch_spec gives it for a launch).
+int batch_spec(const BatchParams& bp);
+cudaError_t batch_blocks_per_sm(int mode, int cols, int spec, int warps, int smem_bytes, int* blocks);
 cudaError_t batch_launch(const BatchParams& bp, int mode, int cols, int warps, int grid, cudaStream_t stream);
 
 }  // namespace jx

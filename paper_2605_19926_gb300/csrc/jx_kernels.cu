@@ -1,1303 +1,9 @@
-// jx_kernels.cu — the fused environment kernel (sm_103a).
-//
-// One warp owns one environment at a time and walks the whole hot path for
-// it: load the struct-of-arrays state, stage the map in shared memory, step
-// (movement, collision, key / door / goal, reward, episode end), regenerate
-// the map of an ended episode, cast one DDA ray per screen column, project
-// the billboard sprites, and write the frame in row blocks that TMA bulk
-// copies stream from shared memory to HBM. Warps are independent: no block
-// barrier is ever taken, only warp-level synchronisation.
-//
-// Paper passages: DDA ray casting over the tile map (Sec. 2.1); the wall
-// slice from the hit distance, shaded per face (Sec. 2, Sec. 2.1); objects
-// as fixed sprites drawn against a depth buffer (Fig. 1); the key-door rules
-// (Table 1, Table 2); native low-resolution rendering (Sec. 3.1).
-#include <cstdint>
-
-#include "jx_internal.h"
+// jx_kernels.cu — the env kernel (one env config per launch) and its host
+// side: launch shape queries, launches, the per-warp shared memory layout.
+#include "jx_device.cuh"
 
 namespace jx {
 namespace {
-
-constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
-constexpr double kHeadingScale = (2.0 * 3.14159265358979323846) / 16777216.0;  // 2 pi / 2^24
-constexpr int kHMax = 1 << 20;
-constexpr int kLocked = 16;    // + colour (0 red, 1 blue, 2 yellow): locked doors
-constexpr int kUnlocked = 20;  // + colour: unlocked doors
-constexpr int kDoor = kLocked;  // the red locked door of the generated mazes
-constexpr int kTaskAscii = 3;
-constexpr int kSprKey = 1;
-constexpr int kSprGoal = 2;
-constexpr int kSprKeyBlue = 4;
-constexpr int kSprKeyYellow = 5;
-// colour of a key sprite type, -1 for other types
-__host__ __device__ constexpr int key_colour(int type) {
-  return type == kSprKey ? 0 : (type == kSprKeyBlue ? 1 : (type == kSprKeyYellow ? 2 : -1));
-}
-__device__ __forceinline__ bool is_locked(int v) { return (unsigned)(v - kLocked) < 3u; }
-__device__ __forceinline__ bool is_unlocked(int v) { return (unsigned)(v - kUnlocked) < 3u; }
-
-// ------------------------------------------------------------- palette ----
-// Colours packed as 0xYYBBGGRR: the low three bytes are R, G, B and the top
-// byte is the colour's integer BT.601 luma (77 R + 150 G + 29 B + 128) >> 8,
-// the pixel's value in the grayscale frame stack.
-__host__ __device__ constexpr uint32_t luma(uint32_t r, uint32_t g, uint32_t b) { return (77 * r + 150 * g + 29 * b + 128) >> 8; }
-constexpr uint32_t rgb(uint32_t r, uint32_t g, uint32_t b) { return r | (g << 8) | (b << 16) | (luma(r, g, b) << 24); }
-constexpr uint32_t shade34(uint32_t c) {  // y faces: each channel scaled by 3/4 (floor), luma of the result
-  return rgb((((c >> 0) & 255) * 3) >> 2, (((c >> 8) & 255) * 3) >> 2, (((c >> 16) & 255) * 3) >> 2);
-}
-constexpr uint32_t kWall1 = rgb(160, 160, 160);
-constexpr uint32_t kCeil = rgb(48, 48, 56);
-constexpr uint32_t kFloor = rgb(104, 96, 88);
-
-// Colour of a cell value: walls 1..9, locked and unlocked doors by colour,
-// anything else as wall 1.
-constexpr uint32_t cell_rgb(int v) {
-  return v == 2 ? rgb(64, 160, 64)
-       : v == 3 ? rgb(64, 96, 192)
-       : v == 4 ? rgb(176, 144, 80)
-       : v == 5 ? rgb(200, 100, 40)
-       : v == 6 ? rgb(112, 64, 160)
-       : v == 7 ? rgb(40, 160, 160)
-       : v == 8 ? rgb(128, 128, 48)
-       : v == 9 ? rgb(216, 216, 216)
-       : v == kLocked + 0 ? rgb(200, 32, 32)
-       : v == kLocked + 1 ? rgb(32, 64, 200)
-       : v == kLocked + 2 ? rgb(208, 184, 32)
-       : v == kUnlocked + 0 ? rgb(232, 120, 120)
-       : v == kUnlocked + 1 ? rgb(120, 150, 232)
-       : v == kUnlocked + 2 ? rgb(236, 222, 128)
-       : kWall1;
-}
-constexpr int kCellColours = 32;  // palette entries per face; values above draw as wall 1
-
-// [face][cell value]: x faces, then y faces (3/4)
-#define JX_CELLS(f) f(0), f(1), f(2), f(3), f(4), f(5), f(6), f(7), f(8), f(9), f(10), f(11), f(12), f(13), f(14), \
-    f(15), f(16), f(17), f(18), f(19), f(20), f(21), f(22), f(23), f(24), f(25), f(26), f(27), f(28), f(29), f(30), f(31)
-#define JX_X_FACE(v) cell_rgb(v)
-#define JX_Y_FACE(v) shade34(cell_rgb(v))
-__constant__ uint32_t c_wall[2 * kCellColours] = {JX_CELLS(JX_X_FACE), JX_CELLS(JX_Y_FACE)};
-#undef JX_X_FACE
-#undef JX_Y_FACE
-#undef JX_CELLS
-// by sprite type: 1 red key, 2 goal, 3 distractor, 4 blue key, 5 yellow key (others as distractor)
-__constant__ uint32_t c_sprite[8] = {rgb(144, 64, 192), rgb(224, 40, 40), rgb(240, 208, 32), rgb(144, 64, 192),
-                                     rgb(40, 80, 224),  rgb(232, 200, 40), rgb(144, 64, 192), rgb(144, 64, 192)};
-
-// ------------------------------------------------------------ SplitMix64 --
-// Steele, Lea & Flood (OOPSLA 2014): output n of the generator seeded with s
-// is the 64-bit finaliser applied to s + n * gamma.
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ uint64_t splitmix(uint64_t seed, uint64_t n) { return mix64(seed + n * kGamma); }
-// Key of the stream (seed, env, episode, purpose): chained generator outputs.
-__device__ __forceinline__ uint64_t stream_key(uint64_t seed, uint32_t env, uint32_t ep, uint32_t purpose) {
-  return splitmix(splitmix(splitmix(seed, (uint64_t)env + 1), (uint64_t)ep + 1), (uint64_t)purpose + 1);
-}
-__device__ __forceinline__ uint64_t draw_at(uint64_t key, uint32_t index) { return splitmix(key, (uint64_t)index + 1); }
-// uniform integer below n from the high 32 bits (multiply-shift)
-__device__ __forceinline__ uint32_t below32(uint32_t hi, uint32_t n) {
-  return (uint32_t)(((uint64_t)hi * (uint64_t)n) >> 32);
-}
-__device__ __forceinline__ uint32_t below(uint64_t d, uint32_t n) { return below32((uint32_t)(d >> 32), n); }
-
-// ------------------------------------------------------------- bulk copy --
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-__device__ __forceinline__ void bulk_copy(void* gdst, const void* ssrc, uint32_t bytes) {
-  uint32_t s = (uint32_t)__cvta_generic_to_shared(ssrc);
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(gdst), "r"(s), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-
-// Every warp's shared memory starts with a 16-byte header: the mbarrier that
-// bulk global->shared map copies complete on (bytes 0..7), the phase parity
-// the next copy waits for (8..11), and 1 once a copy has timed out (12..15;
-// later copies then use plain loads).
-constexpr int kWarpHeader = 16;
-constexpr int kBulkWaitLimit = 1 << 16;  // try_wait rounds before a copy counts as lost
-
-__device__ __forceinline__ void init_warp_header(uint8_t* wbase, int lane) {
-  if (lane == 0) {
-    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(wbase);
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
-    reinterpret_cast<uint32_t*>(wbase)[2] = 0;
-    reinterpret_cast<uint32_t*>(wbase)[3] = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  __syncwarp();
-}
-
-// n bytes (a multiple of 16, both addresses 16-byte aligned) from global
-// memory to shared memory with one bulk copy issued by lane 0 and completed
-// on the warp's mbarrier; every lane waits, at most kBulkWaitLimit rounds.
-// Returns false (after recording it in the header) when the copy did not
-// complete in time.
-__device__ __forceinline__ bool bulk_load(uint8_t* wbase, uint8_t* sdst, const uint8_t* gsrc, uint32_t n, int lane) {
-  volatile uint32_t* hdr = reinterpret_cast<volatile uint32_t*>(wbase);
-  const uint32_t phase = hdr[2];
-  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(wbase);
-  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(sdst);
-  __syncwarp();
-  if (lane == 0) {
-    // earlier generic-proxy accesses of the destination and the source come first
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    asm volatile("fence.proxy.async.global;\n" ::: "memory");
-    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(bar),
-                 "r"(n)
-                 : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-                 "l"(gsrc), "r"(n), "r"(bar)
-                 : "memory");
-  }
-  uint32_t done = 0;
-  for (int it = 0; it < kBulkWaitLimit && !done; ++it)
-    asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"
-                 : "=r"(done)
-                 : "r"(bar), "r"(phase)
-                 : "memory");
-  const bool ok = __all_sync(0xffffffffu, done != 0);
-  if (lane == 0) {
-    hdr[2] = phase ^ 1u;
-    if (!ok) hdr[3] = 1u;
-  }
-  __syncwarp();
-  return ok;
-}
-// the staging buffer about to be filled has been read out: with two buffers
-// the other one may still be draining, with one every earlier copy is done
-__device__ __forceinline__ void bulk_wait_staging(int staging) {
-  if (staging == 1)
-    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-  else
-    asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read_all() {
-  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
-}
-
-// ------------------------------------------------------------- warp smem --
-__host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; }
-
-// Shared memory of a warp, addressed from one base with the layout offsets
-// of Params (constants), so no pointer lives in a register:
-//   header    16 bytes: the map-copy mbarrier and its phase (see kWarpHeader)
-//   ring      staging * frame_block_bytes (also the maze work space)
-//   gray      staging * gray_block_bytes: the row blocks of the grayscale frame
-//   pal       [2][32] wall colours by face and cell value, then [8] sprite colours by type
-//   map       S * S cell values, row-major
-//   col_rgb   [W] wall colour, chunk-interleaved (see col_slot)
-//   col_top   [W] first wall row, chunk-interleaved
-//   col_bot   [W] first floor row, chunk-interleaved
-//   zbuf      [W] perpendicular distance by column
-//   spr_in    [K] float4 sprite x, y, type (as float)
-//   spr_a     [K] float4 x0, top, 1 / width, 1 / height (pixels)
-//   spr_rect  [K] int4 pixel rectangle to test: first/last column, first/last row
-//   spr_ty    [K] depth;  spr_rgb [K] colour;  spr_kind [K] type
-//   order     [K] visible sprites, far to near
-//   spr_span  [K] first row << 16 | last row the oi-th sprite of that order can cover
-//   obj       [8] int32 key x, key y, goal x, goal y, door x, door y, sprites in use
-// The lane's place in the frame fill: lanes [0, groups * rows) are laid out
-// as `rows` rows of `groups` 8-pixel groups.
-struct FillLane {
-  int groups, rows, my_row, g;
-};
-__device__ __forceinline__ FillLane fill_lane(const Params& p, int lane) {
-  FillLane f;
-  f.groups = p.W >> 3;
-  f.rows = 32 / f.groups;
-  f.my_row = lane / f.groups;
-  f.g = lane - f.my_row * f.groups;
-  return f;
-}
-
-struct WarpSmem {
-  uint8_t* base;
-  FillLane fl;
-  __device__ __forceinline__ uint8_t* ring() const { return base + kWarpHeader; }
-  __device__ __forceinline__ uint8_t* gray_ring(const Params& p) const { return base + p.off_gray; }
-  __device__ __forceinline__ uint32_t* pal(const Params& p) const { return (uint32_t*)(base + p.off_pal); }
-  __device__ __forceinline__ uint8_t* map(const Params& p) const { return base + p.off_map; }
-  __device__ __forceinline__ uint32_t* col_rgb(const Params& p) const { return (uint32_t*)(base + p.off_col_rgb); }
-  __device__ __forceinline__ int32_t* col_top(const Params& p) const { return (int32_t*)(base + p.off_col_top); }
-  __device__ __forceinline__ int32_t* col_bot(const Params& p) const { return (int32_t*)(base + p.off_col_bot); }
-  __device__ __forceinline__ float* zbuf(const Params& p) const { return (float*)(base + p.off_zbuf); }
-  __device__ __forceinline__ float4* spr_in(const Params& p) const { return (float4*)(base + p.off_spr_in); }
-  __device__ __forceinline__ float4* spr_a(const Params& p) const { return (float4*)(base + p.off_spr_a); }
-  __device__ __forceinline__ int4* spr_rect(const Params& p) const { return (int4*)(base + p.off_spr_rect); }
-  __device__ __forceinline__ float* spr_ty(const Params& p) const { return (float*)(base + p.off_spr_ty); }
-  __device__ __forceinline__ uint32_t* spr_rgb(const Params& p) const { return (uint32_t*)(base + p.off_spr_rgb); }
-  __device__ __forceinline__ int32_t* spr_kind(const Params& p) const { return (int32_t*)(base + p.off_spr_kind); }
-  __device__ __forceinline__ int32_t* order(const Params& p) const { return (int32_t*)(base + p.off_order); }
-  __device__ __forceinline__ uint32_t* spr_span(const Params& p) const { return (uint32_t*)(base + p.off_spr_span); }
-  __device__ __forceinline__ int32_t* obj(const Params& p) const { return (int32_t*)(base + p.off_obj); }
-};
-
-constexpr int kPaletteWords = 2 * kCellColours + 8;
-
-// Column data is stored so that the lanes filling one row (8 columns each)
-// read consecutive 16-byte groups: half g (columns 4g..4g+3 of the group) of
-// column group c sits at word (g * groups + c) * 4.
-__device__ __forceinline__ int col_slot(int col, int groups) {
-  const int c = col >> 3, j = col & 7;
-  return (((j >> 2) * groups + c) << 2) | (j & 3);
-}
-
-// ------------------------------------------------------------ env state ----
-// The scalar state of the env a warp is working on (identical in all lanes).
-// Key, goal and door cells and the sprite table live in the warp's shared
-// memory instead (see load_objects).
-struct Env {
-  int cx, cy;    // cell of the position
-  float fx, fy;  // position inside the cell, [0, 1)
-  float c0, s0;  // cos, sin of theta0
-  int turn, t;
-  int keys;  // keys held: bit c for colour c
-};
-
-__device__ __forceinline__ Env load_env(const Params& p, int e) {
-  Env r;
-  const State& st = p.st;
-  r.cx = st.cell_x[e];
-  r.cy = st.cell_y[e];
-  r.fx = st.frac_x[e];
-  r.fy = st.frac_y[e];
-  r.c0 = st.cos0[e];
-  r.s0 = st.sin0[e];
-  r.turn = st.turn[e];  // in [0, turns_per_rev): generated so, checked by set_state
-  r.t = st.t[e];
-  r.keys = st.flags[e] & 7;
-  return r;
-}
-
-// Key / goal / door cells (lanes 0..5) and sprite slots (lane j: slot j) into
-// the warp's shared memory.
-__device__ __forceinline__ void load_objects(const Params& p, const WarpSmem& ws, int e, int lane) {
-  if (lane < 6) ws.obj(p)[lane] = p.st.obj[6 * (size_t)e + lane];
-  if (lane == 6) {
-    const int ns = p.st.nspr[e];
-    ws.obj(p)[6] = ns > p.K ? p.K : ns;  // sprites in use
-  }
-  if (lane < p.K) {
-    const size_t i = (size_t)e * p.K + lane;
-    ws.spr_in(p)[lane] = make_float4(p.st.spr_x[i], p.st.spr_y[i], (float)p.st.spr_type[i], 0.f);
-  }
-}
-
-// heading = theta0 + turn * 2 pi / turns_per_rev: (cos, sin)(theta0), kept in
-// the state, rotated by the table entry of `turn`
-__device__ __forceinline__ void heading(const Params& p, const Env& r, float& c, float& s) {
-  const float2 cs = p.turn_cs[r.turn];
-  c = fmaf(r.c0, cs.x, -r.s0 * cs.y);
-  s = fmaf(r.s0, cs.x, r.c0 * cs.y);
-}
-
-// Byte maps of 4 KB or more (side >= 64) are copied by one bulk copy, smaller
-// ones by 16-byte loads of all lanes.
-__device__ __forceinline__ void stage_map(const Params& p, int e, uint8_t* smap, int lane) {
-  const int n = p.S * p.S;
-  const uint8_t* g = p.st.map + (size_t)e * n;
-  uint8_t* wbase = smap - p.off_map;
-  if (n >= 4096 && (n & 15) == 0 && reinterpret_cast<volatile uint32_t*>(wbase)[3] == 0) {
-    if (bulk_load(wbase, smap, g, (uint32_t)n, lane)) return;
-    if (lane == 0) atomicOr(p.err, 2u);  // the copy was lost: load the map below
-  }
-  if ((n & 15) == 0) {
-    const uint4* src = reinterpret_cast<const uint4*>(g);
-    uint4* dst = reinterpret_cast<uint4*>(smap);
-    for (int i = lane; i < (n >> 4); i += 32) dst[i] = src[i];
-  } else {
-    for (int i = lane; i < n; i += 32) smap[i] = g[i];
-  }
-  __syncwarp();
-}
-
-__device__ __forceinline__ void store_map(const Params& p, int e, const uint8_t* smap, int lane) {
-  const int n = p.S * p.S;
-  uint8_t* g = p.st.map + (size_t)e * n;
-  if (smap == g) return;  // generated in place
-  if ((n & 15) == 0) {
-    const uint4* src = reinterpret_cast<const uint4*>(smap);
-    uint4* dst = reinterpret_cast<uint4*>(g);
-    for (int i = lane; i < (n >> 4); i += 32) dst[i] = src[i];
-  } else {
-    for (int i = lane; i < n; i += 32) g[i] = smap[i];
-  }
-}
-
-// bit k of the result is set iff byte k of x is nonzero
-__device__ __forceinline__ uint32_t nonzero4(uint32_t x) {
-  const uint32_t m = __vcmpne4(x, 0u) & 0x01010101u;
-  return (m * 0x10204080u) >> 28;  // gathers bits 0, 8, 16, 24 into bits 28..31
-}
-
-// The map as a bit plane: bit i of word i / 32 is set iff cell i is nonzero
-// (S * S is a multiple of 32; rows run on across word boundaries).
-__device__ __forceinline__ void stage_map_bits(const Params& p, int e, uint8_t* smap, int lane) {
-  const int words = (p.S * p.S) >> 5;
-  const uint4* g = reinterpret_cast<const uint4*>(p.st.map + (size_t)e * p.S * p.S);
-  uint32_t* w = reinterpret_cast<uint32_t*>(smap);
-  for (int i = lane; i < words; i += 32) {
-    const uint4 a = g[2 * i], b = g[2 * i + 1];
-    w[i] = nonzero4(a.x) | nonzero4(a.y) << 4 | nonzero4(a.z) << 8 | nonzero4(a.w) << 12 | nonzero4(b.x) << 16 |
-           nonzero4(b.y) << 20 | nonzero4(b.z) << 24 | nonzero4(b.w) << 28;
-  }
-  __syncwarp();
-}
-
-template <int MAPK>
-__device__ __forceinline__ bool map_bits(const Params& p) {
-  return MAPK == MAP_BITS || (MAPK == MAP_RUNTIME && p.map_bits != 0);
-}
-
-// cell i of the staged map blocks movement and rays (in bit mode the door's
-// bit is cleared while the key is held, see open_door)
-template <int MAPK>
-__device__ __forceinline__ bool cell_set(const Params& p, const uint8_t* smap, int i) {
-  if (map_bits<MAPK>(p)) return (reinterpret_cast<const uint32_t*>(smap)[i >> 5] >> (i & 31)) & 1u;
-  return smap[i] != 0;
-}
-
-template <int MAPK>
-__device__ __forceinline__ void stage(const Params& p, int e, uint8_t* smap, int lane) {
-  if (map_bits<MAPK>(p))
-    stage_map_bits(p, e, smap, lane);
-  else
-    stage_map(p, e, smap, lane);
-}
-
-// ------------------------------------------------------------ generators --
-// Index of the r-th cell (row-major) of smap[0..n) satisfying pred, or -1.
-template <class Pred>
-__device__ __forceinline__ int nth_cell(int n, uint32_t r, int lane, Pred pred) {
-  for (int base = 0; base < n; base += 32) {
-    int i = base + lane;
-    bool f = i < n && pred(i);
-    uint32_t b = __ballot_sync(0xffffffffu, f);
-    uint32_t c = __popc(b);
-    if (r < c) {
-      for (uint32_t k = 0; k < r; ++k) b &= b - 1;
-      return base + __ffs(b) - 1;
-    }
-    r -= c;
-  }
-  return -1;
-}
-
-template <class Pred>
-__device__ __forceinline__ int count_cells(int n, int lane, Pred pred) {
-  int total = 0;
-  for (int base = 0; base < n; base += 32) {
-    int i = base + lane;
-    total += __popc(__ballot_sync(0xffffffffu, i < n && pred(i)));
-  }
-  return total;
-}
-
-// Writes the scalar fields of a fresh episode (lane 0) and all K sprite slots.
-__device__ void write_episode_state(const Params& p, int e, uint32_t ep, int cell, const int obj[6], int nspr,
-                                    const int* spr_cell, const int* spr_type, int lane) {
-  const State& st = p.st;
-  const int S = p.S;
-  const uint64_t kh = stream_key(p.seed, (uint32_t)e, ep, P_HEADING);
-  if (lane == 0) {
-    st.cell_x[e] = (int16_t)(cell % S);
-    st.cell_y[e] = (int16_t)(cell / S);
-    st.frac_x[e] = 0.5f;
-    st.frac_y[e] = 0.5f;
-    const float th0 = (float)((double)(draw_at(kh, 0) >> 40) * kHeadingScale);
-    double sd, cd;
-    sincos((double)th0, &sd, &cd);
-    st.theta0[e] = th0;
-    st.cos0[e] = (float)cd;
-    st.sin0[e] = (float)sd;
-    st.turn[e] = 0;
-    st.t[e] = 0;
-    st.episode[e] = ep;
-    st.flags[e] = 0;
-    int16_t* o = st.obj + 6 * (size_t)e;
-    for (int k = 0; k < 6; ++k) o[k] = (int16_t)obj[k];
-    st.nspr[e] = (uint8_t)nspr;
-  }
-  for (int k = lane; k < p.K; k += 32) {
-    size_t i = (size_t)e * p.K + k;
-    if (k < nspr) {
-      st.spr_x[i] = (float)(spr_cell[k] % S) + 0.5f;
-      st.spr_y[i] = (float)(spr_cell[k] / S) + 0.5f;
-      st.spr_type[i] = (uint8_t)spr_type[k];
-    } else {
-      st.spr_x[i] = 0.f;
-      st.spr_y[i] = 0.f;
-      st.spr_type[i] = 0;
-    }
-  }
-}
-
-// Rooms: border walls; interior wall iff a 53-bit uniform draw < wall_prob;
-// wall type 1 + (draw mod 4); spawn and decorative sprites on uniformly
-// chosen free cells (row-major enumeration).
-__device__ __forceinline__ void gen_rooms(const Params& p, int e, uint32_t ep, uint8_t* smap, int lane) {
-  const int S = p.S, n = S * S;
-  const uint64_t kw = stream_key(p.seed, (uint32_t)e, ep, P_WALL);
-  for (int i = lane; i < n; i += 32) {
-    uint64_t u = draw_at(kw, (uint32_t)i);
-    int x = i % S, y = i / S;
-    bool border = x == 0 || y == 0 || x == S - 1 || y == S - 1;
-    bool wall = border || (u >> 11) < p.wall_thr;
-    smap[i] = wall ? (uint8_t)(1 + (u & 3)) : (uint8_t)0;
-  }
-  __syncwarp();
-  auto is_free = [&](int i) { return smap[i] == 0; };
-  int n_free = count_cells(n, lane, is_free);
-  if (n_free == 0) {
-    if (lane == 0) smap[(S / 2) * S + S / 2] = 0;
-    __syncwarp();
-    n_free = 1;
-  }
-  uint32_t pick = below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_SPAWN), 0), (uint32_t)n_free);
-  int spawn = nth_cell(n, pick, lane, is_free);
-  int nspr = 0;
-  int spr_cell[kMaxSprites], spr_type[kMaxSprites];
-  if (p.K > 0) {
-    nspr = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_NSPRITES), 0), (uint32_t)p.K + 1);
-    const uint64_t kc = stream_key(p.seed, (uint32_t)e, ep, P_SPRITE_CELL);
-    for (int k = 0; k < nspr; ++k) {
-      uint32_t c = below(draw_at(kc, (uint32_t)k), (uint32_t)n_free);
-      spr_cell[k] = nth_cell(n, c, lane, is_free);
-      spr_type[k] = 3;
-    }
-  }
-  const int obj[6] = {-1, -1, -1, -1, -1, -1};
-  write_episode_state(p, e, ep, spawn, obj, nspr, spr_cell, spr_type, lane);
-  __syncwarp();
-  store_map(p, e, smap, lane);
-  __syncwarp();
-}
-
-// Work space of one maze generation (n = nodes): the per-carve draws, the
-// DFS stack of node cells, and each node's DFS discovery / finish counters.
-struct MazeScratch {
-  uint32_t* rnd;     // [n] high 32 bits of the per-carve draws
-  uint16_t* stack;   // [n] node cells packed as y << 8 | x
-  uint16_t* disc;    // [n] push counter when the node was discovered
-  uint16_t* fin;     // [n] push counter when the node was finished
-  int32_t* result;   // [4] goal node, its depth, the door's two path nodes (packed cells)
-};
-__host__ __device__ __forceinline__ size_t maze_scratch_bytes(int n) {
-  return (size_t)align16(4 * n) + 3 * (size_t)align16(2 * n) + 16;
-}
-__device__ __forceinline__ MazeScratch maze_scratch(uint8_t* q, int n) {
-  MazeScratch m;
-  m.rnd = (uint32_t*)q;
-  q += align16(4 * n);
-  m.stack = (uint16_t*)q;
-  q += align16(2 * n);
-  m.disc = (uint16_t*)q;
-  q += align16(2 * n);
-  m.fin = (uint16_t*)q;
-  q += align16(2 * n);
-  m.result = (int32_t*)q;
-  return m;
-}
-
-// Key-door maze: depth-first backtracker over the nodes at odd coordinates,
-// N/E/S/W neighbour order, one draw per carved passage. A node is unvisited
-// while its cell is still a wall. Because the maze is the DFS tree, a node's
-// BFS distance from the spawn is its stack depth when pushed, and the stack at
-// that moment is its path from the spawn: the goal (deepest node, ties to
-// the smallest row-major index) and the two path nodes around the door are
-// recorded during the walk. The nodes reachable without crossing the door are
-// those outside the door's subtree (a discovery / finish interval test).
-__device__ __forceinline__ void gen_maze(const Params& p, int e, uint32_t ep, uint8_t* smap, uint8_t* scratch, int lane) {
-  const int S = p.S, n_cells = S * S;
-  const int nn = (S - 2) / 2, n = nn * nn;
-  MazeScratch m = maze_scratch(scratch, n);
-  const uint64_t kw = stream_key(p.seed, (uint32_t)e, ep, P_WALL);
-  for (int i = lane; i < n_cells; i += 32) smap[i] = (uint8_t)(1 + (draw_at(kw, (uint32_t)i) & 3));
-  const uint64_t kd = stream_key(p.seed, (uint32_t)e, ep, P_DFS);
-  for (int j = lane; j < n - 1; j += 32) m.rnd[j] = (uint32_t)(draw_at(kd, (uint32_t)j) >> 32);
-  const int start = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_SPAWN), 0), (uint32_t)n);
-  __syncwarp();
-  if (lane == 0) {
-    int vx = 2 * (start % nn) + 1, vy = 2 * (start / nn) + 1, v = start;
-    smap[vy * S + vx] = 0;
-    int sp = 0, pushes = 0, carved = 0;
-    m.stack[sp++] = (uint16_t)(vy << 8 | vx);
-    m.disc[v] = (uint16_t)pushes++;
-    int best_v = start, best_d = 0, door_a = vy << 8 | vx, door_b = door_a;
-    for (;;) {
-      const int c = vy * S + vx;
-      const uint32_t open = (uint32_t)(vy > 1 && smap[c - 2 * S] != 0) | ((uint32_t)(vx < S - 3 && smap[c + 2] != 0) << 1) |
-                            ((uint32_t)(vy < S - 3 && smap[c + 2 * S] != 0) << 2) |
-                            ((uint32_t)(vx > 1 && smap[c - 2] != 0) << 3);
-      if (open == 0) {
-        m.fin[v] = (uint16_t)pushes;
-        if (--sp == 0) break;
-        const int top = m.stack[sp - 1];
-        vx = top & 0xff;
-        vy = top >> 8;
-        v = (vy >> 1) * nn + (vx >> 1);
-        continue;
-      }
-      // the r-th unvisited neighbour in N, E, S, W order
-      uint32_t bits = open;
-      for (uint32_t r = below32(m.rnd[carved++], (uint32_t)__popc(open)); r > 0; --r) bits &= bits - 1;
-      const int d = __ffs(bits) - 1;
-      const int dx = d == 1 ? 1 : (d == 3 ? -1 : 0), dy = d == 0 ? -1 : (d == 2 ? 1 : 0);
-      smap[c + dy * S + dx] = 0;
-      vx += 2 * dx;
-      vy += 2 * dy;
-      smap[vy * S + vx] = 0;
-      v = (vy >> 1) * nn + (vx >> 1);
-      const int depth = sp;
-      m.stack[sp++] = (uint16_t)(vy << 8 | vx);
-      m.disc[v] = (uint16_t)pushes++;
-      if (depth > best_d || (depth == best_d && v < best_v)) {
-        best_v = v;
-        best_d = depth;
-        const int j = (depth + 1) / 2;  // the door sits on edge ceil(depth / 2) of the path
-        door_a = m.stack[j - 1];
-        door_b = m.stack[j];
-      }
-    }
-    m.result[0] = best_v;
-    m.result[1] = best_d;
-    m.result[2] = door_a;
-    m.result[3] = door_b;
-  }
-  __syncwarp();
-  const int goal = m.result[0];
-  const int door_a = m.result[2], door_b = m.result[3];
-  const int dxc = ((door_a & 0xff) + (door_b & 0xff)) >> 1, dyc = ((door_a >> 8) + (door_b >> 8)) >> 1;
-  if (lane == 0) smap[dyc * S + dxc] = (uint8_t)kDoor;
-  // key: uniform over spawn-side nodes except the spawn
-  const int pj = ((door_b >> 8) >> 1) * nn + ((door_b & 0xff) >> 1);
-  const int d0 = m.disc[pj], d1 = m.fin[pj];
-  auto side = [&](int v) {
-    int dv = m.disc[v];
-    return v != start && !(dv >= d0 && dv < d1);
-  };
-  const int n_side = n - (d1 - d0) - 1;
-  int key = start;
-  if (n_side > 0) {
-    uint32_t r = below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_KEY), 0), (uint32_t)n_side);
-    key = nth_cell(n, r, lane, side);
-  }
-  auto cell_of = [&](int v) { return (2 * (v / nn) + 1) * S + 2 * (v % nn) + 1; };
-  const int kc = cell_of(key), gc = cell_of(goal);
-  const int obj[6] = {kc % S, kc / S, gc % S, gc / S, dxc, dyc};
-  int spr_cell[kMaxSprites], spr_type[kMaxSprites];
-  spr_cell[0] = kc;
-  spr_type[0] = kSprKey;
-  spr_cell[1] = gc;
-  spr_type[1] = kSprGoal;
-  int nspr = 2;
-  if (p.task == 2) {
-    // open 8 x 8 rooms (the door kept), then distractors on floor cells
-    __syncwarp();
-    const uint64_t kr = stream_key(p.seed, (uint32_t)e, ep, P_ROOM);
-    const int n_rooms = n_cells / 1024;
-    for (int r = 0; r < n_rooms; ++r) {
-      const int x0 = 1 + (int)below(draw_at(kr, (uint32_t)(2 * r)), (uint32_t)(S - 9));
-      const int y0 = 1 + (int)below(draw_at(kr, (uint32_t)(2 * r + 1)), (uint32_t)(S - 9));
-      for (int j = lane; j < 64; j += 32) {
-        const int i = (y0 + (j >> 3)) * S + x0 + (j & 7);
-        if (smap[i] != kDoor) smap[i] = 0;
-      }
-    }
-    __syncwarp();
-    auto is_free = [&](int i) { return smap[i] == 0; };
-    const int n_free = count_cells(n_cells, lane, is_free);
-    const int nd = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_NSPRITES), 0), (uint32_t)(p.K - 1));
-    const uint64_t ks = stream_key(p.seed, (uint32_t)e, ep, P_SPRITE_CELL);
-    for (int k = 0; k < nd; ++k) {
-      const uint32_t c = below(draw_at(ks, (uint32_t)k), (uint32_t)n_free);
-      spr_cell[2 + k] = nth_cell(n_cells, c, lane, is_free);
-      spr_type[2 + k] = 3;
-    }
-    nspr = 2 + nd;
-  }
-  __syncwarp();
-  write_episode_state(p, e, ep, cell_of(start), obj, nspr, spr_cell, spr_type, lane);
-  store_map(p, e, smap, lane);
-  __syncwarp();
-}
-
-// ASCII maps (Table 2): each episode copies the parsed map; the spawn is
-// uniform over the 'S' cells (over all floor cells when there is none), the
-// keys become sprites on their cells in row-major order, and a goal sprite
-// goes on one 'G' cell drawn uniformly per episode.
-__device__ __forceinline__ void gen_ascii(const Params& p, int e, uint32_t ep, uint8_t* smap, int lane) {
-  const int S = p.S, n = S * S;
-  for (int i = lane; i < n; i += 32) smap[i] = p.tmpl[i];
-  __syncwarp();
-  const uint64_t d = draw_at(stream_key(p.seed, (uint32_t)e, ep, P_SPAWN), 0);
-  auto is_free = [&](int i) { return smap[i] == 0; };
-  int cell;
-  if (p.n_spawn > 0) {
-    cell = p.cand[below(d, (uint32_t)p.n_spawn)];
-  } else {
-    const int n_free = count_cells(n, lane, is_free);
-    cell = nth_cell(n, below(d, (uint32_t)n_free), lane, is_free);
-  }
-  int spr_cell[kMaxSprites], spr_type[kMaxSprites];
-  int obj[6] = {-1, -1, -1, -1, -1, -1};
-  const int32_t* keys = p.cand + p.n_spawn + p.n_goal;
-  int k = 0;
-  for (int i = 0; i < p.n_keys; ++i, ++k) {
-    const int colour = keys[i] & 3;
-    spr_cell[k] = keys[i] >> 2;
-    spr_type[k] = colour == 0 ? kSprKey : (colour == 1 ? kSprKeyBlue : kSprKeyYellow);
-  }
-  if (p.n_keys > 0) {
-    obj[0] = (keys[0] >> 2) % S;
-    obj[1] = (keys[0] >> 2) / S;
-  }
-  if (p.n_goal > 0) {
-    const int g = p.cand[p.n_spawn + below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_GOAL), 0),
-                                           (uint32_t)p.n_goal)];
-    spr_cell[k] = g;
-    spr_type[k] = kSprGoal;
-    ++k;
-    obj[2] = g % S;
-    obj[3] = g / S;
-  }
-  // the first locked door in row-major order
-  for (int base = 0; base < n; base += 32) {
-    const uint32_t b = __ballot_sync(0xffffffffu, base + lane < n && is_locked(smap[base + lane]));
-    if (b) {
-      const int c = base + __ffs(b) - 1;
-      obj[4] = c % S;
-      obj[5] = c / S;
-      break;
-    }
-  }
-  write_episode_state(p, e, ep, cell, obj, k, spr_cell, spr_type, lane);
-  __syncwarp();
-  store_map(p, e, smap, lane);
-  __syncwarp();
-}
-
-// The maze work space lives in the warp's frame staging ring when it fits
-// (32 x 32 mazes need 3.4 KB), else in the global per-warp slot. Inlined
-// behind unlikely branches: a call would make every value live across it
-// spill in the hot loop. A byte map is generated in shared memory and copied
-// out; in bit mode the map is generated in place in the state block and its
-// bit plane staged from there.
-template <int MAPK>
-__device__ __forceinline__ void generate(const Params& p, int e, uint32_t ep, uint8_t* wbase, uint8_t* scratch,
-                                      int lane) {
-  const WarpSmem ws{wbase, fill_lane(p, lane)};
-  const bool bits = map_bits<MAPK>(p);
-  uint8_t* smap = bits ? p.st.map + (size_t)e * p.S * p.S : ws.map(p);
-  if (p.task == 0) {
-    gen_rooms(p, e, ep, smap, lane);
-  } else if (p.task == kTaskAscii) {
-    gen_ascii(p, e, ep, smap, lane);
-  } else {
-    const int nn = (p.S - 2) / 2;
-    uint8_t* work = scratch;
-    if (maze_scratch_bytes(nn * nn) <= (size_t)(p.staging * p.frame_block_bytes)) {
-      if (lane == 0) bulk_wait_read_all();  // the ring's pending frame stores have read it
-      __syncwarp();
-      work = ws.ring();
-    }
-    gen_maze(p, e, ep, smap, work, lane);
-  }
-  if (bits) stage_map_bits(p, e, ws.map(p), lane);
-}
-
-// ------------------------------------------------------------------ step ----
-template <int MAPK>
-__device__ __forceinline__ bool solid(const Params& p, const uint8_t* smap, int S, int x, int y, int keys) {
-  if (x < 0 || y < 0 || x >= S || y >= S) return true;
-  if (map_bits<MAPK>(p)) return cell_set<MAPK>(p, smap, y * S + x);
-  int v = smap[y * S + x];
-  return v != 0 && !(is_locked(v) && ((keys >> (v - kLocked)) & 1));
-}
-
-// Box of half-size r centred at (cx + fx, cy + fy) overlaps no solid cell
-// (closed intervals).
-// floor(v) for v in [-1, 2): fractions stay in [0, 1) and a move or the box
-// half-size is below 1/2, so every box edge lies in that range.
-__device__ __forceinline__ int floor_small(float v) { return (v >= 1.f ? 1 : 0) - (v < 0.f ? 1 : 0); }
-
-template <int MAPK>
-__device__ __forceinline__ bool box_free(const Params& p, const uint8_t* smap, int S, int cx, float fx, int cy,
-                                         float fy, float r, int keys) {
-  const int i0 = cx + floor_small(fx - r), i1 = cx + floor_small(fx + r);
-  const int j0 = cy + floor_small(fy - r), j1 = cy + floor_small(fy + r);
-  bool hit = solid<MAPK>(p, smap, S, i0, j0, keys);
-  if (i1 != i0) hit |= solid<MAPK>(p, smap, S, i1, j0, keys);
-  if (j1 != j0) {
-    hit |= solid<MAPK>(p, smap, S, i0, j1, keys);
-    if (i1 != i0) hit |= solid<MAPK>(p, smap, S, i1, j1, keys);
-  }
-  return !hit;
-}
-
-// An unlocked door opens when the agent walks into it: after a rejected axis
-// move, every unlocked door cell under the box at (cx + fx, cy + fy) turns
-// to floor, in the staged map and in the state block.
-template <int MAPK>
-__device__ __noinline__ void open_unlocked(const Params& p, int e, uint8_t* smap, int cx, float fx, int cy, float fy,
-                                           int lane) {
-  const int S = p.S;
-  const float r = p.radius;
-  const int i0 = cx + floor_small(fx - r), i1 = cx + floor_small(fx + r);
-  const int j0 = cy + floor_small(fy - r), j1 = cy + floor_small(fy + r);
-  uint8_t* g = p.st.map + (size_t)e * S * S;
-  for (int j = j0; j <= j1; ++j)
-    for (int i = i0; i <= i1; ++i) {
-      if (i < 0 || j < 0 || i >= S || j >= S) continue;
-      const int c = j * S + i;
-      if (!is_unlocked(map_bits<MAPK>(p) ? g[c] : smap[c])) continue;
-      if (lane == 0) {
-        g[c] = 0;
-        if (map_bits<MAPK>(p))
-          reinterpret_cast<uint32_t*>(smap)[c >> 5] &= ~(1u << (c & 31));
-        else
-          smap[c] = 0;
-      }
-    }
-  __syncwarp();
-}
-
-// keep the position split as an integer cell plus a fraction in [0, 1)
-__device__ __forceinline__ void renormalise(int& c, float& f) {
-  if (f < 0.f) {
-    f += 1.f;
-    c -= 1;
-    if (f >= 1.f) {  // a tiny negative fraction rounded up to 1
-      f = 0.f;
-      c += 1;
-    }
-  } else if (f >= 1.f) {
-    f -= 1.f;
-    c += 1;
-  }
-}
-
-// One step of env e under action a; the reward and done flag go to output
-// slot `out`. Returns true when the episode ended (the caller regenerates).
-// The pose is written back to the state block only when write_state is set.
-template <int MAPK>
-__device__ __forceinline__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, const int32_t* obj,
-                                         const float4* spr_in,
-                                         int lane, float& c, float& s, int a, size_t out, bool write_state) {
-  if (a > 6) {
-    if (lane == 0) atomicOr(p.err, 1u);
-    a = 0;
-  }
-  if (a == 5) r.turn = r.turn == 0 ? p.tpr - 1 : r.turn - 1;
-  if (a == 6) r.turn = r.turn + 1 == p.tpr ? 0 : r.turn + 1;
-  heading(p, r, c, s);
-  const float ms = p.move;
-  float dx = 0.f, dy = 0.f;
-  if (a == 1) {
-    dx = ms * c;
-    dy = ms * s;
-  } else if (a == 2) {
-    dx = -(ms * c);
-    dy = -(ms * s);
-  } else if (a == 3) {
-    dx = ms * s;
-    dy = -(ms * c);
-  } else if (a == 4) {
-    dx = -(ms * s);
-    dy = ms * c;
-  }
-  const int S = p.S;
-  const float rad = p.radius;
-  const bool doors = p.task == kTaskAscii;  // maps with unlocked doors
-  float nfx = r.fx + dx;
-  if (box_free<MAPK>(p, smap, S, r.cx, nfx, r.cy, r.fy, rad, r.keys)) {
-    r.fx = nfx;
-    renormalise(r.cx, r.fx);
-  } else if (__builtin_expect(doors, 0)) {
-    open_unlocked<MAPK>(p, e, const_cast<uint8_t*>(smap), r.cx, nfx, r.cy, r.fy, lane);
-  }
-  float nfy = r.fy + dy;
-  if (box_free<MAPK>(p, smap, S, r.cx, r.fx, r.cy, nfy, rad, r.keys)) {
-    r.fy = nfy;
-    renormalise(r.cy, r.fy);
-  } else if (__builtin_expect(doors, 0)) {
-    open_unlocked<MAPK>(p, e, const_cast<uint8_t*>(smap), r.cx, r.fx, r.cy, nfy, lane);
-  }
-  // key and goal events from the sprite table (lane j looks at slot j): a key
-  // of a colour not held yet on the agent's cell is picked up; a goal there
-  // is reached
-  uint32_t kbit = 0;
-  bool goal = false;
-  if (lane < obj[6]) {
-    const float4 sp = spr_in[lane];
-    if ((int)floorf(sp.x) == r.cx && (int)floorf(sp.y) == r.cy) {
-      const int type = (int)sp.z;
-      const int kc = key_colour(type);
-      if (kc >= 0 && !((r.keys >> kc) & 1)) kbit = 1u << kc;
-      goal = type == kSprGoal;
-    }
-  }
-  const uint32_t picked = __reduce_or_sync(0xffffffffu, kbit);
-  int ev = (picked ? 1 : 0) | (__any_sync(0xffffffffu, goal) ? 2 : 0);
-  r.keys |= (int)picked;
-  r.t += 1;
-  const bool done = (ev & 2) || (p.horizon > 0 && r.t >= p.horizon);
-  if (lane == 0) {
-    p.rewards[out] = ev == 0 ? p.reward_lut[0] : (ev == 1 ? p.reward_lut[1] : (ev == 2 ? p.reward_lut[2] : p.reward_lut[3]));
-    p.dones[out] = done ? 1 : 0;
-    if (write_state && !done) {
-      const State& st = p.st;
-      st.cell_x[e] = (int16_t)r.cx;
-      st.cell_y[e] = (int16_t)r.cy;
-      st.frac_x[e] = r.fx;
-      st.frac_y[e] = r.fy;
-      st.turn[e] = (int16_t)r.turn;
-      st.t[e] = r.t;
-      st.flags[e] = (uint8_t)r.keys;
-    }
-  }
-  return done;
-}
-
-// ---------------------------------------------------------------- render ----
-// DDA (Sec. 2.1), one crossing per iteration. The next x boundary is at
-// t = (kx + gx) / ax, the next y boundary at (ky + gy) / ay; the
-// cross-multiplied forms are compared, so no division is needed.
-struct Ray {
-  int mx, my, sx, sy, side;
-  float kx, ky;  // boundaries crossed so far (exact small integers)
-  float ax, ay, gx, gy, gxay, gyax;
-  bool done;
-};
-
-__device__ __forceinline__ void ray_init(Ray& q, const Env& r, float rx, float ry, bool valid) {
-  q.mx = r.cx;
-  q.my = r.cy;
-  q.sx = rx < 0.f ? -1 : 1;
-  q.sy = ry < 0.f ? -1 : 1;
-  q.ax = fabsf(rx);
-  q.ay = fabsf(ry);
-  q.gx = rx < 0.f ? r.fx : 1.f - r.fx;
-  q.gy = ry < 0.f ? r.fy : 1.f - r.fy;
-  // an axis the ray never crosses compares as +infinity
-  const float inf = __int_as_float(0x7f800000);
-  q.gxay = q.ax == 0.f ? inf : q.gx * q.ay;
-  q.gyax = q.ay == 0.f ? inf : q.gy * q.ax;
-  q.kx = q.ky = 0.f;
-  q.side = -1;
-  q.done = !valid;
-}
-
-template <int MAPK>
-__device__ __forceinline__ void ray_advance(const Params& p, Ray& q, const uint8_t* smap, int S) {
-  const float lhs = fmaf(q.kx, q.ay, q.gxay);
-  const float rhs = fmaf(q.ky, q.ax, q.gyax);
-  const bool tx = lhs < rhs;
-  q.mx += tx ? q.sx : 0;
-  q.my += tx ? 0 : q.sy;
-  q.kx += tx ? 1.f : 0.f;
-  q.ky += tx ? 0.f : 1.f;
-  q.side = tx ? 0 : 1;
-  const bool out = (unsigned)q.mx >= (unsigned)S || (unsigned)q.my >= (unsigned)S;
-  q.done = out || cell_set<MAPK>(p, smap, q.my * S + q.mx);
-}
-
-// Slice of a finished ray: perp, rows and colour into the column arrays.
-template <int MODE, int MAPK>
-__device__ __forceinline__ void finish_column(const Params& p, int e, const Ray& q, int col, const WarpSmem& ws) {
-  const int S = p.S, H = p.H;
-  float perp;
-  if (q.side == 0)
-    perp = __fdividef((q.kx - 1.f) + q.gx, q.ax);
-  else if (q.side == 1)
-    perp = __fdividef((q.ky - 1.f) + q.gy, q.ay);
-  else
-    perp = __int_as_float(0x7f800000);  // no hit
-  // h = floor(H / perp + 1/2), clamped; top = floor((H - h) / 2)
-  int h;
-  if (perp > 0.f) {
-    const float v = __fdividef((float)H, perp) + 0.5f;
-    h = v >= 1048576.f ? kHMax : (int)floorf(v);
-  } else {
-    h = kHMax;
-  }
-  const int top = (H - h) >> 1;  // arithmetic shift: floor division by 2
-  const int bot = top + h;
-  int v = 1;
-  const bool inside = (unsigned)q.mx < (unsigned)S && (unsigned)q.my < (unsigned)S;
-  if (q.side >= 0 && inside)
-    v = map_bits<MAPK>(p) ? p.st.map[(size_t)e * S * S + q.my * S + q.mx] : ws.map(p)[q.my * S + q.mx];
-  const int slot = col_slot(col, p.W >> 3);
-  uint32_t colour = ws.pal(p)[(q.side == 1 ? kCellColours : 0) + (v < kCellColours ? v : 1)];
-  if (p.shading) {  // distance shading: channels scaled by q / 256, q = 64 + 192 min(h, H) / H
-    const uint32_t qq = 64u + (uint32_t)(192 * (h < H ? h : H)) / (uint32_t)H;
-    const uint32_t R = ((colour & 255u) * qq) >> 8, G = (((colour >> 8) & 255u) * qq) >> 8,
-                   B = (((colour >> 16) & 255u) * qq) >> 8;
-    colour = R | (G << 8) | (B << 16) | (luma(R, G, B) << 24);
-  }
-  ws.col_rgb(p)[slot] = colour;
-  ws.col_top(p)[slot] = top < 0 ? 0 : (top > H ? H : top);
-  ws.col_bot(p)[slot] = bot < 0 ? 0 : (bot > H ? H : bot);
-  ws.zbuf(p)[col] = perp;
-  if (MODE == MODE_RAYS) {
-    int4 hv = make_int4(q.side >= 0 ? q.mx : -1, q.side >= 0 ? q.my : -1, q.side, h);
-    reinterpret_cast<int4*>(p.dbg_hits)[(size_t)e * p.W + col] = hv;
-    p.dbg_perp[(size_t)e * p.W + col] = perp;
-  }
-}
-
-// Cast every column's ray: in each pass lane l marches the rays of columns
-// l + 32 j (j < COLS) together, and the warp leaves the DDA loop when a
-// ballot says every ray has hit.
-template <int MODE, int MAPK, int COLS>
-__device__ __forceinline__ void cast_columns(const Params& p, int e, const Env& r, float c, float s,
-                                             const WarpSmem& ws, int lane) {
-  const int W = p.W, S = p.S;
-  const uint8_t* smap = ws.map(p);
-  const int max_it = 4 * S + 8;
-  for (int col0 = lane; col0 - lane < W; col0 += 32 * COLS) {
-    Ray q[COLS];
-#pragma unroll
-    for (int j = 0; j < COLS; ++j) {
-      const int col = col0 + 32 * j;
-      const bool valid = col < W;
-      const float k = __ldg(p.col_k + (valid ? col : 0));
-      ray_init(q[j], r, fmaf(-k, s, c), fmaf(k, c, s), valid);
-    }
-    for (int it = 0; it < max_it; ++it) {
-      bool all = true;
-#pragma unroll
-      for (int j = 0; j < COLS; ++j) {
-        if (!q[j].done) ray_advance<MAPK>(p, q[j], smap, S);
-        all = all && q[j].done;
-      }
-      if (__all_sync(0xffffffffu, all)) break;
-    }
-#pragma unroll
-    for (int j = 0; j < COLS; ++j)
-      if (col0 + 32 * j < W) finish_column<MODE, MAPK>(p, e, q[j], col0 + 32 * j, ws);
-  }
-  __syncwarp();
-}
-
-// Project sprites (lane j takes sprite j) and order the visible ones far to
-// near (equal depths: higher index first, so the lower index is drawn last).
-// A sprite at depth ty is 0.25 W / (tan(fov/2) ty) columns wide, centred on
-// column (W/2)(1 + tx/ty), and (H/2) / ty rows high from row H/2 down.
-__device__ __forceinline__ int project_sprites(const Params& p, const Env& r, float c, float s, const WarpSmem& ws,
-                                               int lane) {
-  const int W = p.W, H = p.H;
-  bool vis = false;
-  float ty = 0.f;
-  const int nspr = ws.obj(p)[6];
-  if (lane < nspr) {
-    const float4 sp = ws.spr_in(p)[lane];
-    const int type = (int)sp.z;
-    const float vx = (sp.x - (float)r.cx) - r.fx;
-    const float vy = (sp.y - (float)r.cy) - r.fy;
-    ty = fmaf(vx, c, vy * s);
-    const int kc = key_colour(type);
-    vis = type != 0 && !(kc >= 0 && ((r.keys >> kc) & 1)) && ty > 0.1f;
-    if (vis) {
-      const float inv_ty = __frcp_rn(ty);
-      const float tx = fmaf(-vx, s, vy * c) * p.inv_tan_half;
-      const float wd = 0.25f * (float)W * p.inv_tan_half * inv_ty;
-      const float ht = 0.5f * (float)H * inv_ty;
-      const float x0 = fmaf(0.5f * (float)W, fmaf(tx, inv_ty, 1.f), -0.5f * wd);
-      const float top = 0.5f * (float)H;
-      ws.spr_a(p)[lane] = make_float4(x0, top, ty * (4.f * p.tan_half / (float)W), ty * (2.f / (float)H));
-      // pixel centres that can fall inside [x0, x0 + wd) x [top, top + ht), one pixel of slack
-      const int cA = (int)floorf(fmaxf(x0 - 1.f, -1.f));
-      const int cB = (int)floorf(fminf(x0 + wd + 1.f, (float)W));
-      const int rA = (int)floorf(fmaxf(top - 1.f, -1.f));
-      const int rB = (int)floorf(fminf(top + ht + 1.f, (float)H));
-      ws.spr_rect(p)[lane] =
-          make_int4(cA < 0 ? 0 : cA, cB > W - 1 ? W - 1 : cB, rA < 0 ? 0 : rA, rB > H - 1 ? H - 1 : rB);
-      ws.spr_ty(p)[lane] = ty;
-      ws.spr_rgb(p)[lane] = ws.pal(p)[2 * kCellColours + (type & 7)];
-      ws.spr_kind(p)[lane] = kc >= 0 ? 1 : (type == kSprGoal ? 2 : 3);  // mask: diamond, rectangle, disc
-    }
-  }
-  const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
-  int rank = 0;
-  for (int k = 0; k < nspr; ++k) {
-    const float tk = __shfl_sync(0xffffffffu, ty, k);
-    const bool vk = (vmask >> k) & 1;
-    if (vis && vk && (tk > ty || (tk == ty && k > lane))) ++rank;
-  }
-  if (vis) ws.order(p)[rank] = lane;
-  __syncwarp();
-  return __popc(vmask);
-}
-
-// Pack 8 pixel colours (0x00BBGGRR) into 24 bytes of RGB.
-__device__ __forceinline__ void store24(uint8_t* dst, const uint32_t px[8]) {
-  uint2* d = reinterpret_cast<uint2*>(dst);
-  d[0] = make_uint2(__byte_perm(px[0], px[1], 0x4210), __byte_perm(px[1], px[2], 0x5421));
-  d[1] = make_uint2(__byte_perm(px[2], px[3], 0x6542), __byte_perm(px[4], px[5], 0x4210));
-  d[2] = make_uint2(__byte_perm(px[5], px[6], 0x5421), __byte_perm(px[6], px[7], 0x6542));
-}
-
-// The lane's 8 columns. Because every slice is centred, a row above H/2 is
-// ceiling or wall and a row at or below it is wall or floor: one compare per
-// pixel.
-struct Group {
-  int top[8], bot[8];
-  uint32_t rgb[8];
-};
-
-__device__ __forceinline__ void load_group(const Params& p, const WarpSmem& ws, int g, int groups, Group& gr) {
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int slot = (h * groups + g) << 2;
-    const int4 t4 = *reinterpret_cast<const int4*>(ws.col_top(p) + slot);
-    const int4 b4 = *reinterpret_cast<const int4*>(ws.col_bot(p) + slot);
-    const uint4 c4 = *reinterpret_cast<const uint4*>(ws.col_rgb(p) + slot);
-    gr.top[4 * h + 0] = t4.x, gr.top[4 * h + 1] = t4.y, gr.top[4 * h + 2] = t4.z, gr.top[4 * h + 3] = t4.w;
-    gr.bot[4 * h + 0] = b4.x, gr.bot[4 * h + 1] = b4.y, gr.bot[4 * h + 2] = b4.z, gr.bot[4 * h + 3] = b4.w;
-    gr.rgb[4 * h + 0] = c4.x, gr.rgb[4 * h + 1] = c4.y, gr.rgb[4 * h + 2] = c4.z, gr.rgb[4 * h + 3] = c4.w;
-  }
-}
-
-// Fill rows [r0, r1) of the frame into `buf` (row-major RGB), then draw the
-// sprites over them.
-__device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, uint8_t* buf, uint8_t* gbuf, int r0,
-                                          int r1, int nvis, int lane) {
-  const int W = p.W, H = p.H, rowb = 3 * W, mid = H >> 1;
-  const bool gray = gbuf != nullptr;
-  const int groups = ws.fl.groups;  // lanes per row, 8 pixels (24 bytes) each
-  const int rpp = ws.fl.rows;       // rows per pass
-  const int my_row = ws.fl.my_row, g = ws.fl.g;
-  if (my_row < rpp) {
-    Group gr;
-    load_group(p, ws, g, groups, gr);
-    for (int row = r0 + my_row; row < r1; row += rpp) {
-      uint32_t px[8];
-      if (row < mid) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) px[k] = row < gr.top[k] ? kCeil : gr.rgb[k];
-      } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) px[k] = row < gr.bot[k] ? gr.rgb[k] : kFloor;
-      }
-      store24(buf + (row - r0) * rowb + g * 24, px);
-      if (gray) {  // the luma bytes (top byte of each colour) of the 8 pixels
-        const uint32_t lo = __byte_perm(__byte_perm(px[0], px[1], 0x0073), __byte_perm(px[2], px[3], 0x0073), 0x5410);
-        const uint32_t hi = __byte_perm(__byte_perm(px[4], px[5], 0x0073), __byte_perm(px[6], px[7], 0x0073), 0x5410);
-        *reinterpret_cast<uint2*>(gbuf + (row - r0) * W + g * 8) = make_uint2(lo, hi);
-      }
-    }
-  }
-  __syncwarp();
-  // sprites, far to near; lanes take columns. For a column, the covered rows
-  // are those whose centre has v in [0, 1) with |2v - 1| below the mask's
-  // half-height at this u (key: 1 - |2u - 1|, disc: sqrt(1 - (2u - 1)^2)).
-  // the sprites whose rows meet this block, far to near
-  const uint32_t span = lane < nvis ? ws.spr_span(p)[lane] : 0xFFFF0000u;
-  uint32_t hits = __ballot_sync(0xffffffffu, (int)(span >> 16) < r1 && (int)(span & 0xffffu) >= r0);
-  while (hits) {
-    const int oi = __ffs(hits) - 1;
-    hits &= hits - 1;
-    const int j = ws.order(p)[oi];
-    const int4 rc = ws.spr_rect(p)[j];
-    const int rA = rc.z < r0 ? r0 : rc.z;
-    const int rB = rc.w > r1 - 1 ? r1 - 1 : rc.w;
-    if (rc.x > rc.y || rA > rB) continue;
-    const float4 a = ws.spr_a(p)[j];  // x0, top, 1/width, 1/height
-    const float ty = ws.spr_ty(p)[j];
-    const uint32_t rgbv = ws.spr_rgb(p)[j];
-    const int kind = ws.spr_kind(p)[j];
-    for (int col = rc.x + lane; col <= rc.y; col += 32) {
-      const float u = ((float)col + 0.5f - a.x) * a.z;
-      if (!(u >= 0.f && u < 1.f && ty < ws.zbuf(p)[col])) continue;
-      const float au = fabsf(fmaf(2.f, u, -1.f));
-      const float half = kind == 1 ? 1.f - au : (kind == 2 ? 2.f : sqrtf(fmaxf(0.f, fmaf(-au, au, 1.f))));
-      uint8_t* px = buf + col * 3;
-      for (int row = rA; row <= rB; ++row) {
-        const float v = ((float)row + 0.5f - a.y) * a.w;
-        if (v >= 0.f && v < 1.f && fabsf(fmaf(2.f, v, -1.f)) < half) {
-          uint8_t* q = px + (row - r0) * rowb;
-          q[0] = (uint8_t)(rgbv & 255);
-          q[1] = (uint8_t)((rgbv >> 8) & 255);
-          q[2] = (uint8_t)((rgbv >> 16) & 255);
-          if (gray) gbuf[(row - r0) * W + col] = (uint8_t)(rgbv >> 24);
-        }
-      }
-    }
-    __syncwarp();
-  }
-}
-
-// GRAY: 0 no grayscale stack, 1 a stack, 2 as p.st.gray says (batched kernel).
-template <int MODE, int MAPK, int COLS, int GRAY>
-__device__ __forceinline__ void render_env(const Params& p, int e, const Env& r, float c, float s,
-                                           const WarpSmem& ws, int lane, int& slot, uint8_t* frame) {
-  cast_columns<MODE, MAPK, COLS>(p, e, r, c, s, ws, lane);
-  if (MODE == MODE_RAYS) return;
-  const int nvis = project_sprites(p, r, c, s, ws, lane);  // ends with __syncwarp
-  const int H = p.H, W = p.W, rowb = 3 * W;
-  if (lane < nvis) {  // rows each sprite of the far-to-near order can cover
-    const int4 rc = ws.spr_rect(p)[ws.order(p)[lane]];
-    ws.spr_span(p)[lane] = rc.x <= rc.y ? ((uint32_t)rc.z << 16) | (uint32_t)rc.w : 0xFFFF0000u;
-  }
-  __syncwarp();
-  const bool gray_on = GRAY == 1 || (GRAY == 2 && p.st.gray != nullptr);
-  for (int r0 = 0; r0 < H; r0 += p.rows_per_block) {
-    const int r1 = r0 + p.rows_per_block < H ? r0 + p.rows_per_block : H;
-    uint8_t* buf = ws.ring() + slot * p.frame_block_bytes;
-    uint8_t* gbuf = gray_on ? ws.gray_ring(p) + slot * p.gray_block_bytes : nullptr;
-    if (lane == 0) bulk_wait_staging(p.staging);
-    __syncwarp();
-    fill_block(p, ws, buf, gbuf, r0, r1, nvis, lane);
-    fence_proxy_async_smem();
-    __syncwarp();
-    if (lane == 0) {
-      bulk_copy(frame + (size_t)r0 * rowb, buf, (uint32_t)((r1 - r0) * rowb));
-      if (gray_on) {
-        // grayscale stack: plane t mod 4, or all four planes for an episode's first frame
-        const size_t plane = (size_t)H * W;
-        uint8_t* g0 = p.st.gray + (size_t)e * 4 * plane + (size_t)r0 * W;
-        const uint32_t gbytes = (uint32_t)((r1 - r0) * W);
-        if (r.t == 0) {
-          for (int k = 0; k < 4; ++k) bulk_copy(g0 + k * plane, gbuf, gbytes);
-        } else {
-          bulk_copy(g0 + (size_t)(r.t & 3) * plane, gbuf, gbytes);
-        }
-      }
-      bulk_commit();
-    }
-    slot = slot + 1 == p.staging ? 0 : slot + 1;
-  }
-}
-
-// Locked doors of the colours held open for rays (and, in bit mode, for
-// collisions): their cells are cleared in the staged map, which the state
-// block keeps as written. Run after staging and whenever the keys change.
-// Generated mazes have one red door (the door cell of the state); ASCII maps
-// are scanned.
-template <int MAPK>
-__device__ __noinline__ void open_doors(const Params& p, int e, int keys, const WarpSmem& ws, int lane) {
-  if (keys == 0) return;
-  const int S = p.S, n = S * S;
-  const uint8_t* g = p.st.map + (size_t)e * n;
-  uint8_t* smap = ws.map(p);
-  if (p.task == kTaskAscii) {
-    for (int i = lane; i < n; i += 32) {
-      const int v = map_bits<MAPK>(p) ? g[i] : smap[i];
-      if (!(is_locked(v) && ((keys >> (v - kLocked)) & 1))) continue;
-      if (map_bits<MAPK>(p))
-        atomicAnd(reinterpret_cast<uint32_t*>(smap) + (i >> 5), ~(1u << (i & 31)));
-      else
-        smap[i] = 0;
-    }
-  } else if (keys & 1) {
-    const int2 door = *reinterpret_cast<const int2*>(ws.obj(p) + 4);
-    if (lane == 0 && door.x >= 0 && door.y >= 0 && door.x < S && door.y < S) {
-      const int i = door.y * S + door.x;
-      if (map_bits<MAPK>(p)) {
-        if (g[i] == kDoor) reinterpret_cast<uint32_t*>(smap)[i >> 5] &= ~(1u << (i & 31));
-      } else if (smap[i] == kDoor) {
-        smap[i] = 0;
-      }
-    }
-  }
-  __syncwarp();
-}
-
-// Everything one launch does for env e: MODE_ROLLOUT runs p.steps steps with
-// the env's scalar state in registers and its map in shared memory.
-template <int MODE, int MAPK, int COLS, int GRAY>
-__device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, uint8_t* scratch, int lane,
-                                        int& slot) {
-  const WarpSmem ws{wbase, fill_lane(p, lane)};
-  const size_t frame_bytes = (size_t)3 * p.H * p.W;
-  if (MODE == MODE_ROLLOUT) {
-    Env r = load_env(p, e);
-    load_objects(p, ws, e, lane);
-    stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
-    open_doors<MAPK>(p, e, r.keys, ws, lane);
-    int a_next = p.actions[e];
-    for (int t = 0; t < p.steps; ++t) {
-      const int a = a_next;
-      if (t + 1 < p.steps) a_next = p.actions[(size_t)(t + 1) * p.out_stride + e];
-      float c, s;
-      const size_t out = (size_t)t * p.out_stride + e;
-      const int keys0 = r.keys;
-      if (__builtin_expect(step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), ws.spr_in(p), lane, c, s, a, out, false), 0)) {
-        const uint32_t ep = p.st.episode[e] + 1;
-        __syncwarp();
-        generate<MAPK>(p, e, ep, wbase, scratch, lane);
-        r = load_env(p, e);
-        load_objects(p, ws, e, lane);
-        __syncwarp();
-        heading(p, r, c, s);
-      }
-      if (__builtin_expect(r.keys != keys0, 0)) open_doors<MAPK>(p, e, r.keys, ws, lane);
-      render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot,
-                                         p.frames + (size_t)t * p.frame_step + (size_t)e * frame_bytes);
-      __syncwarp();
-    }
-    if (lane == 0) {
-      const State& st = p.st;
-      st.cell_x[e] = (int16_t)r.cx;
-      st.cell_y[e] = (int16_t)r.cy;
-      st.frac_x[e] = r.fx;
-      st.frac_y[e] = r.fy;
-      st.turn[e] = (int16_t)r.turn;
-      st.t[e] = r.t;
-      st.flags[e] = (uint8_t)r.keys;
-    }
-    __syncwarp();
-    return;
-  }
-  Env r;
-  float c, s;
-  if (MODE == MODE_RESET) {
-    generate<MAPK>(p, e, 0u, wbase, scratch, lane);
-    r = load_env(p, e);
-    load_objects(p, ws, e, lane);
-    __syncwarp();
-    heading(p, r, c, s);
-  } else {
-    r = load_env(p, e);
-    load_objects(p, ws, e, lane);
-    stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
-    open_doors<MAPK>(p, e, r.keys, ws, lane);
-    if (MODE == MODE_STEP) {
-      const int keys0 = r.keys;
-      if (__builtin_expect(
-              step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), ws.spr_in(p), lane, c, s, (int)p.actions[e], (size_t)e,
-                             true), 0)) {
-        const uint32_t ep = p.st.episode[e] + 1;
-        __syncwarp();
-        generate<MAPK>(p, e, ep, wbase, scratch, lane);
-        r = load_env(p, e);
-        load_objects(p, ws, e, lane);
-        __syncwarp();
-        heading(p, r, c, s);
-      } else if (r.keys != keys0) {
-        open_doors<MAPK>(p, e, r.keys, ws, lane);
-      }
-    } else {
-      heading(p, r, c, s);
-    }
-  }
-  render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
-  __syncwarp();
-}
-
-__device__ __forceinline__ void write_palette(const Params& p, const WarpSmem& ws, int lane) {
-  ws.pal(p)[lane] = c_wall[lane];
-  ws.pal(p)[32 + lane] = c_wall[32 + lane];
-  if (lane < 8) ws.pal(p)[64 + lane] = c_sprite[lane];
-  __syncwarp();
-}
 
 template <int MODE, int MAPK, int GRAY>
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
@@ -1314,67 +20,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   for (int e = gw; e < p.n; e += nw) run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot);
   // shared memory stays allocated until the bulk stores have read it
   if (lane == 0) bulk_wait_read_all();
-}
-
-// One launch over the groups of a batch. Each group has a work queue (a
-// counter of handed-out envs); a warp drains the groups' queues in order,
-// one env at a time, fetching its next ticket while it works on the current
-// env. The last warp to finish zeroes the counters for the next launch.
-template <int MODE, int COLS>
-__global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
-    batch_kernel(const __grid_constant__ BatchParams bp) {
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wpb = blockDim.x >> 5;
-  uint8_t* const wbase = smem_raw + warp * bp.warp_bytes;
-  init_warp_header(wbase, lane);
-  const int gw = blockIdx.x * wpb + warp;
-  int slot = 0;
-  bool fresh = true;  // nothing of an earlier group is pending in the ring
-  for (int g = 0; g < bp.n_groups; ++g) {
-    const Params& p = bp.g[g];
-    uint32_t ticket = 0;
-    if (lane == 0) {
-      // a drained queue is skipped without an atomic
-      ticket = *reinterpret_cast<volatile uint32_t*>(bp.queue + g);
-      if (ticket < (uint32_t)p.n) ticket = atomicAdd(bp.queue + g, 1u);
-    }
-    ticket = __shfl_sync(0xffffffffu, ticket, 0);
-    if (ticket >= (uint32_t)p.n) continue;
-    if (!fresh && lane == 0) bulk_wait_read_all();  // the layout changes under the ring
-    __syncwarp();
-    write_palette(p, WarpSmem{wbase, fill_lane(p, lane)}, lane);
-    fresh = false;
-    slot = 0;
-    uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;
-    while (ticket < (uint32_t)p.n) {
-      uint32_t next = 0;
-      if (lane == 0) next = atomicAdd(bp.queue + g, 1u);
-      run_env<MODE, MAP_RUNTIME, COLS, 2>(p, (int)ticket, wbase, scratch, lane, slot);
-      ticket = __shfl_sync(0xffffffffu, next, 0);
-    }
-  }
-  if (lane == 0) {
-    bulk_wait_read_all();
-    __threadfence();
-    const uint32_t nw = gridDim.x * wpb;
-    if (atomicAdd(bp.queue + kMaxGroups, 1u) == nw - 1) {
-      for (int g = 0; g < bp.n_groups; ++g) atomicExch(bp.queue + g, 0u);
-      atomicExch(bp.queue + kMaxGroups, 0u);
-    }
-  }
-}
-
-// A kernel's dynamic shared memory limit is a property of the function, shared
-// by every env in the process: it is raised to the device's opt-in maximum (never
-// lowered), so envs of different sizes can coexist.
-template <class Kernel>
-cudaError_t raise_smem_limit(Kernel kernel) {
-  int dev = 0, optin = 0;
-  cudaError_t err = cudaGetDevice(&dev);
-  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (err == cudaSuccess) err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  return err;
 }
 
 // The env kernel of a mode for p's map kind and grayscale stack.
@@ -1396,21 +41,6 @@ template <int MODE>
 void launch_mode(const Params& p, int grid, cudaStream_t stream) {
   env_kernel_of<MODE>(p)<<<grid, kThreads, block_smem_bytes(p), stream>>>(p);
 }
-
-template <int MODE>
-auto batch_kernel_for(int cols) {
-  return cols == 2 ? batch_kernel<MODE, 2> : batch_kernel<MODE, 1>;
-}
-
-auto batch_kernel_of(int mode, int cols) {
-  switch (mode) {
-    case MODE_RESET: return batch_kernel_for<MODE_RESET>(cols);
-    case MODE_ROLLOUT: return batch_kernel_for<MODE_ROLLOUT>(cols);
-    case MODE_RENDER: return batch_kernel_for<MODE_RENDER>(cols);
-    default: return batch_kernel_for<MODE_STEP>(cols);
-  }
-}
-
 }  // namespace
 
 void layout_warp_smem(Params& p) {
@@ -1469,18 +99,4 @@ cudaError_t launch(const Params& p, int mode, int grid, cudaStream_t stream) {
   }
   return cudaGetLastError();
 }
-
-cudaError_t batch_blocks_per_sm(int mode, int cols, int warps, int smem_bytes, int* blocks) {
-  auto k = batch_kernel_of(mode, cols);
-  cudaError_t err = raise_smem_limit(k);
-  if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, 32 * warps, smem_bytes);
-}
-
-cudaError_t batch_launch(const BatchParams& bp, int mode, int cols, int warps, int grid, cudaStream_t stream) {
-  auto k = batch_kernel_of(mode, cols);
-  k<<<grid, 32 * warps, (size_t)bp.warp_bytes * warps, stream>>>(bp);
-  return cudaGetLastError();
-}
-
 }  // namespace jx

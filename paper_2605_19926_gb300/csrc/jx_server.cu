@@ -143,7 +143,7 @@ struct jx_server {
   std::unordered_map<int32_t, Session*> sessions;
   std::vector<Slot> slots;
   cudaStream_t admin = nullptr;  // resets of newly opened sessions
-  std::map<int, int> occupancy;  // block shared memory bytes -> blocks per SM
+  std::map<int, int> occupancy;  // 2 x block shared memory bytes + kernel spec -> blocks per SM
   std::mutex mu;
   std::mutex open_mu;  // serialises the admin stream
   std::condition_variable cv_work, cv_done;
@@ -167,14 +167,15 @@ void free_session(jx_server* sv, Session* s) {
   delete s;
 }
 
-int blocks_per_sm(jx_server* sv, int smem) {
-  auto it = sv->occupancy.find(smem);
+int blocks_per_sm(jx_server* sv, int smem, int spec) {
+  const int key = smem * 2 + spec;
+  auto it = sv->occupancy.find(key);
   if (it != sv->occupancy.end()) return it->second;
   int b = 0;
-  if (jx::batch_blocks_per_sm(jx::MODE_STEP, sv->tiling.cols_per_lane, sv->tiling.warps_per_block, smem, &b) !=
+  if (jx::batch_blocks_per_sm(jx::MODE_STEP, sv->tiling.cols_per_lane, spec, sv->tiling.warps_per_block, smem, &b) !=
       cudaSuccess)
     b = 0;
-  sv->occupancy[smem] = b;
+  sv->occupancy[key] = b;
   return b;
 }
 
@@ -209,7 +210,7 @@ jx_status dispatch(jx_server* sv, Slot& sl, std::vector<Session*>& chosen) {
   bp.warp_bytes = warp_bytes;
   bp.queue = sl.queue;
   const int wpb = sv->tiling.warps_per_block, smem = warp_bytes * wpb;
-  const int bps = blocks_per_sm(sv, smem);
+  const int bps = blocks_per_sm(sv, smem, jx::batch_spec(bp));
   if (bps < 1) return fail(JX_ECUDA, "batched kernel cannot be resident with %d bytes of shared memory", smem);
   const int64_t grid = std::min<int64_t>((int64_t)bps * sv->num_sms, (total + wpb - 1) / wpb);
   cudaError_t err = cudaMemcpyAsync(sl.d_actions, sl.h_actions, off, cudaMemcpyHostToDevice, sl.stream);
