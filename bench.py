@@ -732,7 +732,20 @@ def main():
             p1.record(stream)
         stream.synchronize()
         pms = p0.elapsed_time(p1)
+        # its per-call latency, one step at a time with a host sync (as the batch's p50 / p99)
+        plat = []
+        with torch.cuda.stream(stream):
+            for i in range(min(args.plain_steps, args.latency_steps)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                penv.step(pa[i], pf, pr, pd, stream)
+                b.record(stream)
+                b.synchronize()
+                plat.append(a.elapsed_time(b))
+        plat.sort()
         plain = {"value": args.plain_steps / (pms / 1e3), "unit": "env-steps/s", "ms_per_step": pms / args.plain_steps,
+                 "p50_step_ms": plat[len(plat) // 2] if plat else None,
+                 "p99_step_ms": plat[min(len(plat) - 1, int(0.99 * len(plat)))] if plat else None,
                  "workload": f"1 env, 16x16 random rooms (p = 0.25), 64x64 RGB, {args.plain_steps} uniform random steps, "
                              "one jx_step launch per step"}
         penv.close()

@@ -148,3 +148,22 @@ def test_server_counters_struct_matches_header(jx):
     body = re.search(r"typedef struct \{([^}]*)\} jx_server_counters;", text).group(1)
     names = re.findall(r"^\s*(?:u?int\d+_t)\s+(\w+);", body, re.M)
     assert names == [f[0] for f in jx.ServerCounters._fields_]
+
+
+def test_serving_inputs():
+    """Serving sessions: batch sizes log-uniform in [16, 4096], map sides 32 or 64,
+    64 x 64 key-door mazes; Poisson arrivals with a 2 ms mean gap; all seeded."""
+    import numpy as np
+
+    sessions = [inputs.serving_session(3, a, k) for a in range(64) for k in range(8)]
+    n = np.array([s["n_envs"] for s in sessions])
+    assert n.min() >= 16 and n.max() <= 4096
+    logs = np.log(n)
+    assert abs(logs.mean() - (np.log(16) + np.log(4096)) / 2) < 0.3
+    assert {s["map_side"] for s in sessions} == {32, 64}
+    assert all(s["frame_h"] == s["frame_w"] == 64 and s["task"] == inputs.TASK_MAZE_KEYDOOR for s in sessions)
+    assert len({s["seed"] for s in sessions}) == len(sessions)
+    assert inputs.serving_session(3, 5, 2) == sessions[5 * 8 + 2]
+    gaps = inputs.arrival_gaps(3, 7, 20000)
+    assert abs(gaps.mean() - 2e-3) < 1e-4 and (gaps > 0).all()
+    assert (inputs.arrival_gaps(3, 7, 20000) == gaps).all()
