@@ -196,8 +196,8 @@ __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; 
 //   pal       [2][32] wall colours by face and cell value, then [8] sprite colours by type
 //   map       S * S cell values, row-major
 //   col_rgb   [W] wall colour, chunk-interleaved (see col_slot)
-//   col_top   [W] first wall row, chunk-interleaved
-//   col_bot   [W] first floor row, chunk-interleaved
+//   col_top   [W] bytes: 127 + first wall row (at most H/2), by column
+//   col_bot   [W] bytes: 127 + first floor row - H/2 (at least 0), by column
 //   zbuf      [W] perpendicular distance by column
 //   spr_in    [K] float4 sprite x, y, type (as float)
 //   spr_a     [K] float4 x0, top, 1 / width, 1 / height (pixels)
@@ -228,8 +228,8 @@ struct WarpSmem {
   __device__ __forceinline__ uint32_t* pal(const Params& p) const { return (uint32_t*)(base + p.off_pal); }
   __device__ __forceinline__ uint8_t* map(const Params& p) const { return base + p.off_map; }
   __device__ __forceinline__ uint32_t* col_rgb(const Params& p) const { return (uint32_t*)(base + p.off_col_rgb); }
-  __device__ __forceinline__ int32_t* col_top(const Params& p) const { return (int32_t*)(base + p.off_col_top); }
-  __device__ __forceinline__ int32_t* col_bot(const Params& p) const { return (int32_t*)(base + p.off_col_bot); }
+  __device__ __forceinline__ uint8_t* col_top(const Params& p) const { return base + p.off_col_top; }
+  __device__ __forceinline__ uint8_t* col_bot(const Params& p) const { return base + p.off_col_bot; }
   __device__ __forceinline__ float* zbuf(const Params& p) const { return (float*)(base + p.off_zbuf); }
   __device__ __forceinline__ float4* spr_in(const Params& p) const { return (float4*)(base + p.off_spr_in); }
   __device__ __forceinline__ float4* spr_a(const Params& p) const { return (float4*)(base + p.off_spr_a); }
@@ -946,8 +946,9 @@ __device__ __forceinline__ void finish_column(const Params& p, int e, const Ray&
     colour = R | (G << 8) | (B << 16) | (luma(R, G, B) << 24);
   }
   ws.col_rgb(p)[slot] = colour;
-  ws.col_top(p)[slot] = top < 0 ? 0 : (top > H ? H : top);
-  ws.col_bot(p)[slot] = bot < 0 ? 0 : (bot > H ? H : bot);
+  // h >= 0, so top <= H/2 <= bot: clamped to [0, H] they fit the byte offsets
+  ws.col_top(p)[col] = (uint8_t)(127 + (top < 0 ? 0 : top));
+  ws.col_bot(p)[col] = (uint8_t)(127 + (bot > H ? H : bot) - (H >> 1));
   ws.zbuf(p)[col] = perp;
   if (MODE == MODE_RAYS) {
     int4 hv = make_int4(q.side >= 0 ? q.mx : -1, q.side >= 0 ? q.my : -1, q.side, h);
@@ -1040,37 +1041,34 @@ __device__ __forceinline__ int project_sprites(const Params& p, const Env& r, fl
   return __popc(vmask);
 }
 
-// Pack 8 pixel colours (0x00BBGGRR) into 24 bytes of RGB.
-__device__ __forceinline__ void store24(uint8_t* dst, const uint32_t px[8]) {
-  uint2* d = reinterpret_cast<uint2*>(dst);
-  d[0] = make_uint2(__byte_perm(px[0], px[1], 0x4210), __byte_perm(px[1], px[2], 0x5421));
-  d[1] = make_uint2(__byte_perm(px[2], px[3], 0x6542), __byte_perm(px[4], px[5], 0x4210));
-  d[2] = make_uint2(__byte_perm(px[5], px[6], 0x5421), __byte_perm(px[6], px[7], 0x6542));
+// Four pixels of colour c as the three words of their 12 RGB bytes.
+__host__ __device__ constexpr uint32_t rgb_word(uint32_t c, int k) {
+  return k == 0 ? (c & 0xFFFFFFu) | (c << 24)                       // R G B R
+         : k == 1 ? ((c >> 8) & 0xFFFFu) | ((c & 0xFFFFu) << 16)   // G B R G
+                  : ((c >> 16) & 255u) | ((c & 0xFFFFFFu) << 8);   // B R G B
 }
 
-// The lane's 8 columns. Because every slice is centred, a row above H/2 is
-// ceiling or wall and a row at or below it is wall or floor: one compare per
-// pixel.
-struct Group {
-  int top[8], bot[8];
-  uint32_t rgb[8];
-};
-
-__device__ __forceinline__ void load_group(const Params& p, const WarpSmem& ws, int g, int groups, Group& gr) {
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int slot = (h * groups + g) << 2;
-    const int4 t4 = *reinterpret_cast<const int4*>(ws.col_top(p) + slot);
-    const int4 b4 = *reinterpret_cast<const int4*>(ws.col_bot(p) + slot);
-    const uint4 c4 = *reinterpret_cast<const uint4*>(ws.col_rgb(p) + slot);
-    gr.top[4 * h + 0] = t4.x, gr.top[4 * h + 1] = t4.y, gr.top[4 * h + 2] = t4.z, gr.top[4 * h + 3] = t4.w;
-    gr.bot[4 * h + 0] = b4.x, gr.bot[4 * h + 1] = b4.y, gr.bot[4 * h + 2] = b4.z, gr.bot[4 * h + 3] = b4.w;
-    gr.rgb[4 * h + 0] = c4.x, gr.rgb[4 * h + 1] = c4.y, gr.rgb[4 * h + 2] = c4.z, gr.rgb[4 * h + 3] = c4.w;
-  }
+// prmt with every selector nibble's sign bit set: byte j of the result is
+// 0xFF or 0x00 as bit 7 of byte (SEL >> 4j) & 3 of x is set or clear.
+template <uint32_t SEL>
+__device__ __forceinline__ uint32_t sign_bytes(uint32_t x) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, 0, %2;" : "=r"(d) : "r"(x), "n"(SEL));
+  return d;
 }
+__device__ __forceinline__ uint32_t select_bytes(uint32_t m, uint32_t a, uint32_t b) { return (m & a) | (~m & b); }
 
 // Fill rows [r0, r1) of the frame into `buf` (row-major RGB), then draw the
 // sprites over them.
+//
+// A lane owns 8 columns of a row: two quads of 4 pixels, 12 bytes = 3 words
+// each. Because every slice is centred, a row above H/2 is ceiling or wall
+// and a row at or below it is wall or floor. Byte k of d = (127 + top_k) -
+// row (all bytes at once) is in [0, 255], so no borrow crosses bytes, and
+// its bit 7 is set exactly when row < top_k; sign-replicating prmt turns
+// those bits into byte masks laid out like the pixels' RGB bytes, and one
+// select per word picks ceiling or wall. Rows below the middle do the same
+// with 127 + bot_k - H/2 and row - H/2 (wall or floor).
 __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, uint8_t* buf, uint8_t* gbuf, int r0,
                                           int r1, int nvis, int lane) {
   const int W = p.W, H = p.H, rowb = 3 * W, mid = H >> 1;
@@ -1079,22 +1077,50 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
   const int rpp = ws.fl.rows;       // rows per pass
   const int my_row = ws.fl.my_row, g = ws.fl.g;
   if (my_row < rpp) {
-    Group gr;
-    load_group(p, ws, g, groups, gr);
-    for (int row = r0 + my_row; row < r1; row += rpp) {
-      uint32_t px[8];
-      if (row < mid) {
+    const uint2 t8 = *reinterpret_cast<const uint2*>(ws.col_top(p) + 8 * g);
+    const uint2 b8 = *reinterpret_cast<const uint2*>(ws.col_bot(p) + 8 * g);
+    uint32_t wq[6], yq[2];  // wall RGB words of the two quads, wall luma bytes
 #pragma unroll
-        for (int k = 0; k < 8; ++k) px[k] = row < gr.top[k] ? kCeil : gr.rgb[k];
-      } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) px[k] = row < gr.bot[k] ? gr.rgb[k] : kFloor;
+    for (int h = 0; h < 2; ++h) {
+      const uint4 c = *reinterpret_cast<const uint4*>(ws.col_rgb(p) + ((h * groups + g) << 2));
+      wq[3 * h + 0] = __byte_perm(c.x, c.y, 0x4210);
+      wq[3 * h + 1] = __byte_perm(c.y, c.z, 0x5421);
+      wq[3 * h + 2] = __byte_perm(c.z, c.w, 0x6542);
+      yq[h] = __byte_perm(__byte_perm(c.x, c.y, 0x0073), __byte_perm(c.z, c.w, 0x0073), 0x5410);
+    }
+    const uint32_t step = (uint32_t)rpp * 0x01010101u;
+    int row = r0 + my_row;
+    uint2* dst = reinterpret_cast<uint2*>(buf + my_row * rowb + g * 24);
+    uint2* gdst = reinterpret_cast<uint2*>((gray ? gbuf : buf) + my_row * W + g * 8);  // written only with gray
+    const int dstep = rpp * rowb / 8, gstep = rpp * W / 8;
+    const int lim = r1 < mid ? r1 : mid;
+    if (row < lim) {  // ceiling or wall
+      uint32_t d0 = t8.x - (uint32_t)row * 0x01010101u, d1 = t8.y - (uint32_t)row * 0x01010101u;
+      for (; row < lim; row += rpp, d0 -= step, d1 -= step, dst += dstep, gdst += gstep) {
+        dst[0] = make_uint2(select_bytes(sign_bytes<0x9888>(d0), rgb_word(kCeil, 0), wq[0]),
+                            select_bytes(sign_bytes<0xAA99>(d0), rgb_word(kCeil, 1), wq[1]));
+        dst[1] = make_uint2(select_bytes(sign_bytes<0xBBBA>(d0), rgb_word(kCeil, 2), wq[2]),
+                            select_bytes(sign_bytes<0x9888>(d1), rgb_word(kCeil, 0), wq[3]));
+        dst[2] = make_uint2(select_bytes(sign_bytes<0xAA99>(d1), rgb_word(kCeil, 1), wq[4]),
+                            select_bytes(sign_bytes<0xBBBA>(d1), rgb_word(kCeil, 2), wq[5]));
+        if (gray)
+          *gdst = make_uint2(select_bytes(sign_bytes<0xBA98>(d0), (kCeil >> 24) * 0x01010101u, yq[0]),
+                             select_bytes(sign_bytes<0xBA98>(d1), (kCeil >> 24) * 0x01010101u, yq[1]));
       }
-      store24(buf + (row - r0) * rowb + g * 24, px);
-      if (gray) {  // the luma bytes (top byte of each colour) of the 8 pixels
-        const uint32_t lo = __byte_perm(__byte_perm(px[0], px[1], 0x0073), __byte_perm(px[2], px[3], 0x0073), 0x5410);
-        const uint32_t hi = __byte_perm(__byte_perm(px[4], px[5], 0x0073), __byte_perm(px[6], px[7], 0x0073), 0x5410);
-        *reinterpret_cast<uint2*>(gbuf + (row - r0) * W + g * 8) = make_uint2(lo, hi);
+    }
+    if (row < r1) {  // wall or floor
+      const uint32_t rr = (uint32_t)(row - mid) * 0x01010101u;
+      uint32_t d0 = b8.x - rr, d1 = b8.y - rr;
+      for (; row < r1; row += rpp, d0 -= step, d1 -= step, dst += dstep, gdst += gstep) {
+        dst[0] = make_uint2(select_bytes(sign_bytes<0x9888>(d0), wq[0], rgb_word(kFloor, 0)),
+                            select_bytes(sign_bytes<0xAA99>(d0), wq[1], rgb_word(kFloor, 1)));
+        dst[1] = make_uint2(select_bytes(sign_bytes<0xBBBA>(d0), wq[2], rgb_word(kFloor, 2)),
+                            select_bytes(sign_bytes<0x9888>(d1), wq[3], rgb_word(kFloor, 0)));
+        dst[2] = make_uint2(select_bytes(sign_bytes<0xAA99>(d1), wq[4], rgb_word(kFloor, 1)),
+                            select_bytes(sign_bytes<0xBBBA>(d1), wq[5], rgb_word(kFloor, 2)));
+        if (gray)
+          *gdst = make_uint2(select_bytes(sign_bytes<0xBA98>(d0), yq[0], (kFloor >> 24) * 0x01010101u),
+                             select_bytes(sign_bytes<0xBA98>(d1), yq[1], (kFloor >> 24) * 0x01010101u));
       }
     }
   }

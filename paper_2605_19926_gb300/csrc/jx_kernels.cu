@@ -56,8 +56,8 @@ void layout_warp_smem(Params& p) {
   p.off_pal = take(4 * kPaletteWords);
   p.off_map = take(p.map_smem_bytes);
   p.off_col_rgb = take(4 * p.W);
-  p.off_col_top = take(4 * p.W);
-  p.off_col_bot = take(4 * p.W);
+  p.off_col_top = take(p.W);
+  p.off_col_bot = take(p.W);
   p.off_zbuf = take(4 * p.W);
   p.off_spr_in = take(16 * K);
   p.off_spr_a = take(16 * K);
