@@ -347,9 +347,11 @@ __device__ __forceinline__ uint32_t nonzero4(uint32_t x) {
 
 // The map as a bit plane: bit i of word i / 32 is set iff cell i is nonzero
 // (S * S is a multiple of 32; rows run on across word boundaries).
-__device__ __forceinline__ void stage_map_bits(const Params& p, int e, uint8_t* smap, int lane) {
+// The bytes are read from `src` (16-byte aligned; the state block's map when null).
+__device__ __forceinline__ void stage_map_bits(const Params& p, int e, uint8_t* smap, int lane,
+                                               const uint8_t* src = nullptr) {
   const int words = (p.S * p.S) >> 5;
-  const uint4* g = reinterpret_cast<const uint4*>(p.st.map + (size_t)e * p.S * p.S);
+  const uint4* g = reinterpret_cast<const uint4*>(src ? src : p.st.map + (size_t)e * p.S * p.S);
   uint32_t* w = reinterpret_cast<uint32_t*>(smap);
   for (int i = lane; i < words; i += 32) {
     const uint4 a = g[2 * i], b = g[2 * i + 1];
@@ -696,29 +698,32 @@ __device__ __forceinline__ void gen_ascii(const Params& p, int e, uint32_t ep, u
 // (32 x 32 mazes need 3.4 KB), else in the global per-warp slot. Inlined
 // behind unlikely branches: a call would make every value live across it
 // spill in the hot loop. A byte map is generated in shared memory and copied
-// out; in bit mode the map is generated in place in the state block and its
-// bit plane staged from there.
+// out. In bit mode the byte map is generated in the ring, after the maze work
+// space, when both fit there (the one-lane DFS then never waits on global
+// memory), else in place in the state block; the bit plane is staged from it.
 template <int MAPK>
 __device__ __forceinline__ void generate(const Params& p, int e, uint32_t ep, uint8_t* wbase, uint8_t* scratch,
                                       int lane) {
   const WarpSmem ws{wbase, fill_lane(p, lane)};
   const bool bits = map_bits<MAPK>(p);
-  uint8_t* smap = bits ? p.st.map + (size_t)e * p.S * p.S : ws.map(p);
+  const bool maze = p.task != 0 && p.task != kTaskAscii;
+  const size_t ring = (size_t)p.staging * p.frame_block_bytes;
+  const size_t work_bytes = maze ? maze_scratch_bytes(((p.S - 2) / 2) * ((p.S - 2) / 2)) : 0;
+  const bool work_in_ring = maze && work_bytes <= ring;
+  const bool map_in_ring = bits && (size_t)align16((int)work_bytes) + (size_t)p.S * p.S <= ring;
+  if (work_in_ring || map_in_ring) {
+    if (lane == 0) bulk_wait_read_all();  // the ring's pending frame stores have read it
+    __syncwarp();
+  }
+  uint8_t* smap = !bits ? ws.map(p) : (map_in_ring ? ws.ring() + align16((int)work_bytes) : p.st.map + (size_t)e * p.S * p.S);
   if (p.task == 0) {
     gen_rooms(p, e, ep, smap, lane);
   } else if (p.task == kTaskAscii) {
     gen_ascii(p, e, ep, smap, lane);
   } else {
-    const int nn = (p.S - 2) / 2;
-    uint8_t* work = scratch;
-    if (maze_scratch_bytes(nn * nn) <= (size_t)(p.staging * p.frame_block_bytes)) {
-      if (lane == 0) bulk_wait_read_all();  // the ring's pending frame stores have read it
-      __syncwarp();
-      work = ws.ring();
-    }
-    gen_maze(p, e, ep, smap, work, lane);
+    gen_maze(p, e, ep, smap, work_in_ring ? ws.ring() : scratch, lane);
   }
-  if (bits) stage_map_bits(p, e, ws.map(p), lane);
+  if (bits) stage_map_bits(p, e, ws.map(p), lane, map_in_ring ? smap : nullptr);
 }
 
 // ------------------------------------------------------------------ step ----
