@@ -230,12 +230,7 @@ def run_uneven(args):
 
     groups = inputs.uneven_groups(n_envs=args.uneven_envs, seed=2 + rank)
     envs = [jx.Env(c, local) for c in groups]
-    pinned = None
-    if args.tiling:
-        pinned = jx.Tiling()
-        vals = [int(v) for v in args.tiling.split(",")] + [1]
-        (pinned.warps_per_block, pinned.cols_per_lane, pinned.bits_min_side, pinned.max_rows_per_block,
-         pinned.staging_buffers) = vals[:5]
+    pinned = parse_tiling(jx, args.tiling)
     batch = jx.Batch(envs, pinned)
     N, F = batch.n, batch.frame_bytes
     dev = torch.device("cuda", local)
@@ -313,7 +308,7 @@ def run_uneven(args):
         "metric": "env-steps/s incl. render (frames/s), uneven batch", "value": tuned_leg["value"],
         "unit": "env-steps/s", "n_gpus": world, "steps": K, "warmup": T, "ms_per_step": tuned_ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "16,384 envs per GPU, random-wall rooms p=0.3, map side uniform in {16,32,64,128}, "
+        "config": {"workload": f"{N:,} envs per GPU, random-wall rooms p=0.3, map side uniform in {{16,32,64,128}}, "
                                "square RGB frames uniform in {32,64,96,128}, 0-8 sprites, uniform random actions",
                    "groups": len(groups), "n_envs_per_gpu": N, "frame_bytes_per_step": F,
                    "parallelism": f"replicas x{world}",
@@ -332,6 +327,16 @@ def run_uneven(args):
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def parse_tiling(jx, text: str):
+    """`w,c,b,r[,s]` -> a jx.Tiling (staging buffers default to 1), or None for ''."""
+    if not text:
+        return None
+    t = jx.Tiling()
+    vals = [int(v) for v in text.split(",")] + [1]
+    (t.warps_per_block, t.cols_per_lane, t.bits_min_side, t.max_rows_per_block, t.staging_buffers) = vals[:5]
+    return t
 
 
 def run_large(args):
@@ -360,7 +365,9 @@ def run_large(args):
     dev = torch.device("cuda", local)
     env = jx.Env(cfg, local)
     tuned = None
-    if not args.no_autotune:
+    if args.tiling:
+        env.tiling = parse_tiling(jx, args.tiling)  # the batched kernel with this tiling
+    elif not args.no_autotune:
         # the env's own kernel against the batched kernel's tilings, before timing
         tuned = env.autotune(mode=1, steps=args.large_slots, max_trials=args.tune_trials)
     T = args.large_slots
@@ -579,7 +586,8 @@ def main():
                     help="skip jx_autotune before timing (the env's own kernel with its fixed tiles)")
     ap.add_argument("--uneven-slots", type=int, default=16, help="steps per rollout launch of the uneven batch")
     ap.add_argument("--uneven-envs", type=int, default=16384)
-    ap.add_argument("--tiling", default="", help="uneven batch: w,c,b,r tiling to use instead of autotuning")
+    ap.add_argument("--tiling", default="",
+                    help="uneven batch and large scale: w,c,b,r[,s] batched-kernel tiling to use instead of autotuning")
     ap.add_argument("--tune-trials", type=int, default=1000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
