@@ -99,6 +99,52 @@ def test_full_size_batched_mazes_sampled():
     stats.check()
 
 
+def test_full_size_all_envs_200_steps():
+    """All 4096 envs of the benchmark's workload checked against the oracle:
+    the reset, then 200 steps with every 25th step stepped and rendered by the
+    oracle from the GPU's pre-step state."""
+    cfg = inputs.batched_keydoor_mazes()
+    run = Run(cfg)
+    stats = Stats()
+    check_reset(run, stats)
+    lockstep(run, stats, 200, seed=1, check_every=25)
+    assert stats.env_steps == 8 * cfg["n_envs"]
+    stats.check()
+
+
+def test_full_size_10000_steps_sampled():
+    """The benchmark's workload run for 10,000 steps through jx_rollout in its
+    launch shape (128 steps per launch); every 1024 steps, 64 sampled envs take
+    two steps in lockstep with the oracle (pre-step state from the GPU). Every
+    env crosses the 500-step horizon about 20 times."""
+    cfg = inputs.batched_keydoor_mazes()
+    N, H, W, T = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"], 128
+    run = Run(cfg)
+    stats = Stats()
+    rng = np.random.default_rng(17)
+    idx = np.sort(rng.choice(N, 64, replace=False))
+    check_reset(run, stats, idx)
+    frames = torch.empty((T, N, H, W, 3), dtype=torch.uint8, device=run.dev)
+    rewards = torch.empty((T, N), dtype=torch.float32, device=run.dev)
+    dones = torch.empty((T, N), dtype=torch.uint8, device=run.dev)
+    s, n_done, launches = 0, 0, 0
+    while s < 10000:
+        acts = torch.from_numpy(inputs.action_stream(1, T, N, first_step=s)).to(run.dev)
+        run.env.rollout(acts, frames, rewards, dones)
+        n_done += int(dones.sum().item())
+        s += T
+        launches += 1
+        if launches % 8 == 0 or s >= 10000:
+            lockstep(run, stats, 2, seed=1, first_step=s, idx=idx)
+            s += 2
+    del frames
+    run.env.sync_status()
+    assert stats.env_steps == 2 * 64 * 10
+    ep = run.state(np.arange(N))["episode"]
+    assert ep.min() >= 19 and n_done >= 19 * N
+    stats.check()
+
+
 def test_render_only_and_state_roundtrip():
     cfg = inputs.maze_keydoor(n_envs=20, map_side=16, seed=2, horizon=0)
     run = Run(cfg)
