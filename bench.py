@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -37,10 +38,18 @@ KERNEL_SOURCES = ["paper_2605_19926_gb300/csrc/jx_device.cuh", "paper_2605_19926
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
+def kernel_code(text: str) -> str:
+    """Source text without comments and blank space: edits to comments leave
+    the compiled kernel, and so the traffic record, valid."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        h.update(kernel_code(open(os.path.join(ROOT, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -695,7 +695,7 @@ __device__ __forceinline__ void gen_ascii(const Params& p, int e, uint32_t ep, u
 }
 
 // The maze work space lives in the warp's frame staging ring when it fits
-// (32 x 32 mazes need 3.4 KB), else in the global per-warp slot. Inlined
+// (32 x 32 mazes need 2.3 KB), else in the global per-warp slot. Inlined
 // behind unlikely branches: a call would make every value live across it
 // spill in the hot loop. A byte map is generated in shared memory and copied
 // out. In bit mode the byte map is generated in the ring, after the maze work
