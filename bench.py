@@ -53,6 +53,18 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def recorded_traffic(n_envs: int, launch_steps: int, path: str = TRAFFIC_FILE):
+    """DRAM bytes of one launch from the ncu record, scaled from the captured
+    launch by the env-steps processed; None when the record is missing, is
+    for another env count, or was taken on other kernel code."""
+    if not os.path.exists(path):
+        return None
+    tf = json.load(open(path))
+    if tf.get("kernel_source_sha") != kernel_source_sha() or tf.get("n_envs") != n_envs:
+        return None
+    return tf["dram_bytes_per_env_step"] * n_envs * launch_steps
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -792,12 +804,7 @@ def main():
     peak, peak_src = 6800.0, "fallback"
     if os.path.exists(peaks_path):
         peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
-    traffic = None
-    if os.path.exists(TRAFFIC_FILE):
-        tf = json.load(open(TRAFFIC_FILE))
-        if tf.get("kernel_source_sha") == kernel_source_sha() and tf.get("n_envs") == N:
-            # scaled from the captured launch to this one by the env-steps processed
-            traffic = tf["dram_bytes_per_env_step"] * N * launch_steps
+    traffic = recorded_traffic(N, launch_steps)
 
     if rank != 0:
         if world > 1:

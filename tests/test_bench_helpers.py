@@ -1,0 +1,57 @@
+"""Host-side helpers of bench.py: the kernel source hash that keys the
+recorded DRAM traffic, the tiling parser, and the reference arm's sample."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_kernel_code_ignores_comments_and_blank_space():
+    a = "int x = 1; // one\n/* block\n comment */ int y =  2;\n"
+    b = "int x = 1;\n\n   int y = 2; // two"
+    assert bench.kernel_code(a) == bench.kernel_code(b) == "int x = 1; int y = 2;"
+    assert bench.kernel_code("int x = 1;") != bench.kernel_code("int x = 2;")
+
+
+def test_kernel_source_hash_is_stable_and_sees_code(tmp_path, monkeypatch):
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() { int a = 1; }\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", ["k.cu"])
+    h0 = bench.kernel_source_sha()
+    src.write_text("// a comment\n__global__ void k() {\n  int a = 1;  /* same code */\n}\n")
+    assert bench.kernel_source_sha() == h0
+    src.write_text("__global__ void k() { int a = 2; }\n")
+    assert bench.kernel_source_sha() != h0
+
+
+def test_parse_tiling():
+    from paper_2605_19926_gb300 import jx
+
+    assert bench.parse_tiling(jx, "") is None
+    t = bench.parse_tiling(jx, "4,1,64,8")
+    assert t.as_tuple() == (4, 1, 64, 8, 1)  # staging buffers default to one
+    assert bench.parse_tiling(jx, "2,2,128,16,2").as_tuple() == (2, 2, 128, 16, 2)
+    with pytest.raises(ValueError):
+        bench.parse_tiling(jx, "4,x,64,8")
+
+
+def test_recorded_traffic_only_for_the_same_kernel_code(tmp_path, monkeypatch):
+    """The recorded DRAM bytes apply only to the kernel code they were taken
+    on and to the same env count; otherwise traffic is reported as null."""
+    import json
+
+    rec = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "abc")
+    rec.write_text(json.dumps({"kernel_source_sha": "abc", "n_envs": 4096, "dram_bytes_per_env_step": 10000.0}))
+    assert bench.recorded_traffic(4096, 128, str(rec)) == 10000.0 * 4096 * 128
+    assert bench.recorded_traffic(2048, 128, str(rec)) is None
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "def")
+    assert bench.recorded_traffic(4096, 128, str(rec)) is None
+    assert bench.recorded_traffic(4096, 128, str(tmp_path / "missing.json")) is None
