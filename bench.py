@@ -35,7 +35,11 @@ METRIC = "env-steps/s incl. render (frames/s) at 64x64 RGB"
 GRAPH_STEPS = 128  # default launches per CUDA graph = rollout buffer slots
 KERNEL_SOURCES = ["paper_2605_19926_gb300/csrc/jx_device.cuh", "paper_2605_19926_gb300/csrc/jx_kernels.cu",
                   "paper_2605_19926_gb300/csrc/jx_internal.h"]
+BATCH_KERNEL_SOURCES = ["paper_2605_19926_gb300/csrc/jx_device.cuh", "paper_2605_19926_gb300/csrc/jx_batch_kernels.cu",
+                        "paper_2605_19926_gb300/csrc/jx_internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+TRAFFIC_UNEVEN_FILE = os.path.join(ROOT, "profiles", "traffic_uneven.json")
+TRAFFIC_LARGE_FILE = os.path.join(ROOT, "profiles", "traffic_large.json")
 
 
 def kernel_code(text: str) -> str:
@@ -46,21 +50,27 @@ def kernel_code(text: str) -> str:
     return " ".join(text.split())
 
 
-def kernel_source_sha() -> str:
+def kernel_source_sha(sources=None) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES if sources is None else sources:
         h.update(kernel_code(open(os.path.join(ROOT, f)).read()).encode())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(n_envs: int, launch_steps: int, path: str = TRAFFIC_FILE):
+def recorded_traffic(n_envs: int, launch_steps: int, path: str = TRAFFIC_FILE, sources=None, tiling=None):
     """DRAM bytes of one launch from the ncu record, scaled from the captured
-    launch by the env-steps processed; None when the record is missing, is
-    for another env count, or was taken on other kernel code."""
+    launch by the env-steps processed; None when the record is missing, was
+    taken on other kernel code or another batched-kernel tiling, or is for
+    another env count without saying that its traffic grows in proportion to
+    the env-steps."""
     if not os.path.exists(path):
         return None
     tf = json.load(open(path))
-    if tf.get("kernel_source_sha") != kernel_source_sha() or tf.get("n_envs") != n_envs:
+    if tf.get("kernel_source_sha") != kernel_source_sha(sources):
+        return None
+    if "tiling" in tf and (tiling is None or list(tf["tiling"]) != list(tiling)):
+        return None
+    if tf.get("n_envs") != n_envs and not tf.get("scales_with_env_steps"):
         return None
     return tf["dram_bytes_per_env_step"] * n_envs * launch_steps
 
@@ -339,7 +349,10 @@ def run_uneven(args):
                    "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
                               "entry": "jx_batch_rollout", "steps_per_launch": T}},
         "roofline": {"bound": "hbm", "achieved": tuned_leg["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": tuned_leg["frac"], "traffic": None, "peak_source": peak_src,
+                     "frac": tuned_leg["frac"],
+                     "traffic": recorded_traffic(N, T, TRAFFIC_UNEVEN_FILE, BATCH_KERNEL_SOURCES,
+                                                 tuned.as_tuple()),
+                     "peak_source": peak_src,
                      "algorithmic_bytes_per_env_step": bpes},
         "fixed_tiles": leg(fixed_ms, fixed_tiling), "autotuned": tuned_leg,
         "autotune": {"trials": len(trials), "seconds": tune_s, "mode": "rollout", "steps_per_trial": T},
@@ -449,7 +462,9 @@ def run_large(args):
                    "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
                               "entry": "jx_rollout", "steps_per_launch": T}},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                     "traffic": None, "peak_source": peak_src, "algorithmic_bytes_per_env_step": bpes},
+                     "traffic": recorded_traffic(N, T, TRAFFIC_LARGE_FILE, BATCH_KERNEL_SOURCES,
+                                                 env.tiling.as_tuple()),
+                     "peak_source": peak_src, "algorithmic_bytes_per_env_step": bpes},
         "reset_seconds": reset_s, "episode_ends_in_last_launch": n_done,
         "tiling": tiling_dict(env.tiling),
         "autotune_trials": len(tuned) if tuned else 0,

@@ -48,10 +48,35 @@ def test_recorded_traffic_only_for_the_same_kernel_code(tmp_path, monkeypatch):
     import json
 
     rec = tmp_path / "traffic.json"
-    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "abc")
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda sources=None: "abc")
     rec.write_text(json.dumps({"kernel_source_sha": "abc", "n_envs": 4096, "dram_bytes_per_env_step": 10000.0}))
     assert bench.recorded_traffic(4096, 128, str(rec)) == 10000.0 * 4096 * 128
     assert bench.recorded_traffic(2048, 128, str(rec)) is None
-    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "def")
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda sources=None: "def")
     assert bench.recorded_traffic(4096, 128, str(rec)) is None
     assert bench.recorded_traffic(4096, 128, str(tmp_path / "missing.json")) is None
+
+
+def test_recorded_traffic_scaling_and_tiling(tmp_path, monkeypatch):
+    """A record taken on a smaller case applies to other env counts only when
+    it says its traffic grows with the env-steps, and a batched-kernel record
+    only to the tiling it was captured with."""
+    import json
+
+    rec = tmp_path / "traffic.json"
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda sources=None: "abc")
+    rec.write_text(json.dumps({"kernel_source_sha": "abc", "n_envs": 4096, "dram_bytes_per_env_step": 100.0,
+                               "scales_with_env_steps": True, "tiling": [4, 1, 64, 8, 1]}))
+    assert bench.recorded_traffic(65536, 8, str(rec), tiling=(4, 1, 64, 8, 1)) == 100.0 * 65536 * 8
+    assert bench.recorded_traffic(65536, 8, str(rec), tiling=(0, 0, 0, 0, 0)) is None
+    assert bench.recorded_traffic(65536, 8, str(rec)) is None
+
+
+def test_committed_records_are_well_formed():
+    import json
+
+    for path in (bench.TRAFFIC_FILE, bench.TRAFFIC_UNEVEN_FILE, bench.TRAFFIC_LARGE_FILE):
+        rec = json.load(open(path))
+        assert rec["dram_bytes_per_env_step"] == pytest.approx(
+            (rec["dram_bytes_read"] + rec["dram_bytes_write"]) / (rec["n_envs"] * rec["capture_steps_per_launch"]),
+            abs=0.1)
