@@ -57,6 +57,13 @@ def kernel_source_sha(sources=None) -> str:
     return h.hexdigest()[:16]
 
 
+def tiling_key(t, sides) -> tuple:
+    """A batched-kernel tiling as the kernel sees it on maps of the given
+    sides: bits_min_side matters only through which maps become bit planes."""
+    w, c, b, r, st = (int(v) for v in t)
+    return (w, c, tuple(b > 0 and s >= b and s % 8 == 0 for s in sides), r, st)
+
+
 def recorded_traffic(n_envs: int, launch_steps: int, path: str = TRAFFIC_FILE, sources=None, tiling=None):
     """DRAM bytes of one launch from the ncu record, scaled from the captured
     launch by the env-steps processed; None when the record is missing, was
@@ -68,8 +75,10 @@ def recorded_traffic(n_envs: int, launch_steps: int, path: str = TRAFFIC_FILE, s
     tf = json.load(open(path))
     if tf.get("kernel_source_sha") != kernel_source_sha(sources):
         return None
-    if "tiling" in tf and (tiling is None or list(tf["tiling"]) != list(tiling)):
-        return None
+    if "tiling" in tf:
+        sides = tf.get("map_sides", [])
+        if tiling is None or tiling_key(tf["tiling"], sides) != tiling_key(tiling, sides):
+            return None
     if tf.get("n_envs") != n_envs and not tf.get("scales_with_env_steps"):
         return None
     return tf["dram_bytes_per_env_step"] * n_envs * launch_steps

@@ -80,3 +80,9 @@ def test_committed_records_are_well_formed():
         assert rec["dram_bytes_per_env_step"] == pytest.approx(
             (rec["dram_bytes_read"] + rec["dram_bytes_write"]) / (rec["n_envs"] * rec["capture_steps_per_launch"]),
             abs=0.1)
+
+
+def test_tiling_key_sees_only_the_effective_map_kind():
+    assert bench.tiling_key((4, 1, 8, 8, 1), [128]) == bench.tiling_key((4, 1, 64, 8, 1), [128])
+    assert bench.tiling_key((4, 1, 8, 8, 1), [16, 128]) != bench.tiling_key((4, 1, 64, 8, 1), [16, 128])
+    assert bench.tiling_key((4, 1, 0, 8, 1), [128]) != bench.tiling_key((4, 1, 128, 8, 1), [128])
