@@ -155,7 +155,13 @@ jx_status check_env(const jx_env* env) {
 jx_status run(jx_env* env, const jx::Params& p, int mode, void* stream) {
   DeviceGuard g(env->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  cudaError_t err = jx::launch(p, mode, env->grid, static_cast<cudaStream_t>(stream));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p.nx_ep && (mode == jx::MODE_STEP || mode == jx::MODE_ROLLOUT || mode == jx::MODE_RESET)) {
+    cudaError_t err = jx::pregen_launch(p, mode == jx::MODE_ROLLOUT ? p.steps : 1, mode == jx::MODE_RESET, s);
+    if (err != cudaSuccess) return cuda_fail(err, "pre-generation launch");
+    env->launches.fetch_add(1, std::memory_order_relaxed);
+  }
+  cudaError_t err = jx::launch(p, mode, env->grid, s);
   if (err != cudaSuccess) return cuda_fail(err, "kernel launch");
   env->launches.fetch_add(1, std::memory_order_relaxed);
   return JX_OK;
@@ -418,6 +424,34 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
     p.n_keys = (int32_t)am->keys.size();
   }
   p.gen_scratch = env->scratch;
+  if (env->owns_mem && jx::pregen_wanted(c.task, c.map_side, c.horizon)) {
+    // next-episode block: the state fields before the grayscale stack, the
+    // episode each env's entry holds, and one walk work slot per env; without
+    // the memory, episodes are built where they start, as for other configs
+    const size_t N = c.n_envs, nx_bytes = env->field_off[JX_F_GRAY];
+    const size_t stride = jx::pregen_work_bytes(c.map_side);
+    const size_t off_ep = align256(nx_bytes), off_work = off_ep + align256(4 * N);
+    if (cudaMalloc(&env->nx_mem, off_work + stride * N) == cudaSuccess &&
+        cudaMemset(env->nx_mem + off_ep, 0xFF, 4 * N) == cudaSuccess) {
+      auto nx = [&](int f) { return env->nx_mem + env->field_off[f]; };
+      p.nx = jx::State{reinterpret_cast<int16_t*>(nx(JX_F_CELL_X)), reinterpret_cast<int16_t*>(nx(JX_F_CELL_Y)),
+                       reinterpret_cast<float*>(nx(JX_F_FRAC_X)), reinterpret_cast<float*>(nx(JX_F_FRAC_Y)),
+                       reinterpret_cast<float*>(nx(JX_F_THETA0)), reinterpret_cast<int16_t*>(nx(JX_F_TURN)),
+                       reinterpret_cast<int32_t*>(nx(JX_F_T)), reinterpret_cast<uint32_t*>(nx(JX_F_EPISODE)),
+                       nx(JX_F_FLAGS), reinterpret_cast<int16_t*>(nx(JX_F_OBJ)), nx(JX_F_NSPR),
+                       reinterpret_cast<float*>(nx(JX_F_SPR_X)), reinterpret_cast<float*>(nx(JX_F_SPR_Y)),
+                       nx(JX_F_SPR_TYPE), nx(JX_F_MAP), reinterpret_cast<float*>(nx(JX_F_COS0)),
+                       reinterpret_cast<float*>(nx(JX_F_SIN0)), nullptr};
+      p.nx_ep = reinterpret_cast<uint32_t*>(env->nx_mem + off_ep);
+      p.nx_work = env->nx_mem + off_work;
+      p.nx_work_stride = stride;
+      p.nx_lanes = (int32_t)N;
+    } else {
+      if (env->nx_mem) cudaFree(env->nx_mem);
+      env->nx_mem = nullptr;
+      (void)cudaGetLastError();
+    }
+  }
   // the memset and the table copy are done before the handle is returned
   if ((err = cudaStreamSynchronize(0)) != cudaSuccess) {
     jx_destroy(env);
@@ -504,6 +538,7 @@ jx_status jx_destroy(jx_env* env) {
     // an env in caller memory frees nothing on the device: no synchronisation
     if (env->owns_mem || env->stage) cudaDeviceSynchronize();
     if (env->owns_mem && env->mem) cudaFree(env->mem);
+    if (env->nx_mem) cudaFree(env->nx_mem);
     if (env->stage) cudaFree(env->stage);
   }
   delete env;

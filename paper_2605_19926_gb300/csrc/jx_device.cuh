@@ -410,10 +410,10 @@ __device__ __forceinline__ int count_cells(int n, int lane, Pred pred) {
   return total;
 }
 
-// Writes the scalar fields of a fresh episode (lane 0) and all K sprite slots.
-__device__ void write_episode_state(const Params& p, int e, uint32_t ep, int cell, const int obj[6], int nspr,
-                                    const int* spr_cell, const int* spr_type, int lane) {
-  const State& st = p.st;
+// Writes the scalar fields of a fresh episode (lane 0) and all K sprite slots
+// (lanes lane, lane + kstep, ...) into st: the state, or the next-episode block.
+__device__ void write_episode_state(const Params& p, const State& st, int e, uint32_t ep, int cell, const int obj[6],
+                                    int nspr, const int* spr_cell, const int* spr_type, int lane, int kstep) {
   const int S = p.S;
   const uint64_t kh = stream_key(p.seed, (uint32_t)e, ep, P_HEADING);
   if (lane == 0) {
@@ -435,7 +435,7 @@ __device__ void write_episode_state(const Params& p, int e, uint32_t ep, int cel
     for (int k = 0; k < 6; ++k) o[k] = (int16_t)obj[k];
     st.nspr[e] = (uint8_t)nspr;
   }
-  for (int k = lane; k < p.K; k += 32) {
+  for (int k = lane; k < p.K; k += kstep) {
     size_t i = (size_t)e * p.K + k;
     if (k < nspr) {
       st.spr_x[i] = (float)(spr_cell[k] % S) + 0.5f;
@@ -484,7 +484,7 @@ __device__ __forceinline__ void gen_rooms(const Params& p, int e, uint32_t ep, u
     }
   }
   const int obj[6] = {-1, -1, -1, -1, -1, -1};
-  write_episode_state(p, e, ep, spawn, obj, nspr, spr_cell, spr_type, lane);
+  write_episode_state(p, p.st, e, ep, spawn, obj, nspr, spr_cell, spr_type, lane, 32);
   __syncwarp();
   store_map(p, e, smap, lane);
   __syncwarp();
@@ -634,9 +634,189 @@ __device__ __forceinline__ void gen_maze(const Params& p, int e, uint32_t ep, ui
     nspr = 2 + nd;
   }
   __syncwarp();
-  write_episode_state(p, e, ep, cell_of(start), obj, nspr, spr_cell, spr_type, lane);
+  write_episode_state(p, p.st, e, ep, cell_of(start), obj, nspr, spr_cell, spr_type, lane, 32);
   store_map(p, e, smap, lane);
   __syncwarp();
+}
+
+// Zero (floor) bytes among the 16 at q (16-byte aligned).
+__device__ __forceinline__ int floor_bytes16(const uint8_t* q) {
+  const uint4 v = *reinterpret_cast<const uint4*>(q);
+  return 16 - __popc(nonzero4(v.x) | nonzero4(v.y) << 4 | nonzero4(v.z) << 8 | nonzero4(v.w) << 12);
+}
+
+// One lane builds episode ep of env e into the next-episode block p.nx: the
+// draws and steps of gen_maze, run serially by the lane (walls, the walk with
+// its stack and discovery / finish counters in the lane's work slot, the door,
+// the key, and for task 2 the rooms and distractors), so that 32 mazes of a
+// warp are built at once. S is a multiple of 4, so S * S is one of 16.
+__device__ void gen_maze_lane(const Params& p, int e, uint32_t ep, uint8_t* work) {
+  const int S = p.S, n_cells = S * S;
+  const int nn = (S - 2) / 2, n = nn * nn;
+  uint8_t* smap = p.nx.map + (size_t)e * n_cells;
+  uint16_t* stack = reinterpret_cast<uint16_t*>(work);
+  uint16_t* disc = stack + n;
+  uint16_t* fin = disc + n;
+  const uint64_t kw = stream_key(p.seed, (uint32_t)e, ep, P_WALL);
+  for (int i = 0; i < n_cells; i += 16) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) v |= (1u + (uint32_t)(draw_at(kw, (uint32_t)(i + 4 * q + b)) & 3)) << (8 * b);
+      w[q] = v;
+    }
+    *reinterpret_cast<uint4*>(smap + i) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  const uint64_t kd = stream_key(p.seed, (uint32_t)e, ep, P_DFS);
+  const int start = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_SPAWN), 0), (uint32_t)n);
+  int vx = 2 * (start % nn) + 1, vy = 2 * (start / nn) + 1, v = start;
+  smap[vy * S + vx] = 0;
+  int sp = 0, pushes = 0;
+  uint32_t carved = 0;
+  stack[sp++] = (uint16_t)(vy << 8 | vx);
+  disc[v] = (uint16_t)pushes++;
+  int best_v = start, best_d = 0, door_a = vy << 8 | vx, door_b = door_a;
+  for (;;) {
+    const int c = vy * S + vx;
+    const uint32_t open = (uint32_t)(vy > 1 && smap[c - 2 * S] != 0) | ((uint32_t)(vx < S - 3 && smap[c + 2] != 0) << 1) |
+                          ((uint32_t)(vy < S - 3 && smap[c + 2 * S] != 0) << 2) |
+                          ((uint32_t)(vx > 1 && smap[c - 2] != 0) << 3);
+    if (open == 0) {
+      fin[v] = (uint16_t)pushes;
+      if (--sp == 0) break;
+      const int top = stack[sp - 1];
+      vx = top & 0xff;
+      vy = top >> 8;
+      v = (vy >> 1) * nn + (vx >> 1);
+      continue;
+    }
+    // the r-th unvisited neighbour in N, E, S, W order
+    uint32_t bits = open;
+    for (uint32_t r = below(draw_at(kd, carved++), (uint32_t)__popc(open)); r > 0; --r) bits &= bits - 1;
+    const int d = __ffs(bits) - 1;
+    const int dx = d == 1 ? 1 : (d == 3 ? -1 : 0), dy = d == 0 ? -1 : (d == 2 ? 1 : 0);
+    smap[c + dy * S + dx] = 0;
+    vx += 2 * dx;
+    vy += 2 * dy;
+    smap[vy * S + vx] = 0;
+    v = (vy >> 1) * nn + (vx >> 1);
+    const int depth = sp;
+    stack[sp++] = (uint16_t)(vy << 8 | vx);
+    disc[v] = (uint16_t)pushes++;
+    if (depth > best_d || (depth == best_d && v < best_v)) {
+      best_v = v;
+      best_d = depth;
+      const int j = (depth + 1) / 2;  // the door sits on edge ceil(depth / 2) of the path
+      door_a = stack[j - 1];
+      door_b = stack[j];
+    }
+  }
+  const int dxc = ((door_a & 0xff) + (door_b & 0xff)) >> 1, dyc = ((door_a >> 8) + (door_b >> 8)) >> 1;
+  smap[dyc * S + dxc] = (uint8_t)kDoor;
+  // key: uniform over spawn-side nodes except the spawn
+  const int pj = ((door_b >> 8) >> 1) * nn + ((door_b & 0xff) >> 1);
+  const int d0 = disc[pj], d1 = fin[pj];
+  const int n_side = n - (d1 - d0) - 1;
+  int key = start;
+  if (n_side > 0) {
+    uint32_t r = below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_KEY), 0), (uint32_t)n_side);
+    for (int u = 0; u < n; ++u) {
+      const int du = disc[u];
+      if (u == start || (du >= d0 && du < d1)) continue;
+      if (r == 0) {
+        key = u;
+        break;
+      }
+      --r;
+    }
+  }
+  auto cell_of = [&](int u) { return (2 * (u / nn) + 1) * S + 2 * (u % nn) + 1; };
+  const int kc = cell_of(key), gc = cell_of(best_v);
+  const int obj[6] = {kc % S, kc / S, gc % S, gc / S, dxc, dyc};
+  int spr_cell[kMaxSprites], spr_type[kMaxSprites];
+  spr_cell[0] = kc;
+  spr_type[0] = kSprKey;
+  spr_cell[1] = gc;
+  spr_type[1] = kSprGoal;
+  int nspr = 2;
+  if (p.task == 2) {
+    // open 8 x 8 rooms (the door kept), then distractors on floor cells
+    const uint64_t kr = stream_key(p.seed, (uint32_t)e, ep, P_ROOM);
+    const int n_rooms = n_cells / 1024;
+    for (int r = 0; r < n_rooms; ++r) {
+      const int x0 = 1 + (int)below(draw_at(kr, (uint32_t)(2 * r)), (uint32_t)(S - 9));
+      const int y0 = 1 + (int)below(draw_at(kr, (uint32_t)(2 * r + 1)), (uint32_t)(S - 9));
+      for (int j = 0; j < 64; ++j) {
+        const int i = (y0 + (j >> 3)) * S + x0 + (j & 7);
+        if (smap[i] != kDoor) smap[i] = 0;
+      }
+    }
+    int n_free = 0;
+    for (int i = 0; i < n_cells; i += 16) n_free += floor_bytes16(smap + i);
+    const int nd = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_NSPRITES), 0), (uint32_t)(p.K - 1));
+    const uint64_t ks = stream_key(p.seed, (uint32_t)e, ep, P_SPRITE_CELL);
+    for (int k = 0; k < nd && n_free > 0; ++k) {
+      uint32_t r = below(draw_at(ks, (uint32_t)k), (uint32_t)n_free);
+      int i = 0;
+      for (;; i += 16) {  // the 16-cell group holding the r-th floor cell
+        const uint32_t f = (uint32_t)floor_bytes16(smap + i);
+        if (r < f) break;
+        r -= f;
+      }
+      for (;; ++i) {
+        if (smap[i] != 0) continue;
+        if (r == 0) break;
+        --r;
+      }
+      spr_cell[2 + k] = i;
+      spr_type[2 + k] = 3;
+    }
+    nspr = 2 + nd;
+  }
+  write_episode_state(p, p.nx, e, ep, cell_of(start), obj, nspr, spr_cell, spr_type, 0, 1);
+}
+
+// Takes over episode ep of env e from the next-episode block: the state
+// fields generation writes, and the map staged into shared memory as bytes
+// or as a bit plane (plain loads from the block, as gen writes them).
+template <int MAPK>
+__device__ __noinline__ void take_next(const Params& p, int e, uint32_t ep, uint8_t* wbase, int lane) {
+  const WarpSmem ws{wbase, FillLane{}};
+  const int n = p.S * p.S;
+  const uint4* src = reinterpret_cast<const uint4*>(p.nx.map + (size_t)e * n);
+  uint4* dst = reinterpret_cast<uint4*>(p.st.map + (size_t)e * n);
+  uint4* sdst = reinterpret_cast<uint4*>(ws.map(p));
+  for (int i = lane; i < (n >> 4); i += 32) {
+    const uint4 v = src[i];
+    dst[i] = v;
+    if (!map_bits<MAPK>(p)) sdst[i] = v;
+  }
+  const State &st = p.st, &nx = p.nx;
+  if (lane == 0) {
+    st.cell_x[e] = nx.cell_x[e];
+    st.cell_y[e] = nx.cell_y[e];
+    st.frac_x[e] = 0.5f;
+    st.frac_y[e] = 0.5f;
+    st.theta0[e] = nx.theta0[e];
+    st.cos0[e] = nx.cos0[e];
+    st.sin0[e] = nx.sin0[e];
+    st.turn[e] = 0;
+    st.t[e] = 0;
+    st.episode[e] = ep;
+    st.flags[e] = 0;
+    st.nspr[e] = nx.nspr[e];
+  }
+  if (lane < 6) st.obj[6 * (size_t)e + lane] = nx.obj[6 * (size_t)e + lane];
+  for (int k = lane; k < p.K; k += 32) {
+    const size_t i = (size_t)e * p.K + k;
+    st.spr_x[i] = nx.spr_x[i];
+    st.spr_y[i] = nx.spr_y[i];
+    st.spr_type[i] = nx.spr_type[i];
+  }
+  __syncwarp();
+  if (map_bits<MAPK>(p)) stage_map_bits(p, e, ws.map(p), lane, p.nx.map + (size_t)e * n);
 }
 
 // ASCII maps (Table 2): each episode copies the parsed map; the spawn is
@@ -688,7 +868,7 @@ __device__ __forceinline__ void gen_ascii(const Params& p, int e, uint32_t ep, u
       break;
     }
   }
-  write_episode_state(p, e, ep, cell, obj, k, spr_cell, spr_type, lane);
+  write_episode_state(p, p.st, e, ep, cell, obj, k, spr_cell, spr_type, lane, 32);
   __syncwarp();
   store_map(p, e, smap, lane);
   __syncwarp();
@@ -704,6 +884,10 @@ __device__ __forceinline__ void gen_ascii(const Params& p, int e, uint32_t ep, u
 template <int MAPK>
 __device__ __forceinline__ void generate(const Params& p, int e, uint32_t ep, uint8_t* wbase, uint8_t* scratch,
                                       int lane) {
+  if (p.nx_ep != nullptr && p.nx_ep[e] == ep) {  // built ahead by the pre-generation kernel
+    take_next<MAPK>(p, e, ep, wbase, lane);
+    return;
+  }
   const WarpSmem ws{wbase, fill_lane(p, lane)};
   const bool bits = map_bits<MAPK>(p);
   const bool maze = p.task != 0 && p.task != kTaskAscii;

@@ -31,6 +31,9 @@ struct jx_env {
   uint8_t* aux = nullptr;
   // maze generation work space, one slot per resident warp
   uint8_t* scratch = nullptr;
+  // next-episode block and work slots of the lane-parallel pre-generation
+  // (owned mazes of side >= 64), or null
+  uint8_t* nx_mem = nullptr;
   // staging buffers of jx_step_host
   uint8_t* stage = nullptr;
   size_t stage_frames_off = 0, stage_rewards_off = 0, stage_dones_off = 0;

@@ -71,6 +71,15 @@ struct Params {
   const float* col_k;     // [W] (2 (c + 1/2) / W - 1) * tan(fov / 2)
   uint8_t* gen_scratch;   // [warps][gen_scratch_stride], maze generation work space
   size_t gen_scratch_stride;
+  // The next episode of each env, built ahead by the lane-parallel
+  // pre-generation kernel (mazes of side >= kPregenMinSide), or all null:
+  // the state fields generation writes, the episode number they hold
+  // (0xFFFFFFFF: none), and one work slot per pre-generation lane.
+  State nx;
+  uint32_t* nx_ep;
+  uint8_t* nx_work;
+  size_t nx_work_stride;
+  int32_t nx_lanes;
   const uint8_t* actions;
   uint8_t* frames;
   float* rewards;
@@ -117,6 +126,13 @@ void layout_warp_smem(Params& p);
 // Dynamic shared memory bytes of one block.
 int block_smem_bytes(const Params& p);
 size_t gen_scratch_bytes(int task, int S);
+// Lane-parallel pre-generation: for maze tasks of side >= kPregenMinSide (a
+// multiple of 4) with a horizon, one lane per env builds the episode the env
+// will start within the next `steps` steps (reset: episode 0) into p.nx.
+constexpr int kPregenMinSide = 64;
+bool pregen_wanted(int task, int S, int horizon);
+size_t pregen_work_bytes(int S);
+cudaError_t pregen_launch(const Params& p, int steps, bool reset, cudaStream_t stream);
 
 // Configure (attributes) and query occupancy of the kernel for `mode`.
 cudaError_t kernel_blocks_per_sm(const Params& p, int mode, int* blocks);

@@ -22,6 +22,29 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   if (lane == 0) bulk_wait_read_all();
 }
 
+// Lane-parallel pre-generation: lane i builds, for envs i, i + lanes, ...,
+// the episode each will start within the next `steps` steps (its horizon
+// falls in them) or, for a reset, episode 0, unless the block holds it already.
+__global__ void __launch_bounds__(128) pregen_kernel(const __grid_constant__ Params p, int steps, int reset) {
+  const int lane_id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lane_id >= p.nx_lanes) return;
+  uint8_t* work = p.nx_work + (size_t)lane_id * p.nx_work_stride;
+  for (int e = lane_id; e < p.n; e += p.nx_lanes) {
+    uint32_t ep = 0;
+    bool need;
+    if (reset) {
+      need = p.nx_ep[e] != 0u;
+    } else {
+      ep = p.st.episode[e] + 1;
+      need = p.horizon > 0 && p.st.t[e] + steps >= p.horizon && p.nx_ep[e] != ep;
+    }
+    if (need) {
+      gen_maze_lane(p, e, ep, work);
+      p.nx_ep[e] = ep;
+    }
+  }
+}
+
 // The env kernel of a mode for p's map kind and grayscale stack.
 template <int MODE>
 auto env_kernel_of(const Params& p) {
@@ -72,6 +95,22 @@ void layout_warp_smem(Params& p) {
 }
 
 int block_smem_bytes(const Params& p) { return p.warp_bytes * kWarpsPerBlock; }
+
+bool pregen_wanted(int task, int S, int horizon) {
+  (void)horizon;  // a reset uses it too
+  return (task == 1 || task == 2) && S >= kPregenMinSide && S % 4 == 0;
+}
+
+size_t pregen_work_bytes(int S) {
+  const size_t n = (size_t)((S - 2) / 2) * ((S - 2) / 2);
+  return (6 * n + 255) & ~(size_t)255;  // stack, discovery and finish counters (uint16)
+}
+
+cudaError_t pregen_launch(const Params& p, int steps, bool reset, cudaStream_t stream) {
+  if (p.nx_ep == nullptr || p.nx_lanes <= 0) return cudaSuccess;
+  pregen_kernel<<<(p.nx_lanes + 127) / 128, 128, 0, stream>>>(p, steps, reset ? 1 : 0);
+  return cudaGetLastError();
+}
 
 size_t gen_scratch_bytes(int task, int S) {
   if (task != 1 && task != 2) return 0;
