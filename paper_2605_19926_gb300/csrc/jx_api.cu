@@ -430,7 +430,8 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
     // the memory, episodes are built where they start, as for other configs
     const size_t N = c.n_envs, nx_bytes = env->field_off[JX_F_GRAY];
     const size_t stride = jx::pregen_work_bytes(c.map_side);
-    const size_t off_ep = align256(nx_bytes), off_work = off_ep + align256(4 * N);
+    const size_t off_ep = align256(nx_bytes), off_count = off_ep + align256(4 * N);
+    const size_t off_work = off_count + 256;
     if (cudaMalloc(&env->nx_mem, off_work + stride * N) == cudaSuccess &&
         cudaMemset(env->nx_mem + off_ep, 0xFF, 4 * N) == cudaSuccess) {
       auto nx = [&](int f) { return env->nx_mem + env->field_off[f]; };
@@ -446,6 +447,11 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
       p.nx_work = env->nx_mem + off_work;
       p.nx_work_stride = stride;
       p.nx_lanes = (int32_t)N;
+      p.nx_count = reinterpret_cast<uint32_t*>(env->nx_mem + off_count);
+      // one lane builds a maze in about three times a warp's time: ahead of
+      // the launch pays once a launch would start mazes on about three times
+      // as many envs as there are resident warps
+      p.nx_min = 3 * env->num_sms * jx::kMinBlocksPerSm;
     } else {
       if (env->nx_mem) cudaFree(env->nx_mem);
       env->nx_mem = nullptr;

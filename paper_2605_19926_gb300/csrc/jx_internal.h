@@ -80,6 +80,11 @@ struct Params {
   uint8_t* nx_work;
   size_t nx_work_stride;
   int32_t nx_lanes;
+  // the envs that need a pre-built episode are counted first; they are built
+  // ahead only when at least nx_min of them do (fewer are faster built where
+  // they start: one lane's build takes longer than a warp's)
+  uint32_t* nx_count;
+  int32_t nx_min;
   const uint8_t* actions;
   uint8_t* frames;
   float* rewards;

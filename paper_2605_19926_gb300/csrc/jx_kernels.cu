@@ -22,23 +22,36 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   if (lane == 0) bulk_wait_read_all();
 }
 
+// Whether env e needs a pre-built episode, and which: the one it starts
+// within the next `steps` steps (its horizon falls in them) or, for a reset,
+// episode 0, unless the next-episode block holds it already.
+__device__ __forceinline__ bool pregen_need(const Params& p, int e, int steps, int reset, uint32_t& ep) {
+  if (reset) {
+    ep = 0;
+    return p.nx_ep[e] != 0u;
+  }
+  ep = p.st.episode[e] + 1;
+  return p.horizon > 0 && p.st.t[e] + steps >= p.horizon && p.nx_ep[e] != ep;
+}
+
+// Counts the envs that need a pre-built episode into *p.nx_count (zeroed before).
+__global__ void __launch_bounds__(128) pregen_count_kernel(const __grid_constant__ Params p, int steps, int reset) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t ep;
+  const bool need = e < p.n && pregen_need(p, e, steps, reset, ep);
+  const uint32_t b = __ballot_sync(0xffffffffu, need);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.nx_count, (uint32_t)__popc(b));
+}
+
 // Lane-parallel pre-generation: lane i builds, for envs i, i + lanes, ...,
-// the episode each will start within the next `steps` steps (its horizon
-// falls in them) or, for a reset, episode 0, unless the block holds it already.
+// the episode each needs, when at least nx_min envs need one.
 __global__ void __launch_bounds__(128) pregen_kernel(const __grid_constant__ Params p, int steps, int reset) {
   const int lane_id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (lane_id >= p.nx_lanes) return;
+  if (lane_id >= p.nx_lanes || *p.nx_count < (uint32_t)p.nx_min) return;
   uint8_t* work = p.nx_work + (size_t)lane_id * p.nx_work_stride;
   for (int e = lane_id; e < p.n; e += p.nx_lanes) {
-    uint32_t ep = 0;
-    bool need;
-    if (reset) {
-      need = p.nx_ep[e] != 0u;
-    } else {
-      ep = p.st.episode[e] + 1;
-      need = p.horizon > 0 && p.st.t[e] + steps >= p.horizon && p.nx_ep[e] != ep;
-    }
-    if (need) {
+    uint32_t ep;
+    if (pregen_need(p, e, steps, reset, ep)) {
       gen_maze_lane(p, e, ep, work);
       p.nx_ep[e] = ep;
     }
@@ -108,6 +121,9 @@ size_t pregen_work_bytes(int S) {
 
 cudaError_t pregen_launch(const Params& p, int steps, bool reset, cudaStream_t stream) {
   if (p.nx_ep == nullptr || p.nx_lanes <= 0) return cudaSuccess;
+  cudaError_t err = cudaMemsetAsync(p.nx_count, 0, sizeof(uint32_t), stream);
+  if (err != cudaSuccess) return err;
+  pregen_count_kernel<<<(p.n + 127) / 128, 128, 0, stream>>>(p, steps, reset ? 1 : 0);
   pregen_kernel<<<(p.nx_lanes + 127) / 128, 128, 0, stream>>>(p, steps, reset ? 1 : 0);
   return cudaGetLastError();
 }

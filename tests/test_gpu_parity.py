@@ -387,6 +387,48 @@ def test_large_scale_mazes_with_rooms_sampled():
     stats.check()
 
 
+def test_pregenerated_episodes_equal_episodes_built_in_place():
+    """Mazes of side >= 64 in batches large enough are built ahead by one lane
+    per env (the next episode of every env whose horizon falls in the launch,
+    and episode 0 at a reset); small batches build them in place, one warp per
+    env. A maze depends only on (seed, env, episode), so envs 0..63 of a
+    16,384-env batch and of a 64-env batch must hold the same state and give
+    the same frames, rewards and dones: at the reset, and over a rollout that
+    crosses the horizon (every env starts episode 1 at step 5)."""
+    big_cfg = inputs.maze_rooms(n_envs=16384, map_side=64, seed=21, horizon=5, max_sprites=8, frame_h=32,
+                                frame_w=32, gray_stack=0)
+    small_cfg = dict(big_cfg, n_envs=64)
+    big, small = Run(big_cfg), Run(small_cfg)
+    big.reset()
+    small.reset()
+    assert torch.equal(big.frames[:64], small.frames)
+
+    def same_state():
+        fb, fs = big.env.fields(big.env.get_state()), small.env.fields(small.env.get_state())
+        for name, a in fs.items():
+            if name != "gray":
+                assert (fb[name][:64] == a).all(), name
+
+    same_state()
+    T = 8
+    acts = torch.from_numpy(inputs.action_stream(22, T, 16384)).to(big.dev)
+    outs = []
+    for run, n, a in ((big, 16384, acts), (small, 64, acts[:, :64].contiguous())):
+        frames = torch.empty((T, n, 32, 32, 3), dtype=torch.uint8, device=run.dev)
+        rewards = torch.empty((T, n), dtype=torch.float32, device=run.dev)
+        dones = torch.empty((T, n), dtype=torch.uint8, device=run.dev)
+        run.env.rollout(a, frames, rewards, dones)
+        torch.cuda.synchronize()
+        outs.append((frames, rewards, dones))
+    (fb, rb, db), (fs, rs, ds) = outs
+    assert int(ds.sum().item()) >= 64  # every env ended its episode (at the horizon, if not before)
+    assert torch.equal(fb[:, :64], fs) and torch.equal(rb[:, :64], rs) and torch.equal(db[:, :64], ds)
+    same_state()
+    assert (big.env.fields(big.env.get_state())["episode"] >= 1).all()
+    big.env.sync_status()
+    small.env.sync_status()
+
+
 def _corridor(text, n=8):
     cfg = dict(inputs.ascii_env("simple", n_envs=n, map_side=16, horizon=0), ascii_map=text)
     run = Run(cfg)
