@@ -132,7 +132,13 @@ typedef struct {
 /* Create N environments on CUDA device `device` and allocate their state in
  * its memory (no episode is generated yet: call jx_reset). The config is
  * validated before any CUDA call, so JX_EINVAL needs no GPU. *out receives
- * the handle, owned by the caller until jx_destroy. */
+ * the handle, owned by the caller until jx_destroy.
+ * Maze tasks (JX_TASK_MAZE_KEYDOOR, JX_TASK_MAZE_ROOMS) with map_side >= 64
+ * and a multiple of 4 also reserve a next-episode block (the state without
+ * the grayscale stack, plus 6 bytes per maze node per env of work space):
+ * when a launch starts episodes on many envs at once, one lane per env builds
+ * them ahead there. Without that memory the env works as for other configs.
+ * Results do not depend on it. */
 jx_status jx_create(const jx_config* cfg, int device, jx_env** out);
 
 /* jx_create for the ASCII task (cfg->task == JX_TASK_ASCII): the map is the
