@@ -159,7 +159,7 @@ jx_status run(jx_env* env, const jx::Params& p, int mode, void* stream) {
   if (p.nx_ep && (mode == jx::MODE_STEP || mode == jx::MODE_ROLLOUT || mode == jx::MODE_RESET)) {
     cudaError_t err = jx::pregen_launch(p, mode == jx::MODE_ROLLOUT ? p.steps : 1, mode == jx::MODE_RESET, s);
     if (err != cudaSuccess) return cuda_fail(err, "pre-generation launch");
-    env->launches.fetch_add(1, std::memory_order_relaxed);
+    env->launches.fetch_add(jx::kPregenKernels, std::memory_order_relaxed);
   }
   cudaError_t err = jx::launch(p, mode, env->grid, s);
   if (err != cudaSuccess) return cuda_fail(err, "kernel launch");

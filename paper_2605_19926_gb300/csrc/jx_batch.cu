@@ -144,7 +144,7 @@ jx_status batch_run(jx_batch* b, int mode, cudaStream_t stream, const uint8_t* a
       if (!bp.g[i].nx_ep) continue;
       cudaError_t err = jx::pregen_launch(bp.g[i], mode == jx::MODE_ROLLOUT ? steps : 1, mode == jx::MODE_RESET, stream);
       if (err != cudaSuccess) return cuda_fail(err, "pre-generation launch");
-      if (count) b->launches.fetch_add(1, std::memory_order_relaxed);
+      if (count) b->launches.fetch_add(jx::kPregenKernels, std::memory_order_relaxed);
     }
   }
   cudaError_t err = jx::batch_launch(bp, mode, b->tiling.cols_per_lane, b->tiling.warps_per_block, b->grid[mode],

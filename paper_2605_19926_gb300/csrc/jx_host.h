@@ -45,6 +45,10 @@ struct jx_env {
 };
 
 namespace jx {
+
+// kernels one pregen_launch launches: the count and the build
+constexpr int kPregenKernels = 2;
+
 namespace host {
 
 extern thread_local std::string g_last_error;
