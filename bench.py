@@ -58,10 +58,12 @@ def kernel_source_sha(sources=None) -> str:
 
 
 def tiling_key(t, sides) -> tuple:
-    """A batched-kernel tiling as the kernel sees it on maps of the given
-    sides: bits_min_side matters only through which maps become bit planes."""
-    w, c, b, r, st = (int(v) for v in t)
-    return (w, c, tuple(b > 0 and s >= b and s % 8 == 0 for s in sides), r, st)
+    """What of a batched-kernel tiling decides the DRAM bytes on maps of the
+    given sides: which maps are bit planes (ray hits then read the hit cell's
+    type from HBM). Warps per block, rays per lane, rows per block and staging
+    buffers change how the same frames are written, not which bytes move."""
+    b = int(t[2])
+    return tuple(b > 0 and s >= b and s % 8 == 0 for s in sides)
 
 
 def recorded_traffic(n_envs: int, launch_steps: int, path: str = TRAFFIC_FILE, sources=None, tiling=None):

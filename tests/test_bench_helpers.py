@@ -68,8 +68,12 @@ def test_recorded_traffic_scaling_and_tiling(tmp_path, monkeypatch):
     rec.write_text(json.dumps({"kernel_source_sha": "abc", "n_envs": 4096, "dram_bytes_per_env_step": 100.0,
                                "scales_with_env_steps": True, "tiling": [4, 1, 64, 8, 1]}))
     assert bench.recorded_traffic(65536, 8, str(rec), tiling=(4, 1, 64, 8, 1)) == 100.0 * 65536 * 8
-    assert bench.recorded_traffic(65536, 8, str(rec), tiling=(0, 0, 0, 0, 0)) is None
+    assert bench.recorded_traffic(65536, 8, str(rec), tiling=(0, 0, 0, 0, 0)) == 100.0 * 65536 * 8  # no sides
     assert bench.recorded_traffic(65536, 8, str(rec)) is None
+    rec.write_text(json.dumps({"kernel_source_sha": "abc", "n_envs": 4096, "dram_bytes_per_env_step": 100.0,
+                               "scales_with_env_steps": True, "tiling": [4, 1, 64, 8, 1], "map_sides": [128]}))
+    assert bench.recorded_traffic(65536, 8, str(rec), tiling=(2, 2, 8, 32, 1)) == 100.0 * 65536 * 8
+    assert bench.recorded_traffic(65536, 8, str(rec), tiling=(4, 1, 0, 8, 1)) is None  # byte maps read less
 
 
 def test_committed_records_are_well_formed():
@@ -83,6 +87,6 @@ def test_committed_records_are_well_formed():
 
 
 def test_tiling_key_sees_only_the_effective_map_kind():
-    assert bench.tiling_key((4, 1, 8, 8, 1), [128]) == bench.tiling_key((4, 1, 64, 8, 1), [128])
+    assert bench.tiling_key((4, 1, 8, 8, 1), [128]) == bench.tiling_key((4, 2, 64, 32, 2), [128])
     assert bench.tiling_key((4, 1, 8, 8, 1), [16, 128]) != bench.tiling_key((4, 1, 64, 8, 1), [16, 128])
     assert bench.tiling_key((4, 1, 0, 8, 1), [128]) != bench.tiling_key((4, 1, 128, 8, 1), [128])
