@@ -1,5 +1,6 @@
-// jx_kernels.cu — the env kernel (one env config per launch) and its host
-// side: launch shape queries, launches, the per-warp shared memory layout.
+// jx_kernels.cu — the env kernel (one env config per launch), the kernels
+// that build next episodes ahead (a count, then one lane per env), and their
+// host side: launch shape queries, launches, the per-warp shared memory layout.
 #include "jx_device.cuh"
 
 namespace jx {
