@@ -279,7 +279,11 @@ jx_status jx_set_state(jx_env* env, const void* h_buf, size_t bytes);
  * JX_EDEVICE when a kernel recorded bad data since the last call. */
 jx_status jx_sync_status(jx_env* env, void* stream);
 
-/* Number of kernel launches this env has issued since creation. */
+/* Number of kernel launches this env has issued since creation. For maze
+ * configs with a next-episode block (see jx_create), jx_reset, jx_step and
+ * jx_rollout each also launch the two kernels that build episodes ahead (a
+ * count, then the build, after a 4-byte cudaMemsetAsync on the same stream;
+ * all capturable in a CUDA graph). */
 jx_status jx_launch_count(const jx_env* env, uint64_t* count);
 
 /* Launch shape of the fused step kernel: grid blocks, threads per block,
