@@ -1,26 +1,38 @@
 """Benchmark: batched env step + render (frames/s) on GB300.
 
-Workload: 4096 envs, 32 x 32 random DFS key-door mazes, 64 x 64 RGB frames,
-horizon 500 with auto-reset, 10,000 steps of uniform random actions (seed 1).
-A step moves, collides, picks up, rewards, resets and renders all envs. The
-timed path runs the pre-drawn action stream through jx_rollout, 128 steps per
-launch; every step writes its frames into slot (step mod 128) of a 6.4 GB
-rollout buffer, so the frame stream never fits the 126 MB L2 and every byte
-goes to HBM. The single-step entry point (jx_step, CUDA graph of 128
-launches) is timed on the same workload beside it, and its per-call latency
-gives p50 / p99.
+Headline workload: 4096 envs, 32 x 32 random DFS key-door mazes, 64 x 64 RGB
+frames, horizon 500 with auto-reset, uniform random actions (seed 1; the
+paper times its environments under a uniform random policy, App. A.1). A step
+moves, collides, picks up, rewards, resets and renders all envs.
 
-Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle on the
-same workload instead (the method's only other implementation here).
+The timed region runs `--steps` steps of the pre-drawn action stream through
+jx_rollout, at most `--ring-slots` steps per launch; step s writes its frames
+into slot (s mod ring) of a rollout buffer of at least four slots (>= 200 MB,
+more than the 126 MB L2), so consecutive steps never reuse L2 lines. Beside
+it, on the same workload:
+  - per_step_launch: jx_step, one launch per step, as a CUDA graph of `ring`
+    launches replayed (the entry point an RL loop that reads each frame
+    before choosing the next action calls);
+  - p50 / p99: per-call latency of jx_step with a host sync after each call;
+  - e2e: jx_step_host with pinned host buffers (actions in, frames, rewards
+    and dones out, every step);
+  - plain_one_env_per_launch: 1 env of 16 x 16 rooms, one jx_step per step;
+  - cpu_baseline: the FP64 oracle on the host cores (all, and one);
+  - uneven, large, serve: bounded runs of the uneven batch, the large-scale
+    workload and the serving loop, each with its own numbers.
+
+Prints one JSON line. ``--workload uneven|large|serve`` runs only that
+workload at full length. ``--impl reference`` times the FP64 CPU oracle on
+the headline workload instead (the method's only other implementation here).
 """
 
 from __future__ import annotations
 
 import argparse
 import hashlib
-import re
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -32,7 +44,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "env-steps/s incl. render (frames/s) at 64x64 RGB"
-GRAPH_STEPS = 128  # default launches per CUDA graph = rollout buffer slots
+GRAPH_STEPS = 128  # default rollout buffer slots = steps per rollout launch = launches per CUDA graph
+MIN_RING = 4  # rollout buffer slots at least: 4 x 50 MB frames > L2
+GRAPH_MIN_STEPS = 128  # the per-step graph leg replays at least this many steps (at most 16 replays)
 KERNEL_SOURCES = ["paper_2605_19926_gb300/csrc/jx_device.cuh", "paper_2605_19926_gb300/csrc/jx_kernels.cu",
                   "paper_2605_19926_gb300/csrc/jx_internal.h"]
 BATCH_KERNEL_SOURCES = ["paper_2605_19926_gb300/csrc/jx_device.cuh", "paper_2605_19926_gb300/csrc/jx_batch_kernels.cu",
@@ -66,12 +80,11 @@ def tiling_key(t, sides) -> tuple:
     return tuple(b > 0 and s >= b and s % 8 == 0 for s in sides)
 
 
-def recorded_traffic(n_envs: int, launch_steps: int, path: str = TRAFFIC_FILE, sources=None, tiling=None):
-    """DRAM bytes of one launch from the ncu record, scaled from the captured
-    launch by the env-steps processed; None when the record is missing, was
-    taken on other kernel code or another batched-kernel tiling, or is for
-    another env count without saying that its traffic grows in proportion to
-    the env-steps."""
+def recorded_traffic_per_env_step(n_envs: int, path: str = TRAFFIC_FILE, sources=None, tiling=None):
+    """DRAM bytes per env-step from the ncu record; None when the record is
+    missing, was taken on other kernel code or another batched-kernel tiling,
+    or is for another env count without saying that its traffic grows in
+    proportion to the env-steps."""
     if not os.path.exists(path):
         return None
     tf = json.load(open(path))
@@ -83,7 +96,14 @@ def recorded_traffic(n_envs: int, launch_steps: int, path: str = TRAFFIC_FILE, s
             return None
     if tf.get("n_envs") != n_envs and not tf.get("scales_with_env_steps"):
         return None
-    return tf["dram_bytes_per_env_step"] * n_envs * launch_steps
+    return float(tf["dram_bytes_per_env_step"])
+
+
+def recorded_traffic(n_envs: int, launch_steps: int, path: str = TRAFFIC_FILE, sources=None, tiling=None):
+    """DRAM bytes of one launch of `launch_steps` steps from the ncu record
+    (scaled from the captured launch by the env-steps processed), or None."""
+    b = recorded_traffic_per_env_step(n_envs, path, sources, tiling)
+    return None if b is None else b * n_envs * launch_steps
 
 
 def dist_env():
@@ -138,12 +158,68 @@ def rollout_bytes(cfg: dict, n_envs: int, steps: int) -> int:
     return n_envs * steps * (3 * H * W + STEP_IO) + n_envs * (STATE_READ + 9 * K + STATE_WRITE)
 
 
+class Plan:
+    """Index arithmetic of the headline run, for any --steps / --warmup.
+
+    The action stream holds warmup + steps rows: rows [0, warmup) drive the
+    untimed warm-up, rows [warmup, warmup + steps) the timed rollout launches.
+    The rollout buffer has `ring` slots; the timed launches cover the steps in
+    order, `ring` steps each and a shorter last one. Legs after the timed
+    region read the stream at wrapped row indices (modulo its length)."""
+
+    def __init__(self, steps: int, warmup: int, ring_slots: int):
+        if steps < 1 or warmup < 0 or ring_slots < 1:
+            raise ValueError(f"steps >= 1, warmup >= 0, ring_slots >= 1 (got {steps}, {warmup}, {ring_slots})")
+        self.steps, self.warmup = steps, warmup
+        self.ring = min(ring_slots, max(steps, MIN_RING))
+        self.stream_len = warmup + steps
+        self.launches = [(warmup + k * self.ring, min(self.ring, steps - k * self.ring))
+                         for k in range(-(-steps // self.ring))]
+        self.n_graph = max(1, min(16, -(-GRAPH_MIN_STEPS // self.ring)))
+
+    def warmup_slot(self, s: int) -> int:
+        return s % self.ring
+
+    def wrapped(self, first: int, count: int) -> list[int]:
+        """Rows first, first + 1, ... of the action stream, wrapped to its length."""
+        return [(first + i) % self.stream_len for i in range(count)]
+
+    def graph_rows(self, c: int) -> list[int]:
+        """Action rows of the c-th replay of the per-step graph (it continues the stream after the timed steps)."""
+        return self.wrapped(self.warmup + self.steps + c * self.ring, self.ring)
+
+
+def roofline(bytes_total: float, ms: float, peak: float, peak_src: str, **extra) -> dict:
+    """HBM roofline of a timed region: algorithmic bytes over the region's time."""
+    achieved = bytes_total / (ms / 1e3) / 1e9
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
+    out.update(extra)
+    return out
+
+
+def measured_peak() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def percentile(xs, q: float):
+    if not len(xs):
+        return None
+    s = sorted(xs)
+    return s[min(len(s) - 1, int(q * len(s)))]
+
+
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling while the GPU works. The median
+    SM clock is taken over the samples with the GPU busy (utilisation >= 50%),
+    over all samples when none is."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, device_index: int):
         self.dev = device_index
@@ -157,6 +233,32 @@ class ClockSampler:
         except OSError:
             self.proc = None
 
+    @staticmethod
+    def summarise(text: str) -> dict | None:
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
+        for line in text.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm, mx = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            try:
+                util = float(parts[9]) if len(parts) > 9 else None
+            except ValueError:
+                util = None
+            reasons = {n for n, v in zip(names, parts[5:9]) if v.lower() == "active"}
+            rows.append((sm, mx, util, reasons))
+        if not rows:
+            return None
+        busy = [r for r in rows if r[2] is not None and r[2] >= 50.0]
+        use = busy or rows
+        reasons = set().union(*(r[3] for r in use))
+        return {"sm_mhz": statistics.median(r[0] for r in use), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(busy)}
+
     def stop(self) -> dict | None:
         if self.proc is None:
             return None
@@ -166,23 +268,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = max(mx, float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return self.summarise(out)
 
 
 def time_oracle(cfg: dict, n_envs: int, n_steps: int, seed: int, nthreads: int) -> tuple[float, int]:
@@ -224,15 +310,14 @@ def run_reference(args, cfg: dict):
     time_oracle(cfg, n_envs, args.warmup, seed=cfg["seed"], nthreads=cores)
     value, used = time_oracle(cfg, n_envs, args.steps, seed=cfg["seed"], nthreads=cores)
     t_total = n_envs * args.steps / value  # the timed stepping, as in `value`
-    steps_total = args.steps
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": args.gpus,
-        "steps": steps_total, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / steps_total,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "4096 envs, 32x32 DFS key-door mazes, 64x64 RGB, horizon 500, random actions",
                    "sample_envs": n_envs},
         "cpu_baseline": {"value": value, "unit": "env-steps/s", "cores": used, "kind": "oracle",
-                         "sample": f"{n_envs} envs x {steps_total} steps of the workload (frames rendered)"},
+                         "sample": f"{n_envs} envs x {args.steps} steps of the workload (frames rendered)"},
         "e2e": {"value": value, "unit": "env-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -246,136 +331,6 @@ def tiling_dict(t) -> dict:
     return d
 
 
-def uneven_bytes_per_env_step(groups: list) -> float:
-    """Mean compulsory HBM bytes per env-step of an uneven batch (as for one env group)."""
-    tot = sum(g["n_envs"] * algorithmic_bytes_per_env_step(g) for g in groups)
-    return tot / sum(g["n_envs"] for g in groups)
-
-
-def run_uneven(args):
-    """Uneven batching: 16,384 envs of 16 (map side, frame size) groups in one
-    persistent launch per rollout; fixed tiles against autotuned tiles, and the
-    autotuned step sequence replayed as a CUDA graph."""
-    import torch
-
-    from paper_2605_19926_gb300 import build, inputs
-
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    if rank == 0:
-        build.build()
-    if world > 1:
-        torch.distributed.barrier()
-    from paper_2605_19926_gb300 import jx
-
-    groups = inputs.uneven_groups(n_envs=args.uneven_envs, seed=2 + rank)
-    envs = [jx.Env(c, local) for c in groups]
-    pinned = parse_tiling(jx, args.tiling)
-    batch = jx.Batch(envs, pinned)
-    N, F = batch.n, batch.frame_bytes
-    dev = torch.device("cuda", local)
-    T = args.uneven_slots
-    K = max(T, (args.steps // T) * T)
-    acts = torch.from_numpy(inputs.action_stream(7 + rank, K + T, N)).to(dev)
-    frames = torch.empty((T, F), dtype=torch.uint8, device=dev)  # T x 0.38 GB > L2
-    rewards = torch.empty((T, N), dtype=torch.float32, device=dev)
-    dones = torch.empty((T, N), dtype=torch.uint8, device=dev)
-    stream = torch.cuda.Stream(device=dev)
-
-    def timed_rollouts() -> tuple[float, int]:
-        with torch.cuda.stream(stream):
-            batch.reset(frames[0], stream)
-            batch.rollout(acts[:T], frames, rewards, dones, stream)  # warm-up
-        stream.synchronize()
-        n0 = batch.launch_count()
-        if world > 1:
-            torch.distributed.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            for c in range(K // T):
-                batch.rollout(acts[T + c * T: T + (c + 1) * T], frames, rewards, dones, stream)
-            e1.record(stream)
-        stream.synchronize()
-        return max_over_ranks(e0.elapsed_time(e1), world, dev), batch.launch_count() - n0
-
-    fixed_ms, _ = timed_rollouts()
-    fixed_tiling = batch.tiling
-    t_tune = time.perf_counter()
-    trials = [] if pinned is not None else batch.autotune(mode=1, steps=T, max_trials=args.tune_trials,
-                                                          stream=stream)
-    tune_s = time.perf_counter() - t_tune
-    tuned = batch.tiling
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    tuned_ms, launches = timed_rollouts()
-    clk = clocks.stop()
-    # the same steps as a CUDA graph of T single-step launches, replayed
-    graph = batch.capture(acts[T: 2 * T], frames, rewards, dones)
-    with torch.cuda.stream(stream):
-        batch.reset(frames[0], stream)
-        graph.launch(stream)
-    stream.synchronize()
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        g0.record(stream)
-        for c in range(K // T):
-            graph.launch(stream)
-        g1.record(stream)
-    stream.synchronize()
-    graph_ms = max_over_ranks(g0.elapsed_time(g1), world, dev)
-    graph.close()
-    if rank != 0:
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return
-    bpes = uneven_bytes_per_env_step(groups)
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peak, peak_src = 6800.0, "fallback"
-    if os.path.exists(peaks_path):
-        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
-
-    def leg(ms, tiling):
-        v = world * N * K / (ms / 1e3)
-        gbs = N * K * bpes / (ms / 1e3) / 1e9 / world
-        return {"value": v, "ms_per_step": ms / K, "achieved_gbs": gbs, "frac": gbs / peak,
-                "tiling": tiling_dict(tiling)}
-
-    shape = batch.launch_shape()
-    tuned_leg = leg(tuned_ms, tuned)
-    line = {
-        "metric": "env-steps/s incl. render (frames/s), uneven batch", "value": tuned_leg["value"],
-        "unit": "env-steps/s", "n_gpus": world, "steps": K, "warmup": T, "ms_per_step": tuned_ms / K,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": f"{N:,} envs per GPU, random-wall rooms p=0.3, map side uniform in {{16,32,64,128}}, "
-                               "square RGB frames uniform in {32,64,96,128}, 0-8 sprites, uniform random actions",
-                   "groups": len(groups), "n_envs_per_gpu": N, "frame_bytes_per_step": F,
-                   "parallelism": f"replicas x{world}",
-                   "l2": f"frames written to a {T}-slot rollout buffer ({T * F / 1e9:.1f} GB) > L2",
-                   "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
-                              "entry": "jx_batch_rollout", "steps_per_launch": T}},
-        "roofline": {"bound": "hbm", "achieved": tuned_leg["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": tuned_leg["frac"],
-                     "traffic": recorded_traffic(N, T, TRAFFIC_UNEVEN_FILE, BATCH_KERNEL_SOURCES,
-                                                 tuned.as_tuple()),
-                     "peak_source": peak_src,
-                     "algorithmic_bytes_per_env_step": bpes},
-        "fixed_tiles": leg(fixed_ms, fixed_tiling), "autotuned": tuned_leg,
-        "autotune": {"trials": len(trials), "seconds": tune_s, "mode": "rollout", "steps_per_trial": T},
-        "graph_steps": {"value": world * N * K / (graph_ms / 1e3), "ms_per_step": graph_ms / K,
-                        "how": f"jx_batch_capture of {T} jx_batch_step launches, replayed"},
-        "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
-
-
 def parse_tiling(jx, text: str):
     """`w,c,b,r[,s]` -> a jx.Tiling (staging buffers default to 1), or None for ''."""
     if not text:
@@ -386,172 +341,282 @@ def parse_tiling(jx, text: str):
     return t
 
 
-def run_large(args):
-    """Large scale: 65,536 envs of 128 x 128 mazes with 8 x 8 rooms, 16 sprite
+def uneven_bytes_per_env_step(groups: list) -> float:
+    """Mean compulsory HBM bytes per env-step of an uneven batch (as for one env group)."""
+    tot = sum(g["n_envs"] * algorithmic_bytes_per_env_step(g) for g in groups)
+    return tot / sum(g["n_envs"] for g in groups)
+
+
+class Gpu:
+    """The process's device context: rank, world, device, the built library."""
+
+    def __init__(self):
+        import torch
+
+        self.torch = torch
+        self.rank, self.world, self.local = dist_env()
+        if self.world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        torch.cuda.set_device(self.local)
+        from paper_2605_19926_gb300 import build
+
+        if self.rank == 0:
+            build.build()
+        if self.world > 1:
+            torch.distributed.barrier()
+        from paper_2605_19926_gb300 import jx
+
+        self.jx = jx
+        self.dev = torch.device("cuda", self.local)
+
+    def barrier(self):
+        if self.world > 1:
+            self.torch.distributed.barrier()
+
+    def close(self):
+        if self.world > 1:
+            self.torch.distributed.destroy_process_group()
+
+    def events(self):
+        return (self.torch.cuda.Event(enable_timing=True), self.torch.cuda.Event(enable_timing=True))
+
+
+def uneven_record(g: Gpu, n_envs: int, slots: int, steps: int, tiling_text: str, tune_trials: int) -> dict | None:
+    """Uneven batching: n_envs envs of 16 (map side, frame size) groups in one
+    persistent launch per rollout of `slots` steps; fixed tiles against
+    autotuned tiles, and the autotuned step sequence replayed as a CUDA graph
+    of `slots` single-step launches. Returns rank 0's record."""
+    torch, jx = g.torch, g.jx
+    from paper_2605_19926_gb300 import inputs
+
+    groups = inputs.uneven_groups(n_envs=n_envs, seed=2 + g.rank)
+    envs = [jx.Env(c, g.local) for c in groups]
+    pinned = parse_tiling(jx, tiling_text)
+    batch = jx.Batch(envs, pinned)
+    N, F = batch.n, batch.frame_bytes
+    T = slots
+    K = max(T, (steps // T) * T)
+    acts = torch.from_numpy(inputs.action_stream(7 + g.rank, K + T, N)).to(g.dev)
+    frames = torch.empty((T, F), dtype=torch.uint8, device=g.dev)  # T x 0.38 GB > L2
+    rewards = torch.empty((T, N), dtype=torch.float32, device=g.dev)
+    dones = torch.empty((T, N), dtype=torch.uint8, device=g.dev)
+    stream = torch.cuda.Stream(device=g.dev)
+
+    def timed_rollouts() -> tuple[float, int]:
+        with torch.cuda.stream(stream):
+            batch.reset(frames[0], stream)
+            batch.rollout(acts[:T], frames, rewards, dones, stream)  # warm-up
+        stream.synchronize()
+        n0 = batch.launch_count()
+        g.barrier()
+        e0, e1 = g.events()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for c in range(K // T):
+                batch.rollout(acts[T + c * T: T + (c + 1) * T], frames, rewards, dones, stream)
+            e1.record(stream)
+        stream.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1), g.world, g.dev), batch.launch_count() - n0
+
+    fixed_ms, _ = timed_rollouts()
+    fixed_tiling = batch.tiling
+    t_tune = time.perf_counter()
+    trials = [] if pinned is not None else batch.autotune(mode=1, steps=T, max_trials=tune_trials, stream=stream)
+    tune_s = time.perf_counter() - t_tune
+    tuned = batch.tiling
+    tuned_ms, launches = timed_rollouts()
+    # the same steps as a CUDA graph of T single-step launches, replayed
+    graph = batch.capture(acts[T: 2 * T], frames, rewards, dones)
+    with torch.cuda.stream(stream):
+        batch.reset(frames[0], stream)
+        graph.launch(stream)
+    stream.synchronize()
+    g0, g1 = g.events()
+    with torch.cuda.stream(stream):
+        g0.record(stream)
+        for c in range(K // T):
+            graph.launch(stream)
+        g1.record(stream)
+    stream.synchronize()
+    graph_ms = max_over_ranks(g0.elapsed_time(g1), g.world, g.dev)
+    graph.close()
+    shape = batch.launch_shape()
+    batch.close()
+    for e in envs:
+        e.close()
+    del frames, rewards, dones, acts
+    if g.rank != 0:
+        return None
+    bpes = uneven_bytes_per_env_step(groups)
+    peak, peak_src = measured_peak()
+
+    def leg(ms, tiling):
+        v = g.world * N * K / (ms / 1e3)
+        gbs = N * K * bpes / (ms / 1e3) / 1e9
+        return {"value": v, "ms_per_step": ms / K, "achieved_gbs": gbs, "frac": gbs / peak,
+                "tiling": tiling_dict(tiling)}
+
+    tuned_leg = leg(tuned_ms, tuned)
+    per_es = recorded_traffic_per_env_step(N, TRAFFIC_UNEVEN_FILE, BATCH_KERNEL_SOURCES, tuned.as_tuple())
+    return {
+        "metric": "env-steps/s incl. render (frames/s), uneven batch", "value": tuned_leg["value"],
+        "unit": "env-steps/s", "n_gpus": g.world, "steps": K, "warmup": T, "ms_per_step": tuned_ms / K,
+        "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{N:,} envs per GPU, random-wall rooms p=0.3, map side uniform in {{16,32,64,128}}, "
+                               "square RGB frames uniform in {32,64,96,128}, 0-8 sprites, uniform random actions",
+                   "groups": len(groups), "n_envs_per_gpu": N, "frame_bytes_per_step": F,
+                   "l2": f"frames written to a {T}-slot rollout buffer ({T * F / 1e9:.1f} GB) > L2",
+                   "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
+                              "entry": "jx_batch_rollout", "steps_per_launch": T}},
+        "roofline": roofline(N * K * bpes, tuned_ms, peak, peak_src,
+                             traffic=None if per_es is None else per_es * N * T,
+                             traffic_unit="DRAM bytes per launch (ncu record, scaled by env-steps)",
+                             algorithmic_bytes_per_env_step=bpes),
+        "fixed_tiles": leg(fixed_ms, fixed_tiling), "autotuned": tuned_leg,
+        "autotune": {"trials": len(trials), "seconds": tune_s, "mode": "rollout", "steps_per_trial": T},
+        "graph_steps": {"value": g.world * N * K / (graph_ms / 1e3), "ms_per_step": graph_ms / K,
+                        "how": f"jx_batch_capture of {T} jx_batch_step launches, replayed"},
+        "gpu_launches": launches,
+    }
+
+
+def large_record(g: Gpu, n_envs: int, slots: int, steps: int, tiling_text: str, tune_trials: int) -> dict | None:
+    """Large scale: n_envs envs of 128 x 128 mazes with 8 x 8 rooms, 16 sprite
     slots, 128 x 128 RGB frames plus the 4-frame grayscale stack written in the
-    same pass, horizon 500, `--steps` (1000) steps of uniform random actions in
-    rollout launches of `--large-slots` steps."""
-    import torch
+    same pass, horizon 500, `steps` steps of uniform random actions in rollout
+    launches of `slots` steps, from a fresh reset (so a run of >= 500 steps
+    crosses the horizon: every env starts its next episode in one launch)."""
+    torch, jx = g.torch, g.jx
+    from paper_2605_19926_gb300 import inputs
 
-    from paper_2605_19926_gb300 import build, inputs
-
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    if rank == 0:
-        build.build()
-    if world > 1:
-        torch.distributed.barrier()
-    from paper_2605_19926_gb300 import jx
-
-    cfg = shard_config(inputs.large_scale(args.large_envs), rank)
+    cfg = shard_config(inputs.large_scale(n_envs), g.rank)
     N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
-    dev = torch.device("cuda", local)
-    env = jx.Env(cfg, local)
+    env = jx.Env(cfg, g.local)
     tuned = None
-    if args.tiling:
-        env.tiling = parse_tiling(jx, args.tiling)  # the batched kernel with this tiling
-    elif not args.no_autotune:
+    if tiling_text:
+        env.tiling = parse_tiling(jx, tiling_text)  # the batched kernel with this tiling
+    elif tune_trials > 0:
         # the env's own kernel against the batched kernel's tilings, before timing
-        tuned = env.autotune(mode=1, steps=args.large_slots, max_trials=args.tune_trials)
-    T = args.large_slots
-    K = max(T, (args.steps // T) * T)
-    acts = torch.from_numpy(inputs.action_stream(cfg["seed"], K + T, N)).to(dev)
-    frames = torch.empty((T, N, H, W, 3), dtype=torch.uint8, device=dev)
-    rewards = torch.empty((T, N), dtype=torch.float32, device=dev)
-    dones = torch.empty((T, N), dtype=torch.uint8, device=dev)
-    stream = torch.cuda.Stream(device=dev)
+        tuned = env.autotune(mode=1, steps=slots, max_trials=tune_trials)
+    T = slots
+    K = max(T, (steps // T) * T)
+    acts = torch.from_numpy(inputs.action_stream(cfg["seed"], K, N)).to(g.dev)
+    frames = torch.empty((T, N, H, W, 3), dtype=torch.uint8, device=g.dev)
+    rewards = torch.empty((K, N), dtype=torch.float32, device=g.dev)
+    dones = torch.empty((K, N), dtype=torch.uint8, device=g.dev)
+    stream = torch.cuda.Stream(device=g.dev)
     t_reset = time.perf_counter()
     with torch.cuda.stream(stream):
         env.reset(frames[0], stream)
     stream.synchronize()
     reset_s = time.perf_counter() - t_reset
-    with torch.cuda.stream(stream):
-        env.rollout(acts[:T], frames, rewards, dones, stream)  # warm-up
-    stream.synchronize()
     n0 = env.launch_count()
-    clocks = ClockSampler(local)
-    if world > 1:
-        torch.distributed.barrier()
-    clocks.start()
-    time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.barrier()
+    evs = [g.events() for _ in range(K // T)]
     with torch.cuda.stream(stream):
-        e0.record(stream)
         for c in range(K // T):
-            env.rollout(acts[T + c * T: T + (c + 1) * T], frames, rewards, dones, stream)
-        e1.record(stream)
+            evs[c][0].record(stream)
+            env.rollout(acts[c * T: (c + 1) * T], frames, rewards[c * T: (c + 1) * T], dones[c * T: (c + 1) * T],
+                        stream)
+            evs[c][1].record(stream)
     stream.synchronize()
-    clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    per_launch = [a.elapsed_time(b) for a, b in evs]
+    ms = max_over_ranks(evs[0][0].elapsed_time(evs[-1][1]), g.world, g.dev)
     launches = env.launch_count() - n0
-    n_done = int(dones.sum().item())
-    if rank != 0:
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return
+    done_steps = dones.sum(dim=1).cpu().numpy()
+    shape = env.launch_shape()
+    tiling = env.tiling
+    env.close()
+    del frames, rewards, dones, acts
+    if g.rank != 0:
+        return None
     gray = H * W  # one plane per env-step (all four at an episode start)
     bpes = algorithmic_bytes_per_env_step(cfg) + gray
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peak, peak_src = 6800.0, "fallback"
-    if os.path.exists(peaks_path):
-        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
-    gbs = N * K * bpes / (ms / 1e3) / 1e9
-    shape = env.launch_shape()
-    line = {
-        "metric": "env-steps/s incl. render (frames/s), 128x128 RGB + gray stack", "value": world * N * K / (ms / 1e3),
-        "unit": "env-steps/s", "n_gpus": world, "steps": K, "warmup": T, "ms_per_step": ms / K,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+    peak, peak_src = measured_peak()
+    # launches whose steps end episodes (the horizon), against the others
+    ends = [int(done_steps[c * T: (c + 1) * T].sum()) for c in range(K // T)]
+    normal = [per_launch[c] for c in range(1, K // T) if ends[c] == 0]
+    per_es = recorded_traffic_per_env_step(N, TRAFFIC_LARGE_FILE, BATCH_KERNEL_SOURCES, tiling.as_tuple())
+    return {
+        "metric": "env-steps/s incl. render (frames/s), 128x128 RGB + gray stack",
+        "value": g.world * N * K / (ms / 1e3), "unit": "env-steps/s", "n_gpus": g.world, "steps": K, "warmup": 0,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{N} envs per GPU, 128x128 DFS mazes with 8x8 open rooms, 16 sprite slots (key, goal, "
                                "0-14 distractors), 128x128 RGB + 4-frame grayscale stack in the same pass, horizon 500, "
-                               "uniform random actions",
-                   "parallelism": f"replicas x{world}",
+                               "uniform random actions, from a fresh reset",
                    "l2": f"frames written to a {T}-slot rollout buffer ({T * N * H * W * 3 / 1e9:.1f} GB) > L2",
                    "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
                               "entry": "jx_rollout", "steps_per_launch": T}},
-        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                     "traffic": recorded_traffic(N, T, TRAFFIC_LARGE_FILE, BATCH_KERNEL_SOURCES,
-                                                 env.tiling.as_tuple()),
-                     "peak_source": peak_src, "algorithmic_bytes_per_env_step": bpes},
-        "reset_seconds": reset_s, "episode_ends_in_last_launch": n_done,
-        "tiling": tiling_dict(env.tiling),
+        "roofline": roofline(N * K * bpes, ms, peak, peak_src,
+                             traffic=None if per_es is None else per_es * N * T,
+                             traffic_unit="DRAM bytes per launch (ncu record, scaled by env-steps)",
+                             algorithmic_bytes_per_env_step=bpes),
+        "reset_seconds": reset_s,
+        "episode_ends": sum(ends),
+        "launch_ms": {"median_normal": statistics.median(normal) if normal else None,
+                      "first": per_launch[0],
+                      "horizon_launches": [{"launch": c, "ms": per_launch[c], "episode_ends": ends[c]}
+                                           for c in range(K // T) if ends[c] > 0]},
+        "tiling": tiling_dict(tiling),
         "autotune_trials": len(tuned) if tuned else 0,
-        "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
+        "gpu_launches": launches,
     }
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
 
 
-def run_serve(args):
-    """Serving: 64 actor groups submit step requests with Poisson arrivals
-    (mean gap 2 ms) to the continuous-batching server. Each group runs
-    sessions of `--session-steps` requests; a session's batch is log-uniform
-    in [16, 4096] envs of 32x32 or 64x64 key-door mazes, 64x64 RGB. Sessions
-    are admitted under a 40 GB state+frame budget. Reports p50 / p99 request
-    latency (submit to completion) and aggregate env-steps/s."""
+def serve_record(g: Gpu, actors: int, duration: float, session_steps: int, budget_gb: float) -> dict | None:
+    """Serving: `actors` actor groups submit step requests with Poisson
+    arrivals (mean gap 2 ms) to the continuous-batching server for `duration`
+    seconds. Each group runs sessions of `session_steps` requests; a session's
+    batch is log-uniform in [16, 4096] envs of 32x32 or 64x64 key-door mazes,
+    64x64 RGB. Sessions are admitted under a `budget_gb` state+frame budget.
+    Reports p50 / p99 request latency (submit to completion) and aggregate
+    env-steps/s over the window after a warm-up."""
     import concurrent.futures as cf
     import heapq
 
-    import torch
+    jx = g.jx
+    from paper_2605_19926_gb300 import inputs
 
-    from paper_2605_19926_gb300 import build, inputs
-
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    if rank == 0:
-        build.build()
-    if world > 1:
-        torch.distributed.barrier()
-    from paper_2605_19926_gb300 import jx
-
-    seed = 3 + rank
-    n_actors, duration, warm = args.actors, args.serve_seconds, min(2.0, args.serve_seconds / 4)
-    server = jx.Server(budget_bytes=int(args.budget_gb * 1e9), max_sessions=4 * n_actors, max_inflight=4,
-                       max_map_side=64, device=local)
+    seed = 3 + g.rank
+    warm = min(2.0, duration / 4)
+    server = jx.Server(budget_bytes=int(budget_gb * 1e9), max_sessions=4 * actors, max_inflight=4,
+                       max_map_side=64, device=g.local)
     pool = cf.ThreadPoolExecutor(max_workers=4)
-    session = [None] * n_actors  # open Session or None
-    opening = [None] * n_actors  # future of a pending open
-    left = [0] * n_actors
-    k_next = [0] * n_actors
-    acts = [None] * n_actors
-    gaps = [inputs.arrival_gaps(seed, a, 1 << 16) for a in range(n_actors)]
-    gi = [0] * n_actors
-    heap = [(float(gaps[a][0]), a) for a in range(n_actors)]
+    session = [None] * actors  # open Session or None
+    opening = [None] * actors  # future of a pending open
+    left = [0] * actors
+    k_next = [0] * actors
+    acts = [None] * actors
+    gaps = [inputs.arrival_gaps(seed, a, 1 << 16) for a in range(actors)]
+    gi = [1] * actors
+    heap = [(float(gaps[a][0]), a) for a in range(actors)]
     heapq.heapify(heap)
-    for a in range(n_actors):
-        gi[a] = 1
     t0 = time.perf_counter()
-    lat_mark = None
     stats_mark = None
     submitted = 0
+    act_bytes = 0
     while heap:
         t_rel, a = heapq.heappop(heap)
         if t_rel > duration:
             break
         while time.perf_counter() - t0 < t_rel:
             pass
-        if lat_mark is None and t_rel >= warm:
+        if stats_mark is None and t_rel >= warm:
             server.latencies()  # drop the warm-up requests
-            stats_mark = (time.perf_counter(), server.stats())
-            lat_mark = True
+            stats_mark = (time.perf_counter(), server.stats(), submitted, act_bytes)
         if session[a] is None and opening[a] is not None and opening[a].done():
             session[a] = opening[a].result()
             opening[a] = None
             if session[a] is not None:
-                left[a] = args.session_steps
+                left[a] = session_steps
                 n = session[a].n
                 acts[a] = np.random.default_rng([seed, a, k_next[a]]).integers(0, 7, size=(8, n), dtype=np.uint8)
         if session[a] is not None:
             session[a].submit(acts[a][left[a] % 8])
             submitted += 1
+            act_bytes += session[a].n
             left[a] -= 1
             if left[a] == 0:
                 session[a].close()
@@ -566,7 +631,7 @@ def run_serve(args):
     st_end = server.stats()
     lat = server.latencies()
     pool.shutdown(wait=True)
-    t_stats0, st0 = stats_mark
+    t_stats0, st0, sub0, ab0 = stats_mark
     window = t_end - t_stats0
     env_steps = st_end["env_steps"] - st0["env_steps"]
     reqs = st_end["requests_done"] - st0["requests_done"]
@@ -574,36 +639,252 @@ def run_serve(args):
     groups = st_end["groups_launched"] - st0["groups_launched"]
     server.close()
     value = env_steps / window
-    p50 = float(np.percentile(lat, 50)) * 1e3 if len(lat) else None
-    p99 = float(np.percentile(lat, 99)) * 1e3 if len(lat) else None
-    tot = max_over_ranks(window * 1e3, world, torch.device("cuda", local))
-    if rank != 0:
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return
-    line = {
-        "metric": "env-steps/s incl. render (frames/s), served requests", "value": value * world,
-        "unit": "env-steps/s", "n_gpus": world, "steps": int(reqs), "warmup": 0,
-        "ms_per_step": tot / max(1, reqs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u8", "data": "synthetic",
-        "config": {"workload": f"{n_actors} actor groups, Poisson arrivals (mean gap 2 ms), sessions of "
-                               f"{args.session_steps} requests, batch log-uniform in [16, 4096] envs, 32x32 or 64x64 "
+    tot = max_over_ranks(window * 1e3, g.world, g.dev)
+    if g.rank != 0:
+        return None
+    return {
+        "metric": "env-steps/s incl. render (frames/s), served requests", "value": value * g.world,
+        "unit": "env-steps/s", "n_gpus": g.world, "requests": int(reqs),
+        "ms_per_request": tot / max(1, reqs), "higher_is_better": True, "scaling": "weak", "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{actors} actor groups, Poisson arrivals (mean gap 2 ms), sessions of "
+                               f"{session_steps} requests, batch log-uniform in [16, 4096] envs, 32x32 or 64x64 "
                                "key-door mazes, 64x64 RGB, continuous batching",
-                   "budget_gb": args.budget_gb, "seconds": duration, "measured_seconds": window,
+                   "budget_gb": budget_gb, "seconds": duration, "measured_seconds": window,
                    "max_inflight_launches": 4},
-        "p50_step_ms": p50, "p99_step_ms": p99,
-        "requests_per_s": reqs / window, "submitted_per_s": submitted / (t_end - t0),
+        "p50_step_ms": float(np.percentile(lat, 50)) * 1e3 if len(lat) else None,
+        "p99_step_ms": float(np.percentile(lat, 99)) * 1e3 if len(lat) else None,
+        "latency_samples": int(len(lat)),
+        "requests_per_s": reqs / window, "submitted_per_s": (submitted - sub0) / window,
         "mean_sessions_per_launch": groups / max(1, launches), "launches": int(launches),
+        "mean_envs_per_request": env_steps / max(1, reqs),
         "server": {k: st_end[k] for k in ("peak_bytes_in_use", "budget_bytes", "peak_sessions",
                                           "peak_inflight_launches", "rejected_opens")},
-        "roofline": None, "cpu_baseline": None,
-        "e2e": {"value": value * world, "unit": "env-steps/s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": 0,
+        "roofline": None,
+        "roofline_note": "latency-bound: the offered load is far below the HBM roofline",
+        "e2e": {"value": value * g.world, "unit": "env-steps/s",
+                "h2d_bytes_per_request": (act_bytes - ab0) / max(1, submitted - sub0), "d2h_bytes_per_request": 0,
                 "how": "host actions submitted per request through jx_server_submit; results stay on the device"},
         "gpu_launches": int(launches),
     }
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+
+
+def headline(g: Gpu, args) -> dict | None:
+    """The headline workload (4096 key-door mazes, 64 x 64) and the legs beside it."""
+    torch, jx = g.torch, g.jx
+    from paper_2605_19926_gb300 import inputs
+
+    base_cfg = inputs.batched_keydoor_mazes(args.n_envs)
+    cfg = shard_config(base_cfg, g.rank)
+    N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
+    plan = Plan(args.steps, args.warmup, args.ring_slots)
+    ring = plan.ring
+    env = jx.Env(cfg, g.local)
+    tuned = None
+    if not args.no_autotune:
+        # the env's own kernel against the batched kernel's tilings, before timing
+        tuned = env.autotune(mode=1, steps=ring, max_trials=args.tune_trials)
+    # inputs resident in HBM before timing: the whole action stream
+    acts_host = inputs.action_stream(cfg["seed"], plan.stream_len, N)
+    acts = torch.from_numpy(acts_host).to(g.dev)
+    graph_acts = [acts.index_select(0, torch.tensor(plan.graph_rows(c), device=g.dev)) for c in range(plan.n_graph)]
+    ring_acts = torch.empty((ring, N), dtype=torch.uint8, device=g.dev)
+    frames = torch.empty((ring, N, H, W, 3), dtype=torch.uint8, device=g.dev)  # 6.4 GB at 128 slots
+    rewards = torch.empty((ring, N), dtype=torch.float32, device=g.dev)
+    dones = torch.empty((ring, N), dtype=torch.uint8, device=g.dev)
+    stream = torch.cuda.Stream(device=g.dev)
+    torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        env.reset(frames[0], stream)
+        for s in range(plan.warmup):
+            k = plan.warmup_slot(s)
+            env.step(acts[s], frames[k], rewards[k], dones[k], stream)
+    stream.synchronize()
+
+    # single-step entry point: a CUDA graph of `ring` jx_step launches
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        for i in range(ring):
+            env.step(ring_acts[i], frames[i], rewards[i], dones[i], torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    # the capture itself ran nothing; the env state is still after the warm-up
+
+    # timed region: the steps in rollout launches of at most `ring` steps
+    launches_before = env.launch_count()
+    g.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = g.events()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for start, n in plan.launches:
+            env.rollout(acts[start: start + n], frames[:n], rewards[:n], dones[:n], stream)
+        ev1.record(stream)
+    stream.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    gpu_launches = env.launch_count() - launches_before
+    t_max = max_over_ranks(ms, g.world, g.dev)
+    g.barrier()
+    value = job_value(g.world, N, args.steps, t_max)
+
+    # the single-step entry point on the same workload (graph replays of `ring` launches)
+    torch.cuda.synchronize()
+    g0, g1 = g.events()
+    with torch.cuda.stream(stream):
+        g0.record(stream)
+        for c in range(plan.n_graph):
+            ring_acts.copy_(graph_acts[c], non_blocking=True)
+            graph.replay()
+        g1.record(stream)
+    stream.synchronize()
+    step_ms = g0.elapsed_time(g1) / (plan.n_graph * ring)
+
+    # per-step latency (eager launch + kernel, one step at a time)
+    lat = []
+    with torch.cuda.stream(stream):
+        for i, row in enumerate(plan.wrapped(plan.warmup, args.latency_steps)):
+            a, b = g.events()
+            a.record(stream)
+            k = i % ring
+            env.step(acts[row], frames[k], rewards[k], dones[k], stream)
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b))
+
+    # the plain method: one environment, one jx_step launch per step (16 x 16 rooms)
+    plain = None
+    if g.rank == 0 and args.plain_steps > 0:
+        pc = inputs.single_env_rooms()
+        penv = jx.Env(pc, g.local)
+        pa = torch.from_numpy(inputs.action_stream(pc["seed"], args.plain_steps, 1)).to(g.dev)
+        pf = torch.empty((1, pc["frame_h"], pc["frame_w"], 3), dtype=torch.uint8, device=g.dev)
+        pr = torch.empty(1, dtype=torch.float32, device=g.dev)
+        pd = torch.empty(1, dtype=torch.uint8, device=g.dev)
+        with torch.cuda.stream(stream):
+            penv.reset(pf, stream)
+            for i in range(min(8, args.plain_steps)):
+                penv.step(pa[i], pf, pr, pd, stream)
+            p0, p1 = g.events()
+            p0.record(stream)
+            for i in range(args.plain_steps):
+                penv.step(pa[i], pf, pr, pd, stream)
+            p1.record(stream)
+        stream.synchronize()
+        pms = p0.elapsed_time(p1)
+        # its per-call latency, one step at a time with a host sync (as the batch's p50 / p99)
+        plat = []
+        with torch.cuda.stream(stream):
+            for i in range(min(args.plain_steps, args.latency_steps)):
+                a, b = g.events()
+                a.record(stream)
+                penv.step(pa[i], pf, pr, pd, stream)
+                b.record(stream)
+                b.synchronize()
+                plat.append(a.elapsed_time(b))
+        plain = {"value": args.plain_steps / (pms / 1e3), "unit": "env-steps/s", "ms_per_step": pms / args.plain_steps,
+                 "p50_step_ms": percentile(plat, 0.5), "p99_step_ms": percentile(plat, 0.99),
+                 "workload": f"1 env, 16x16 random rooms (p = 0.25), 64x64 RGB, {args.plain_steps} uniform random steps, "
+                             "one jx_step launch per step"}
+        penv.close()
+
+    # end to end through the public host-buffer entry point (pinned host memory)
+    h_act = torch.empty(N, dtype=torch.uint8).pin_memory()
+    h_frames = torch.empty((N, H, W, 3), dtype=torch.uint8).pin_memory()
+    h_rew = torch.empty(N, dtype=torch.float32).pin_memory()
+    h_done = torch.empty(N, dtype=torch.uint8).pin_memory()
+    rows = plan.wrapped(plan.warmup, args.e2e_steps + 3)
+    for i in range(3):
+        h_act.numpy()[:] = acts_host[rows[i]]
+        env.step_host(h_act, h_frames, h_rew, h_done, stream)
+    t0 = time.perf_counter()
+    for i in range(args.e2e_steps):
+        h_act.numpy()[:] = acts_host[rows[3 + i]]
+        env.step_host(h_act, h_frames, h_rew, h_done, stream)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = g.world * N * args.e2e_steps / e2e_s  # every rank runs the same count; host clock per rank
+
+    shape = env.launch_shape()
+    tiling = env.tiling
+    graph.reset()
+    env.close()
+    del frames, rewards, dones, acts, graph_acts, ring_acts
+    torch.cuda.empty_cache()
+    if g.rank != 0:
+        return None
+
+    peak, peak_src = measured_peak()
+    bytes_total = sum(rollout_bytes(cfg, N, n) for _, n in plan.launches)
+    per_es = recorded_traffic_per_env_step(N)
+    traffic = None if per_es is None else per_es * N * args.steps / len(plan.launches)
+    step_bytes = algorithmic_bytes_per_env_step(cfg) * N
+    cpu = None
+    if not args.no_cpu_baseline and g.world == 1:
+        import oracle
+
+        oracle.build()
+        v, cores = time_oracle(base_cfg, args.cpu_envs, args.cpu_steps, seed=base_cfg["seed"], nthreads=cpu_cores())
+        # one core as well: the paper frames its CPU comparison per core
+        n1, s1 = max(1, args.cpu_envs // 8), max(1, args.cpu_steps // 6)
+        v1, _ = time_oracle(base_cfg, n1, s1, seed=base_cfg["seed"], nthreads=1)
+        cpu = {"value": v, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_envs} envs x {args.cpu_steps} steps of the workload (frames rendered)",
+               "single_core": {"value": v1, "unit": "env-steps/s", "cores": 1,
+                               "sample": f"{n1} envs x {s1} steps of the workload (frames rendered)"}}
+    return {
+        "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": g.world, "steps": args.steps,
+        "warmup": plan.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "4096 envs per GPU, 32x32 random DFS key-door mazes, 64x64 RGB uint8, horizon 500, "
+                               "auto-reset, uniform random actions, seed 1",
+                   "n_envs_per_gpu": N, "map_side": cfg["map_side"], "frame": f"{H}x{W}x3 uint8",
+                   "parallelism": f"replicas x{g.world}",
+                   "l2": f"frames written to a {ring}-slot rollout buffer ({ring * N * H * W * 3 / 1e9:.2f} GB) > L2",
+                   "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
+                              "entry": "jx_rollout", "steps_per_launch": ring, "timed_launches": len(plan.launches),
+                              "tiling": tiling_dict(tiling), "autotune_trials": len(tuned) if tuned else 0}},
+        "p50_step_ms": percentile(lat, 0.5), "p99_step_ms": percentile(lat, 0.99),
+        "latency": {"how": "jx_step launched alone, host sync after each call, CUDA events around the launch",
+                    "samples": len(lat)},
+        "per_step_launch": {"value": g.world * N / (step_ms / 1e3), "unit": "env-steps/s", "ms_per_step": step_ms,
+                            "roofline": roofline(step_bytes, step_ms, peak, peak_src,
+                                                 algorithmic_bytes_per_launch=step_bytes),
+                            "how": f"jx_step, CUDA graph of {ring} launches, {plan.n_graph} replays"},
+        "plain_one_env_per_launch": plain,
+        "roofline": roofline(bytes_total, t_max, peak, peak_src, traffic=traffic,
+                             traffic_unit="DRAM bytes per launch (ncu record, scaled by env-steps)",
+                             algorithmic_bytes_per_step=bytes_total / args.steps,
+                             algorithmic_bytes_per_launch=bytes_total / len(plan.launches),
+                             kernel="jx_rollout (env kernel, or the batched kernel when autotuned to it)"),
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": N,
+                "d2h_bytes_per_step": N * H * W * 3 + 4 * N + N,
+                "how": f"jx_step_host, pinned host buffers, {args.e2e_steps} steps, host clock"},
+        "gpu_launches": gpu_launches,
+    }
+
+
+def extras(g: Gpu, args) -> dict:
+    """Bounded runs of the uneven batch, the large-scale workload and the
+    serving loop beside the headline (each failure is recorded, not raised)."""
+    out = {}
+    runs = {
+        "uneven": lambda: uneven_record(g, args.uneven_envs, args.uneven_slots, args.extra_uneven_steps, args.tiling,
+                                        args.tune_trials),
+        "large": lambda: large_record(g, args.large_envs, args.large_slots, args.extra_large_steps,
+                                      args.large_tiling, 0),
+        "serve": lambda: serve_record(g, args.actors, args.extra_serve_seconds, args.session_steps, args.budget_gb),
+    }
+    for name, fn in runs.items():
+        t0 = time.perf_counter()
+        try:
+            rec = fn()
+        except Exception as exc:  # recorded in the line: the headline still prints
+            rec = {"error": f"{type(exc).__name__}: {exc}"}
+        if rec is not None:
+            rec["wall_seconds"] = time.perf_counter() - t0
+        out[name] = rec
+        g.torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -619,265 +900,65 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=600)
     ap.add_argument("--ref-envs", type=int, default=0, help="reference arm: envs per step (0: sized to the run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="headline only: skip the uneven / large / serve records")
     ap.add_argument("--plain-steps", type=int, default=1000)
     ap.add_argument("--ring-slots", type=int, default=GRAPH_STEPS,
-                    help="rollout buffer slots = launches per CUDA graph (smaller for profiling captures)")
+                    help="rollout buffer slots = steps per rollout launch = launches per CUDA graph")
     ap.add_argument("--workload", default="mazes", choices=["mazes", "uneven", "serve", "large"],
-                    help="mazes: 4096 key-door mazes (the headline); uneven: 16,384 envs of mixed sizes; "
-                         "serve: the continuous-batching step server under Poisson request arrivals")
+                    help="mazes: 4096 key-door mazes (the headline, with bounded uneven / large / serve records); "
+                         "uneven, large, serve: only that workload, at full length")
     ap.add_argument("--actors", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--extra-serve-seconds", type=float, default=10.0)
     ap.add_argument("--session-steps", type=int, default=250)
     ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--large-envs", type=int, default=65536)
     ap.add_argument("--large-slots", type=int, default=8, help="steps per rollout launch of the large workload")
+    ap.add_argument("--extra-large-steps", type=int, default=512, help="large record beside the headline: steps")
+    ap.add_argument("--large-tiling", default="2,1,128,16,1",
+                    help="large record beside the headline: batched-kernel tiling w,c,b,r[,s] ('' = env kernel)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip jx_autotune before timing (the env's own kernel with its fixed tiles)")
     ap.add_argument("--uneven-slots", type=int, default=16, help="steps per rollout launch of the uneven batch")
     ap.add_argument("--uneven-envs", type=int, default=16384)
+    ap.add_argument("--extra-uneven-steps", type=int, default=128, help="uneven record beside the headline: steps")
     ap.add_argument("--tiling", default="",
                     help="uneven batch and large scale: w,c,b,r[,s] batched-kernel tiling to use instead of autotuning")
     ap.add_argument("--tune-trials", type=int, default=1000)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
-    if args.workload == "large" and args.impl == "jx":
-        if args.steps == ap.get_default("steps"):
-            args.steps = 1000
-        run_large(args)
-        return
-    if args.workload == "serve" and args.impl == "jx":
-        run_serve(args)
-        return
-    if args.workload == "uneven" and args.impl == "jx":
-        if args.steps == ap.get_default("steps"):
-            args.steps = 512
-        run_uneven(args)
-        return
-
-    from paper_2605_19926_gb300 import inputs
-
-    base_cfg = inputs.batched_keydoor_mazes(args.n_envs)
+    default_steps = args.steps == ap.get_default("steps")
     if args.impl == "reference":
-        run_reference(args, base_cfg)
+        from paper_2605_19926_gb300 import inputs
+
+        run_reference(args, inputs.batched_keydoor_mazes(args.n_envs))
         return
 
-    import torch
-
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    from paper_2605_19926_gb300 import build
-
-    if rank == 0:
-        build.build()
-    if world > 1:
-        torch.distributed.barrier()
-    from paper_2605_19926_gb300 import jx
-
-    cfg = shard_config(base_cfg, rank)
-    N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
-    dev = torch.device("cuda", local)
-    env = jx.Env(cfg, local)
-    ring = args.ring_slots
-    tuned = None
-    if not args.no_autotune:
-        # the env's own kernel against the batched kernel's tilings, before timing
-        tuned = env.autotune(mode=1, steps=ring, max_trials=args.tune_trials)
-    total_steps = args.warmup + args.steps
-    # inputs resident in HBM before timing: the whole action stream
-    acts_host = inputs.action_stream(cfg["seed"], total_steps, N)
-    acts = torch.from_numpy(acts_host).to(dev)
-    ring_acts = torch.empty((ring, N), dtype=torch.uint8, device=dev)
-    frames = torch.empty((ring, N, H, W, 3), dtype=torch.uint8, device=dev)  # 6.4 GB rollout buffer at 128 slots
-    rewards = torch.empty((ring, N), dtype=torch.float32, device=dev)
-    dones = torch.empty((ring, N), dtype=torch.uint8, device=dev)
-    stream = torch.cuda.Stream(device=dev)
-    torch.cuda.synchronize()
-
-    with torch.cuda.stream(stream):
-        env.reset(frames[0], stream)
-        for s in range(args.warmup):
-            env.step(acts[s], frames[s % ring], rewards[s % ring], dones[s % ring], stream)
-    stream.synchronize()
-
-    # single-step entry point: a CUDA graph of `ring` jx_step launches
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        for i in range(ring):
-            env.step(ring_acts[i], frames[i], rewards[i], dones[i], torch.cuda.current_stream())
-    torch.cuda.synchronize()
-    # the capture itself ran nothing; the env state is still after the warm-up
-
-    # timed region: the whole action stream in rollout launches of `ring` steps
-    # (each launch writes one frame per env and step into the rollout buffer)
-    n_full, rem = divmod(args.steps, ring)
-    launches_before = env.launch_count()
-    clocks = ClockSampler(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
+    g = Gpu()
+    clocks = ClockSampler(g.local)
     clocks.start()
     time.sleep(0.3)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        ev0.record(stream)
-        s = args.warmup
-        for c in range(n_full):
-            env.rollout(acts[s: s + ring], frames, rewards, dones, stream)
-            s += ring
-        if rem:
-            env.rollout(acts[s: s + rem], frames[:rem], rewards[:rem], dones[:rem], stream)
-            s += rem
-        ev1.record(stream)
-    stream.synchronize()
+    window = "the whole run"
+    if args.workload == "uneven":
+        line = uneven_record(g, args.uneven_envs, args.uneven_slots, 512 if default_steps else args.steps,
+                             args.tiling, args.tune_trials)
+    elif args.workload == "large":
+        line = large_record(g, args.large_envs, args.large_slots, 1000 if default_steps else args.steps, args.tiling,
+                            0 if args.no_autotune else args.tune_trials)
+    elif args.workload == "serve":
+        line = serve_record(g, args.actors, args.serve_seconds, args.session_steps, args.budget_gb)
+    else:
+        line = headline(g, args)
+        window = "the headline's timed region, its legs and the uneven / large / serve records"
+        if line is not None and g.world == 1 and not args.no_extras:
+            line.update(extras(g, args))
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    gpu_launches = env.launch_count() - launches_before
-    t_max = max_over_ranks(ms, world, dev)
-    if world > 1:
-        torch.distributed.barrier()
-    ms_per_step = t_max / args.steps
-    value = job_value(world, N, args.steps, t_max)
-
-    # the single-step entry point on the same workload (graph replays of `ring` launches)
-    n_graph = max(1, min(n_full, 16))
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        g0.record(stream)
-        for c in range(n_graph):
-            ring_acts.copy_(acts[(args.warmup + c * ring) % (total_steps - ring + 1):][:ring], non_blocking=True)
-            graph.replay()
-        g1.record(stream)
-    stream.synchronize()
-    step_ms = g0.elapsed_time(g1) / (n_graph * ring)
-
-    # per-step latency (eager launch + kernel, one step at a time)
-    lat = []
-    with torch.cuda.stream(stream):
-        for i in range(args.latency_steps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            env.step(acts[(args.warmup + i) % total_steps], frames[i % ring], rewards[i % ring], dones[i % ring],
-                     stream)
-            b.record(stream)
-            b.synchronize()
-            lat.append(a.elapsed_time(b))
-    lat.sort()
-    p50 = lat[len(lat) // 2]
-    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))]
-
-    # the plain method: one environment, one jx_step launch per step (16 x 16 rooms, 1000 steps)
-    plain = None
-    if rank == 0 and args.plain_steps > 0:
-        pc = inputs.single_env_rooms()
-        penv = jx.Env(pc, local)
-        pa = torch.from_numpy(inputs.action_stream(pc["seed"], args.plain_steps, 1)).to(dev)
-        pf = torch.empty((1, pc["frame_h"], pc["frame_w"], 3), dtype=torch.uint8, device=dev)
-        pr = torch.empty(1, dtype=torch.float32, device=dev)
-        pd = torch.empty(1, dtype=torch.uint8, device=dev)
-        with torch.cuda.stream(stream):
-            penv.reset(pf, stream)
-            for i in range(8):
-                penv.step(pa[i], pf, pr, pd, stream)
-            p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            p0.record(stream)
-            for i in range(args.plain_steps):
-                penv.step(pa[i], pf, pr, pd, stream)
-            p1.record(stream)
-        stream.synchronize()
-        pms = p0.elapsed_time(p1)
-        # its per-call latency, one step at a time with a host sync (as the batch's p50 / p99)
-        plat = []
-        with torch.cuda.stream(stream):
-            for i in range(min(args.plain_steps, args.latency_steps)):
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                penv.step(pa[i], pf, pr, pd, stream)
-                b.record(stream)
-                b.synchronize()
-                plat.append(a.elapsed_time(b))
-        plat.sort()
-        plain = {"value": args.plain_steps / (pms / 1e3), "unit": "env-steps/s", "ms_per_step": pms / args.plain_steps,
-                 "p50_step_ms": plat[len(plat) // 2] if plat else None,
-                 "p99_step_ms": plat[min(len(plat) - 1, int(0.99 * len(plat)))] if plat else None,
-                 "workload": f"1 env, 16x16 random rooms (p = 0.25), 64x64 RGB, {args.plain_steps} uniform random steps, "
-                             "one jx_step launch per step"}
-        penv.close()
-
-    # end to end through the public host-buffer entry point
-    h_act = torch.empty(N, dtype=torch.uint8).pin_memory()
-    h_frames = torch.empty((N, H, W, 3), dtype=torch.uint8).pin_memory()
-    h_rew = torch.empty(N, dtype=torch.float32).pin_memory()
-    h_done = torch.empty(N, dtype=torch.uint8).pin_memory()
-    for i in range(3):
-        h_act.numpy()[:] = acts_host[i]
-        env.step_host(h_act, h_frames, h_rew, h_done, stream)
-    t0 = time.perf_counter()
-    for i in range(args.e2e_steps):
-        h_act.numpy()[:] = acts_host[(i + 3) % total_steps]
-        env.step_host(h_act, h_frames, h_rew, h_done, stream)
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * N * args.e2e_steps / e2e_s  # every rank runs the same count; host clock per rank
-
-    launch_steps = ring if n_full else rem
-    bytes_per_launch = rollout_bytes(cfg, N, launch_steps)
-    launch_ms = t_max / max(1, gpu_launches)
-    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peak, peak_src = 6800.0, "fallback"
-    if os.path.exists(peaks_path):
-        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
-    traffic = recorded_traffic(N, launch_steps)
-
-    if rank != 0:
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        import oracle
-
-        oracle.build()
-        v, cores = time_oracle(base_cfg, args.cpu_envs, args.cpu_steps, seed=base_cfg["seed"], nthreads=cpu_cores())
-        # one core as well: the paper frames its CPU comparison per core
-        n1, s1 = max(1, args.cpu_envs // 8), max(1, args.cpu_steps // 6)
-        v1, _ = time_oracle(base_cfg, n1, s1, seed=base_cfg["seed"], nthreads=1)
-        cpu = {"value": v, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_envs} envs x {args.cpu_steps} steps of the workload (frames rendered)",
-               "single_core": {"value": v1, "unit": "env-steps/s", "cores": 1,
-                               "sample": f"{n1} envs x {s1} steps of the workload (frames rendered)"}}
-    shape = env.launch_shape()
-    line = {
-        "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "4096 envs per GPU, 32x32 random DFS key-door mazes, 64x64 RGB uint8, horizon 500, "
-                               "auto-reset, uniform random actions, seed 1",
-                   "n_envs_per_gpu": N, "map_side": cfg["map_side"], "frame": f"{H}x{W}x3",
-                   "parallelism": f"replicas x{world}",
-                   "l2": f"frames written to a {ring}-slot rollout buffer ({ring * N * H * W * 3 / 1e9:.1f} GB) > L2",
-                   "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
-                              "entry": "jx_rollout", "steps_per_launch": ring,
-                              "tiling": tiling_dict(env.tiling), "autotune_trials": len(tuned) if tuned else 0}},
-        "p50_step_ms": p50, "p99_step_ms": p99,
-        "per_step_launch": {"value": world * N / (step_ms / 1e3), "unit": "env-steps/s", "ms_per_step": step_ms,
-                            "how": f"jx_step, CUDA graph of {ring} launches"},
-        "plain_one_env_per_launch": plain,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                     "algorithmic_bytes_per_launch": bytes_per_launch},
-        "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "env-steps/s", "h2d_bytes_per_step": N,
-                "d2h_bytes_per_step": N * H * W * 3 + 4 * N + N},
-        "gpu_launches": gpu_launches,
-        "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    if line is not None:
+        if clk is not None:
+            clk["window"] = window
+        line["clocks"] = clk
+        print(json.dumps(line), flush=True)
+    g.close()
 
 
 if __name__ == "__main__":

@@ -90,3 +90,64 @@ def test_tiling_key_sees_only_the_effective_map_kind():
     assert bench.tiling_key((4, 1, 8, 8, 1), [128]) == bench.tiling_key((4, 2, 64, 32, 2), [128])
     assert bench.tiling_key((4, 1, 8, 8, 1), [16, 128]) != bench.tiling_key((4, 1, 64, 8, 1), [16, 128])
     assert bench.tiling_key((4, 1, 0, 8, 1), [128]) != bench.tiling_key((4, 1, 128, 8, 1), [128])
+
+
+@pytest.mark.parametrize("steps,warmup,ring_slots", [(20, 5, 128), (1, 3, 128), (129, 16, 128), (10000, 16, 128),
+                                                     (3, 3, 2), (128, 3, 128), (500, 4, 7)])
+def test_plan_indexes_stay_inside_the_action_stream(steps, warmup, ring_slots):
+    """Every row the headline run reads lies inside the action stream it draws
+    (warmup + steps rows), the timed launches cover exactly the timed steps in
+    order, each fits the rollout buffer, and the graph replays read full rings."""
+    p = bench.Plan(steps, warmup, ring_slots)
+    assert p.stream_len == warmup + steps
+    assert 1 <= p.ring <= ring_slots
+    assert p.ring >= min(ring_slots, bench.MIN_RING)
+    covered = []
+    for start, n in p.launches:
+        assert 1 <= n <= p.ring
+        assert 0 <= start and start + n <= p.stream_len
+        covered.extend(range(start, start + n))
+    assert covered == list(range(warmup, warmup + steps))
+    assert all(0 <= p.warmup_slot(s) < p.ring for s in range(warmup))
+    assert 1 <= p.n_graph <= 16
+    for c in range(p.n_graph):
+        rows = p.graph_rows(c)
+        assert len(rows) == p.ring and all(0 <= r < p.stream_len for r in rows)
+    rows = p.wrapped(warmup, 300)
+    assert len(rows) == 300 and all(0 <= r < p.stream_len for r in rows)
+
+
+def test_plan_rejects_empty_runs():
+    with pytest.raises(ValueError):
+        bench.Plan(0, 3, 128)
+    with pytest.raises(ValueError):
+        bench.Plan(10, 3, 0)
+
+
+@pytest.mark.parametrize("steps,warmup", [(20, 5), (1, 3), (129, 16), (10000, 16)])
+def test_headline_roofline_is_bytes_per_step_times_steps_over_time(steps, warmup):
+    """roofline.achieved = the timed launches' algorithmic bytes / the timed
+    region: bytes per step x steps / seconds, whatever the launch split (a
+    short last launch is not counted as a full one)."""
+    from paper_2605_19926_gb300 import inputs
+
+    cfg = inputs.batched_keydoor_mazes()
+    p = bench.Plan(steps, warmup, 128)
+    total = sum(bench.rollout_bytes(cfg, 4096, n) for _, n in p.launches)
+    per_step = total / steps
+    ms = 0.0096 * steps  # a made-up timed region
+    r = bench.roofline(total, ms, 6785.5, "measured")
+    assert r["achieved"] == pytest.approx(per_step * steps / (ms / 1e3) / 1e9)
+    assert r["frac"] == pytest.approx(per_step / (ms / steps / 1e3) / 1e9 / 6785.5)
+    # frames dominate: per step a little over 4096 frames of 64 x 64 x 3 bytes
+    assert 4096 * 12288 < per_step < 4096 * 12400
+
+
+def test_clock_summary_uses_busy_samples():
+    rows = ["0, 1000, 2070, 100.0, 0x0, Not Active, Not Active, Not Active, Not Active, 0",
+            "0, 1950, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Active, 100",
+            "0, 1965, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active, 98"]
+    s = bench.ClockSampler.summarise("\n".join(rows))
+    assert s["sm_mhz"] == pytest.approx(1957.5) and s["samples"] == 3 and s["samples_under_load"] == 2
+    assert s["reasons"] == ["sw_power_cap"] and s["sm_max_mhz"] == 2070
+    assert bench.ClockSampler.summarise("") is None
