@@ -143,6 +143,9 @@ def lib() -> ctypes.CDLL:
         L.jxo_step_render_batch.argtypes = [P, P, P, i32, P, P, P, P, P, P, P, i32]
         L.jxo_render_batch.argtypes = [P, P, i32, P, P, P, i32]
         L.jxo_generate_batch.argtypes = [P, P, P, P, i32, i32]
+        L.jxo_render_batch_biased.argtypes = [P, P, i32, P, P, P, i32, i32]
+        L.jxo_step_batch_biased.argtypes = [P, P, P, i32, P, i32, i32, i32, i32, P, P, P, i32]
+        L.jxo_step_biased.argtypes = [P, i32, P, i32, i32, i32, i32, i32, P, P, P]
         L.jxo_gray.argtypes = [P, ctypes.c_int64, P]
         L.jxo_gray.restype = None
         L.jxo_parse_ascii.argtypes = [ctypes.c_char_p, i32, P]
@@ -238,7 +241,11 @@ def step(cfg: np.ndarray, env_index, envs: np.ndarray, actions, frames=False, ra
     return out
 
 
-def render(cfg: np.ndarray, envs: np.ndarray, rays=True, ambiguous=True, nthreads: int = 1) -> dict:
+def render(cfg: np.ndarray, envs: np.ndarray, rays=True, ambiguous=True, nthreads: int = 1, bias: int = 0) -> dict:
+    """Frames (and rays, ambiguity flags) of the envs' current states. ``bias``
+    +1 / -1 casts every ray with its near ties taken towards the x / y
+    boundary: the frame of one of the decisions a corner ray admits."""
+    envs = np.ascontiguousarray(envs)
     n = envs.shape[0]
     H, W = int(cfg["frame_h"][0]), int(cfg["frame_w"][0])
     out = {"frames": np.zeros((n, H, W, 3), np.uint8)}
@@ -246,10 +253,29 @@ def render(cfg: np.ndarray, envs: np.ndarray, rays=True, ambiguous=True, nthread
         out["rays"] = np.zeros((n, W), RAY_DTYPE)
     if ambiguous:
         out["ambiguous"] = np.zeros((n, H, W), np.uint8)
-    rc = lib().jxo_render_batch(_ptr(cfg), _ptr(envs), n, _ptr(out["frames"]), _ptr(out.get("rays")),
-                                _ptr(out.get("ambiguous")), nthreads)
+    rc = lib().jxo_render_batch_biased(_ptr(cfg), _ptr(envs), n, _ptr(out["frames"]), _ptr(out.get("rays")),
+                                       _ptr(out.get("ambiguous")), bias, nthreads)
     if rc != 0:
-        raise ValueError("oracle: invalid config")
+        raise ValueError("oracle: invalid config or bias")
+    return out
+
+
+def step_biased(cfg: np.ndarray, env_index, envs: np.ndarray, actions, coll_x: int, coll_y: int, pick_x: int,
+                pick_y: int, nthreads: int = 1) -> dict:
+    """``step`` (no frames) with the decisions a near tie admits taken one way:
+    coll_x / coll_y +1 let a collision test within the tie tolerance pass, -1
+    block it; pick_x / pick_y shift the key / goal test point by -1, 0 or +1
+    times the tolerance. All zero is ``step``."""
+    env_index = np.ascontiguousarray(np.atleast_1d(env_index), dtype=np.int32)
+    n = envs.shape[0]
+    actions = np.ascontiguousarray(actions, dtype=np.uint8)
+    assert actions.shape == (n,) and env_index.shape == (n,) and envs.flags["C_CONTIGUOUS"]
+    out = {"rewards": np.zeros(n, np.float32), "dones": np.zeros(n, np.uint8), "events": np.zeros(n, np.int32)}
+    rc = lib().jxo_step_batch_biased(_ptr(cfg), _ptr(env_index), _ptr(envs), n, _ptr(actions), coll_x, coll_y,
+                                     pick_x, pick_y, _ptr(out["rewards"]), _ptr(out["dones"]), _ptr(out["events"]),
+                                     nthreads)
+    if rc != 0:
+        raise ValueError("oracle: invalid config, action or bias")
     return out
 
 

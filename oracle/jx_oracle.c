@@ -589,8 +589,23 @@ static int pickup_events(const jxo_env* e, double px, double py, int* picked) {
   return ev;
 }
 
-int jxo_step(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t action, double* reward,
-             int32_t* done, int32_t* events) {
+/* A collision test with its finite-precision tie taken a chosen way: bias 0
+ * the exact test; +1 a test that growing or shrinking the box by
+ * JXO_EPS_CELL would flip lets the box move (the smaller box's answer), -1
+ * blocks it (the larger box's answer). */
+static int box_free_biased(const jxo_config* cfg, const jxo_env* e, double px, double py, int32_t bias) {
+  if (bias != 0 && box_near_tie(cfg, e, px, py)) return bias > 0;
+  return box_free(cfg, e, px, py);
+}
+
+/* One step (movement, collision, key / goal events, reward, episode end,
+ * auto-reset). coll_x / coll_y bias the x and y collision tests as
+ * box_free_biased; pick_x / pick_y (-1, 0, +1) move the point where key and
+ * goal events are evaluated by that many JXO_EPS_CELL along x and y. All zero
+ * is the exact step. */
+static int step_impl(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t action, int32_t coll_x,
+                     int32_t coll_y, int32_t pick_x, int32_t pick_y, double* reward, int32_t* done,
+                     int32_t* events) {
   if (!config_ok(cfg) || action < 0 || action > 6) return -1;
   double th = heading(cfg, e);
   double c = cos(th), s = sin(th);
@@ -608,13 +623,13 @@ int jxo_step(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t actio
   int near = 0;
   double nx = e->x + dx;
   near |= box_near_tie(cfg, e, nx, e->y);
-  if (!box_free(cfg, e, nx, e->y)) {
+  if (!box_free_biased(cfg, e, nx, e->y, coll_x)) {
     open_unlocked(cfg, e, nx, e->y);
     nx = e->x;
   }
   double ny = e->y + dy;
   near |= box_near_tie(cfg, e, nx, ny);
-  if (!box_free(cfg, e, nx, ny)) {
+  if (!box_free_biased(cfg, e, nx, ny, coll_y)) {
     open_unlocked(cfg, e, nx, ny);
     ny = e->y;
   }
@@ -622,12 +637,13 @@ int jxo_step(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t actio
   e->y = ny;
 
   int picked = 0;
-  int ev = pickup_events(e, nx, ny, &picked);
+  int ev = pickup_events(e, nx + pick_x * JXO_EPS_CELL, ny + pick_y * JXO_EPS_CELL, &picked);
   /* a key or goal event that moving the position by JXO_EPS_CELL could flip */
+  int ev0 = pickup_events(e, nx, ny, NULL);
   for (int k = 0; k < 4; ++k) {
     double px = nx + ((k & 1) ? JXO_EPS_CELL : -JXO_EPS_CELL);
     double py = ny + ((k & 2) ? JXO_EPS_CELL : -JXO_EPS_CELL);
-    if (pickup_events(e, px, py, NULL) != ev) near = 1;
+    if (pickup_events(e, px, py, NULL) != ev0) near = 1;
   }
   e->keys |= picked;
   *reward = cfg->step_reward + ((ev & JXO_EV_KEY) ? cfg->key_reward : 0.0) +
@@ -638,6 +654,20 @@ int jxo_step(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t actio
   *events = ev | (near ? JXO_EV_NEAR_TIE : 0);
   if (d) jxo_generate(cfg, env_index, e->episode + 1, e);
   return 0;
+}
+
+int jxo_step(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t action, double* reward,
+             int32_t* done, int32_t* events) {
+  return step_impl(cfg, env_index, e, action, 0, 0, 0, 0, reward, done, events);
+}
+
+int jxo_step_biased(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t action, int32_t coll_x,
+                    int32_t coll_y, int32_t pick_x, int32_t pick_y, double* reward, int32_t* done,
+                    int32_t* events) {
+  if (coll_x < -1 || coll_x > 1 || coll_y < -1 || coll_y > 1 || pick_x < -1 || pick_x > 1 || pick_y < -1 ||
+      pick_y > 1)
+    return -1;
+  return step_impl(cfg, env_index, e, action, coll_x, coll_y, pick_x, pick_y, reward, done, events);
 }
 
 /* ------------------------------------------------------------ raycast ----
@@ -760,7 +790,12 @@ static sprite_screen project_sprite(const jxo_config* cfg, const jxo_env* e, int
   return o;
 }
 
-int jxo_render(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray* rays, uint8_t* ambiguous) {
+/* The frame with every column's ray cast under `bias` (see jxo_cast): 0 the
+ * exact frame. A biased frame is one of the frames a corner ray admits, so
+ * its ambiguity flags leave out the whole-column flag of corner rays (the
+ * caller compares such a column against the variant its ray took). */
+static int render_impl(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray* rays,
+                       uint8_t* ambiguous, int32_t bias) {
   if (!config_ok(cfg)) return -1;
   int H = cfg->frame_h, W = cfg->frame_w;
   double th = heading(cfg, e);
@@ -775,7 +810,7 @@ int jxo_render(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray*
     double cx = 2.0 * (col + 0.5) / W - 1.0;
     double rx = c - cx * T * s, ry = s + cx * T * c;
     jxo_ray* r = &col_rays[col];
-    jxo_cast(cfg, e, e->x, e->y, rx, ry, 0, r);
+    jxo_cast(cfg, e, e->x, e->y, rx, ry, bias, r);
     slice_rows(H, r->perp, r);
     r->corner = 0;
     if (want_flags) {
@@ -814,7 +849,7 @@ int jxo_render(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray*
       px[2] = rgb[2];
     }
     if (ambiguous) {
-      if (r->corner) {
+      if (r->corner && bias == 0) {
         for (int row = 0; row < H; ++row) ambiguous[row * W + col] = 1;
       } else if (r->h_ambiguous && cfg->shading) {
         /* a one-row change of h recolours the whole slice */
@@ -883,6 +918,16 @@ int jxo_render(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray*
   return 0;
 }
 
+int jxo_render(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray* rays, uint8_t* ambiguous) {
+  return render_impl(cfg, e, frame, rays, ambiguous, 0);
+}
+
+int jxo_render_biased(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray* rays, uint8_t* ambiguous,
+                      int32_t bias) {
+  if (bias < -1 || bias > 1) return -1;
+  return render_impl(cfg, e, frame, rays, ambiguous, bias);
+}
+
 /* ------------------------------------------------------------ batches ---- */
 static int clamp_threads(int32_t nthreads) { return nthreads < 1 ? 1 : nthreads; }
 
@@ -908,15 +953,38 @@ int jxo_step_render_batch(const jxo_config* cfg, const int32_t* env_index, jxo_e
   return err ? -1 : 0;
 }
 
-int jxo_render_batch(const jxo_config* cfg, const jxo_env* envs, int32_t n, uint8_t* frames, jxo_ray* rays,
-                     uint8_t* ambiguous, int32_t nthreads) {
-  if (!config_ok(cfg)) return -1;
+int jxo_render_batch_biased(const jxo_config* cfg, const jxo_env* envs, int32_t n, uint8_t* frames, jxo_ray* rays,
+                            uint8_t* ambiguous, int32_t bias, int32_t nthreads) {
+  if (!config_ok(cfg) || bias < -1 || bias > 1) return -1;
   size_t fb = (size_t)cfg->frame_h * cfg->frame_w;
   int err = 0;
 #pragma omp parallel for num_threads(clamp_threads(nthreads)) schedule(dynamic, 4) reduction(| : err)
   for (int32_t i = 0; i < n; ++i)
-    err |= jxo_render(cfg, &envs[i], frames + fb * 3 * i, rays ? rays + (size_t)cfg->frame_w * i : NULL,
-                      ambiguous ? ambiguous + fb * i : NULL) != 0;
+    err |= render_impl(cfg, &envs[i], frames + fb * 3 * i, rays ? rays + (size_t)cfg->frame_w * i : NULL,
+                       ambiguous ? ambiguous + fb * i : NULL, bias) != 0;
+  return err ? -1 : 0;
+}
+
+int jxo_render_batch(const jxo_config* cfg, const jxo_env* envs, int32_t n, uint8_t* frames, jxo_ray* rays,
+                     uint8_t* ambiguous, int32_t nthreads) {
+  return jxo_render_batch_biased(cfg, envs, n, frames, rays, ambiguous, 0, nthreads);
+}
+
+/* jxo_step_biased over n environments with one bias choice for all (no frames). */
+int jxo_step_batch_biased(const jxo_config* cfg, const int32_t* env_index, jxo_env* envs, int32_t n,
+                          const uint8_t* actions, int32_t coll_x, int32_t coll_y, int32_t pick_x, int32_t pick_y,
+                          float* rewards, uint8_t* dones, int32_t* events, int32_t nthreads) {
+  if (!config_ok(cfg)) return -1;
+  int err = 0;
+#pragma omp parallel for num_threads(clamp_threads(nthreads)) schedule(dynamic, 4) reduction(| : err)
+  for (int32_t i = 0; i < n; ++i) {
+    double r;
+    int32_t d, ev;
+    err |= jxo_step_biased(cfg, env_index[i], &envs[i], actions[i], coll_x, coll_y, pick_x, pick_y, &r, &d, &ev) != 0;
+    rewards[i] = (float)r;
+    dones[i] = (uint8_t)d;
+    events[i] = ev;
+  }
   return err ? -1 : 0;
 }
 

@@ -170,9 +170,24 @@ int jxo_step(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t actio
 int jxo_cast(const jxo_config* cfg, const jxo_env* e, double ox, double oy, double rx, double ry,
              int32_t bias, jxo_ray* out);
 
+/* jxo_step with the decisions finite precision may flip taken a chosen way,
+ * to enumerate the outcomes a near tie (JXO_EV_NEAR_TIE) admits. coll_x,
+ * coll_y in {-1, 0, +1} for the x and y collision tests: 0 exact; +1 a test
+ * within JXO_EPS_CELL of flipping lets the box move; -1 blocks it. pick_x,
+ * pick_y in {-1, 0, +1}: key and goal events are evaluated at the position
+ * moved by that many JXO_EPS_CELL. All zero is jxo_step. Returns 0 or -1. */
+int jxo_step_biased(const jxo_config* cfg, int32_t env_index, jxo_env* e, int32_t action, int32_t coll_x,
+                    int32_t coll_y, int32_t pick_x, int32_t pick_y, double* reward, int32_t* done,
+                    int32_t* events);
+
 /* Render one frame [H][W][3]. rays (W entries) and ambiguous ([H][W]) may be NULL. */
 int jxo_render(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray* rays,
                uint8_t* ambiguous);
+/* jxo_render with every ray cast under `bias` (-1, 0, +1; see jxo_cast): the
+ * frame of one tie decision for all corner rays. Corner columns are then not
+ * flagged as wholly ambiguous (only their slice edges, as other columns). */
+int jxo_render_biased(const jxo_config* cfg, const jxo_env* e, uint8_t* frame, jxo_ray* rays,
+                      uint8_t* ambiguous, int32_t bias);
 
 /* Batched helpers over n environments (OpenMP over environments when nthreads > 1).
  * frames / rays / ambiguous may be NULL. rewards are rounded to float32. */
@@ -181,6 +196,11 @@ int jxo_step_render_batch(const jxo_config* cfg, const int32_t* env_index, jxo_e
                           uint8_t* frames, jxo_ray* rays, uint8_t* ambiguous, int32_t nthreads);
 int jxo_render_batch(const jxo_config* cfg, const jxo_env* envs, int32_t n, uint8_t* frames,
                      jxo_ray* rays, uint8_t* ambiguous, int32_t nthreads);
+int jxo_render_batch_biased(const jxo_config* cfg, const jxo_env* envs, int32_t n, uint8_t* frames,
+                            jxo_ray* rays, uint8_t* ambiguous, int32_t bias, int32_t nthreads);
+int jxo_step_batch_biased(const jxo_config* cfg, const int32_t* env_index, jxo_env* envs, int32_t n,
+                          const uint8_t* actions, int32_t coll_x, int32_t coll_y, int32_t pick_x, int32_t pick_y,
+                          float* rewards, uint8_t* dones, int32_t* events, int32_t nthreads);
 int jxo_generate_batch(const jxo_config* cfg, const int32_t* env_index, const uint32_t* episode,
                        jxo_env* out, int32_t n, int32_t nthreads);
 
