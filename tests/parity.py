@@ -3,15 +3,23 @@
 Tolerances (from the accuracy rules the hot path is held to):
 - bit-exact: rewards (float32), done flags, key/door state, episode counters,
   generated maps, spawn cells and object cells; hit cell and hit side of every
-  ray the oracle does not flag as a corner ray (a finite-precision tie within
-  1e-5 cells could change it); corner rays must stay <= 0.1%;
+  ray;
 - pose within 1e-5 absolute; perpendicular distance within 1e-5 relative;
 - pixels: at most 1e-4 of all pixels may differ, and only pixels the oracle
   flags as lying on an edge that finite precision can move (slice edges whose
-  height rounding is within tolerance, sprite silhouette edges, corner-ray
-  columns).
-Steps whose collision or pickup decision the oracle flags as a near tie
-(within 1e-5 cells) are excluded for that env and counted (<= 1%).
+  height rounding is within tolerance, sprite silhouette edges).
+
+Where finite precision admits more than one correct result, the GPU's result
+must be one of them, and nothing is skipped:
+- a corner ray (a DDA tie within 1e-5 cells, or a hit within 1e-5 of a grid
+  corner) must hit the cell and side of the oracle's cast with its ties taken
+  towards x or towards y, and its column must match the frame of that choice;
+  corner rays are counted and must stay <= 0.1% of rays;
+- a near-tie step (a collision or pickup decision within 1e-5 cells of
+  flipping) must equal the oracle's step with those decisions taken one of
+  the ways they admit (rewards, done, keys, counters exact, pose within 1e-5);
+  near ties are counted per run (consecutive checked steps of one env in one
+  episode) and the runs must stay <= 0.1% of env-steps.
 """
 
 from __future__ import annotations
@@ -29,13 +37,13 @@ TOL_POSE = 1e-5
 TOL_PERP_REL = 1e-5
 PIXEL_FRAC = 1e-4
 CORNER_FRAC = 1e-3
-# Steps whose collision or pickup decision lies within 1e-5 cells of flipping
-# are excluded and counted. An agent whose box edge ends within 1e-5 of a wall
-# boundary (a heading within a few hundredths of a degree of an axis) stays
-# ambiguous for every step it keeps pushing into that wall, so one env of a
-# small batch can give several such steps in a row: at most 1% of env-steps.
-NEAR_TIE_FRAC = 1e-2
+# Near-tie steps are checked against every outcome the tie admits and counted
+# per run: an agent whose box edge ends within 1e-5 of a wall face stays in the
+# tie for every step it keeps pushing into that wall, one run of steps.
+NEAR_TIE_FRAC = 1e-3
 NTHREADS = max(1, min(16, os.cpu_count() or 1))
+# the decisions a near tie admits: (collision x, collision y, pickup x, pickup y) biases
+TIE_VARIANTS = [(cx, cy, px, py) for cx in (1, -1) for cy in (1, -1) for px in (1, -1) for py in (1, -1)]
 
 
 def oracle_cfg(cfg: dict) -> np.ndarray:
@@ -73,17 +81,29 @@ class Stats:
     pixel_mismatch: int = 0
     rays: int = 0
     corner_rays: int = 0
+    corner_rays_other_way: int = 0  # corner rays the GPU took the other way from the exact FP64 cast
     env_steps: int = 0
-    near_ties: int = 0
+    near_ties: int = 0  # near-tie env-steps (each checked against the outcomes it admits)
+    near_tie_runs: int = 0
+    near_ties_other_way: int = 0  # near-tie steps whose GPU outcome differs from the exact FP64 step
     key_events: int = 0
     goal_events: int = 0
     resets: int = 0
     notes: list = field(default_factory=list)
+    _tie_last: dict = field(default_factory=dict, repr=False)
+
+    def tie(self, key, episode: int, step: int, step_gap: int):
+        """Count a near-tie env-step; a new run unless the same env's previous
+        checked step (same episode) was one too."""
+        self.near_ties += 1
+        if self._tie_last.get(key) != (episode, step - step_gap):
+            self.near_tie_runs += 1
+        self._tie_last[key] = (episode, step)
 
     def check(self):
         assert self.pixel_mismatch <= PIXEL_FRAC * max(self.pixels, 1), self
         assert self.corner_rays <= CORNER_FRAC * max(self.rays, 1), self
-        assert self.near_ties <= max(2, NEAR_TIE_FRAC * self.env_steps), self
+        assert self.near_tie_runs <= max(1, NEAR_TIE_FRAC * self.env_steps), self
 
 
 def compare_generated(gpu: np.ndarray, ref: np.ndarray, S: int, K: int, where: str = ""):
@@ -101,10 +121,45 @@ def compare_generated(gpu: np.ndarray, ref: np.ndarray, S: int, K: int, where: s
         assert (gpu["spr_y"][:, :K] == ref["spr_y"][:, :K].astype(np.float32)).all()
 
 
-def compare_frames(gpu_frames: np.ndarray, ref: dict, stats: Stats, mask=None):
-    of, amb = ref["frames"], ref["ambiguous"].astype(bool)
-    if mask is not None:
-        gpu_frames, of, amb = gpu_frames[mask], of[mask], amb[mask]
+def render_ref(ocfg: np.ndarray, states: np.ndarray) -> dict:
+    """The oracle's frames, rays and ambiguity flags of `states`, plus, for the
+    envs that have a corner ray, the frames with every tie taken towards x
+    (+1) and towards y (-1): the results a corner ray admits."""
+    states = np.ascontiguousarray(states)
+    ref = oracle.render(ocfg, states, nthreads=NTHREADS)
+    ec = np.nonzero(ref["rays"]["corner"].any(axis=1))[0]
+    ref["variants"] = {"envs": ec}
+    if len(ec):
+        for b in (1, -1):
+            ref["variants"][b] = oracle.render(ocfg, states[ec], nthreads=NTHREADS, bias=b)
+    return ref
+
+
+def _variant_rows(ref: dict, e: int):
+    """Row of env e in the biased renders."""
+    ec = ref["variants"]["envs"]
+    k = int(np.searchsorted(ec, e))
+    assert k < len(ec) and ec[k] == e
+    return k
+
+
+def compare_frames(gpu_frames: np.ndarray, ref: dict, stats: Stats):
+    """Every pixel equals the oracle's, except where the oracle flags an edge
+    that finite precision can move; a corner-ray column must equal the column
+    of the oracle frame with that ray's tie taken one of its two ways."""
+    of, amb = ref["frames"].copy(), ref["ambiguous"].astype(bool)
+    corner = ref["rays"]["corner"].astype(bool)
+    for e, c in np.argwhere(corner):
+        k = _variant_rows(ref, e)
+        for b in (1, -1):
+            v = ref["variants"][b]
+            vamb = v["ambiguous"][k, :, c].astype(bool)
+            if ((gpu_frames[e, :, c] == v["frames"][k, :, c]).all(axis=-1) | vamb).all():
+                of[e, :, c] = v["frames"][k, :, c]
+                amb[e, :, c] = vamb
+                break
+        else:
+            raise AssertionError(f"corner column ({e}, {c}) matches neither tie decision")
     mism = (gpu_frames != of).any(axis=-1)
     bad = mism & ~amb
     if bad.any():
@@ -114,21 +169,39 @@ def compare_frames(gpu_frames: np.ndarray, ref: dict, stats: Stats, mask=None):
     stats.pixel_mismatch += int(mism.sum())
 
 
-def compare_rays(hits: np.ndarray, perp: np.ndarray, ref: dict, stats: Stats, mask=None):
+def _perp_ok(po: np.ndarray, pg: np.ndarray) -> np.ndarray:
+    pg = pg.astype(np.float64)
+    diff = np.where(po == pg, 0.0, np.abs(pg - po))
+    rel = np.where(po > 0, diff / np.where(po > 0, po, 1.0), diff)
+    return rel <= TOL_PERP_REL
+
+
+def compare_rays(hits: np.ndarray, perp: np.ndarray, ref: dict, stats: Stats):
+    """Hit cell and side exact, perp within 1e-5 relative, slice height exact
+    unless its rounding is within tolerance; a corner ray must equal the
+    oracle's cast with its tie taken towards x or towards y."""
     rays = ref["rays"]
-    if mask is not None:
-        hits, perp, rays = hits[mask], perp[mask], rays[mask]
     corner = rays["corner"].astype(bool)
     ok = ~corner
     assert (hits[..., 0][ok] == rays["cell_x"][ok]).all(), "hit cell x"
     assert (hits[..., 1][ok] == rays["cell_y"][ok]).all(), "hit cell y"
     assert (hits[..., 2][ok] == rays["side"][ok]).all(), "hit side"
-    po, pg = rays["perp"][ok], perp[ok].astype(np.float64)
-    diff = np.where(po == pg, 0.0, np.abs(pg - po))
-    rel = np.where(po > 0, diff / np.where(po > 0, po, 1.0), diff)
-    assert rel.max(initial=0.0) <= TOL_PERP_REL, f"perp rel err {rel.max()}"
+    assert _perp_ok(rays["perp"][ok], perp[ok]).all(), "perp relative error"
     hok = ok & ~rays["h_ambiguous"].astype(bool)
     assert (hits[..., 3][hok] == rays["h"][hok]).all(), "slice height"
+    for e, c in np.argwhere(corner):
+        k = _variant_rows(ref, e)
+        for b in (1, -1):
+            r = ref["variants"][b]["rays"][k, c]
+            if (hits[e, c, 0], hits[e, c, 1], hits[e, c, 2]) != (r["cell_x"], r["cell_y"], r["side"]):
+                continue
+            assert _perp_ok(np.array([r["perp"]]), np.array([perp[e, c]])).all(), f"corner ray ({e}, {c}) perp"
+            assert r["h_ambiguous"] or hits[e, c, 3] == r["h"], f"corner ray ({e}, {c}) slice height"
+            if (r["cell_x"], r["cell_y"], r["side"]) != (rays["cell_x"][e, c], rays["cell_y"][e, c], rays["side"][e, c]):
+                stats.corner_rays_other_way += 1
+            break
+        else:
+            raise AssertionError(f"corner ray ({e}, {c}) hit {tuple(hits[e, c, :3])} matches neither tie decision")
     stats.rays += corner.size
     stats.corner_rays += int(corner.sum())
 
@@ -204,7 +277,7 @@ def check_reset(run: Run, stats: Stats, idx=None):
     ref = oracle.generate(run.ocfg, idx.astype(np.int32), 0, nthreads=NTHREADS)
     compare_generated(gpu, ref, run.env.S, run.env.K, "at reset")
     # render parity on the exact same state (the GPU's, decoded)
-    out = oracle.render(run.ocfg, gpu, nthreads=NTHREADS)
+    out = render_ref(run.ocfg, gpu)
     compare_frames(run.frames.cpu().numpy()[idx], out, stats)
     hits, perp = run.rays()
     compare_rays(hits[idx], perp[idx], out, stats)
@@ -216,6 +289,71 @@ def forward_biased_actions(seed: int, step: int, n: int) -> np.ndarray:
     rng = np.random.default_rng([seed, step, 77])
     other = rng.choice(np.array([3, 4, 5, 6], np.uint8), size=n)
     return np.where(rng.random(n) < 0.6, np.uint8(1), other).astype(np.uint8)
+
+
+def _same_state(g: np.ndarray, r: np.ndarray, done: bool, S: int, K: int) -> bool:
+    """One env record of the GPU equals the oracle's after a step: a fresh
+    episode exactly (done), else counters, keys and map exactly and the pose
+    within TOL_POSE."""
+    n = S * S
+    if not (g["map"][:n] == r["map"][:n]).all():
+        return False
+    if any(g[k] != r[k] for k in ("turn", "t", "episode", "keys")):
+        return False
+    if done:
+        return (all(g[k] == r[k] for k in ("x", "y", "key_x", "key_y", "goal_x", "goal_y", "door_x", "door_y",
+                                           "n_sprites"))
+                and np.float32(g["theta0"]) == np.float32(r["theta0"])
+                and (g["spr_type"][:K] == r["spr_type"][:K]).all())
+    return abs(g["x"] - r["x"]) <= TOL_POSE and abs(g["y"] - r["y"]) <= TOL_POSE
+
+
+def check_step(ocfg: np.ndarray, idx: np.ndarray, pre: np.ndarray, actions: np.ndarray, cur: np.ndarray,
+               rewards: np.ndarray, dones: np.ndarray, S: int, K: int, stats: Stats, step: int, where: str = "",
+               key=(), step_gap: int = 1):
+    """Step the oracle from `pre` (the GPU's pre-step states of envs idx) and
+    compare with the GPU's rewards, dones and post-step states `cur`. A
+    near-tie step must equal the oracle's step under one of the decisions the
+    tie admits."""
+    idx = np.asarray(idx, dtype=np.int32)
+    ref_st = np.ascontiguousarray(pre).copy()
+    ref = oracle.step(ocfg, idx, ref_st, actions, nthreads=NTHREADS)
+    ev = ref["events"]
+    near = (ev & oracle.EV_NEAR_TIE) != 0
+    ok = ~near
+    stats.env_steps += len(idx)
+    stats.key_events += int(((ev & oracle.EV_KEY) != 0)[ok].sum())
+    stats.goal_events += int(((ev & oracle.EV_GOAL) != 0)[ok].sum())
+    assert (rewards[ok] == ref["rewards"][ok]).all(), f"rewards differ at step {step} {where}"
+    assert (dones[ok] == ref["dones"][ok]).all(), f"dones differ at step {step} {where}"
+    done = (ref["dones"] == 1) & ok
+    stats.resets += int(done.sum())
+    if done.any():
+        compare_generated(cur[done], ref_st[done], S, K, f"after auto-reset at step {step} {where}")
+    live = ok & ~done
+    for name in ("turn", "t", "episode", "keys"):
+        assert (cur[name][live] == ref_st[name][live]).all(), f"{name} differs at step {step} {where}"
+    assert (cur["map"][live][:, : S * S] == ref_st["map"][live][:, : S * S]).all(), f"map differs at step {step} {where}"
+    for name in ("x", "y"):
+        err = np.abs(cur[name][live] - ref_st[name][live])
+        assert err.max(initial=0.0) <= TOL_POSE, f"{name} err {err.max()} at step {step} {where}"
+    nt = np.nonzero(near)[0]
+    if not len(nt):
+        return
+    sub = np.ascontiguousarray(pre[nt])
+    outs = []
+    for v in TIE_VARIANTS:
+        st = sub.copy()
+        o = oracle.step_biased(ocfg, idx[nt], st, actions[nt], *v, nthreads=NTHREADS)
+        outs.append((o, st))
+    for j, e in enumerate(nt):
+        stats.tie(key + (int(idx[e]),), int(pre["episode"][e]), step, step_gap)
+        match = [(o["rewards"][j] == rewards[e] and o["dones"][j] == dones[e] and
+                  _same_state(cur[e], st[j], bool(o["dones"][j]), S, K)) for o, st in outs]
+        assert any(match), f"env {idx[e]} near-tie step {step} {where}: GPU outcome is none of the tie's outcomes"
+        exact = (ref["rewards"][e] == rewards[e] and ref["dones"][e] == dones[e] and
+                 _same_state(cur[e], ref_st[e], bool(ref["dones"][e]), S, K))
+        stats.near_ties_other_way += int(not exact)
 
 
 def lockstep(run: Run, stats: Stats, n_steps: int, seed: int, first_step: int = 0, idx=None, check_every: int = 1,
@@ -239,28 +377,10 @@ def lockstep(run: Run, stats: Stats, n_steps: int, seed: int, first_step: int = 
         if run.gray is not None:
             run.gray.check(run.env)
         cur = run.state(idx)
-        ref = oracle.step(run.ocfg, idx.astype(np.int32), prev, a[idx], nthreads=NTHREADS)
-        ev = ref["events"]
-        near = (ev & oracle.EV_NEAR_TIE) != 0
-        ok = ~near
-        stats.env_steps += len(idx)
-        stats.near_ties += int(near.sum())
-        stats.key_events += int(((ev & oracle.EV_KEY) != 0)[ok].sum())
-        stats.goal_events += int(((ev & oracle.EV_GOAL) != 0)[ok].sum())
-        assert (rewards[idx][ok] == ref["rewards"][ok]).all(), f"rewards differ at step {s}"
-        assert (dones[idx][ok] == ref["dones"][ok]).all(), f"dones differ at step {s}"
-        done = (ref["dones"] == 1) & ok
-        stats.resets += int(done.sum())
-        if done.any():
-            compare_generated(cur[done], prev[done], run.env.S, run.env.K, f"after auto-reset at step {s}")
-        live = ok & ~done
-        for name in ("turn", "t", "episode", "keys"):
-            assert (cur[name][live] == prev[name][live]).all(), f"{name} differs at step {s}"
-        for name in ("x", "y"):
-            err = np.abs(cur[name][live] - prev[name][live])
-            assert err.max(initial=0.0) <= TOL_POSE, f"{name} err {err.max()} at step {s}"
+        check_step(run.ocfg, idx, prev, a[idx], cur, rewards[idx], dones[idx], run.env.S, run.env.K, stats, s,
+                   step_gap=check_every)
         # render parity on the exact post-step state of the GPU
-        rr = oracle.render(run.ocfg, cur, nthreads=NTHREADS)
+        rr = render_ref(run.ocfg, cur)
         compare_frames(frames[idx], rr, stats)
         hits, perp = run.rays()
         compare_rays(hits[idx], perp[idx], rr, stats)
@@ -353,7 +473,7 @@ def batch_check_reset(run: BatchRun, stats: Stats):
         gpu = to_oracle(env, env.get_state())
         ref = oracle.generate(run.ocfgs[i], np.arange(env.n, dtype=np.int32), 0, nthreads=NTHREADS)
         compare_generated(gpu, ref, env.S, env.K, f"at batch reset, group {i}")
-        compare_frames(run.group_frames(frames, i), oracle.render(run.ocfgs[i], gpu, nthreads=NTHREADS), stats)
+        compare_frames(run.group_frames(frames, i), render_ref(run.ocfgs[i], gpu), stats)
 
 
 def batch_lockstep(run: BatchRun, stats: Stats, n_steps: int, seed: int, first_step: int = 0, check_every: int = 1,
@@ -372,24 +492,7 @@ def batch_lockstep(run: BatchRun, stats: Stats, n_steps: int, seed: int, first_s
         for i, env in enumerate(run.envs):
             es, _ = run.batch.group_slices(i)
             idx = np.arange(env.n, dtype=np.int32)
-            ref = oracle.step(run.ocfgs[i], idx, prev[i], a[es], nthreads=NTHREADS)
-            ev = ref["events"]
-            ok = (ev & oracle.EV_NEAR_TIE) == 0
-            stats.env_steps += env.n
-            stats.near_ties += int((~ok).sum())
-            stats.key_events += int(((ev & oracle.EV_KEY) != 0)[ok].sum())
-            stats.goal_events += int(((ev & oracle.EV_GOAL) != 0)[ok].sum())
-            assert (rewards[es][ok] == ref["rewards"][ok]).all(), f"rewards differ, group {i} step {s}"
-            assert (dones[es][ok] == ref["dones"][ok]).all(), f"dones differ, group {i} step {s}"
-            done = (ref["dones"] == 1) & ok
-            stats.resets += int(done.sum())
-            if done.any():
-                compare_generated(cur[i][done], prev[i][done], env.S, env.K, f"auto-reset, group {i} step {s}")
-            live = ok & ~done
-            for name in ("turn", "t", "episode", "keys"):
-                assert (cur[i][name][live] == prev[i][name][live]).all(), f"{name}, group {i} step {s}"
-            for name in ("x", "y"):
-                err = np.abs(cur[i][name][live] - prev[i][name][live])
-                assert err.max(initial=0.0) <= TOL_POSE, f"{name} err {err.max()}, group {i} step {s}"
-            rr = oracle.render(run.ocfgs[i], cur[i], nthreads=NTHREADS)
+            check_step(run.ocfgs[i], idx, prev[i], a[es], cur[i], rewards[es], dones[es], env.S, env.K, stats, s,
+                       f"group {i}", key=(i,), step_gap=check_every)
+            rr = render_ref(run.ocfgs[i], cur[i])
             compare_frames(run.group_frames(frames, i), rr, stats)

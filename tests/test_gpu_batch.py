@@ -8,7 +8,8 @@ import torch
 import oracle
 from paper_2605_19926_gb300 import inputs, jx
 from parity import (NTHREADS, BatchRun, Run, Stats, batch_check_reset, batch_lockstep, check_door_crossings,
-                    compare_frames, compare_generated, forward_biased_actions, script_goal_and_door, to_oracle)
+                    check_step, compare_frames, compare_generated, forward_biased_actions, render_ref,
+                    script_goal_and_door, to_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -215,7 +216,7 @@ def test_full_size_uneven_batch_sampled():
         gpu = to_oracle(env, env.get_state(), idx[i])
         ref = oracle.generate(run.ocfgs[i], idx[i], 0, nthreads=NTHREADS)
         compare_generated(gpu, ref, env.S, env.K, f"group {i}")
-        compare_frames(run.group_frames(frames, i)[idx[i]], oracle.render(run.ocfgs[i], gpu, nthreads=NTHREADS), stats)
+        compare_frames(run.group_frames(frames, i)[idx[i]], render_ref(run.ocfgs[i], gpu), stats)
     T = 3
     acts = np.stack([inputs.actions(5, s, run.batch.n) for s in range(T)])
     step_frames = []
@@ -226,15 +227,9 @@ def test_full_size_uneven_batch_sampled():
         for i, env in enumerate(run.envs):
             es, _ = run.batch.group_slices(i)
             cur = to_oracle(env, env.get_state(), idx[i])
-            ref = oracle.step(run.ocfgs[i], idx[i], prev[i], acts[s][es][idx[i]], nthreads=NTHREADS)
-            ok = (ref["events"] & oracle.EV_NEAR_TIE) == 0
-            stats.env_steps += len(idx[i])
-            stats.near_ties += int((~ok).sum())
-            assert (rewards[es][idx[i]][ok] == ref["rewards"][ok]).all()
-            assert (dones[es][idx[i]][ok] == ref["dones"][ok]).all()
-            for name in ("x", "y"):
-                assert np.abs(cur[name][ok] - prev[i][name][ok]).max(initial=0.0) <= 1e-5
-            rr = oracle.render(run.ocfgs[i], cur, nthreads=NTHREADS)
+            check_step(run.ocfgs[i], idx[i], prev[i], acts[s][es][idx[i]], cur, rewards[es][idx[i]],
+                       dones[es][idx[i]], env.S, env.K, stats, s, f"group {i}", key=(i,))
+            rr = render_ref(run.ocfgs[i], cur)
             compare_frames(run.group_frames(frames, i)[idx[i]], rr, stats)
     stats.check()
     # the same three steps as one rollout launch from a fresh reset

@@ -5,8 +5,9 @@ import torch
 
 import oracle
 from paper_2605_19926_gb300 import inputs, jx
-from parity import (NTHREADS, Run, Stats, check_door_crossings, check_reset, compare_frames, compare_generated,
-                    compare_rays, forward_biased_actions, lockstep, script_goal_and_door, to_oracle)
+from parity import (NTHREADS, Run, Stats, check_door_crossings, check_reset, check_step, compare_frames,
+                    compare_generated, compare_rays, forward_biased_actions, lockstep, render_ref, script_goal_and_door,
+                    to_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -157,7 +158,7 @@ def test_render_only_and_state_roundtrip():
     run.env.render(run.frames)
     torch.cuda.synchronize()
     gpu = run.frames.cpu().numpy()
-    ref = oracle.render(run.ocfg, to_oracle(run.env, blob), nthreads=NTHREADS)
+    ref = render_ref(run.ocfg, to_oracle(run.env, blob))
     stats = Stats()
     compare_frames(gpu, ref, stats)
     stats.check()
@@ -178,7 +179,7 @@ def test_degenerate_poses_axis_rays_and_boundaries():
     run.env.set_state(blob)
     run.env.render(run.frames)
     torch.cuda.synchronize()
-    ref = oracle.render(run.ocfg, to_oracle(run.env, blob), nthreads=NTHREADS)
+    ref = render_ref(run.ocfg, to_oracle(run.env, blob))
     stats = Stats()
     compare_frames(run.frames.cpu().numpy(), ref, stats)
     hits, perp = run.rays()
@@ -323,7 +324,7 @@ def test_envs_of_different_sizes_coexist():
         fs, _, _ = small.step(inputs.actions(2, s, 3))
     stats = Stats()
     for run in (big, small):
-        ref = oracle.render(run.ocfg, run.state(), nthreads=NTHREADS)
+        ref = render_ref(run.ocfg, run.state())
         run.env.render(run.frames)
         torch.cuda.synchronize()
         compare_frames(run.frames.cpu().numpy(), ref, stats)
@@ -354,36 +355,67 @@ def test_rollout_with_gray_stack_matches_step_sequence(name, T):
 
 def test_large_scale_mazes_with_rooms_sampled():
     """65,536 envs of 128 x 128 mazes with rooms, 16 sprite slots, 128 x 128 RGB and
-    the grayscale stack: 24 sampled envs against the oracle at reset and over
-    4 steps; their grayscale stacks against the host model."""
+    the grayscale stack, in the launch configuration the benchmark times (the
+    batched kernel with its pinned tiling): 64 sampled envs against the oracle at
+    reset, then, after rollouts up to step 496, in lockstep for 10 steps across
+    the 500-step horizon, where every env takes over its pre-built next episode
+    in one launch: rewards, dones, pose, turn, counters, keys, maps, regenerated
+    episodes, frames, rays and grayscale stacks."""
+    import bench
+
     cfg = inputs.large_scale()
+    N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
     run = Run(cfg)
+    run.env.tiling = bench.parse_tiling(jx, bench.LARGE_TILING)
     stats = Stats()
     rng = np.random.default_rng(12)
-    idx = np.sort(rng.choice(cfg["n_envs"], 24, replace=False))
-    idx[-1] = cfg["n_envs"] - 1
+    idx = np.sort(rng.choice(N, 64, replace=False))
+    idx[-1] = N - 1
     run.reset()
-    gpu = run.state(idx)
+    blob = run.env.get_state()
+    gpu = to_oracle(run.env, blob, idx)
     ref = oracle.generate(run.ocfg, idx.astype(np.int32), 0, nthreads=NTHREADS)
     compare_generated(gpu, ref, run.env.S, run.env.K, "at reset")
-    compare_frames(run.frames.cpu().numpy()[idx], oracle.render(run.ocfg, gpu, nthreads=NTHREADS), stats)
-    g = oracle.gray(run.frames.cpu().numpy()[idx])
-    f = run.env.fields(run.env.get_state())
-    assert (f["gray"][idx] == g[:, None]).all()
-    for s in range(4):
-        prev = run.state(idx)
-        a = inputs.actions(4, s, cfg["n_envs"])
+    rr = render_ref(run.ocfg, gpu)
+    compare_frames(run.frames.cpu().numpy()[idx], rr, stats)
+    hits, perp = run.rays()
+    compare_rays(hits[idx], perp[idx], rr, stats)
+    assert (run.env.fields(blob)["gray"][idx] == oracle.gray(run.frames.cpu().numpy()[idx])[:, None]).all()
+    # rollouts (4 steps per launch) up to step 496
+    T, first = 4, 496
+    acts = torch.from_numpy(inputs.action_stream(4, first, N)).to(run.dev)
+    frames = torch.empty((T, N, H, W, 3), dtype=torch.uint8, device=run.dev)
+    rewards = torch.empty((T, N), dtype=torch.float32, device=run.dev)
+    dones = torch.empty((T, N), dtype=torch.uint8, device=run.dev)
+    for c in range(first // T):
+        run.env.rollout(acts[c * T:(c + 1) * T], frames, rewards, dones)
+    torch.cuda.synchronize()
+    del frames, acts
+    run.env.sync_status()
+    blob = run.env.get_state()
+    assert (run.env.fields(blob)["t"] == first).all()
+    n_reset = 0
+    for s in range(first, first + 10):
+        prev = to_oracle(run.env, blob, idx)
+        a = inputs.actions(4, s, N)
         frames, rewards, dones = run.step(a)
-        cur = run.state(idx)
-        r = oracle.step(run.ocfg, idx.astype(np.int32), prev, a[idx], nthreads=NTHREADS)
-        ok = (r["events"] & oracle.EV_NEAR_TIE) == 0
-        assert (rewards[idx][ok] == r["rewards"][ok]).all() and (dones[idx][ok] == r["dones"][ok]).all()
-        assert np.abs(cur["x"][ok] - prev["x"][ok]).max(initial=0.0) <= 1e-5
-        compare_frames(frames[idx], oracle.render(run.ocfg, cur, nthreads=NTHREADS), stats)
-        f = run.env.fields(run.env.get_state())
+        blob = run.env.get_state()
+        f = run.env.fields(blob)
+        cur = to_oracle(run.env, blob, idx)
+        check_step(run.ocfg, idx, prev, a[idx], cur, rewards[idx], dones[idx], run.env.S, run.env.K, stats, s)
+        rr = render_ref(run.ocfg, cur)
+        compare_frames(frames[idx], rr, stats)
+        hits, perp = run.rays()
+        compare_rays(hits[idx], perp[idx], rr, stats)
         t = f["t"][idx]
-        planes = f["gray"][idx][np.arange(len(idx)), t % 4]
-        assert (planes == oracle.gray(frames[idx])).all()
+        g = oracle.gray(frames[idx])
+        planes = f["gray"][idx]
+        assert (planes[np.arange(len(idx)), t % 4] == g).all()
+        assert (planes[t == 0] == g[t == 0][:, None]).all()  # a fresh episode's frame in all four planes
+        n_reset += int(dones.sum())
+    assert n_reset >= N  # every env crossed the horizon
+    assert (f["episode"] >= 1).all()
+    run.env.sync_status()
     stats.check()
 
 

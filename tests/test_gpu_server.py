@@ -9,7 +9,7 @@ import torch
 
 import oracle
 from paper_2605_19926_gb300 import inputs, jx
-from parity import NTHREADS, Run, Stats, compare_frames, to_oracle
+from parity import NTHREADS, Run, Stats, compare_frames, render_ref, to_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -157,7 +157,7 @@ def test_served_frames_match_oracle():
         for r in range(30):
             server.wait(s.submit(inputs.actions(96, r, 24)), timeout=30.0)
             torch.cuda.synchronize()
-            ref = oracle.render(ocfg, to_oracle(s.env, s.env.get_state()), nthreads=NTHREADS)
+            ref = render_ref(ocfg, to_oracle(s.env, s.env.get_state()))
             compare_frames(s.frames.cpu().numpy(), ref, stats)
         s.close()
     stats.check()
