@@ -217,14 +217,18 @@ jx_status jx_step_host(jx_env* env, void* stream, const uint8_t* h_actions, uint
  * caching allocator, or a loop that may not take the implicit
  * synchronisation of a first-use cudaMalloc. It behaves like jx_step_host but
  * stages actions, frames, rewards and dones in a fixed array inside the
- * library (JX_STATIC_STAGING_BYTES per device, reserved when the library is
- * loaded and kept until the process exits) instead of buffers allocated on
- * first use, and it calls no allocating routine. The paper has no counterpart:
- * this is a deployment convenience of this library.
+ * library (JX_STATIC_STAGING_BYTES per device, kept until the process exits)
+ * instead of buffers allocated on first use, and it calls no allocating
+ * routine. The paper has no counterpart: this is a deployment convenience of
+ * this library.
  *  - Limit: the batch needs N * (3 H W + 6) bytes plus 256-byte alignment of
  *    four buffers; larger batches return JX_EINVAL with the sizes.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - The array of a device is reserved when the first env on that device is
+ *    created: jx_create, jx_create_ascii and jx_create_in look up its device
+ *    address (cudaGetSymbolAddress), which under CUDA's lazy module loading
+ *    is what loads it. So this call itself reserves nothing, and the memory
+ *    is taken while the caller can still afford it: create the env before
+ *    handing the rest of the device to a caching allocator.
  *  - All calls on a device share the one array, which keeps the last call's
  *    contents; every byte a call reads is written earlier in the same call.
  *    Calls that overlap on the GPU (several envs or threads on different

@@ -222,6 +222,36 @@ const char* jx_last_error(void) { return jx::host::g_last_error.c_str(); }
 
 }  // extern "C"
 
+// Staging for jx_step_host_static: a fixed array in every device's memory,
+// held until the process exits. Host code cannot use the name as a device
+// address; the per-device address comes from cudaGetSymbolAddress, which
+// jx_create (every path that keeps an env) calls with the env's device
+// current. Under CUDA's lazy module loading that lookup is what loads this
+// file's module and so reserves the array: it happens when the env is made,
+// not inside the first jx_step_host_static call.
+static __device__ __align__(256) uint8_t g_static_staging[JX_STATIC_STAGING_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Address of the staging array on `device`, which must be the current device
+// (looked up once per device).
+jx_status static_staging(int device, uint8_t** out) {
+  if (device < 0 || device >= kMaxDevices) return fail(JX_EINVAL, "device %d beyond %d", device, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[device]) {
+    void* ptr = nullptr;
+    cudaError_t err = cudaGetSymbolAddress(&ptr, g_static_staging);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress of the static staging array");
+    g_static_ptr[device] = ptr;
+  }
+  *out = static_cast<uint8_t*>(g_static_ptr[device]);
+  return JX_OK;
+}
+}  // namespace
+
 namespace {
 
 // jx_create / jx_env_bytes / jx_create_in. Everything that does not need
@@ -362,6 +392,15 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
     env->owns_mem = true;
   }
   env->mem_bytes = total;
+  {
+    // reserve the static staging array of this device now (see static_staging)
+    uint8_t* unused = nullptr;
+    if (jx_status st2 = static_staging(device, &unused)) {
+      if (env->owns_mem) cudaFree(env->mem);
+      delete env;
+      return st2;
+    }
+  }
   env->state = env->mem;
   env->aux = env->mem + off_aux;
   env->scratch = scratch_bytes ? env->mem + off_scratch : nullptr;
@@ -642,33 +681,6 @@ jx_status jx_step_host(jx_env* env, void* stream, const uint8_t* h_actions, uint
   if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(err, "host step");
   return JX_OK;
 }
-
-// Staging for jx_step_host_static: a fixed array in every device's memory,
-// reserved when the library is loaded and held until the process exits.
-// Host code cannot use the name as a device address; the per-device address
-// comes from cudaGetSymbolAddress.
-static __device__ __align__(256) uint8_t g_static_staging[JX_STATIC_STAGING_BYTES];
-
-namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mutex;
-void* g_static_ptr[kMaxDevices] = {};
-
-// Address of the staging array on the current device (looked up on the first
-// call per device).
-jx_status static_staging(int device, uint8_t** out) {
-  if (device < 0 || device >= kMaxDevices) return fail(JX_EINVAL, "device %d beyond %d", device, kMaxDevices);
-  std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_ptr[device]) {
-    void* ptr = nullptr;
-    cudaError_t err = cudaGetSymbolAddress(&ptr, g_static_staging);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress of the static staging array");
-    g_static_ptr[device] = ptr;
-  }
-  *out = static_cast<uint8_t*>(g_static_ptr[device]);
-  return JX_OK;
-}
-}  // namespace
 
 jx_status jx_step_host_static(jx_env* env, void* stream, const uint8_t* h_actions, uint8_t* h_frames,
                               float* h_rewards, uint8_t* h_dones) {

@@ -7,8 +7,9 @@ jx_step_host_static stages through a fixed array inside the library instead
 of the buffers jx_step_host allocates on first use. These tests check, through
 the C ABI, that it returns exactly what jx_step_host returns on two calls in a
 row (the second call ends every episode and regenerates the maps, and runs on
-the array the first call left behind), and that batches too large for the
-array are refused. This file is collected last on purpose.
+the array the first call left behind) while the device's free memory stays
+the same across each call, and that batches too large for the array are
+refused. This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -49,8 +50,13 @@ def test_static_staging_matches_host_step_two_calls(jx):
     fn, rn, dn = _host_buffers(cfg)
     for s in range(2):
         act = torch.from_numpy(inputs.actions(23, s, N)).pin_memory()
-        ref.step_host(act, fr, rr, dr)
+        ref.step_host(act, fr, rr, dr)  # also loads the step kernel the static call launches
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         new.step_host_static(act, fn, rn, dn)
+        torch.cuda.synchronize()
+        # the array was reserved when the env was created: the call takes no device memory
+        assert torch.cuda.mem_get_info()[0] == free0, f"free device memory changed on call {s}"
         assert torch.equal(fr, fn), f"frames differ on call {s}"
         assert torch.equal(rr, rn) and torch.equal(dr, dn), f"rewards / dones differ on call {s}"
     assert int(dn.sum()) == N  # the second call ended every episode
