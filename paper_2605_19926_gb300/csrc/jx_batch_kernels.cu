@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
   init_warp_header(wbase, lane);
   const int gw = blockIdx.x * wpb + warp;
   int slot = 0;
+  const uint3 no_palette = make_uint3(0u, 0u, 0u);  // written once per group (write_palette), not per env
   bool fresh = true;  // nothing of an earlier group is pending in the ring
   for (int g = 0; g < bp.n_groups; ++g) {
     const Params& p = bp.g[g];
@@ -42,9 +43,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
       uint32_t next = 0;
       if (lane == 0) next = atomicAdd(bp.queue + g, 1u);
       if (SPEC == 1)
-        run_env<MODE, MAP_BITS, COLS, 0>(p, (int)ticket, wbase, scratch, lane, slot);
+        run_env<MODE, MAP_BITS, COLS, 0>(p, (int)ticket, wbase, scratch, lane, slot, no_palette, false);
       else
-        run_env<MODE, MAP_RUNTIME, COLS, 2>(p, (int)ticket, wbase, scratch, lane, slot);
+        run_env<MODE, MAP_RUNTIME, COLS, 2>(p, (int)ticket, wbase, scratch, lane, slot, no_palette, false);
       ticket = __shfl_sync(0xffffffffu, next, 0);
     }
   }

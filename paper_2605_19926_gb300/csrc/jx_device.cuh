@@ -74,19 +74,23 @@ constexpr uint32_t cell_rgb(int v) {
        : kWall1;
 }
 constexpr int kCellColours = 32;  // palette entries per face; values above draw as wall 1
+constexpr int kPaletteWords = 2 * kCellColours + 8;
 
-// [face][cell value]: x faces, then y faces (3/4)
+// [face][cell value]: x faces, then y faces (3/4); then the sprite colours by
+// type: 1 red key, 2 goal, 3 distractor, 4 blue key, 5 yellow key (others as
+// distractor). In global memory, not the constant bank: every lane reads its
+// own entries, which the constant cache would serve one address at a time.
 #define JX_CELLS(f) f(0), f(1), f(2), f(3), f(4), f(5), f(6), f(7), f(8), f(9), f(10), f(11), f(12), f(13), f(14), \
     f(15), f(16), f(17), f(18), f(19), f(20), f(21), f(22), f(23), f(24), f(25), f(26), f(27), f(28), f(29), f(30), f(31)
 #define JX_X_FACE(v) cell_rgb(v)
 #define JX_Y_FACE(v) shade34(cell_rgb(v))
-__constant__ uint32_t c_wall[2 * kCellColours] = {JX_CELLS(JX_X_FACE), JX_CELLS(JX_Y_FACE)};
+__device__ uint32_t g_palette[kPaletteWords] = {
+    JX_CELLS(JX_X_FACE), JX_CELLS(JX_Y_FACE),
+    rgb(144, 64, 192), rgb(224, 40, 40), rgb(240, 208, 32), rgb(144, 64, 192),
+    rgb(40, 80, 224),  rgb(232, 200, 40), rgb(144, 64, 192), rgb(144, 64, 192)};
 #undef JX_X_FACE
 #undef JX_Y_FACE
 #undef JX_CELLS
-// by sprite type: 1 red key, 2 goal, 3 distractor, 4 blue key, 5 yellow key (others as distractor)
-__constant__ uint32_t c_sprite[8] = {rgb(144, 64, 192), rgb(224, 40, 40), rgb(240, 208, 32), rgb(144, 64, 192),
-                                     rgb(40, 80, 224),  rgb(232, 200, 40), rgb(144, 64, 192), rgb(144, 64, 192)};
 
 // ------------------------------------------------------------ SplitMix64 --
 // Steele, Lea & Flood (OOPSLA 2014): output n of the generator seeded with s
@@ -247,14 +251,26 @@ struct WarpSmem {
   __device__ __forceinline__ int32_t* obj(const Params& p) const { return (int32_t*)(base + p.off_obj); }
 };
 
-constexpr int kPaletteWords = 2 * kCellColours + 8;
-
 // Column data is stored so that the lanes filling one row (8 columns each)
 // read consecutive 16-byte groups: half g (columns 4g..4g+3 of the group) of
 // column group c sits at word (g * groups + c) * 4.
 __device__ __forceinline__ int col_slot(int col, int groups) {
   const int c = col >> 3, j = col & 7;
   return (((j >> 2) * groups + c) << 2) | (j & 3);
+}
+
+// The palette words of this lane: entries lane, 32 + lane and 64 + (lane & 7).
+__device__ __forceinline__ uint3 load_palette(int lane) {
+  return make_uint3(__ldg(g_palette + lane), __ldg(g_palette + 32 + lane), __ldg(g_palette + 64 + (lane & 7)));
+}
+__device__ __forceinline__ void store_palette(const Params& p, const WarpSmem& ws, const uint3& w, int lane) {
+  ws.pal(p)[lane] = w.x;
+  ws.pal(p)[32 + lane] = w.y;
+  if (lane < 8) ws.pal(p)[64 + lane] = w.z;
+}
+__device__ __forceinline__ void write_palette(const Params& p, const WarpSmem& ws, int lane) {
+  store_palette(p, ws, load_palette(lane), lane);
+  __syncwarp();
 }
 
 // ------------------------------------------------------------ env state ----
@@ -300,10 +316,12 @@ __device__ __forceinline__ void load_objects(const Params& p, const WarpSmem& ws
 
 // heading = theta0 + turn * 2 pi / turns_per_rev: (cos, sin)(theta0), kept in
 // the state, rotated by the table entry of `turn`
-__device__ __forceinline__ void heading(const Params& p, const Env& r, float& c, float& s) {
-  const float2 cs = p.turn_cs[r.turn];
+__device__ __forceinline__ void heading_from(const Env& r, float2 cs, float& c, float& s) {
   c = fmaf(r.c0, cs.x, -r.s0 * cs.y);
   s = fmaf(r.s0, cs.x, r.c0 * cs.y);
+}
+__device__ __forceinline__ void heading(const Params& p, const Env& r, float& c, float& s) {
+  heading_from(r, p.turn_cs[r.turn], c, s);
 }
 
 // Byte maps of 4 KB or more (side >= 64) are copied by one bulk copy, smaller
@@ -981,20 +999,26 @@ __device__ __forceinline__ void renormalise(int& c, float& f) {
   }
 }
 
-// One step of env e under action a; the reward and done flag go to output
-// slot `out`. Returns true when the episode ended (the caller regenerates).
-// The pose is written back to the state block only when write_state is set.
-template <int MAPK>
-__device__ __forceinline__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, const int32_t* obj,
-                                         const float4* spr_in,
-                                         int lane, float& c, float& s, int a, size_t out, bool write_state) {
+// An action outside 0..6 is recorded in the error word and taken as a no-op;
+// a turn action moves `turn` one step around the circle of turns_per_rev.
+__device__ __forceinline__ int turn_for(const Params& p, Env& r, int a, int lane) {
   if (a > 6) {
     if (lane == 0) atomicOr(p.err, 1u);
     a = 0;
   }
   if (a == 5) r.turn = r.turn == 0 ? p.tpr - 1 : r.turn - 1;
   if (a == 6) r.turn = r.turn + 1 == p.tpr ? 0 : r.turn + 1;
-  heading(p, r, c, s);
+  return a;
+}
+
+// One step of env e under action a (already checked by turn_for, with the
+// heading (c, s) of the turned agent); the reward and done flag go to output
+// slot `out`. Returns true when the episode ended (the caller regenerates).
+// The pose is written back to the state block only when write_state is set.
+template <int MAPK>
+__device__ __forceinline__ bool step_env(const Params& p, int e, Env& r, const uint8_t* smap, const int32_t* obj,
+                                         const float4* spr_in, int lane, float c, float s, int a, size_t out,
+                                         bool write_state) {
   const float ms = p.move;
   float dx = 0.f, dy = 0.f;
   if (a == 1) {
@@ -1202,28 +1226,32 @@ __device__ __forceinline__ int project_sprites(const Params& p, const Env& r, fl
     const float vy = (sp.y - (float)r.cy) - r.fy;
     ty = fmaf(vx, c, vy * s);
     const int kc = key_colour(type);
-    vis = type != 0 && !(kc >= 0 && ((r.keys >> kc) & 1)) && ty > 0.1f;
-    if (vis) {
+    if (type != 0 && !(kc >= 0 && ((r.keys >> kc) & 1)) && ty > 0.1f) {
       const float inv_ty = __frcp_rn(ty);
       const float tx = fmaf(-vx, s, vy * c) * p.inv_tan_half;
       const float wd = 0.25f * (float)W * p.inv_tan_half * inv_ty;
       const float ht = 0.5f * (float)H * inv_ty;
       const float x0 = fmaf(0.5f * (float)W, fmaf(tx, inv_ty, 1.f), -0.5f * wd);
       const float top = 0.5f * (float)H;
-      ws.spr_a(p)[lane] = make_float4(x0, top, ty * (4.f * p.tan_half / (float)W), ty * (2.f / (float)H));
       // pixel centres that can fall inside [x0, x0 + wd) x [top, top + ht), one pixel of slack
-      const int cA = (int)floorf(fmaxf(x0 - 1.f, -1.f));
-      const int cB = (int)floorf(fminf(x0 + wd + 1.f, (float)W));
+      int cA = (int)floorf(fmaxf(x0 - 1.f, -1.f));
+      int cB = (int)floorf(fminf(x0 + wd + 1.f, (float)W));
       const int rA = (int)floorf(fmaxf(top - 1.f, -1.f));
       const int rB = (int)floorf(fminf(top + ht + 1.f, (float)H));
-      ws.spr_rect(p)[lane] =
-          make_int4(cA < 0 ? 0 : cA, cB > W - 1 ? W - 1 : cB, rA < 0 ? 0 : rA, rB > H - 1 ? H - 1 : rB);
-      ws.spr_ty(p)[lane] = ty;
-      ws.spr_rgb(p)[lane] = ws.pal(p)[2 * kCellColours + (type & 7)];
-      ws.spr_kind(p)[lane] = kc >= 0 ? 1 : (type == kSprGoal ? 2 : 3);  // mask: diamond, rectangle, disc
+      cA = cA < 0 ? 0 : cA;
+      cB = cB > W - 1 ? W - 1 : cB;
+      vis = cA <= cB;  // some column of the screen
+      if (vis) {
+        ws.spr_a(p)[lane] = make_float4(x0, top, ty * (4.f * p.tan_half / (float)W), ty * (2.f / (float)H));
+        ws.spr_rect(p)[lane] = make_int4(cA, cB, rA < 0 ? 0 : rA, rB > H - 1 ? H - 1 : rB);
+        ws.spr_ty(p)[lane] = ty;
+        ws.spr_rgb(p)[lane] = ws.pal(p)[2 * kCellColours + (type & 7)];
+        ws.spr_kind(p)[lane] = kc >= 0 ? 1 : (type == kSprGoal ? 2 : 3);  // mask: diamond, rectangle, disc
+      }
     }
   }
   const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
+  if (vmask == 0u) return 0;  // nothing on screen (warp-uniform)
   int rank = 0;
   for (int k = 0; k < nspr; ++k) {
     const float tk = __shfl_sync(0xffffffffu, ty, k);
@@ -1319,6 +1347,7 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
     }
   }
   __syncwarp();
+  if (nvis == 0) return;  // warp-uniform
   // sprites, far to near; lanes take columns. For a column, the covered rows
   // are those whose centre has v in [0, 1) with |2v - 1| below the mask's
   // half-height at this u (key: 1 - |2u - 1|, disc: sqrt(1 - (2u - 1)^2)).
@@ -1434,34 +1463,151 @@ __device__ __noinline__ void open_doors(const Params& p, int e, int keys, const 
   __syncwarp();
 }
 
+// What a launch reads of env e before its first step, fetched in one round of
+// independent loads so that their latencies overlap: the scalar state, the
+// key / goal / door cells and sprite count (lanes 0..6), the sprite slots
+// (lane j: slot j), the map when it holds at most 1 KB (two 16-byte chunks a
+// lane), the first action, and for the single step the turn table's entries
+// lane, 32 + lane and 64 + lane (tables of at most 96 turns).
+struct Prefetch {
+  Env r;
+  int obj;
+  float4 spr;
+  uint4 m0, m1;
+  float2 tc0, tc1, tc2;
+  int action;
+};
+
+template <int MAPK>
+__device__ __forceinline__ bool small_map(const Params& p) {
+  const int n = p.S * p.S;
+  return n <= 1024 && (n & 31) == 0;
+}
+
+template <int MODE, int MAPK>
+__device__ __forceinline__ Prefetch prefetch(const Params& p, int e, int lane) {
+  Prefetch q;
+  const State& st = p.st;
+  q.r = load_env(p, e);
+  q.obj = lane < 6 ? (int)st.obj[6 * (size_t)e + lane] : (lane == 6 ? (int)st.nspr[e] : 0);
+  q.spr = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (lane < p.K) {
+    const size_t i = (size_t)e * p.K + lane;
+    q.spr = make_float4(st.spr_x[i], st.spr_y[i], (float)st.spr_type[i], 0.f);
+  }
+  q.m0 = q.m1 = make_uint4(0u, 0u, 0u, 0u);
+  if (small_map<MAPK>(p)) {
+    const int n = p.S * p.S;
+    const uint4* g = reinterpret_cast<const uint4*>(st.map + (size_t)e * n);
+    if (map_bits<MAPK>(p)) {  // word `lane` of the bit plane: cells 32 lane .. 32 lane + 31
+      if (lane < (n >> 5)) {
+        q.m0 = g[2 * lane];
+        q.m1 = g[2 * lane + 1];
+      }
+    } else {
+      if (lane < (n >> 4)) q.m0 = g[lane];
+      if (lane + 32 < (n >> 4)) q.m1 = g[lane + 32];
+    }
+  }
+  q.action = (MODE == MODE_STEP || MODE == MODE_ROLLOUT) ? (int)p.actions[e] : 0;
+  q.tc0 = q.tc1 = q.tc2 = make_float2(0.f, 0.f);
+  if (MODE == MODE_STEP && p.tpr <= 96) {
+    if (lane < p.tpr) q.tc0 = p.turn_cs[lane];
+    if (lane + 32 < p.tpr) q.tc1 = p.turn_cs[lane + 32];
+    if (lane + 64 < p.tpr) q.tc2 = p.turn_cs[lane + 64];
+  }
+  return q;
+}
+
+// The prefetched objects, sprites and map into the warp's shared memory
+// (maps too large to prefetch are staged here); ends with __syncwarp.
+template <int MAPK>
+__device__ __forceinline__ void stage_prefetched(const Params& p, const WarpSmem& ws, int e, const Prefetch& q,
+                                                 int lane) {
+  if (lane < 6) ws.obj(p)[lane] = q.obj;
+  if (lane == 6) ws.obj(p)[6] = q.obj > p.K ? p.K : q.obj;  // sprites in use
+  if (lane < p.K) ws.spr_in(p)[lane] = q.spr;
+  if (!small_map<MAPK>(p)) {
+    stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
+    return;
+  }
+  const int n = p.S * p.S;
+  if (map_bits<MAPK>(p)) {
+    if (lane < (n >> 5))
+      reinterpret_cast<uint32_t*>(ws.map(p))[lane] =
+          nonzero4(q.m0.x) | nonzero4(q.m0.y) << 4 | nonzero4(q.m0.z) << 8 | nonzero4(q.m0.w) << 12 |
+          nonzero4(q.m1.x) << 16 | nonzero4(q.m1.y) << 20 | nonzero4(q.m1.z) << 24 | nonzero4(q.m1.w) << 28;
+  } else {
+    uint4* dst = reinterpret_cast<uint4*>(ws.map(p));
+    if (lane < (n >> 4)) dst[lane] = q.m0;
+    if (lane + 32 < (n >> 4)) dst[lane + 32] = q.m1;
+  }
+  __syncwarp();
+}
+
+// Turn table entry `turn`: from the prefetched registers (lane turn mod 32
+// holds it) when the table has at most 96 entries, else from global memory.
+__device__ __forceinline__ float2 turn_entry(const Params& p, const Prefetch& q, int turn) {
+  if (p.tpr > 96) return p.turn_cs[turn];
+  const int src = turn & 31;
+  const float2 a = make_float2(__shfl_sync(0xffffffffu, q.tc0.x, src), __shfl_sync(0xffffffffu, q.tc0.y, src));
+  const float2 b = make_float2(__shfl_sync(0xffffffffu, q.tc1.x, src), __shfl_sync(0xffffffffu, q.tc1.y, src));
+  const float2 c = make_float2(__shfl_sync(0xffffffffu, q.tc2.x, src), __shfl_sync(0xffffffffu, q.tc2.y, src));
+  return turn < 32 ? a : (turn < 64 ? b : c);
+}
+
+// An ended episode: the next one (built here or taken over from the
+// next-episode block), its state and objects reloaded, and its heading.
+// Inlined behind the callers' unlikely branches (see generate).
+template <int MAPK>
+__device__ __forceinline__ void next_episode(const Params& p, int e, Env& r, const WarpSmem& ws, uint8_t* scratch,
+                                          int lane, float& c, float& s) {
+  const uint32_t ep = p.st.episode[e] + 1;
+  __syncwarp();
+  generate<MAPK>(p, e, ep, ws.base, scratch, lane);
+  r = load_env(p, e);
+  load_objects(p, ws, e, lane);
+  __syncwarp();
+  heading(p, r, c, s);
+}
+
 // Everything one launch does for env e: MODE_ROLLOUT runs p.steps steps with
-// the env's scalar state in registers and its map in shared memory.
+// the env's scalar state in registers and its map in shared memory. The
+// palette `pal` (this lane's words) is stored first when store_pal is set.
 template <int MODE, int MAPK, int COLS, int GRAY>
 __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, uint8_t* scratch, int lane,
-                                        int& slot) {
+                                        int& slot, const uint3& pal, bool store_pal) {
   const WarpSmem ws{wbase, fill_lane(p, lane)};
   const size_t frame_bytes = (size_t)3 * p.H * p.W;
-  if (MODE == MODE_ROLLOUT) {
-    Env r = load_env(p, e);
+  if (MODE == MODE_RESET) {
+    if (store_pal) store_palette(p, ws, pal, lane);
+    generate<MAPK>(p, e, 0u, wbase, scratch, lane);
+    const Env r = load_env(p, e);
     load_objects(p, ws, e, lane);
-    stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
-    open_doors<MAPK>(p, e, r.keys, ws, lane);
-    int a_next = p.actions[e];
+    __syncwarp();
+    float c, s;
+    heading(p, r, c, s);
+    render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
+    __syncwarp();
+    return;
+  }
+  const Prefetch q = prefetch<MODE, MAPK>(p, e, lane);
+  if (store_pal) store_palette(p, ws, pal, lane);
+  Env r = q.r;
+  stage_prefetched<MAPK>(p, ws, e, q, lane);  // ends with __syncwarp
+  open_doors<MAPK>(p, e, r.keys, ws, lane);
+  if (MODE == MODE_ROLLOUT) {
+    int a_next = q.action;
     for (int t = 0; t < p.steps; ++t) {
-      const int a = a_next;
+      int a = a_next;
       if (t + 1 < p.steps) a_next = p.actions[(size_t)(t + 1) * p.out_stride + e];
-      float c, s;
       const size_t out = (size_t)t * p.out_stride + e;
       const int keys0 = r.keys;
-      if (__builtin_expect(step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), ws.spr_in(p), lane, c, s, a, out, false), 0)) {
-        const uint32_t ep = p.st.episode[e] + 1;
-        __syncwarp();
-        generate<MAPK>(p, e, ep, wbase, scratch, lane);
-        r = load_env(p, e);
-        load_objects(p, ws, e, lane);
-        __syncwarp();
-        heading(p, r, c, s);
-      }
+      a = turn_for(p, r, a, lane);
+      float c, s;
+      heading(p, r, c, s);
+      if (__builtin_expect(step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), ws.spr_in(p), lane, c, s, a, out, false), 0))
+        next_episode<MAPK>(p, e, r, ws, scratch, lane, c, s);
       if (__builtin_expect(r.keys != keys0, 0)) open_doors<MAPK>(p, e, r.keys, ws, lane);
       render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot,
                                          p.frames + (size_t)t * p.frame_step + (size_t)e * frame_bytes);
@@ -1480,46 +1626,20 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
     __syncwarp();
     return;
   }
-  Env r;
   float c, s;
-  if (MODE == MODE_RESET) {
-    generate<MAPK>(p, e, 0u, wbase, scratch, lane);
-    r = load_env(p, e);
-    load_objects(p, ws, e, lane);
-    __syncwarp();
-    heading(p, r, c, s);
+  if (MODE == MODE_STEP) {
+    const int keys0 = r.keys;
+    const int a = turn_for(p, r, q.action, lane);
+    heading_from(r, turn_entry(p, q, r.turn), c, s);
+    if (__builtin_expect(step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), ws.spr_in(p), lane, c, s, a, (size_t)e, true),
+                         0))
+      next_episode<MAPK>(p, e, r, ws, scratch, lane, c, s);
+    else if (r.keys != keys0)
+      open_doors<MAPK>(p, e, r.keys, ws, lane);
   } else {
-    r = load_env(p, e);
-    load_objects(p, ws, e, lane);
-    stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
-    open_doors<MAPK>(p, e, r.keys, ws, lane);
-    if (MODE == MODE_STEP) {
-      const int keys0 = r.keys;
-      if (__builtin_expect(
-              step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), ws.spr_in(p), lane, c, s, (int)p.actions[e], (size_t)e,
-                             true), 0)) {
-        const uint32_t ep = p.st.episode[e] + 1;
-        __syncwarp();
-        generate<MAPK>(p, e, ep, wbase, scratch, lane);
-        r = load_env(p, e);
-        load_objects(p, ws, e, lane);
-        __syncwarp();
-        heading(p, r, c, s);
-      } else if (r.keys != keys0) {
-        open_doors<MAPK>(p, e, r.keys, ws, lane);
-      }
-    } else {
-      heading(p, r, c, s);
-    }
+    heading(p, r, c, s);
   }
   render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
-  __syncwarp();
-}
-
-__device__ __forceinline__ void write_palette(const Params& p, const WarpSmem& ws, int lane) {
-  ws.pal(p)[lane] = c_wall[lane];
-  ws.pal(p)[32 + lane] = c_wall[32 + lane];
-  if (lane < 8) ws.pal(p)[64 + lane] = c_sprite[lane];
   __syncwarp();
 }
 

@@ -12,13 +12,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   extern __shared__ __align__(128) uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* const wbase = smem_raw + warp * p.warp_bytes;
+  const uint3 pal = load_palette(lane);  // stored with the first env's prefetched state
   init_warp_header(wbase, lane);
-  write_palette(p, WarpSmem{wbase, fill_lane(p, lane)}, lane);
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
   uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;
   int slot = 0;
-  for (int e = gw; e < p.n; e += nw) run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot);
+  for (int e = gw; e < p.n; e += nw) run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, e == gw);
   // shared memory stays allocated until the bulk stores have read it
   if (lane == 0) bulk_wait_read_all();
 }
