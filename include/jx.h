@@ -135,10 +135,10 @@ typedef struct {
  * the handle, owned by the caller until jx_destroy.
  * Maze tasks (JX_TASK_MAZE_KEYDOOR, JX_TASK_MAZE_ROOMS) with map_side >= 64
  * and a multiple of 4 also reserve a next-episode block (the state without
- * the grayscale stack, plus 6 bytes per maze node per env of work space):
- * when a launch starts episodes on many envs at once, one lane per env builds
- * them ahead there. Without that memory the env works as for other configs.
- * Results do not depend on it. */
+ * the grayscale stack, plus 4 bytes per maze node per env of work space):
+ * when many envs will start episodes within the next few launches, one lane
+ * per env builds them ahead there, spread over those launches. Without that
+ * memory the env works as for other configs. Results do not depend on it. */
 jx_status jx_create(const jx_config* cfg, int device, jx_env** out);
 
 /* jx_create for the ASCII task (cfg->task == JX_TASK_ASCII): the map is the
@@ -326,8 +326,7 @@ typedef struct jx_graph jx_graph;
  *                      held in shared memory as bit planes (1 bit per cell)
  *                      instead of byte grids; 0 = byte grids for all
  *  max_rows_per_block  frame rows per staged shared-memory block (upper
- *                      bound, 1..64; lowered to fit 28 warps per SM and to
- *                      whole fill passes)
+ *                      bound, 1..64; lowered to fit 28 warps per SM)
  *  staging_buffers     row-block staging buffers per warp: 1 (a block waits
  *                      for the copy-out of the one before; larger blocks fit)
  *                      or 2 (fill one while the other drains) */

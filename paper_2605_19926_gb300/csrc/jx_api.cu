@@ -190,13 +190,14 @@ jx_status cuda_fail(cudaError_t err, const char* what) {
 
 void choose_rows(Params& p, int max_rows, int warps, int blocks, size_t smem_per_sm, size_t reserved) {
   const int rowb = 3 * p.W;
-  const int pass_rows = 32 / (p.W / 8) > 0 ? 32 / (p.W / 8) : 1;
-  // candidates: whole fill passes up to max_rows (or the whole frame when it is
-  // shorter); the largest with which `blocks` warps fit, else the smallest
+  // candidates: up to max_rows (or the whole frame when it is shorter); the
+  // largest with which `blocks` warps fit, else the smallest. A block need not
+  // be whole fill passes (the lanes past its last row idle in the last pass):
+  // wide frames leave room for few rows, and every block costs a copy-out and
+  // a pass over the sprites.
   const int top = p.H < max_rows ? p.H : max_rows;
   int best = 0, smallest = 0;
   for (int rows = top; rows >= 1; --rows) {
-    if (rows < p.H && rows % pass_rows != 0 && rows != top) continue;
     smallest = rows;
     Params q = p;
     q.rows_per_block = rows;

@@ -216,13 +216,13 @@ __host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; 
 //   spr_span  [K] first row << 16 | last row the oi-th sprite of that order can cover
 //   obj       [8] int32 key x, key y, goal x, goal y, door x, door y, sprites in use
 // The lane's place in the frame fill: lanes [0, groups * rows) are laid out
-// as `rows` rows of `groups` 8-pixel groups.
+// as `rows` rows of `groups` 16-pixel groups (48 bytes: three 16-byte stores).
 struct FillLane {
   int groups, rows, my_row, g;
 };
 __device__ __forceinline__ FillLane fill_lane(const Params& p, int lane) {
   FillLane f;
-  f.groups = p.W >> 3;
+  f.groups = p.W >> 4;
   f.rows = 32 / f.groups;
   f.my_row = lane / f.groups;
   f.g = lane - f.my_row * f.groups;
@@ -251,11 +251,11 @@ struct WarpSmem {
   __device__ __forceinline__ int32_t* obj(const Params& p) const { return (int32_t*)(base + p.off_obj); }
 };
 
-// Column data is stored so that the lanes filling one row (8 columns each)
-// read consecutive 16-byte groups: half g (columns 4g..4g+3 of the group) of
-// column group c sits at word (g * groups + c) * 4.
+// Column data is stored so that the lanes filling one row (16 columns each)
+// read consecutive 16-byte groups: quad q (columns 4q..4q+3 of the group) of
+// column group c sits at word (q * groups + c) * 4.
 __device__ __forceinline__ int col_slot(int col, int groups) {
-  const int c = col >> 3, j = col & 7;
+  const int c = col >> 4, j = col & 15;
   return (((j >> 2) * groups + c) << 2) | (j & 3);
 }
 
@@ -325,7 +325,8 @@ __device__ __forceinline__ void heading(const Params& p, const Env& r, float& c,
 }
 
 // Byte maps of 4 KB or more (side >= 64) are copied by one bulk copy, smaller
-// ones by 16-byte loads of all lanes.
+// ones by 16-byte loads of all lanes. The warp header is read only on the
+// bulk path (kernels initialise it only where maps of that size occur).
 __device__ __forceinline__ void stage_map(const Params& p, int e, uint8_t* smap, int lane) {
   const int n = p.S * p.S;
   const uint8_t* g = p.st.map + (size_t)e * n;
@@ -663,18 +664,65 @@ __device__ __forceinline__ int floor_bytes16(const uint8_t* q) {
   return 16 - __popc(nonzero4(v.x) | nonzero4(v.y) << 4 | nonzero4(v.z) << 8 | nonzero4(v.w) << 12);
 }
 
+// Shared-memory words one pre-generation lane needs for mazes of side S: the
+// walk's visited bits (one per node) and parent directions (two bits per node).
+__host__ __device__ __forceinline__ int pregen_lane_words(int S) {
+  const int n = ((S - 2) / 2) * ((S - 2) / 2);
+  return ((n + 31) >> 5) + ((n + 15) >> 4);
+}
+
 // One lane builds episode ep of env e into the next-episode block p.nx: the
-// draws and steps of gen_maze, run serially by the lane (walls, the walk with
-// its stack and discovery / finish counters in the lane's work slot, the door,
-// the key, and for task 2 the rooms and distractors), so that 32 mazes of a
-// warp are built at once. S is a multiple of 4, so S * S is one of 16.
-__device__ void gen_maze_lane(const Params& p, int e, uint32_t ep, uint8_t* work) {
+// draws and steps of gen_maze, run serially by the lane, so that 32 mazes of
+// a warp are built at once. S is a multiple of 4, so S * S is one of 16.
+//
+// The lane's shared-memory words (word w at sm[w * vstride]) hold the walk's
+// state: a visited bit per node (a node is visited exactly when gen_maze's
+// map byte of it is floor) and the direction back to the node's parent (two
+// bits per node). Backtracking follows the parent directions, so no stack is
+// kept; the stack depth is a counter, and the door's path nodes (at depths
+// ceil(d / 2) - 1 and ceil(d / 2) on the path to the deepest node, depth d)
+// are found afterwards by walking up from that node. The discovery and finish
+// counters go to the lane's work slot in global memory (written in the walk,
+// read once for the key). After the walk the words hold the floor-cell counts
+// of 256-cell chunks for the distractor draws.
+//
+// The lanes of warp_mask build mazes of one side together: every walk takes
+// exactly 2 n - 1 iterations (n - 1 pushes, n pops), and the lanes meet at
+// each iteration, so the warp runs the 32 walks side by side instead of one
+// diverged lane after another.
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
+}
+
+__device__ void gen_maze_lane(const Params& p, int e, uint32_t ep, uint8_t* work, uint32_t* sm, int vstride,
+                              uint32_t warp_mask) {
   const int S = p.S, n_cells = S * S;
   const int nn = (S - 2) / 2, n = nn * nn;
+  const int vwords = (n + 31) >> 5, dwords = (n + 15) >> 4;
   uint8_t* smap = p.nx.map + (size_t)e * n_cells;
-  uint16_t* stack = reinterpret_cast<uint16_t*>(work);
-  uint16_t* disc = stack + n;
-  uint16_t* fin = disc + n;
+  uint16_t* disc = reinterpret_cast<uint16_t*>(work);  // 16-byte aligned (the key search reads it 8 at a time)
+  uint16_t* fin = reinterpret_cast<uint16_t*>(work + align16(2 * n));
+  // the walk state through shared-space addresses: its loads need not wait
+  // for the lane's global stores (map bytes, counters), which never alias it
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm), sstride = 4u * (uint32_t)vstride;
+  const uint32_t dbase = sbase + (uint32_t)vwords * sstride;
+  for (int w = 0; w < vwords; ++w) sts32(sbase + (uint32_t)w * sstride, 0u);
+  for (int w = 0; w < dwords; ++w) sts32(dbase + (uint32_t)w * sstride, 0u);
+  auto seen = [&](int u) { return (lds32(sbase + (uint32_t)(u >> 5) * sstride) >> (u & 31)) & 1u; };
+  auto mark = [&](int u) {
+    const uint32_t a = sbase + (uint32_t)(u >> 5) * sstride;
+    sts32(a, lds32(a) | 1u << (u & 31));
+  };
+  auto parent_dir = [&](int u) { return (int)((lds32(dbase + (uint32_t)(u >> 4) * sstride) >> (2 * (u & 15))) & 3u); };
+  auto set_parent_dir = [&](int u, int d) {  // d: 0 N, 1 E, 2 S, 3 W; the word's old bits of u are 0
+    const uint32_t a = dbase + (uint32_t)(u >> 4) * sstride;
+    sts32(a, lds32(a) | (uint32_t)d << (2 * (u & 15)));
+  };
   const uint64_t kw = stream_key(p.seed, (uint32_t)e, ep, P_WALL);
   for (int i = 0; i < n_cells; i += 16) {
     uint32_t w[4];
@@ -691,63 +739,101 @@ __device__ void gen_maze_lane(const Params& p, int e, uint32_t ep, uint8_t* work
   const int start = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_SPAWN), 0), (uint32_t)n);
   int vx = 2 * (start % nn) + 1, vy = 2 * (start / nn) + 1, v = start;
   smap[vy * S + vx] = 0;
-  int sp = 0, pushes = 0;
+  mark(v);
+  int sp = 1, pushes = 0;  // stack size: the current node's depth is sp - 1
   uint32_t carved = 0;
-  stack[sp++] = (uint16_t)(vy << 8 | vx);
+  // the walk's draws (high 32 bits), computed eight at a time ahead of use
+  uint32_t draws[8];
+#pragma unroll
+  for (int h = 0; h < 8; ++h) draws[h] = (uint32_t)(draw_at(kd, (uint32_t)h) >> 32);
   disc[v] = (uint16_t)pushes++;
-  int best_v = start, best_d = 0, door_a = vy << 8 | vx, door_b = door_a;
-  for (;;) {
-    const int c = vy * S + vx;
-    const uint32_t open = (uint32_t)(vy > 1 && smap[c - 2 * S] != 0) | ((uint32_t)(vx < S - 3 && smap[c + 2] != 0) << 1) |
-                          ((uint32_t)(vy < S - 3 && smap[c + 2 * S] != 0) << 2) |
-                          ((uint32_t)(vx > 1 && smap[c - 2] != 0) << 3);
+  int best_v = start, best_d = 0;
+  for (int it = 0; it < 2 * n - 1; ++it) {
+    __syncwarp(warp_mask);
+    const uint32_t open = (uint32_t)(vy > 1 && !seen(v - nn)) | ((uint32_t)(vx < S - 3 && !seen(v + 1)) << 1) |
+                          ((uint32_t)(vy < S - 3 && !seen(v + nn)) << 2) | ((uint32_t)(vx > 1 && !seen(v - 1)) << 3);
     if (open == 0) {
       fin[v] = (uint16_t)pushes;
-      if (--sp == 0) break;
-      const int top = stack[sp - 1];
-      vx = top & 0xff;
-      vy = top >> 8;
+      if (--sp == 0) continue;  // the spawn, finished: the walk's last iteration
+      const int d = parent_dir(v);  // back to the parent
+      vx += d == 1 ? 2 : (d == 3 ? -2 : 0);
+      vy += d == 2 ? 2 : (d == 0 ? -2 : 0);
       v = (vy >> 1) * nn + (vx >> 1);
       continue;
     }
     // the r-th unvisited neighbour in N, E, S, W order
+    uint32_t hi = draws[0];
+#pragma unroll
+    for (int h = 0; h < 7; ++h) draws[h] = draws[h + 1];
+    if ((++carved & 7u) == 0u) {
+#pragma unroll
+      for (int h = 0; h < 8; ++h) draws[h] = (uint32_t)(draw_at(kd, carved + (uint32_t)h) >> 32);
+    } else {
+      draws[7] = 0u;  // refilled when the window of eight is used up
+    }
     uint32_t bits = open;
-    for (uint32_t r = below(draw_at(kd, carved++), (uint32_t)__popc(open)); r > 0; --r) bits &= bits - 1;
+    for (uint32_t r = below32(hi, (uint32_t)__popc(open)); r > 0; --r) bits &= bits - 1;
     const int d = __ffs(bits) - 1;
     const int dx = d == 1 ? 1 : (d == 3 ? -1 : 0), dy = d == 0 ? -1 : (d == 2 ? 1 : 0);
-    smap[c + dy * S + dx] = 0;
+    smap[(vy + dy) * S + vx + dx] = 0;
     vx += 2 * dx;
     vy += 2 * dy;
     smap[vy * S + vx] = 0;
     v = (vy >> 1) * nn + (vx >> 1);
-    const int depth = sp;
-    stack[sp++] = (uint16_t)(vy << 8 | vx);
+    mark(v);
+    set_parent_dir(v, d ^ 2);
+    const int depth = sp++;
     disc[v] = (uint16_t)pushes++;
     if (depth > best_d || (depth == best_d && v < best_v)) {
       best_v = v;
       best_d = depth;
-      const int j = (depth + 1) / 2;  // the door sits on edge ceil(depth / 2) of the path
-      door_a = stack[j - 1];
-      door_b = stack[j];
     }
   }
-  const int dxc = ((door_a & 0xff) + (door_b & 0xff)) >> 1, dyc = ((door_a >> 8) + (door_b >> 8)) >> 1;
+  // the door sits on edge ceil(d / 2) of the path to the deepest node: between
+  // its path nodes at depths j - 1 (a) and j (b), j = ceil(d / 2)
+  const int j = (best_d + 1) / 2;
+  int bx = 2 * (best_v % nn) + 1, by = 2 * (best_v / nn) + 1;
+  for (int k = best_d; k > j; --k) {
+    const int d = parent_dir((by >> 1) * nn + (bx >> 1));
+    bx += d == 1 ? 2 : (d == 3 ? -2 : 0);
+    by += d == 2 ? 2 : (d == 0 ? -2 : 0);
+  }
+  int ax = bx, ay = by;
+  if (j > 0) {
+    const int d = parent_dir((by >> 1) * nn + (bx >> 1));
+    ax += d == 1 ? 2 : (d == 3 ? -2 : 0);
+    ay += d == 2 ? 2 : (d == 0 ? -2 : 0);
+  }
+  const int dxc = (ax + bx) >> 1, dyc = (ay + by) >> 1;
   smap[dyc * S + dxc] = (uint8_t)kDoor;
-  // key: uniform over spawn-side nodes except the spawn
-  const int pj = ((door_b >> 8) >> 1) * nn + ((door_b & 0xff) >> 1);
+  // key: uniform over spawn-side nodes except the spawn (outside the door's
+  // subtree: discovery counter outside [disc, fin) of its path node b)
+  const int pj = (by >> 1) * nn + (bx >> 1);
   const int d0 = disc[pj], d1 = fin[pj];
   const int n_side = n - (d1 - d0) - 1;
   int key = start;
   if (n_side > 0) {
     uint32_t r = below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_KEY), 0), (uint32_t)n_side);
-    for (int u = 0; u < n; ++u) {
-      const int du = disc[u];
-      if (u == start || (du >= d0 && du < d1)) continue;
-      if (r == 0) {
-        key = u;
+    for (int u0 = 0; u0 < n; u0 += 8) {  // eight counters a load (the work slot is 16-byte aligned)
+      const uint4 q = *reinterpret_cast<const uint4*>(disc + u0);
+      const uint32_t dq[4] = {q.x, q.y, q.z, q.w};
+      int found = -1;
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const int u = u0 + h;
+        const int du = (int)((dq[h >> 1] >> (16 * (h & 1))) & 0xffffu);
+        const bool side = u < n && u != start && !(du >= d0 && du < d1);
+        if (side && found < 0) {
+          if (r == 0)
+            found = u;
+          else
+            --r;
+        }
+      }
+      if (found >= 0) {
+        key = found;
         break;
       }
-      --r;
     }
   }
   auto cell_of = [&](int u) { return (2 * (u / nn) + 1) * S + 2 * (u % nn) + 1; };
@@ -766,29 +852,57 @@ __device__ void gen_maze_lane(const Params& p, int e, uint32_t ep, uint8_t* work
     for (int r = 0; r < n_rooms; ++r) {
       const int x0 = 1 + (int)below(draw_at(kr, (uint32_t)(2 * r)), (uint32_t)(S - 9));
       const int y0 = 1 + (int)below(draw_at(kr, (uint32_t)(2 * r + 1)), (uint32_t)(S - 9));
-      for (int j = 0; j < 64; ++j) {
-        const int i = (y0 + (j >> 3)) * S + x0 + (j & 7);
-        if (smap[i] != kDoor) smap[i] = 0;
+      for (int j2 = 0; j2 < 64; ++j2) {
+        const int i = (y0 + (j2 >> 3)) * S + x0 + (j2 & 7);
+        if (i != dyc * S + dxc) smap[i] = 0;  // the door cell is the only kDoor
       }
     }
+    // floor cells per 256-cell chunk (the visited bits are no longer needed)
+    const int n_chunks = n_cells >> 8;
     int n_free = 0;
-    for (int i = 0; i < n_cells; i += 16) n_free += floor_bytes16(smap + i);
+    for (int ch = 0; ch < n_chunks; ++ch) {
+      const uint4* g = reinterpret_cast<const uint4*>(smap + (ch << 8));
+      uint4 q[16];
+#pragma unroll
+      for (int h = 0; h < 16; ++h) q[h] = g[h];
+      int f = 0;
+#pragma unroll
+      for (int h = 0; h < 16; ++h)
+        f += 16 - __popc(nonzero4(q[h].x) | nonzero4(q[h].y) << 4 | nonzero4(q[h].z) << 8 | nonzero4(q[h].w) << 12);
+      sm[ch * vstride] = (uint32_t)f;
+      n_free += f;
+    }
     const int nd = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_NSPRITES), 0), (uint32_t)(p.K - 1));
     const uint64_t ks = stream_key(p.seed, (uint32_t)e, ep, P_SPRITE_CELL);
     for (int k = 0; k < nd && n_free > 0; ++k) {
       uint32_t r = below(draw_at(ks, (uint32_t)k), (uint32_t)n_free);
-      int i = 0;
-      for (;; i += 16) {  // the 16-cell group holding the r-th floor cell
-        const uint32_t f = (uint32_t)floor_bytes16(smap + i);
+      int ch = 0;
+      for (;; ++ch) {  // the chunk holding the r-th floor cell
+        const uint32_t f = sm[ch * vstride];
         if (r < f) break;
         r -= f;
       }
-      for (;; ++i) {
-        if (smap[i] != 0) continue;
-        if (r == 0) break;
-        --r;
+      const uint4* g = reinterpret_cast<const uint4*>(smap + (ch << 8));
+      uint4 q[16];
+#pragma unroll
+      for (int h = 0; h < 16; ++h) q[h] = g[h];
+      int cell = -1;
+#pragma unroll
+      for (int h = 0; h < 16; ++h) {  // the r-th zero byte of the chunk
+        const uint32_t z = ~(nonzero4(q[h].x) | nonzero4(q[h].y) << 4 | nonzero4(q[h].z) << 8 | nonzero4(q[h].w) << 12) &
+                           0xffffu;
+        const uint32_t c = (uint32_t)__popc(z);
+        if (cell < 0) {
+          if (r < c) {
+            uint32_t zz = z;
+            for (uint32_t t = 0; t < r; ++t) zz &= zz - 1;
+            cell = (ch << 8) + 16 * h + __ffs(zz) - 1;
+          } else {
+            r -= c;
+          }
+        }
       }
-      spr_cell[2 + k] = i;
+      spr_cell[2 + k] = cell;
       spr_type[2 + k] = 3;
     }
     nspr = 2 + nd;
@@ -943,18 +1057,29 @@ __device__ __forceinline__ bool solid(const Params& p, const uint8_t* smap, int 
 // half-size is below 1/2, so every box edge lies in that range.
 __device__ __forceinline__ int floor_small(float v) { return (v >= 1.f ? 1 : 0) - (v < 0.f ? 1 : 0); }
 
+// Solidity of the 3 x 3 cells around cell (cx, cy), one lane per cell: bit
+// 3 (dy + 1) + (dx + 1) for the cell at offset (dx, dy), dx, dy in {-1, 0, 1}.
+// A move of at most half a cell by a box of half-size below one half keeps
+// both axis tests of a step inside these cells (see box_hits).
 template <int MAPK>
-__device__ __forceinline__ bool box_free(const Params& p, const uint8_t* smap, int S, int cx, float fx, int cy,
-                                         float fy, float r, int keys) {
-  const int i0 = cx + floor_small(fx - r), i1 = cx + floor_small(fx + r);
-  const int j0 = cy + floor_small(fy - r), j1 = cy + floor_small(fy + r);
-  bool hit = solid<MAPK>(p, smap, S, i0, j0, keys);
-  if (i1 != i0) hit |= solid<MAPK>(p, smap, S, i1, j0, keys);
-  if (j1 != j0) {
-    hit |= solid<MAPK>(p, smap, S, i0, j1, keys);
-    if (i1 != i0) hit |= solid<MAPK>(p, smap, S, i1, j1, keys);
-  }
-  return !hit;
+__device__ __forceinline__ uint32_t solid3x3(const Params& p, const uint8_t* smap, int cx, int cy, int keys,
+                                             int lane) {
+  const int k = lane < 9 ? lane : 4;
+  const int dy = (k * 11 >> 5) - 1;  // k / 3 for k < 9
+  const int dx = k - 3 * (dy + 1) - 1;
+  const bool sld = lane < 9 && solid<MAPK>(p, smap, p.S, cx + dx, cy + dy, keys);
+  return __ballot_sync(0xffffffffu, sld);
+}
+
+// The box of half-size r centred at (cx + fx, cy + fy) overlaps a solid cell
+// of mask m (solid3x3 around cell (ox, oy)); closed intervals, touching counts.
+__device__ __forceinline__ bool box_hits(uint32_t m, int ox, int oy, int cx, float fx, int cy, float fy, float r) {
+  const int i0 = cx - ox + floor_small(fx - r), i1 = cx - ox + floor_small(fx + r);
+  const int j0 = cy - oy + floor_small(fy - r), j1 = cy - oy + floor_small(fy + r);
+  const uint32_t cols = ((2u << (i1 - i0)) - 1u) << (i0 + 1);  // offsets i0..i1 of one row
+  bool hit = ((m >> (3 * (j0 + 1))) & cols) != 0u;
+  if (j1 != j0) hit |= ((m >> (3 * (j1 + 1))) & cols) != 0u;
+  return hit;
 }
 
 // An unlocked door opens when the agent walks into it: after a rejected axis
@@ -1034,18 +1159,21 @@ __device__ __forceinline__ bool step_env(const Params& p, int e, Env& r, const u
     dx = -(ms * s);
     dy = ms * c;
   }
-  const int S = p.S;
   const float rad = p.radius;
   const bool doors = p.task == kTaskAscii;  // maps with unlocked doors
+  // both axis tests read the solidity of the cells around the start cell
+  const int ox = r.cx, oy = r.cy;
+  uint32_t m = solid3x3<MAPK>(p, smap, ox, oy, r.keys, lane);
   float nfx = r.fx + dx;
-  if (box_free<MAPK>(p, smap, S, r.cx, nfx, r.cy, r.fy, rad, r.keys)) {
+  if (!box_hits(m, ox, oy, r.cx, nfx, r.cy, r.fy, rad)) {
     r.fx = nfx;
     renormalise(r.cx, r.fx);
   } else if (__builtin_expect(doors, 0)) {
     open_unlocked<MAPK>(p, e, const_cast<uint8_t*>(smap), r.cx, nfx, r.cy, r.fy, lane);
+    m = solid3x3<MAPK>(p, smap, ox, oy, r.keys, lane);  // opened doors are floor now
   }
   float nfy = r.fy + dy;
-  if (box_free<MAPK>(p, smap, S, r.cx, r.fx, r.cy, nfy, rad, r.keys)) {
+  if (!box_hits(m, ox, oy, r.cx, r.fx, r.cy, nfy, rad)) {
     r.fy = nfy;
     renormalise(r.cy, r.fy);
   } else if (__builtin_expect(doors, 0)) {
@@ -1155,7 +1283,7 @@ __device__ __forceinline__ void finish_column(const Params& p, int e, const Ray&
   const bool inside = (unsigned)q.mx < (unsigned)S && (unsigned)q.my < (unsigned)S;
   if (q.side >= 0 && inside)
     v = map_bits<MAPK>(p) ? p.st.map[(size_t)e * S * S + q.my * S + q.mx] : ws.map(p)[q.my * S + q.mx];
-  const int slot = col_slot(col, p.W >> 3);
+  const int slot = col_slot(col, p.W >> 4);
   uint32_t colour = ws.pal(p)[(q.side == 1 ? kCellColours : 0) + (v < kCellColours ? v : 1)];
   if (p.shading) {  // distance shading: channels scaled by q / 256, q = 64 + 192 min(h, H) / H
     const uint32_t qq = 64u + (uint32_t)(192 * (h < H ? h : H)) / (uint32_t)H;
@@ -1178,9 +1306,15 @@ __device__ __forceinline__ void finish_column(const Params& p, int e, const Ray&
 // Cast every column's ray: in each pass lane l marches the rays of columns
 // l + 32 j (j < COLS) together, and the warp leaves the DDA loop when a
 // ballot says every ray has hit.
+// The column table's entries lane and 32 + lane (0 beyond the frame), fetched
+// ahead with the env's state: the first two passes of cast_columns use them.
+__device__ __forceinline__ float2 col_k_pair(const Params& p, int lane) {
+  return make_float2(__ldg(p.col_k + lane), lane + 32 < p.W ? __ldg(p.col_k + lane + 32) : 0.f);
+}
+
 template <int MODE, int MAPK, int COLS>
 __device__ __forceinline__ void cast_columns(const Params& p, int e, const Env& r, float c, float s,
-                                             const WarpSmem& ws, int lane) {
+                                             const WarpSmem& ws, int lane, float2 k01) {
   const int W = p.W, S = p.S;
   const uint8_t* smap = ws.map(p);
   const int max_it = 4 * S + 8;
@@ -1190,7 +1324,8 @@ __device__ __forceinline__ void cast_columns(const Params& p, int e, const Env& 
     for (int j = 0; j < COLS; ++j) {
       const int col = col0 + 32 * j;
       const bool valid = col < W;
-      const float k = __ldg(p.col_k + (valid ? col : 0));
+      const int m = (col - lane) >> 5;  // column col = lane + 32 m
+      const float k = m == 0 ? k01.x : (m == 1 ? k01.y : __ldg(p.col_k + (valid ? col : 0)));
       ray_init(q[j], r, fmaf(-k, s, c), fmaf(k, c, s), valid);
     }
     for (int it = 0; it < max_it; ++it) {
@@ -1218,6 +1353,7 @@ __device__ __forceinline__ int project_sprites(const Params& p, const Env& r, fl
   const int W = p.W, H = p.H;
   bool vis = false;
   float ty = 0.f;
+  int cA = 0, cB = -1;
   const int nspr = ws.obj(p)[6];
   if (lane < nspr) {
     const float4 sp = ws.spr_in(p)[lane];
@@ -1227,15 +1363,17 @@ __device__ __forceinline__ int project_sprites(const Params& p, const Env& r, fl
     ty = fmaf(vx, c, vy * s);
     const int kc = key_colour(type);
     if (type != 0 && !(kc >= 0 && ((r.keys >> kc) & 1)) && ty > 0.1f) {
-      const float inv_ty = __frcp_rn(ty);
+      // 1/ty within an ulp or two: pixel positions move by far less than the
+      // 1e-3 pixel the silhouette-edge tolerance allows
+      const float inv_ty = __fdividef(1.f, ty);
       const float tx = fmaf(-vx, s, vy * c) * p.inv_tan_half;
       const float wd = 0.25f * (float)W * p.inv_tan_half * inv_ty;
       const float ht = 0.5f * (float)H * inv_ty;
       const float x0 = fmaf(0.5f * (float)W, fmaf(tx, inv_ty, 1.f), -0.5f * wd);
       const float top = 0.5f * (float)H;
       // pixel centres that can fall inside [x0, x0 + wd) x [top, top + ht), one pixel of slack
-      int cA = (int)floorf(fmaxf(x0 - 1.f, -1.f));
-      int cB = (int)floorf(fminf(x0 + wd + 1.f, (float)W));
+      cA = (int)floorf(fmaxf(x0 - 1.f, -1.f));
+      cB = (int)floorf(fminf(x0 + wd + 1.f, (float)W));
       const int rA = (int)floorf(fmaxf(top - 1.f, -1.f));
       const int rB = (int)floorf(fminf(top + ht + 1.f, (float)H));
       cA = cA < 0 ? 0 : cA;
@@ -1250,8 +1388,22 @@ __device__ __forceinline__ int project_sprites(const Params& p, const Env& r, fl
       }
     }
   }
-  const uint32_t vmask = __ballot_sync(0xffffffffu, vis);
-  if (vmask == 0u) return 0;  // nothing on screen (warp-uniform)
+  const uint32_t cand = __ballot_sync(0xffffffffu, vis);
+  if (cand == 0u) return 0;  // nothing on screen (warp-uniform)
+  // A pixel is drawn only where the sprite is nearer than its column's wall:
+  // a sprite behind the walls at every column it can cover is culled here
+  // (the lanes scan its columns together).
+  uint32_t vmask = 0u;
+  for (uint32_t m = cand; m != 0u; m &= m - 1u) {
+    const int j = __ffs(m) - 1;
+    const int a = __shfl_sync(0xffffffffu, cA, j), b = __shfl_sync(0xffffffffu, cB, j);
+    const float tj = __shfl_sync(0xffffffffu, ty, j);
+    bool nearer = false;
+    for (int col = a + lane; col <= b; col += 32) nearer |= tj < ws.zbuf(p)[col];
+    if (__any_sync(0xffffffffu, nearer)) vmask |= 1u << j;
+  }
+  if (vmask == 0u) return 0;
+  vis = (vmask >> lane) & 1u;
   int rank = 0;
   for (int k = 0; k < nspr; ++k) {
     const float tk = __shfl_sync(0xffffffffu, ty, k);
@@ -1283,66 +1435,82 @@ __device__ __forceinline__ uint32_t select_bytes(uint32_t m, uint32_t a, uint32_
 // Fill rows [r0, r1) of the frame into `buf` (row-major RGB), then draw the
 // sprites over them.
 //
-// A lane owns 8 columns of a row: two quads of 4 pixels, 12 bytes = 3 words
-// each. Because every slice is centred, a row above H/2 is ceiling or wall
-// and a row at or below it is wall or floor. Byte k of d = (127 + top_k) -
-// row (all bytes at once) is in [0, 255], so no borrow crosses bytes, and
-// its bit 7 is set exactly when row < top_k; sign-replicating prmt turns
-// those bits into byte masks laid out like the pixels' RGB bytes, and one
-// select per word picks ceiling or wall. Rows below the middle do the same
-// with 127 + bot_k - H/2 and row - H/2 (wall or floor).
+// A lane owns 16 columns of a row: four quads of 4 pixels, 12 bytes = 3 words
+// each, stored as three 16-byte words. Because every slice is centred, a row
+// above H/2 is ceiling or wall and a row at or below it is wall or floor.
+// Byte k of d = (127 + top_k) - row (all bytes at once) is in [0, 255], so no
+// borrow crosses bytes, and its bit 7 is set exactly when row < top_k;
+// sign-replicating prmt turns those bits into byte masks laid out like the
+// pixels' RGB bytes, and one select per word picks ceiling or wall. Rows
+// below the middle do the same with 127 + bot_k - H/2 and row - H/2 (wall or
+// floor).
+#define JX_QUAD_WORDS(d, A0, A1, A2, B0, B1, B2)                                        \
+  select_bytes(sign_bytes<0x9888>(d), A0, B0), select_bytes(sign_bytes<0xAA99>(d), A1, B1), \
+      select_bytes(sign_bytes<0xBBBA>(d), A2, B2)
+// GRAYF: the block also writes its rows of the grayscale frame into gbuf.
+template <bool GRAYF>
 __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, uint8_t* buf, uint8_t* gbuf, int r0,
                                           int r1, int nvis, int lane) {
   const int W = p.W, H = p.H, rowb = 3 * W, mid = H >> 1;
-  const bool gray = gbuf != nullptr;
-  const int groups = ws.fl.groups;  // lanes per row, 8 pixels (24 bytes) each
+  const int groups = ws.fl.groups;  // lanes per row, 16 pixels (48 bytes) each
   const int rpp = ws.fl.rows;       // rows per pass
   const int my_row = ws.fl.my_row, g = ws.fl.g;
   if (my_row < rpp) {
-    const uint2 t8 = *reinterpret_cast<const uint2*>(ws.col_top(p) + 8 * g);
-    const uint2 b8 = *reinterpret_cast<const uint2*>(ws.col_bot(p) + 8 * g);
-    uint32_t wq[6], yq[2];  // wall RGB words of the two quads, wall luma bytes
+    const uint4 t16 = *reinterpret_cast<const uint4*>(ws.col_top(p) + 16 * g);
+    const uint4 b16 = *reinterpret_cast<const uint4*>(ws.col_bot(p) + 16 * g);
+    uint32_t wq[12], yq[4];  // wall RGB words of the four quads, wall luma bytes
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 4; ++h) {
       const uint4 c = *reinterpret_cast<const uint4*>(ws.col_rgb(p) + ((h * groups + g) << 2));
       wq[3 * h + 0] = __byte_perm(c.x, c.y, 0x4210);
       wq[3 * h + 1] = __byte_perm(c.y, c.z, 0x5421);
       wq[3 * h + 2] = __byte_perm(c.z, c.w, 0x6542);
-      yq[h] = __byte_perm(__byte_perm(c.x, c.y, 0x0073), __byte_perm(c.z, c.w, 0x0073), 0x5410);
+      if (GRAYF) yq[h] = __byte_perm(__byte_perm(c.x, c.y, 0x0073), __byte_perm(c.z, c.w, 0x0073), 0x5410);
     }
+    constexpr uint32_t C0 = rgb_word(kCeil, 0), C1 = rgb_word(kCeil, 1), C2 = rgb_word(kCeil, 2);
+    constexpr uint32_t F0 = rgb_word(kFloor, 0), F1 = rgb_word(kFloor, 1), F2 = rgb_word(kFloor, 2);
+    constexpr uint32_t CY = (kCeil >> 24) * 0x01010101u, FY = (kFloor >> 24) * 0x01010101u;
     const uint32_t step = (uint32_t)rpp * 0x01010101u;
     int row = r0 + my_row;
-    uint2* dst = reinterpret_cast<uint2*>(buf + my_row * rowb + g * 24);
-    uint2* gdst = reinterpret_cast<uint2*>((gray ? gbuf : buf) + my_row * W + g * 8);  // written only with gray
-    const int dstep = rpp * rowb / 8, gstep = rpp * W / 8;
+    // this lane's 48 RGB bytes (and 16 luma bytes) in its first row
+    uint4* dst = reinterpret_cast<uint4*>(buf + my_row * rowb + g * 48);
+    uint4* gdst = reinterpret_cast<uint4*>((GRAYF ? gbuf : buf) + my_row * W + g * 16);
+    const int dstep = rpp * rowb / 16, gstep = rpp * W / 16;
     const int lim = r1 < mid ? r1 : mid;
     if (row < lim) {  // ceiling or wall
-      uint32_t d0 = t8.x - (uint32_t)row * 0x01010101u, d1 = t8.y - (uint32_t)row * 0x01010101u;
-      for (; row < lim; row += rpp, d0 -= step, d1 -= step, dst += dstep, gdst += gstep) {
-        dst[0] = make_uint2(select_bytes(sign_bytes<0x9888>(d0), rgb_word(kCeil, 0), wq[0]),
-                            select_bytes(sign_bytes<0xAA99>(d0), rgb_word(kCeil, 1), wq[1]));
-        dst[1] = make_uint2(select_bytes(sign_bytes<0xBBBA>(d0), rgb_word(kCeil, 2), wq[2]),
-                            select_bytes(sign_bytes<0x9888>(d1), rgb_word(kCeil, 0), wq[3]));
-        dst[2] = make_uint2(select_bytes(sign_bytes<0xAA99>(d1), rgb_word(kCeil, 1), wq[4]),
-                            select_bytes(sign_bytes<0xBBBA>(d1), rgb_word(kCeil, 2), wq[5]));
-        if (gray)
-          *gdst = make_uint2(select_bytes(sign_bytes<0xBA98>(d0), (kCeil >> 24) * 0x01010101u, yq[0]),
-                             select_bytes(sign_bytes<0xBA98>(d1), (kCeil >> 24) * 0x01010101u, yq[1]));
+      const uint32_t rr = (uint32_t)row * 0x01010101u;
+      uint32_t d0 = t16.x - rr, d1 = t16.y - rr, d2 = t16.z - rr, d3 = t16.w - rr;
+      for (; row < lim; row += rpp, d0 -= step, d1 -= step, d2 -= step, d3 -= step, dst += dstep) {
+        const uint32_t a[12] = {JX_QUAD_WORDS(d0, C0, C1, C2, wq[0], wq[1], wq[2]),
+                                JX_QUAD_WORDS(d1, C0, C1, C2, wq[3], wq[4], wq[5]),
+                                JX_QUAD_WORDS(d2, C0, C1, C2, wq[6], wq[7], wq[8]),
+                                JX_QUAD_WORDS(d3, C0, C1, C2, wq[9], wq[10], wq[11])};
+        dst[0] = make_uint4(a[0], a[1], a[2], a[3]);
+        dst[1] = make_uint4(a[4], a[5], a[6], a[7]);
+        dst[2] = make_uint4(a[8], a[9], a[10], a[11]);
+        if (GRAYF) {
+          *gdst = make_uint4(select_bytes(sign_bytes<0xBA98>(d0), CY, yq[0]), select_bytes(sign_bytes<0xBA98>(d1), CY, yq[1]),
+                             select_bytes(sign_bytes<0xBA98>(d2), CY, yq[2]), select_bytes(sign_bytes<0xBA98>(d3), CY, yq[3]));
+          gdst += gstep;
+        }
       }
     }
     if (row < r1) {  // wall or floor
       const uint32_t rr = (uint32_t)(row - mid) * 0x01010101u;
-      uint32_t d0 = b8.x - rr, d1 = b8.y - rr;
-      for (; row < r1; row += rpp, d0 -= step, d1 -= step, dst += dstep, gdst += gstep) {
-        dst[0] = make_uint2(select_bytes(sign_bytes<0x9888>(d0), wq[0], rgb_word(kFloor, 0)),
-                            select_bytes(sign_bytes<0xAA99>(d0), wq[1], rgb_word(kFloor, 1)));
-        dst[1] = make_uint2(select_bytes(sign_bytes<0xBBBA>(d0), wq[2], rgb_word(kFloor, 2)),
-                            select_bytes(sign_bytes<0x9888>(d1), wq[3], rgb_word(kFloor, 0)));
-        dst[2] = make_uint2(select_bytes(sign_bytes<0xAA99>(d1), wq[4], rgb_word(kFloor, 1)),
-                            select_bytes(sign_bytes<0xBBBA>(d1), wq[5], rgb_word(kFloor, 2)));
-        if (gray)
-          *gdst = make_uint2(select_bytes(sign_bytes<0xBA98>(d0), yq[0], (kFloor >> 24) * 0x01010101u),
-                             select_bytes(sign_bytes<0xBA98>(d1), yq[1], (kFloor >> 24) * 0x01010101u));
+      uint32_t d0 = b16.x - rr, d1 = b16.y - rr, d2 = b16.z - rr, d3 = b16.w - rr;
+      for (; row < r1; row += rpp, d0 -= step, d1 -= step, d2 -= step, d3 -= step, dst += dstep) {
+        const uint32_t a[12] = {JX_QUAD_WORDS(d0, wq[0], wq[1], wq[2], F0, F1, F2),
+                                JX_QUAD_WORDS(d1, wq[3], wq[4], wq[5], F0, F1, F2),
+                                JX_QUAD_WORDS(d2, wq[6], wq[7], wq[8], F0, F1, F2),
+                                JX_QUAD_WORDS(d3, wq[9], wq[10], wq[11], F0, F1, F2)};
+        dst[0] = make_uint4(a[0], a[1], a[2], a[3]);
+        dst[1] = make_uint4(a[4], a[5], a[6], a[7]);
+        dst[2] = make_uint4(a[8], a[9], a[10], a[11]);
+        if (GRAYF) {
+          *gdst = make_uint4(select_bytes(sign_bytes<0xBA98>(d0), yq[0], FY), select_bytes(sign_bytes<0xBA98>(d1), yq[1], FY),
+                             select_bytes(sign_bytes<0xBA98>(d2), yq[2], FY), select_bytes(sign_bytes<0xBA98>(d3), yq[3], FY));
+          gdst += gstep;
+        }
       }
     }
   }
@@ -1379,19 +1547,20 @@ __device__ __forceinline__ void fill_block(const Params& p, const WarpSmem& ws, 
           q[0] = (uint8_t)(rgbv & 255);
           q[1] = (uint8_t)((rgbv >> 8) & 255);
           q[2] = (uint8_t)((rgbv >> 16) & 255);
-          if (gray) gbuf[(row - r0) * W + col] = (uint8_t)(rgbv >> 24);
+          if (GRAYF) gbuf[(row - r0) * W + col] = (uint8_t)(rgbv >> 24);
         }
       }
     }
     __syncwarp();
   }
 }
+#undef JX_QUAD_WORDS
 
 // GRAY: 0 no grayscale stack, 1 a stack, 2 as p.st.gray says (batched kernel).
 template <int MODE, int MAPK, int COLS, int GRAY>
 __device__ __forceinline__ void render_env(const Params& p, int e, const Env& r, float c, float s,
-                                           const WarpSmem& ws, int lane, int& slot, uint8_t* frame) {
-  cast_columns<MODE, MAPK, COLS>(p, e, r, c, s, ws, lane);
+                                           const WarpSmem& ws, int lane, int& slot, uint8_t* frame, float2 k01) {
+  cast_columns<MODE, MAPK, COLS>(p, e, r, c, s, ws, lane, k01);
   if (MODE == MODE_RAYS) return;
   const int nvis = project_sprites(p, r, c, s, ws, lane);  // ends with __syncwarp
   const int H = p.H, W = p.W, rowb = 3 * W;
@@ -1407,7 +1576,10 @@ __device__ __forceinline__ void render_env(const Params& p, int e, const Env& r,
     uint8_t* gbuf = gray_on ? ws.gray_ring(p) + slot * p.gray_block_bytes : nullptr;
     if (lane == 0) bulk_wait_staging(p.staging);
     __syncwarp();
-    fill_block(p, ws, buf, gbuf, r0, r1, nvis, lane);
+    if (gray_on)
+      fill_block<true>(p, ws, buf, gbuf, r0, r1, nvis, lane);
+    else
+      fill_block<false>(p, ws, buf, gbuf, r0, r1, nvis, lane);
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) {
@@ -1467,14 +1639,16 @@ __device__ __noinline__ void open_doors(const Params& p, int e, int keys, const 
 // independent loads so that their latencies overlap: the scalar state, the
 // key / goal / door cells and sprite count (lanes 0..6), the sprite slots
 // (lane j: slot j), the map when it holds at most 1 KB (two 16-byte chunks a
-// lane), the first action, and for the single step the turn table's entries
-// lane, 32 + lane and 64 + lane (tables of at most 96 turns).
+// lane), the first action, the column table's first two entries of the lane,
+// and for the single step the turn table's entries lane, 32 + lane and
+// 64 + lane (tables of at most 96 turns).
 struct Prefetch {
   Env r;
   int obj;
   float4 spr;
   uint4 m0, m1;
   float2 tc0, tc1, tc2;
+  float2 k01;  // column table entries lane, 32 + lane
   int action;
 };
 
@@ -1510,6 +1684,7 @@ __device__ __forceinline__ Prefetch prefetch(const Params& p, int e, int lane) {
     }
   }
   q.action = (MODE == MODE_STEP || MODE == MODE_ROLLOUT) ? (int)p.actions[e] : 0;
+  q.k01 = col_k_pair(p, lane);
   q.tc0 = q.tc1 = q.tc2 = make_float2(0.f, 0.f);
   if (MODE == MODE_STEP && p.tpr <= 96) {
     if (lane < p.tpr) q.tc0 = p.turn_cs[lane];
@@ -1587,7 +1762,8 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
     __syncwarp();
     float c, s;
     heading(p, r, c, s);
-    render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
+    render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes,
+                                       col_k_pair(p, lane));
     __syncwarp();
     return;
   }
@@ -1610,7 +1786,7 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
         next_episode<MAPK>(p, e, r, ws, scratch, lane, c, s);
       if (__builtin_expect(r.keys != keys0, 0)) open_doors<MAPK>(p, e, r.keys, ws, lane);
       render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot,
-                                         p.frames + (size_t)t * p.frame_step + (size_t)e * frame_bytes);
+                                         p.frames + (size_t)t * p.frame_step + (size_t)e * frame_bytes, q.k01);
       __syncwarp();
     }
     if (lane == 0) {
@@ -1639,7 +1815,7 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
   } else {
     heading(p, r, c, s);
   }
-  render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes);
+  render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes, q.k01);
   __syncwarp();
 }
 

@@ -135,6 +135,8 @@ size_t gen_scratch_bytes(int task, int S);
 // multiple of 4) with a horizon, one lane per env builds the episode the env
 // will start within the next `steps` steps (reset: episode 0) into p.nx.
 constexpr int kPregenMinSide = 64;
+constexpr int kPregenThreads = 32;  // pre-generation lanes per block (each with its walk state in shared memory)
+constexpr int kPregenSpread = 4;    // coinciding horizons are built over this many launches ahead
 bool pregen_wanted(int task, int S, int horizon);
 size_t pregen_work_bytes(int S);
 cudaError_t pregen_launch(const Params& p, int steps, bool reset, cudaStream_t stream);

@@ -13,7 +13,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* const wbase = smem_raw + warp * p.warp_bytes;
   const uint3 pal = load_palette(lane);  // stored with the first env's prefetched state
-  init_warp_header(wbase, lane);
+  // the header's mbarrier serves only bulk copies of byte maps of 4 KB or more
+  if (!p.map_bits && p.S * p.S >= 4096) init_warp_header(wbase, lane);
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
   uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;
@@ -24,15 +25,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
 }
 
 // Whether env e needs a pre-built episode, and which: the one it starts
-// within the next `steps` steps (its horizon falls in them) or, for a reset,
-// episode 0, unless the next-episode block holds it already.
+// soon, or for a reset episode 0, unless the next-episode block holds it
+// already. "Soon" spreads the builds of envs whose horizons coincide over the
+// last kPregenSpread launches before it, a contiguous part of the envs in
+// each (so a warp's lanes build together): env e of part q = e * kPregenSpread
+// / n is built once its horizon falls within the next steps * (1 + q) steps.
 __device__ __forceinline__ bool pregen_need(const Params& p, int e, int steps, int reset, uint32_t& ep) {
   if (reset) {
     ep = 0;
     return p.nx_ep[e] != 0u;
   }
   ep = p.st.episode[e] + 1;
-  return p.horizon > 0 && p.st.t[e] + steps >= p.horizon && p.nx_ep[e] != ep;
+  const int q = (int)(((int64_t)e * kPregenSpread) / p.n);
+  return p.horizon > 0 && p.st.t[e] + steps * (1 + q) >= p.horizon && p.nx_ep[e] != ep;
 }
 
 // Counts the envs that need a pre-built episode into *p.nx_count (zeroed before).
@@ -45,15 +50,22 @@ __global__ void __launch_bounds__(128) pregen_count_kernel(const __grid_constant
 }
 
 // Lane-parallel pre-generation: lane i builds, for envs i, i + lanes, ...,
-// the episode each needs, when at least nx_min envs need one.
-__global__ void __launch_bounds__(128) pregen_kernel(const __grid_constant__ Params p, int steps, int reset) {
+// the episode each needs, when at least nx_min envs need one. Each lane keeps
+// its walk's state in shared memory (kPregenThreads lanes a block,
+// pregen_lane_words words each: under 48 KB a block for side 128).
+__global__ void __launch_bounds__(kPregenThreads) pregen_kernel(const __grid_constant__ Params p, int steps, int reset) {
+  extern __shared__ uint32_t pregen_sm[];
+  if (*p.nx_count < (uint32_t)p.nx_min) return;  // the whole grid
   const int lane_id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (lane_id >= p.nx_lanes || *p.nx_count < (uint32_t)p.nx_min) return;
-  uint8_t* work = p.nx_work + (size_t)lane_id * p.nx_work_stride;
-  for (int e = lane_id; e < p.n; e += p.nx_lanes) {
-    uint32_t ep;
-    if (pregen_need(p, e, steps, reset, ep)) {
-      gen_maze_lane(p, e, ep, work);
+  const int lane = threadIdx.x & 31;
+  // lanes below nx_lanes own a work slot; the loop runs the same iterations
+  // in all lanes of a warp (its condition is the warp's first env)
+  for (int e = lane_id; e - lane < p.n; e += p.nx_lanes) {
+    uint32_t ep = 0;
+    const bool need = lane_id < p.nx_lanes && e < p.n && pregen_need(p, e, steps, reset, ep);
+    const uint32_t m = __ballot_sync(0xffffffffu, need);
+    if (need) {
+      gen_maze_lane(p, e, ep, p.nx_work + (size_t)lane_id * p.nx_work_stride, pregen_sm + threadIdx.x, blockDim.x, m);
       p.nx_ep[e] = ep;
     }
   }
@@ -117,7 +129,7 @@ bool pregen_wanted(int task, int S, int horizon) {
 
 size_t pregen_work_bytes(int S) {
   const size_t n = (size_t)((S - 2) / 2) * ((S - 2) / 2);
-  return (6 * n + 255) & ~(size_t)255;  // stack, discovery and finish counters (uint16)
+  return (4 * n + 16 + 255) & ~(size_t)255;  // discovery and finish counters (uint16, the first 16-byte aligned)
 }
 
 cudaError_t pregen_launch(const Params& p, int steps, bool reset, cudaStream_t stream) {
@@ -125,7 +137,9 @@ cudaError_t pregen_launch(const Params& p, int steps, bool reset, cudaStream_t s
   cudaError_t err = cudaMemsetAsync(p.nx_count, 0, sizeof(uint32_t), stream);
   if (err != cudaSuccess) return err;
   pregen_count_kernel<<<(p.n + 127) / 128, 128, 0, stream>>>(p, steps, reset ? 1 : 0);
-  pregen_kernel<<<(p.nx_lanes + 127) / 128, 128, 0, stream>>>(p, steps, reset ? 1 : 0);
+  const size_t lane_bytes = (size_t)kPregenThreads * pregen_lane_words(p.S) * sizeof(uint32_t);
+  pregen_kernel<<<(p.nx_lanes + kPregenThreads - 1) / kPregenThreads, kPregenThreads, lane_bytes, stream>>>(
+      p, steps, reset ? 1 : 0);
   return cudaGetLastError();
 }
 
