@@ -238,6 +238,17 @@ jx_status jx_step_host(jx_env* env, void* stream, const uint8_t* h_actions, uint
 jx_status jx_step_host_static(jx_env* env, void* stream, const uint8_t* h_actions, uint8_t* h_frames,
                               float* h_rewards, uint8_t* h_dones);
 
+/* Test and debug hook: the number of mbarrier polls a warp makes before a
+ * bulk copy of a byte map (maps of 4 KB or more held as bytes) counts as
+ * late (default 65536). A late copy sets bit 2 of the device error word (see
+ * jx_sync_status) and is waited for up to a further fixed bound; a copy that
+ * does not complete then counts as lost: its warp leaves that env and its
+ * later envs of the launch unstepped (their outputs keep old contents) and
+ * never reuses the copy's buffer. 0 makes every copy late, exercising that
+ * path on a healthy device. Applies to later launches of the env (its own
+ * kernel, and its tuned batch). JX_EINVAL for rounds < 0. */
+jx_status jx_debug_wait_limit(jx_env* env, int32_t rounds);
+
 /* Per-column ray results of the current state (test and debug hook):
  *  d_hits [N][W][4] int32: hit cell x, hit cell y, side (0: x face, 1: y face),
  *         slice height h in rows;
@@ -280,7 +291,9 @@ jx_status jx_get_state(jx_env* env, void* h_buf, size_t bytes);
 jx_status jx_set_state(jx_env* env, const void* h_buf, size_t bytes);
 
 /* Wait for `stream`, then read and clear the device error word: JX_OK, or
- * JX_EDEVICE when a kernel recorded bad data since the last call. */
+ * JX_EDEVICE when a kernel recorded bad data since the last call (bit 0: an
+ * action outside 0..6, taken as a no-op; bit 1: a bulk map copy completed
+ * late or was lost, see jx_debug_wait_limit). */
 jx_status jx_sync_status(jx_env* env, void* stream);
 
 /* Number of kernel launches this env has issued since creation. For maze

@@ -149,7 +149,13 @@ jx_status batch_run(jx_batch* b, int mode, cudaStream_t stream, const uint8_t* a
   }
   cudaError_t err = jx::batch_launch(bp, mode, b->tiling.cols_per_lane, b->tiling.warps_per_block, b->grid[mode],
                                      stream);
-  if (err != cudaSuccess) return cuda_fail(err, "batched kernel launch");
+  if (err != cudaSuccess) {
+    // The kernel's last warp clears the work-queue counters for the next
+    // launch; a launch that failed may not have got there, so clear them here
+    // (on the same stream) or every later launch would find drained queues.
+    (void)cudaMemsetAsync(bp.queue, 0, sizeof(uint32_t) * (jx::kMaxGroups + 1), stream);
+    return cuda_fail(err, "batched kernel launch");
+  }
   if (count) b->launches.fetch_add(1, std::memory_order_relaxed);
   return JX_OK;
 }

@@ -23,7 +23,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
   int slot = 0;
   const uint3 no_palette = make_uint3(0u, 0u, 0u);  // written once per group (write_palette), not per env
   bool fresh = true;  // nothing of an earlier group is pending in the ring
-  for (int g = 0; g < bp.n_groups; ++g) {
+  bool lost = false;  // a map copy of this warp was lost: it takes no further env
+  for (int g = 0; g < bp.n_groups && !lost; ++g) {
     const Params& p = bp.g[g];
     uint32_t ticket = 0;
     if (lane == 0) {
@@ -43,9 +44,10 @@ __global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
       uint32_t next = 0;
       if (lane == 0) next = atomicAdd(bp.queue + g, 1u);
       if (SPEC == 1)
-        run_env<MODE, MAP_BITS, COLS, 0>(p, (int)ticket, wbase, scratch, lane, slot, no_palette, false);
+        lost = !run_env<MODE, MAP_BITS, COLS, 0>(p, (int)ticket, wbase, scratch, lane, slot, no_palette, false);
       else
-        run_env<MODE, MAP_RUNTIME, COLS, 2>(p, (int)ticket, wbase, scratch, lane, slot, no_palette, false);
+        lost = !run_env<MODE, MAP_RUNTIME, COLS, 2>(p, (int)ticket, wbase, scratch, lane, slot, no_palette, false);
+      if (lost) break;  // the counters are still cleared below: every warp reaches the end
       ticket = __shfl_sync(0xffffffffu, next, 0);
     }
   }

@@ -130,10 +130,20 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 
 // Every warp's shared memory starts with a 16-byte header: the mbarrier that
 // bulk global->shared map copies complete on (bytes 0..7), the phase parity
-// the next copy waits for (8..11), and 1 once a copy has timed out (12..15;
-// later copies then use plain loads).
+// the next copy waits for (8..11), and 1 once a copy was lost (12..15).
 constexpr int kWarpHeader = 16;
-constexpr int kBulkWaitLimit = 1 << 16;  // try_wait rounds before a copy counts as lost
+constexpr int kBulkDrainLimit = 1 << 22;  // further rounds before a late copy counts as lost
+
+// One bounded round of try_wait polls of the warp's mbarrier for `phase`;
+// returns 1 once it has completed.
+__device__ __forceinline__ uint32_t bulk_poll(uint32_t bar, uint32_t phase, int rounds, uint32_t done) {
+  for (int it = 0; it < rounds && !done; ++it)
+    asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"
+                 : "=r"(done)
+                 : "r"(bar), "r"(phase)
+                 : "memory");
+  return done;
+}
 
 __device__ __forceinline__ void init_warp_header(uint8_t* wbase, int lane) {
   if (lane == 0) {
@@ -148,10 +158,13 @@ __device__ __forceinline__ void init_warp_header(uint8_t* wbase, int lane) {
 
 // n bytes (a multiple of 16, both addresses 16-byte aligned) from global
 // memory to shared memory with one bulk copy issued by lane 0 and completed
-// on the warp's mbarrier; every lane waits, at most kBulkWaitLimit rounds.
-// Returns false (after recording it in the header) when the copy did not
-// complete in time.
-__device__ __forceinline__ bool bulk_load(uint8_t* wbase, uint8_t* sdst, const uint8_t* gsrc, uint32_t n, int lane) {
+// on the warp's mbarrier. Every lane waits at most first_rounds polls; a copy
+// still pending then is late, and the lanes wait up to kBulkDrainLimit more
+// polls for it before giving it up: its bytes may still land in `sdst` at any
+// time, so the caller must not reuse the buffer (the header records it).
+// Returns 0 (in time), 1 (late, complete now) or 2 (lost).
+__device__ __forceinline__ int bulk_load(uint8_t* wbase, uint8_t* sdst, const uint8_t* gsrc, uint32_t n, int lane,
+                                         int first_rounds) {
   volatile uint32_t* hdr = reinterpret_cast<volatile uint32_t*>(wbase);
   const uint32_t phase = hdr[2];
   const uint32_t bar = (uint32_t)__cvta_generic_to_shared(wbase);
@@ -168,19 +181,18 @@ __device__ __forceinline__ bool bulk_load(uint8_t* wbase, uint8_t* sdst, const u
                  "l"(gsrc), "r"(n), "r"(bar)
                  : "memory");
   }
-  uint32_t done = 0;
-  for (int it = 0; it < kBulkWaitLimit && !done; ++it)
-    asm volatile("{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}\n"
-                 : "=r"(done)
-                 : "r"(bar), "r"(phase)
-                 : "memory");
-  const bool ok = __all_sync(0xffffffffu, done != 0);
+  uint32_t done = bulk_poll(bar, phase, first_rounds, 0u);
+  int state = 0;
+  if (!__all_sync(0xffffffffu, done != 0)) {
+    done = bulk_poll(bar, phase, kBulkDrainLimit, done);
+    state = __all_sync(0xffffffffu, done != 0) ? 1 : 2;
+  }
   if (lane == 0) {
     hdr[2] = phase ^ 1u;
-    if (!ok) hdr[3] = 1u;
+    if (state == 2) hdr[3] = 1u;
   }
   __syncwarp();
-  return ok;
+  return state;
 }
 // the staging buffer about to be filled has been read out: with two buffers
 // the other one may still be draining, with one every earlier copy is done
@@ -326,14 +338,18 @@ __device__ __forceinline__ void heading(const Params& p, const Env& r, float& c,
 
 // Byte maps of 4 KB or more (side >= 64) are copied by one bulk copy, smaller
 // ones by 16-byte loads of all lanes. The warp header is read only on the
-// bulk path (kernels initialise it only where maps of that size occur).
-__device__ __forceinline__ void stage_map(const Params& p, int e, uint8_t* smap, int lane) {
+// bulk path (kernels initialise it only where maps of that size occur). A
+// late copy sets bit 2 of the error word; a lost one also returns false: the
+// warp then leaves the env (and any later env) untouched.
+__device__ __forceinline__ bool stage_map(const Params& p, int e, uint8_t* smap, int lane) {
   const int n = p.S * p.S;
   const uint8_t* g = p.st.map + (size_t)e * n;
   uint8_t* wbase = smap - p.off_map;
-  if (n >= 4096 && (n & 15) == 0 && reinterpret_cast<volatile uint32_t*>(wbase)[3] == 0) {
-    if (bulk_load(wbase, smap, g, (uint32_t)n, lane)) return;
-    if (lane == 0) atomicOr(p.err, 2u);  // the copy was lost: load the map below
+  if (n >= 4096 && (n & 15) == 0) {
+    if (reinterpret_cast<volatile uint32_t*>(wbase)[3] != 0) return false;  // an earlier copy was lost
+    const int st = bulk_load(wbase, smap, g, (uint32_t)n, lane, p.bulk_wait_rounds);
+    if (st != 0 && lane == 0) atomicOr(p.err, 2u);
+    return st != 2;
   }
   if ((n & 15) == 0) {
     const uint4* src = reinterpret_cast<const uint4*>(g);
@@ -343,6 +359,7 @@ __device__ __forceinline__ void stage_map(const Params& p, int e, uint8_t* smap,
     for (int i = lane; i < n; i += 32) smap[i] = g[i];
   }
   __syncwarp();
+  return true;
 }
 
 __device__ __forceinline__ void store_map(const Params& p, int e, const uint8_t* smap, int lane) {
@@ -394,11 +411,12 @@ __device__ __forceinline__ bool cell_set(const Params& p, const uint8_t* smap, i
 }
 
 template <int MAPK>
-__device__ __forceinline__ void stage(const Params& p, int e, uint8_t* smap, int lane) {
-  if (map_bits<MAPK>(p))
+__device__ __forceinline__ bool stage(const Params& p, int e, uint8_t* smap, int lane) {
+  if (map_bits<MAPK>(p)) {
     stage_map_bits(p, e, smap, lane);
-  else
-    stage_map(p, e, smap, lane);
+    return true;
+  }
+  return stage_map(p, e, smap, lane);
 }
 
 // ------------------------------------------------------------ generators --
@@ -1695,17 +1713,15 @@ __device__ __forceinline__ Prefetch prefetch(const Params& p, int e, int lane) {
 }
 
 // The prefetched objects, sprites and map into the warp's shared memory
-// (maps too large to prefetch are staged here); ends with __syncwarp.
+// (maps too large to prefetch are staged here); ends with __syncwarp. False
+// when the map's copy was lost (see stage_map).
 template <int MAPK>
-__device__ __forceinline__ void stage_prefetched(const Params& p, const WarpSmem& ws, int e, const Prefetch& q,
+__device__ __forceinline__ bool stage_prefetched(const Params& p, const WarpSmem& ws, int e, const Prefetch& q,
                                                  int lane) {
   if (lane < 6) ws.obj(p)[lane] = q.obj;
   if (lane == 6) ws.obj(p)[6] = q.obj > p.K ? p.K : q.obj;  // sprites in use
   if (lane < p.K) ws.spr_in(p)[lane] = q.spr;
-  if (!small_map<MAPK>(p)) {
-    stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
-    return;
-  }
+  if (!small_map<MAPK>(p)) return stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
   const int n = p.S * p.S;
   if (map_bits<MAPK>(p)) {
     if (lane < (n >> 5))
@@ -1718,6 +1734,7 @@ __device__ __forceinline__ void stage_prefetched(const Params& p, const WarpSmem
     if (lane + 32 < (n >> 4)) dst[lane + 32] = q.m1;
   }
   __syncwarp();
+  return true;
 }
 
 // Turn table entry `turn`: from the prefetched registers (lane turn mod 32
@@ -1749,8 +1766,9 @@ __device__ __forceinline__ void next_episode(const Params& p, int e, Env& r, con
 // Everything one launch does for env e: MODE_ROLLOUT runs p.steps steps with
 // the env's scalar state in registers and its map in shared memory. The
 // palette `pal` (this lane's words) is stored first when store_pal is set.
+// Returns false when the env's map copy was lost: the warp must stop.
 template <int MODE, int MAPK, int COLS, int GRAY>
-__device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, uint8_t* scratch, int lane,
+__device__ __forceinline__ bool run_env(const Params& p, int e, uint8_t* wbase, uint8_t* scratch, int lane,
                                         int& slot, const uint3& pal, bool store_pal) {
   const WarpSmem ws{wbase, fill_lane(p, lane)};
   const size_t frame_bytes = (size_t)3 * p.H * p.W;
@@ -1765,12 +1783,12 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
     render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes,
                                        col_k_pair(p, lane));
     __syncwarp();
-    return;
+    return true;
   }
   const Prefetch q = prefetch<MODE, MAPK>(p, e, lane);
   if (store_pal) store_palette(p, ws, pal, lane);
   Env r = q.r;
-  stage_prefetched<MAPK>(p, ws, e, q, lane);  // ends with __syncwarp
+  if (!stage_prefetched<MAPK>(p, ws, e, q, lane)) return false;  // ends with __syncwarp
   open_doors<MAPK>(p, e, r.keys, ws, lane);
   if (MODE == MODE_ROLLOUT) {
     int a_next = q.action;
@@ -1800,7 +1818,7 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
       st.flags[e] = (uint8_t)r.keys;
     }
     __syncwarp();
-    return;
+    return true;
   }
   float c, s;
   if (MODE == MODE_STEP) {
@@ -1817,6 +1835,7 @@ __device__ __forceinline__ void run_env(const Params& p, int e, uint8_t* wbase, 
   }
   render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes, q.k01);
   __syncwarp();
+  return true;
 }
 
 // A kernel's dynamic shared memory limit is a property of the function, shared

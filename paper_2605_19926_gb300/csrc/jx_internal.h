@@ -10,6 +10,7 @@
 namespace jx {
 
 constexpr int kMaxSprites = 16;
+constexpr int kBulkWaitRounds = 1 << 16;  // default try_wait polls before a bulk map copy counts as late
 constexpr int kMaxSide = 128;
 constexpr int kMaxH = 256;
 constexpr int kMaxW = 256;
@@ -111,6 +112,7 @@ struct Params {
   // per-warp shared memory layout (byte offsets from the warp's base; set by layout_warp_smem)
   int32_t off_gray, off_pal, off_map, off_col_rgb, off_col_top, off_col_bot, off_zbuf, off_spr_in, off_spr_a, off_spr_rect,
       off_spr_ty, off_spr_rgb, off_spr_kind, off_order, off_spr_span, off_obj, warp_bytes;
+  int32_t bulk_wait_rounds;  // try_wait polls before a bulk map copy counts as late (jx_debug_wait_limit)
   float move, radius, tan_half, inv_tan_half;
   float reward_lut[4];
   uint64_t seed;

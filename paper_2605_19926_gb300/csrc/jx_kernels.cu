@@ -19,7 +19,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   const int nw = gridDim.x * kWarpsPerBlock;
   uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;
   int slot = 0;
-  for (int e = gw; e < p.n; e += nw) run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, e == gw);
+  for (int e = gw; e < p.n; e += nw)
+    if (!run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, e == gw)) break;  // a copy was lost
   // shared memory stays allocated until the bulk stores have read it
   if (lane == 0) bulk_wait_read_all();
 }

@@ -226,6 +226,66 @@ def test_invalid_action_is_reported_and_ignored():
     assert (after["frac_x"] == b["frac_x"]).all() and (after["t"] == b["t"] + 1).all()
 
 
+def test_late_bulk_map_copy_is_reported_and_results_unchanged():
+    """Byte maps of 4 KB or more reach shared memory by one bulk copy whose
+    wait is bounded. With the first wait's limit at 0 every copy counts as
+    late: the kernel waits on (bounded) until the copy lands, records bit 2 of
+    the error word, and its steps and rollouts equal those of the default
+    limit, bit for bit. (A copy that never lands cannot be made on a healthy
+    device; its path skips the env and is not run here.)"""
+    from paper_2605_19926_gb300 import jx
+
+    cfg = inputs.rooms(n_envs=96, map_side=68, wall_prob=0.3, seed=31, max_sprites=4)  # 68 x 68 byte maps
+    a, b = Run(cfg), Run(cfg)
+    b.env.debug_wait_limit(0)
+    a.reset()
+    b.reset()
+    for s in range(10):
+        act = inputs.actions(31, s, cfg["n_envs"])
+        fa, ra, da = a.step(act)
+        fb, rb, db = b.step(act)
+        assert (fa == fb).all() and (ra == rb).all() and (da == db).all(), s
+    T, N = 6, cfg["n_envs"]
+    acts = torch.from_numpy(inputs.action_stream(32, T, N)).to(a.dev)
+    outs = []
+    for run in (a, b):
+        fr = torch.zeros((T, N, cfg["frame_h"], cfg["frame_w"], 3), dtype=torch.uint8, device=run.dev)
+        rw = torch.zeros((T, N), dtype=torch.float32, device=run.dev)
+        dn = torch.zeros((T, N), dtype=torch.uint8, device=run.dev)
+        run.env.rollout(acts, fr, rw, dn)
+        torch.cuda.synchronize()
+        outs.append((fr.cpu(), rw.cpu(), dn.cpu()))
+    assert all(torch.equal(x, y) for x, y in zip(*outs))
+    assert (a.env.get_state() == b.env.get_state()).all()
+    a.env.sync_status()
+    with pytest.raises(jx.JxError) as ei:
+        b.env.sync_status()
+    assert ei.value.status == jx.EDEVICE and "late" in str(ei.value)
+    b.env.sync_status()  # cleared
+    with pytest.raises(jx.JxError):
+        b.env.debug_wait_limit(-1)
+    # the batched kernel's late path: a batch over an env with the limit at 0
+    # steps like the env kernel, and its work queues stay usable
+    c, d = Run(cfg), Run(cfg)
+    c.env.debug_wait_limit(0)
+    c.reset()
+    d.reset()
+    t = jx.Tiling()
+    (t.warps_per_block, t.cols_per_lane, t.bits_min_side, t.max_rows_per_block, t.staging_buffers) = (2, 1, 0, 16, 1)
+    batch = jx.Batch([c.env], t)
+    bf = torch.zeros((N, cfg["frame_h"], cfg["frame_w"], 3), dtype=torch.uint8, device=c.dev)
+    for s in range(3):
+        act = inputs.actions(33, s, N)
+        c.actions.copy_(torch.from_numpy(act))
+        batch.step(c.actions, bf, c.rewards, c.dones)
+        fd, rd, dd = d.step(act)
+        torch.cuda.synchronize()
+        assert (bf.cpu().numpy() == fd).all() and (c.rewards.cpu().numpy() == rd).all(), s
+    with pytest.raises(jx.JxError):
+        c.env.sync_status()
+    batch.close()
+
+
 def test_step_host_matches_device_step():
     cfg = inputs.maze_keydoor(n_envs=50, map_side=16, seed=4, horizon=25)
     a, b = Run(cfg), Run(cfg)
