@@ -175,12 +175,17 @@ jx_status jx_destroy(jx_env* env);
 
 /* Start episode 0 of every environment: generate its map, spawn, heading and
  * sprites from (seed, env index, episode), then render the first frame of
- * each into d_frames ([N][H][W][3]). Asynchronous on `stream`. */
+ * each into d_frames ([N][H][W][3]). Asynchronous on `stream`.
+ * Paper: the environment interface's reset returning the first observation
+ * (Sec. 1, Sec. 3.1); key-door task layout (Table 1, Table 2). */
 jx_status jx_reset(jx_env* env, void* stream, uint8_t* d_frames);
 
 /* One environment step of all N environments, fused in one kernel:
  * action -> movement with wall collision -> key pickup / goal -> reward ->
  * episode end -> auto-reset of ended episodes (next episode's map) -> render.
+ * Paper: the step of the environment interface, batched over environments
+ * (Sec. 1, Sec. 3.1); keys, locked doors and the goal (Table 2); the render
+ * as in jx_render (Sec. 2.1, Fig. 1).
  *  d_actions [N] uint8 in 0..6 (see JX_ACT_*), read;
  *  d_frames  [N][H][W][3] uint8, written: the frame after the step (for an
  *            env whose episode ended, the first frame of its next episode);
@@ -191,8 +196,9 @@ jx_status jx_step(jx_env* env, void* stream, const uint8_t* d_actions, uint8_t* 
                   uint8_t* d_dones);
 
 /* `steps` consecutive calls of jx_step in one kernel launch, for action
- * streams known in advance (uniform random policies, replayed or scripted
- * actions): step t reads d_actions + t*N and writes d_frames + t*N*H*W*3,
+ * streams known in advance (uniform random policies, as the paper's speed
+ * measurements use, App. A.1; replayed or scripted actions): step t reads
+ * d_actions + t*N and writes d_frames + t*N*H*W*3,
  * d_rewards + t*N and d_dones + t*N. The results are identical to the
  * sequence of jx_step calls.
  *  d_actions [steps][N] uint8; d_frames [steps][N][H][W][3] uint8;
@@ -202,7 +208,11 @@ jx_status jx_step(jx_env* env, void* stream, const uint8_t* d_actions, uint8_t* 
 jx_status jx_rollout(jx_env* env, void* stream, const uint8_t* d_actions, int32_t steps, uint8_t* d_frames,
                      float* d_rewards, uint8_t* d_dones);
 
-/* Render the current state of all environments into d_frames (no state change). */
+/* Render the current state of all environments into d_frames (no state
+ * change): one DDA ray per screen column over the tile map (Sec. 2.1), a wall
+ * slice from the perpendicular hit distance shaded per face (Sec. 2.1),
+ * billboard sprites against the per-column depth buffer (Fig. 1), at the
+ * frame's native resolution (Sec. 3.1). */
 jx_status jx_render(jx_env* env, void* stream, uint8_t* d_frames);
 
 /* jx_step with host buffers: copies h_actions to the device, steps, copies
