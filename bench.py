@@ -815,7 +815,8 @@ def headline(g: Gpu, args) -> dict | None:
     e2e_s = time.perf_counter() - t0
     e2e_value = g.world * N * args.e2e_steps / e2e_s  # every rank runs the same count; host clock per rank
 
-    shape = env.launch_shape()
+    shape, chunk = env.rollout_shape(ring)  # the timed launches
+    step_shape = env.launch_shape()
     tiling = env.tiling
     graph.reset()
     env.close()
@@ -852,7 +853,8 @@ def headline(g: Gpu, args) -> dict | None:
                    "parallelism": f"replicas x{g.world}",
                    "l2": f"frames written to a {ring}-slot rollout buffer ({ring * N * H * W * 3 / 1e9:.2f} GB) > L2",
                    "launch": {"grid": shape.grid, "block": shape.block, "smem_bytes": shape.smem,
-                              "entry": "jx_rollout", "steps_per_launch": ring, "timed_launches": len(plan.launches),
+                              "entry": "jx_rollout", "steps_per_launch": ring, "handoff_chunk_steps": chunk,
+                              "timed_launches": len(plan.launches), "step_grid": step_shape.grid,
                               "tiling": tiling_dict(tiling), "autotune_trials": len(tuned) if tuned else 0}},
         "p50_step_ms": percentile(lat, 0.5), "p99_step_ms": percentile(lat, 0.99),
         "latency": {"how": "jx_step launched alone, host sync after each call, CUDA events around the launch",

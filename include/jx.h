@@ -204,7 +204,14 @@ jx_status jx_step(jx_env* env, void* stream, const uint8_t* d_actions, uint8_t* 
  *  d_actions [steps][N] uint8; d_frames [steps][N][H][W][3] uint8;
  *  d_rewards [steps][N] float32; d_dones [steps][N] uint8.
  * Each env's pose stays in registers and its map in shared memory across the
- * steps. Asynchronous on `stream`; allocates nothing. steps >= 1. */
+ * steps. Rollouts of 64 steps or more (envs without a grayscale stack) are cut
+ * into chunks of 12 steps that the launch's warps take in turn: a warp that
+ * finishes a chunk takes the next free one, of any env, and the chunk after
+ * it starts once its env's previous chunk has stored the state (a hand-off
+ * through device memory that a late partner cannot stall for more than a
+ * bounded wait; bit 2 of the device error word records one that ran out).
+ * Asynchronous on `stream`; allocates nothing. steps >= 1. Launches of one
+ * env must be ordered on one stream (they share its hand-off words). */
 jx_status jx_rollout(jx_env* env, void* stream, const uint8_t* d_actions, int32_t steps, uint8_t* d_frames,
                      float* d_rewards, uint8_t* d_dones);
 
@@ -303,7 +310,8 @@ jx_status jx_set_state(jx_env* env, const void* h_buf, size_t bytes);
 /* Wait for `stream`, then read and clear the device error word: JX_OK, or
  * JX_EDEVICE when a kernel recorded bad data since the last call (bit 0: an
  * action outside 0..6, taken as a no-op; bit 1: a bulk map copy completed
- * late or was lost, see jx_debug_wait_limit). */
+ * late or was lost, see jx_debug_wait_limit; bit 2: a rollout hand-off
+ * between warps ran out of its bounded wait, see jx_rollout). */
 jx_status jx_sync_status(jx_env* env, void* stream);
 
 /* Number of kernel launches this env has issued since creation. For maze
@@ -316,6 +324,13 @@ jx_status jx_launch_count(const jx_env* env, uint64_t* count);
 /* Launch shape of the fused step kernel: grid blocks, threads per block,
  * dynamic shared memory bytes per block. */
 jx_status jx_launch_shape(const jx_env* env, int32_t* grid, int32_t* block, int32_t* smem_bytes);
+
+/* Launch shape of a jx_rollout of `steps` steps: as jx_launch_shape, plus the
+ * steps per hand-off chunk (0: every warp runs whole envs). For an env routed
+ * through the batched kernel (jx_autotune), the batch's shape and chunk 0.
+ * JX_EINVAL for steps < 1. */
+jx_status jx_rollout_shape(const jx_env* env, int32_t steps, int32_t* grid, int32_t* block, int32_t* smem_bytes,
+                           int32_t* chunk);
 
 /* ------------------------------------------------------------------------
  * Batches: env groups of different map and frame sizes in one launch.

@@ -152,6 +152,23 @@ jx_status check_env(const jx_env* env) {
   return JX_OK;
 }
 
+// Steps per hand-off chunk of a rollout launch of the env kernel (0: each
+// warp runs whole envs). Measured on the 4096-env maze workload (10,000 steps
+// in 128-step launches): chunks of 12 steps on 5/8 of the resident warps run
+// at 9.10-9.16 us per step against 9.44-9.46 us for whole envs on all of
+// them (the warps of an SM are served unequally, and the hand-off lets the
+// faster ones take more chunks; with fewer warps than envs a warp always finds
+// an item whose env is free). Rollouts of 20 steps lose more to the hand-off
+// latency than they gain. Envs with a grayscale stack run whole: their planes
+// are written by bulk copies four steps apart, which two warps could reorder.
+int rollout_chunk(const jx_env* env, int steps) {
+  if (env->cfg.gray_stack || steps < jx::kHandoffMinSteps) return 0;
+  int chunk = jx::kHandoffChunk;
+  const int64_t n = env->cfg.n_envs;
+  while (n * ((steps + chunk - 1) / chunk) >= (int64_t)1 << 31) chunk *= 2;  // item numbers stay below 2^31
+  return chunk < steps ? chunk : steps;
+}
+
 jx_status run(jx_env* env, const jx::Params& p, int mode, void* stream) {
   DeviceGuard g(env->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
@@ -161,8 +178,13 @@ jx_status run(jx_env* env, const jx::Params& p, int mode, void* stream) {
     if (err != cudaSuccess) return cuda_fail(err, "pre-generation launch");
     env->launches.fetch_add(jx::kPregenKernels, std::memory_order_relaxed);
   }
-  cudaError_t err = jx::launch(p, mode, env->grid, s);
-  if (err != cudaSuccess) return cuda_fail(err, "kernel launch");
+  cudaError_t err = jx::launch(p, mode, mode == jx::MODE_ROLLOUT && p.chunk > 0 ? env->grid_handoff : env->grid, s);
+  if (err != cudaSuccess) {
+    // a failed rollout launch may leave the hand-off words set (the kernel
+    // zeroes them as it ends): clear them on the same stream
+    if (mode == jx::MODE_ROLLOUT && p.chunk > 0) (void)cudaMemsetAsync(p.work, 0, env->work_bytes, s);
+    return cuda_fail(err, "kernel launch");
+  }
   env->launches.fetch_add(1, std::memory_order_relaxed);
   return JX_OK;
 }
@@ -282,12 +304,14 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
 
   const jx_config& c = *cfg;
   const int W = c.frame_w, tpr = c.turns_per_rev;
-  // aux block: error word | turn table | column table | ASCII map and candidates
+  // aux block: error word | turn table | column table | ASCII map and
+  // candidates | rollout hand-off words (zero between launches)
   const size_t aux_err = 0, aux_turn = 256, aux_col = align256(aux_turn + 8 * (size_t)tpr);
   const size_t aux_tmpl = align256(aux_col + 4 * (size_t)W);
   const size_t n_cand = am ? am->spawn.size() + am->goal.size() + am->keys.size() : 0;
   const size_t aux_cand = align256(aux_tmpl + (am ? am->cells.size() : 0));
-  const size_t aux_bytes = align256(aux_cand + 4 * n_cand);
+  const size_t aux_work = align256(aux_cand + 4 * n_cand);
+  const size_t aux_bytes = align256(aux_work + 4 * (2 + (size_t)c.n_envs));
 
   jx::Params& p = env->base;
   p.n = c.n_envs;
@@ -366,6 +390,12 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
   const long need = (c.n_envs + jx::kWarpsPerBlock - 1) / jx::kWarpsPerBlock;
   const long cap = (long)bps * env->num_sms;
   env->grid = (int)(need < cap ? need : cap);
+  {
+    // hand-off rollouts: 5/8 of the resident warps, and at most 5 warps per 8 envs
+    const long by_sm = cap * 5 / 8, by_envs = ((long)c.n_envs * 5 / 8 + jx::kWarpsPerBlock - 1) / jx::kWarpsPerBlock;
+    env->grid_handoff = (int)(by_sm < by_envs ? by_sm : by_envs);
+    if (env->grid_handoff < 1) env->grid_handoff = 1;
+  }
   // maze work space: one slot per warp of the grid
   p.gen_scratch_stride = jx::gen_scratch_bytes(c.task, c.map_side);
   const size_t scratch_bytes = p.gen_scratch_stride * (size_t)env->grid * jx::kWarpsPerBlock;
@@ -457,6 +487,8 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
   p.err = reinterpret_cast<uint32_t*>(env->aux + aux_err);
   p.turn_cs = reinterpret_cast<const float2*>(env->aux + aux_turn);
   p.col_k = reinterpret_cast<const float*>(env->aux + aux_col);
+  p.work = reinterpret_cast<uint32_t*>(env->aux + aux_work);
+  env->work_bytes = 4 * (2 + (size_t)c.n_envs);
   if (am) {
     p.tmpl = env->aux + aux_tmpl;
     p.cand = reinterpret_cast<const int32_t*>(env->aux + aux_cand);
@@ -628,6 +660,7 @@ jx_status jx_rollout(jx_env* env, void* stream, const uint8_t* d_actions, int32_
   p.rewards = d_rewards;
   p.dones = d_dones;
   p.steps = steps;
+  p.chunk = rollout_chunk(env, steps);
   return run(env, p, jx::MODE_ROLLOUT, stream);
 }
 
@@ -956,6 +989,22 @@ jx_status jx_launch_shape(const jx_env* env, int32_t* grid, int32_t* block, int3
   if (grid) *grid = env->grid;
   if (block) *block = jx::kThreads;
   if (smem_bytes) *smem_bytes = env->smem_block;
+  return JX_OK;
+}
+
+jx_status jx_rollout_shape(const jx_env* env, int32_t steps, int32_t* grid, int32_t* block, int32_t* smem_bytes,
+                           int32_t* chunk) {
+  if (jx_status st = check_env(env)) return st;
+  if (steps < 1) return fail(JX_EINVAL, "steps must be >= 1 (got %d)", steps);
+  if (env->use_batch) {
+    if (chunk) *chunk = 0;
+    return jx_batch_launch_shape(env->tuned, grid, block, smem_bytes);
+  }
+  const int c = rollout_chunk(env, steps);
+  if (grid) *grid = c > 0 ? env->grid_handoff : env->grid;
+  if (block) *block = jx::kThreads;
+  if (smem_bytes) *smem_bytes = env->smem_block;
+  if (chunk) *chunk = c;
   return JX_OK;
 }
 

@@ -43,10 +43,11 @@ __global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
     while (ticket < (uint32_t)p.n) {
       uint32_t next = 0;
       if (lane == 0) next = atomicAdd(bp.queue + g, 1u);
+      const int e = (int)ticket;
       if (SPEC == 1)
-        lost = !run_env<MODE, MAP_BITS, COLS, 0>(p, (int)ticket, wbase, scratch, lane, slot, no_palette, false);
+        lost = !run_env<MODE, MAP_BITS, COLS, 0>(p, e, wbase, scratch, lane, slot, no_palette, false, 0, p.steps);
       else
-        lost = !run_env<MODE, MAP_RUNTIME, COLS, 2>(p, (int)ticket, wbase, scratch, lane, slot, no_palette, false);
+        lost = !run_env<MODE, MAP_RUNTIME, COLS, 2>(p, e, wbase, scratch, lane, slot, no_palette, false, 0, p.steps);
       if (lost) break;  // the counters are still cleared below: every warp reaches the end
       ticket = __shfl_sync(0xffffffffu, next, 0);
     }

@@ -1677,7 +1677,7 @@ __device__ __forceinline__ bool small_map(const Params& p) {
 }
 
 template <int MODE, int MAPK>
-__device__ __forceinline__ Prefetch prefetch(const Params& p, int e, int lane) {
+__device__ __forceinline__ Prefetch prefetch(const Params& p, int e, int t0, int lane) {
   Prefetch q;
   const State& st = p.st;
   q.r = load_env(p, e);
@@ -1701,7 +1701,7 @@ __device__ __forceinline__ Prefetch prefetch(const Params& p, int e, int lane) {
       if (lane + 32 < (n >> 4)) q.m1 = g[lane + 32];
     }
   }
-  q.action = (MODE == MODE_STEP || MODE == MODE_ROLLOUT) ? (int)p.actions[e] : 0;
+  q.action = (MODE == MODE_STEP || MODE == MODE_ROLLOUT) ? (int)p.actions[(size_t)t0 * p.out_stride + e] : 0;
   q.k01 = col_k_pair(p, lane);
   q.tc0 = q.tc1 = q.tc2 = make_float2(0.f, 0.f);
   if (MODE == MODE_STEP && p.tpr <= 96) {
@@ -1763,13 +1763,14 @@ __device__ __forceinline__ void next_episode(const Params& p, int e, Env& r, con
   heading(p, r, c, s);
 }
 
-// Everything one launch does for env e: MODE_ROLLOUT runs p.steps steps with
-// the env's scalar state in registers and its map in shared memory. The
-// palette `pal` (this lane's words) is stored first when store_pal is set.
+// Everything one launch does for env e: MODE_ROLLOUT runs the launch's steps
+// t0 .. t1 - 1 with the env's scalar state in registers and its map in shared
+// memory (the state is loaded before step t0 and stored after step t1 - 1).
+// The palette `pal` (this lane's words) is stored first when store_pal is set.
 // Returns false when the env's map copy was lost: the warp must stop.
 template <int MODE, int MAPK, int COLS, int GRAY>
 __device__ __forceinline__ bool run_env(const Params& p, int e, uint8_t* wbase, uint8_t* scratch, int lane,
-                                        int& slot, const uint3& pal, bool store_pal) {
+                                        int& slot, const uint3& pal, bool store_pal, int t0 = 0, int t1 = 0) {
   const WarpSmem ws{wbase, fill_lane(p, lane)};
   const size_t frame_bytes = (size_t)3 * p.H * p.W;
   if (MODE == MODE_RESET) {
@@ -1785,16 +1786,16 @@ __device__ __forceinline__ bool run_env(const Params& p, int e, uint8_t* wbase, 
     __syncwarp();
     return true;
   }
-  const Prefetch q = prefetch<MODE, MAPK>(p, e, lane);
+  const Prefetch q = prefetch<MODE, MAPK>(p, e, t0, lane);
   if (store_pal) store_palette(p, ws, pal, lane);
   Env r = q.r;
   if (!stage_prefetched<MAPK>(p, ws, e, q, lane)) return false;  // ends with __syncwarp
   open_doors<MAPK>(p, e, r.keys, ws, lane);
   if (MODE == MODE_ROLLOUT) {
     int a_next = q.action;
-    for (int t = 0; t < p.steps; ++t) {
+    for (int t = t0; t < t1; ++t) {
       int a = a_next;
-      if (t + 1 < p.steps) a_next = p.actions[(size_t)(t + 1) * p.out_stride + e];
+      if (t + 1 < t1) a_next = p.actions[(size_t)(t + 1) * p.out_stride + e];
       const size_t out = (size_t)t * p.out_stride + e;
       const int keys0 = r.keys;
       a = turn_for(p, r, a, lane);

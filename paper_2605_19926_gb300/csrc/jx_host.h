@@ -16,6 +16,7 @@ struct jx_env {
   int num_sms = 0;
   int blocks_per_sm = 0;
   int grid = 0;
+  int grid_handoff = 0;  // blocks of a rollout launch in hand-off chunks (see rollout_chunk)
   int smem_block = 0;
   jx::Params base{};
   // one device block: state | aux | scratch (owned, or in the caller's memory)
@@ -27,8 +28,9 @@ struct jx_env {
   size_t state_bytes = 0;
   size_t field_off[JX_F_COUNT] = {};
   size_t field_size[JX_F_COUNT] = {};
-  // device error word, turn table, column table
+  // device error word, turn table, column table, rollout hand-off words
   uint8_t* aux = nullptr;
+  size_t work_bytes = 0;
   // maze generation work space, one slot per resident warp
   uint8_t* scratch = nullptr;
   // next-episode block and work slots of the lane-parallel pre-generation

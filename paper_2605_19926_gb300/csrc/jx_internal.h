@@ -18,6 +18,9 @@ constexpr int kWarpsPerBlock = 2;  // envs in flight per block of the env kernel
 constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kMaxStaging = 2;  // frame row-block staging buffers per warp: 1 or 2
 constexpr int kMinBlocksPerSm = 28;  // register budget: 28 warps resident per SM
+constexpr int kHandoffPolls = 1 << 22;  // polls (about 0.25 us apart) before a rollout hand-off counts as late
+constexpr int kHandoffMinSteps = 64;    // rollouts of at least this many steps run in hand-off chunks
+constexpr int kHandoffChunk = 12;       // steps per hand-off chunk
 
 enum Mode { MODE_STEP = 0, MODE_RESET = 1, MODE_RENDER = 2, MODE_RAYS = 3, MODE_ROLLOUT = 4 };
 
@@ -94,6 +97,15 @@ struct Params {
   float* dbg_perp;
   int32_t n, S, H, W, K, horizon, tpr, task;
   int32_t steps;  // steps of one rollout launch (actions / outputs are [steps][out_stride][...])
+  // Rollout hand-off (env kernel, MODE_ROLLOUT, chunk > 0): the launch's steps
+  // are cut into chunks of `chunk` steps, and warps take (env, chunk) items in
+  // chunk-major order from the counter work[0]; chunk k of env e starts once
+  // work[2 + e] == k, which the warp that ran chunk k - 1 stores (0 after the
+  // last chunk). work[1] counts the warps that finished; the last one zeroes
+  // work[0] and work[1]. chunk == 0: each warp runs whole envs (e = warp,
+  // warp + warps, ...).
+  uint32_t* work;
+  int32_t chunk;
   int32_t out_stride;  // envs per step in the action / reward / done arrays (n, or a batch's total)
   size_t frame_step;   // bytes per step in the frame array (n frames, or a batch's total)
   int32_t map_bits;    // the map is staged as a bit plane (see MapKind)

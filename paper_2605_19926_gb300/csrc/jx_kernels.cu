@@ -6,21 +6,100 @@
 namespace jx {
 namespace {
 
+// ---- rollout hand-off (Params::work): a rollout launch's steps in chunks,
+// (env, chunk) items handed out in chunk-major order, so that every warp
+// stays busy until the launch's last items: warps of one SM are served
+// unequally by the schedulers, and an env bound to a warp for all its steps
+// would leave the launch waiting on the slowest warps.
+
+__device__ __forceinline__ uint32_t take_item(const Params& p, int lane) {
+  uint32_t v = 0;
+  if (lane == 0) v = atomicAdd(p.work, 1u);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// Waits until chunk k - 1 of env e is published (work[2 + e] == k). The
+// warp that holds it is running: it took the item before this warp took a
+// later one, and waits only on earlier items itself. False after
+// kHandoffPolls polls.
+__device__ __forceinline__ bool await_chunk(const Params& p, int e, uint32_t k) {
+  const uint32_t* f = p.work + 2 + e;
+  for (int i = 0; i < kHandoffPolls; ++i) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    if (__all_sync(0xffffffffu, v == k)) return true;
+    __nanosleep(200);
+  }
+  return false;
+}
+
+// Publishes a finished chunk of env e: every lane's stores of the state (and
+// of a new episode's map, objects and sprites) are visible before the flag.
+__device__ __forceinline__ void publish_chunk(const Params& p, int e, uint32_t v, int lane) {
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p.work + 2 + e), "r"(v) : "memory");
+}
+
+// Launched as a programmatic dependent of the kernel before it on the stream
+// (see launch_mode): a launch may be scheduled while the one before it
+// drains, and runs its prologue (the constant palette, the warp header in
+// shared memory) meanwhile. griddepcontrol.wait then holds it until every
+// earlier kernel on the stream has completed and its writes are visible;
+// nothing before the wait reads memory that a kernel writes, or writes global
+// memory. The single-step modes release their dependents at once (a step is
+// one wave of blocks, so the next step's blocks take the slots the first
+// finished ones leave); the long modes release them as their warps finish,
+// so that no waiting block holds a slot through a rollout. Without the launch
+// attribute these instructions do nothing.
 template <int MODE, int MAPK, int GRAY>
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
     env_kernel(const __grid_constant__ Params p) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
+  constexpr bool kEarlyRelease = MODE == MODE_STEP || MODE == MODE_RENDER || MODE == MODE_RAYS;
+  if (kEarlyRelease) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* const wbase = smem_raw + warp * p.warp_bytes;
   const uint3 pal = load_palette(lane);  // stored with the first env's prefetched state
   // the header's mbarrier serves only bulk copies of byte maps of 4 KB or more
   if (!p.map_bits && p.S * p.S >= 4096) init_warp_header(wbase, lane);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
   uint8_t* scratch = p.gen_scratch ? p.gen_scratch + (size_t)gw * p.gen_scratch_stride : nullptr;
   int slot = 0;
+  if (MODE == MODE_ROLLOUT && p.chunk > 0) {
+    const uint32_t nch = (uint32_t)((p.steps + p.chunk - 1) / p.chunk);
+    const uint32_t items = (uint32_t)p.n * nch;  // below 2^31 (the host caps it)
+    bool first = true, lost = false;
+    for (uint32_t item = take_item(p, lane); item < items;) {
+      const uint32_t next = take_item(p, lane);  // its latency overlaps this item
+      const int e = (int)(item % (uint32_t)p.n);
+      const uint32_t k = item / (uint32_t)p.n;
+      if (k > 0 && !await_chunk(p, e, k) && lane == 0) atomicOr(p.err, 4u);
+      const int t0 = (int)k * p.chunk, t1 = t0 + p.chunk < p.steps ? t0 + p.chunk : p.steps;
+      // after a lost map copy the warp only passes its items on (their envs
+      // keep their state; the error word says so) and never touches the ring
+      if (!lost) lost = !run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, first, t0, t1);
+      first = false;
+      publish_chunk(p, e, k + 1 == nch ? 0u : k + 1, lane);
+      item = next;
+    }
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (lane == 0) {
+      bulk_wait_read_all();
+      __threadfence();
+      if (atomicAdd(p.work + 1, 1u) == (uint32_t)nw - 1) {
+        atomicExch(p.work, 0u);
+        atomicExch(p.work + 1, 0u);
+      }
+    }
+    return;
+  }
   for (int e = gw; e < p.n; e += nw)
-    if (!run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, e == gw)) break;  // a copy was lost
+    if (!run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, e == gw, 0, p.steps))
+      break;  // a copy was lost
+  if (!kEarlyRelease) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // shared memory stays allocated until the bulk stores have read it
   if (lane == 0) bulk_wait_read_all();
 }
@@ -87,9 +166,22 @@ cudaError_t blocks_per_sm_mode(const Params& p, int* blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kThreads, block_smem_bytes(p));
 }
 
+// Programmatic stream serialisation: the launch may overlap the tail of the
+// kernel before it on the stream up to its griddepcontrol.wait (consecutive
+// steps in a CUDA graph then start without a launch gap).
 template <int MODE>
-void launch_mode(const Params& p, int grid, cudaStream_t stream) {
-  env_kernel_of<MODE>(p)<<<grid, kThreads, block_smem_bytes(p), stream>>>(p);
+cudaError_t launch_mode(const Params& p, int grid, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = (size_t)block_smem_bytes(p);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, env_kernel_of<MODE>(p), p);
 }
 }  // namespace
 
@@ -162,12 +254,11 @@ cudaError_t kernel_blocks_per_sm(const Params& p, int mode, int* blocks) {
 
 cudaError_t launch(const Params& p, int mode, int grid, cudaStream_t stream) {
   switch (mode) {
-    case MODE_STEP: launch_mode<MODE_STEP>(p, grid, stream); break;
-    case MODE_RESET: launch_mode<MODE_RESET>(p, grid, stream); break;
-    case MODE_RENDER: launch_mode<MODE_RENDER>(p, grid, stream); break;
-    case MODE_ROLLOUT: launch_mode<MODE_ROLLOUT>(p, grid, stream); break;
-    default: launch_mode<MODE_RAYS>(p, grid, stream); break;
+    case MODE_STEP: return launch_mode<MODE_STEP>(p, grid, stream);
+    case MODE_RESET: return launch_mode<MODE_RESET>(p, grid, stream);
+    case MODE_RENDER: return launch_mode<MODE_RENDER>(p, grid, stream);
+    case MODE_ROLLOUT: return launch_mode<MODE_ROLLOUT>(p, grid, stream);
+    default: return launch_mode<MODE_RAYS>(p, grid, stream);
   }
-  return cudaGetLastError();
 }
 }  // namespace jx

@@ -36,6 +36,7 @@ SYMBOLS = [
     "jx_create", "jx_create_ascii", "jx_destroy", "jx_reset", "jx_step", "jx_rollout", "jx_render", "jx_step_host",
     "jx_step_host_static", "jx_debug_rays", "jx_debug_wait_limit",
     "jx_state_bytes", "jx_state_field", "jx_get_state", "jx_set_state", "jx_sync_status", "jx_launch_count",
+    "jx_rollout_shape",
     "jx_launch_shape", "jx_last_error",
     "jx_tiling_default", "jx_batch_create", "jx_batch_destroy", "jx_batch_info", "jx_batch_group",
     "jx_batch_set_tiling", "jx_batch_get_tiling", "jx_batch_launch_shape", "jx_batch_launch_count",
@@ -127,6 +128,7 @@ def _load() -> ctypes.CDLL:
         "jx_sync_status": [P, P],
         "jx_launch_count": [P, P],
         "jx_launch_shape": [P, P, P, P],
+        "jx_rollout_shape": [P, i32, P, P, P, P],
         "jx_tiling_default": [P],
         "jx_batch_create": [P, i32, P, P],
         "jx_batch_destroy": [P],
@@ -337,6 +339,13 @@ class Env:
         g, b, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         _check(lib.jx_launch_shape(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(s)))
         return Shape(g.value, b.value, s.value)
+
+    def rollout_shape(self, steps: int) -> tuple[Shape, int]:
+        """Launch shape of a jx_rollout of `steps` steps and its steps per hand-off chunk."""
+        g, b, s, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib.jx_rollout_shape(self._h, steps, ctypes.byref(g), ctypes.byref(b), ctypes.byref(s),
+                                    ctypes.byref(c)))
+        return Shape(g.value, b.value, s.value), c.value
 
     def autotune(self, mode: int = 1, steps: int = 8, max_trials: int = 1000, stream=None):
         """Time the env's own kernel (trial 0) against the batched kernel's tilings; keep

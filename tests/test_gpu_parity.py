@@ -365,6 +365,38 @@ def test_rollout_matches_step_sequence(name, T):
         assert n_done > 0
 
 
+@pytest.mark.parametrize("name,T", [("maze32_ragged", 90), ("maze6_events", 150), ("ascii_coloured_rooms_shaded", 64),
+                                    ("rooms16_sprites_40x48", 77)])
+def test_handoff_rollout_equals_whole_env_launches(name, T):
+    """A rollout of 64 or more steps runs in hand-off chunks of 12 steps that
+    move between warps; shorter rollouts run each env on one warp. One chunked
+    launch of T steps must equal launches of at most 32 steps covering the
+    same steps, bit for bit, and leave the device error word clear."""
+    cfg = CASES[name]
+    N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
+    a, b = Run(cfg), Run(cfg)
+    shape, chunk = b.env.rollout_shape(T)
+    assert chunk == 12 and shape.grid <= b.env.launch_shape().grid
+    assert a.env.rollout_shape(32)[1] == 0
+    a.reset()
+    b.reset()
+    acts = torch.from_numpy(inputs.action_stream(29, T, N)).to(a.dev)
+    out = []
+    for run, parts in ((b, [(0, T)]), (a, [(s, min(32, T - s)) for s in range(0, T, 32)])):
+        frames = torch.zeros((T, N, H, W, 3), dtype=torch.uint8, device=run.dev)
+        rewards = torch.zeros((T, N), dtype=torch.float32, device=run.dev)
+        dones = torch.zeros((T, N), dtype=torch.uint8, device=run.dev)
+        for s, n in parts:
+            run.env.rollout(acts[s:s + n], frames[s:s + n], rewards[s:s + n], dones[s:s + n])
+        torch.cuda.synchronize()
+        out.append((frames, rewards, dones))
+    (fb, rb, db), (fa, ra, da) = out
+    assert torch.equal(fa, fb) and torch.equal(ra, rb) and torch.equal(da, db)
+    assert (a.env.get_state() == b.env.get_state()).all()
+    b.env.sync_status()
+    a.env.sync_status()
+
+
 def test_rollout_full_size_across_horizon():
     """4096 envs, 32 x 32 key-door mazes, in the benchmark's launch shape: a
     64-step rollout that crosses the 500-step horizon (every env resets)."""
