@@ -52,6 +52,20 @@ __device__ __forceinline__ void publish_chunk(const Params& p, int e, uint32_t v
 // finished ones leave); the long modes release them as their warps finish,
 // so that no waiting block holds a slot through a rollout. Without the launch
 // attribute these instructions do nothing.
+// The end of a launch that hands out work from Params::work: the warp's bulk
+// stores have read its shared memory, and the last warp to get here zeroes
+// the counters for the next launch.
+__device__ __forceinline__ void finish_items(const Params& p, int nw, int lane) {
+  if (lane == 0) {
+    bulk_wait_read_all();
+    __threadfence();
+    if (atomicAdd(p.work + 1, 1u) == (uint32_t)nw - 1) {
+      atomicExch(p.work, 0u);
+      atomicExch(p.work + 1, 0u);
+    }
+  }
+}
+
 template <int MODE, int MAPK, int GRAY>
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
     env_kernel(const __grid_constant__ Params p) {
@@ -86,14 +100,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
       item = next;
     }
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    if (lane == 0) {
-      bulk_wait_read_all();
-      __threadfence();
-      if (atomicAdd(p.work + 1, 1u) == (uint32_t)nw - 1) {
-        atomicExch(p.work, 0u);
-        atomicExch(p.work + 1, 0u);
-      }
-    }
+    finish_items(p, nw, lane);
     return;
   }
   for (int e = gw; e < p.n; e += nw)
