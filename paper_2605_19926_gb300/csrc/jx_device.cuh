@@ -1276,17 +1276,41 @@ __device__ __forceinline__ void ray_advance(const Params& p, Ray& q, const uint8
   q.done = out || cell_set<MAPK>(p, smap, q.my * S + q.mx);
 }
 
-// Slice of a finished ray: perp, rows and colour into the column arrays.
-template <int MODE, int MAPK>
-__device__ __forceinline__ void finish_column(const Params& p, int e, const Ray& q, int col, const WarpSmem& ws) {
-  const int S = p.S, H = p.H;
+// A finished ray's hit: perpendicular distance, face, and the hit cell's
+// value. With bit-plane maps the value is a load from the state block; it is
+// issued here and first used by finish_column, after the next pass's DDA, so
+// that its latency overlaps that loop.
+struct Hit {
   float perp;
+  int side, v, col, mx, my;
+};
+
+template <int MAPK>
+__device__ __forceinline__ Hit hit_of(const Params& p, int e, const Ray& q, int col, const WarpSmem& ws) {
+  const int S = p.S;
+  Hit h;
   if (q.side == 0)
-    perp = __fdividef((q.kx - 1.f) + q.gx, q.ax);
+    h.perp = __fdividef((q.kx - 1.f) + q.gx, q.ax);
   else if (q.side == 1)
-    perp = __fdividef((q.ky - 1.f) + q.gy, q.ay);
+    h.perp = __fdividef((q.ky - 1.f) + q.gy, q.ay);
   else
-    perp = __int_as_float(0x7f800000);  // no hit
+    h.perp = __int_as_float(0x7f800000);  // no hit
+  h.side = q.side;
+  h.col = col;
+  h.mx = q.mx;
+  h.my = q.my;
+  h.v = 1;
+  const bool inside = (unsigned)q.mx < (unsigned)S && (unsigned)q.my < (unsigned)S;
+  if (q.side >= 0 && inside)
+    h.v = map_bits<MAPK>(p) ? p.st.map[(size_t)e * S * S + q.my * S + q.mx] : ws.map(p)[q.my * S + q.mx];
+  return h;
+}
+
+// Slice of a hit: rows and colour into the column arrays.
+template <int MODE>
+__device__ __forceinline__ void finish_column(const Params& p, int e, const Hit& q, const WarpSmem& ws) {
+  const int H = p.H, col = q.col;
+  const float perp = q.perp;
   // h = floor(H / perp + 1/2), clamped; top = floor((H - h) / 2)
   int h;
   if (perp > 0.f) {
@@ -1297,10 +1321,7 @@ __device__ __forceinline__ void finish_column(const Params& p, int e, const Ray&
   }
   const int top = (H - h) >> 1;  // arithmetic shift: floor division by 2
   const int bot = top + h;
-  int v = 1;
-  const bool inside = (unsigned)q.mx < (unsigned)S && (unsigned)q.my < (unsigned)S;
-  if (q.side >= 0 && inside)
-    v = map_bits<MAPK>(p) ? p.st.map[(size_t)e * S * S + q.my * S + q.mx] : ws.map(p)[q.my * S + q.mx];
+  const int v = q.v;
   const int slot = col_slot(col, p.W >> 4);
   uint32_t colour = ws.pal(p)[(q.side == 1 ? kCellColours : 0) + (v < kCellColours ? v : 1)];
   if (p.shading) {  // distance shading: channels scaled by q / 256, q = 64 + 192 min(h, H) / H
@@ -1336,6 +1357,11 @@ __device__ __forceinline__ void cast_columns(const Params& p, int e, const Env& 
   const int W = p.W, S = p.S;
   const uint8_t* smap = ws.map(p);
   const int max_it = 4 * S + 8;
+  // single steps (latency-bound) finish a lane's hit after its next ray;
+  // the other modes at once (a rollout keeps more state live across the loop)
+  constexpr bool kDefer = MODE == MODE_STEP;
+  Hit last;  // the lane's previous hit, finished after the next one is found
+  bool pending = false;
   for (int col0 = lane; col0 - lane < W; col0 += 32 * COLS) {
     Ray q[COLS];
 #pragma unroll
@@ -1357,8 +1383,18 @@ __device__ __forceinline__ void cast_columns(const Params& p, int e, const Env& 
     }
 #pragma unroll
     for (int j = 0; j < COLS; ++j)
-      if (col0 + 32 * j < W) finish_column<MODE, MAPK>(p, e, q[j], col0 + 32 * j, ws);
+      if (col0 + 32 * j < W) {
+        const Hit h = hit_of<MAPK>(p, e, q[j], col0 + 32 * j, ws);
+        if (!kDefer) {
+          finish_column<MODE>(p, e, h, ws);
+          continue;
+        }
+        if (pending) finish_column<MODE>(p, e, last, ws);
+        last = h;
+        pending = true;
+      }
   }
+  if (kDefer && pending) finish_column<MODE>(p, e, last, ws);
   __syncwarp();
 }
 
@@ -1422,12 +1458,13 @@ __device__ __forceinline__ int project_sprites(const Params& p, const Env& r, fl
   }
   if (vmask == 0u) return 0;
   vis = (vmask >> lane) & 1u;
-  int rank = 0;
-  for (int k = 0; k < nspr; ++k) {
-    const float tk = __shfl_sync(0xffffffffu, ty, k);
-    const bool vk = (vmask >> k) & 1;
-    if (vis && vk && (tk > ty || (tk == ty && k > lane))) ++rank;
-  }
+  int rank = 0;  // visible sprites farther than this one (or as far, of higher index)
+  if (vmask & (vmask - 1u))
+    for (uint32_t m = vmask; m != 0u; m &= m - 1u) {
+      const int k = __ffs(m) - 1;
+      const float tk = __shfl_sync(0xffffffffu, ty, k);
+      if (vis && (tk > ty || (tk == ty && k > lane))) ++rank;
+    }
   if (vis) ws.order(p)[rank] = lane;
   __syncwarp();
   return __popc(vmask);
@@ -1790,7 +1827,7 @@ __device__ __forceinline__ bool run_env(const Params& p, int e, uint8_t* wbase, 
   if (store_pal) store_palette(p, ws, pal, lane);
   Env r = q.r;
   if (!stage_prefetched<MAPK>(p, ws, e, q, lane)) return false;  // ends with __syncwarp
-  open_doors<MAPK>(p, e, r.keys, ws, lane);
+  if (r.keys != 0) open_doors<MAPK>(p, e, r.keys, ws, lane);
   if (MODE == MODE_ROLLOUT) {
     int a_next = q.action;
     for (int t = t0; t < t1; ++t) {

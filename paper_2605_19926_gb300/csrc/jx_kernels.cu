@@ -74,9 +74,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   if (kEarlyRelease) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint8_t* const wbase = smem_raw + warp * p.warp_bytes;
-  const uint3 pal = load_palette(lane);  // stored with the first env's prefetched state
+  write_palette(p, WarpSmem{wbase, FillLane{}}, lane);  // a constant table: before the wait
   // the header's mbarrier serves only bulk copies of byte maps of 4 KB or more
   if (!p.map_bits && p.S * p.S >= 4096) init_warp_header(wbase, lane);
+  const uint3 pal = make_uint3(0u, 0u, 0u);  // stored above, not per env
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   if (MODE == MODE_ROLLOUT && p.chunk > 0) {
     const uint32_t nch = (uint32_t)((p.steps + p.chunk - 1) / p.chunk);
     const uint32_t items = (uint32_t)p.n * nch;  // below 2^31 (the host caps it)
-    bool first = true, lost = false;
+    bool lost = false;
     for (uint32_t item = take_item(p, lane); item < items;) {
       const uint32_t next = take_item(p, lane);  // its latency overlaps this item
       const int e = (int)(item % (uint32_t)p.n);
@@ -94,8 +95,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
       const int t0 = (int)k * p.chunk, t1 = t0 + p.chunk < p.steps ? t0 + p.chunk : p.steps;
       // after a lost map copy the warp only passes its items on (their envs
       // keep their state; the error word says so) and never touches the ring
-      if (!lost) lost = !run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, first, t0, t1);
-      first = false;
+      if (!lost) lost = !run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, false, t0, t1);
       publish_chunk(p, e, k + 1 == nch ? 0u : k + 1, lane);
       item = next;
     }
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
     return;
   }
   for (int e = gw; e < p.n; e += nw)
-    if (!run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, e == gw, 0, p.steps))
+    if (!run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, false, 0, p.steps))
       break;  // a copy was lost
   if (!kEarlyRelease) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // shared memory stays allocated until the bulk stores have read it
