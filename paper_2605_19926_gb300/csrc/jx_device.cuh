@@ -760,14 +760,16 @@ __device__ void gen_maze_lane(const Params& p, int e, uint32_t ep, uint8_t* work
   mark(v);
   int sp = 1, pushes = 0;  // stack size: the current node's depth is sp - 1
   uint32_t carved = 0;
-  // the walk's draws (high 32 bits), computed eight at a time ahead of use
-  uint32_t draws[8];
-#pragma unroll
-  for (int h = 0; h < 8; ++h) draws[h] = (uint32_t)(draw_at(kd, (uint32_t)h) >> 32);
   disc[v] = (uint16_t)pushes++;
   int best_v = start, best_d = 0;
   for (int it = 0; it < 2 * n - 1; ++it) {
     __syncwarp(warp_mask);
+    // the draw a carve in this iteration takes (its high 32 bits), computed by
+    // every lane of the warp together whether it carves or backtracks: lanes
+    // carve at different iterations, and a draw computed only where it is
+    // used would run once for every different set of carving lanes
+    uint32_t hi = (uint32_t)(draw_at(kd, carved) >> 32);
+    asm volatile("" : "+r"(hi));  // keeps the draw ahead of the branch
     const uint32_t open = (uint32_t)(vy > 1 && !seen(v - nn)) | ((uint32_t)(vx < S - 3 && !seen(v + 1)) << 1) |
                           ((uint32_t)(vy < S - 3 && !seen(v + nn)) << 2) | ((uint32_t)(vx > 1 && !seen(v - 1)) << 3);
     if (open == 0) {
@@ -780,17 +782,12 @@ __device__ void gen_maze_lane(const Params& p, int e, uint32_t ep, uint8_t* work
       continue;
     }
     // the r-th unvisited neighbour in N, E, S, W order
-    uint32_t hi = draws[0];
-#pragma unroll
-    for (int h = 0; h < 7; ++h) draws[h] = draws[h + 1];
-    if ((++carved & 7u) == 0u) {
-#pragma unroll
-      for (int h = 0; h < 8; ++h) draws[h] = (uint32_t)(draw_at(kd, carved + (uint32_t)h) >> 32);
-    } else {
-      draws[7] = 0u;  // refilled when the window of eight is used up
-    }
+    ++carved;
     uint32_t bits = open;
-    for (uint32_t r = below32(hi, (uint32_t)__popc(open)); r > 0; --r) bits &= bits - 1;
+    const uint32_t r = below32(hi, (uint32_t)__popc(open));  // below 4: drop the r lowest set bits
+    if (r > 0u) bits &= bits - 1u;
+    if (r > 1u) bits &= bits - 1u;
+    if (r > 2u) bits &= bits - 1u;
     const int d = __ffs(bits) - 1;
     const int dx = d == 1 ? 1 : (d == 3 ? -1 : 0), dy = d == 0 ? -1 : (d == 2 ? 1 : 0);
     smap[(vy + dy) * S + vx + dx] = 0;
