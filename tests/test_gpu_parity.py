@@ -397,6 +397,41 @@ def test_handoff_rollout_equals_whole_env_launches(name, T):
     a.env.sync_status()
 
 
+def test_handoff_rollout_replayed_in_a_cuda_graph():
+    """A chunked rollout captured in a CUDA graph and replayed twice equals two
+    eager launches from the same state: the hand-off counters are zeroed by
+    each launch's last warp, so every replay finds them as the first did."""
+    cfg = CASES["maze32_ragged"]
+    N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
+    T = 70
+    a, b = Run(cfg), Run(cfg)
+    a.reset()
+    b.reset()
+    acts = torch.from_numpy(inputs.action_stream(31, T, N)).to(a.dev)
+
+    def bufs(run):
+        return (torch.zeros((T, N, H, W, 3), dtype=torch.uint8, device=run.dev),
+                torch.zeros((T, N), dtype=torch.float32, device=run.dev),
+                torch.zeros((T, N), dtype=torch.uint8, device=run.dev))
+
+    fa, ra, da = bufs(a)
+    fb, rb, db = bufs(b)
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        b.env.rollout(acts, fb, rb, db, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    for rep in range(2):
+        a.env.rollout(acts, fa, ra, da)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(fa, fb) and torch.equal(ra, rb) and torch.equal(da, db), rep
+        assert (a.env.get_state() == b.env.get_state()).all(), rep
+    graph.reset()
+    a.env.sync_status()
+    b.env.sync_status()
+
+
 def test_rollout_full_size_across_horizon():
     """4096 envs, 32 x 32 key-door mazes, in the benchmark's launch shape: a
     64-step rollout that crosses the 500-step horizon (every env resets)."""
