@@ -1259,7 +1259,10 @@ __device__ __forceinline__ void ray_init(Ray& q, const Env& r, float rx, float r
   q.done = !valid;
 }
 
-template <int MAPK>
+// One crossing. CHECK: a cell outside the map ends the ray (as wall 1);
+// without it the map's border must be solid and the ray start inside it, so
+// that every ray hits before it could leave (see mark_border).
+template <int MAPK, bool CHECK>
 __device__ __forceinline__ void ray_advance(const Params& p, Ray& q, const uint8_t* smap, int S) {
   const float lhs = fmaf(q.kx, q.ay, q.gxay);
   const float rhs = fmaf(q.ky, q.ax, q.gyax);
@@ -1269,8 +1272,34 @@ __device__ __forceinline__ void ray_advance(const Params& p, Ray& q, const uint8
   q.kx += tx ? 1.f : 0.f;
   q.ky += tx ? 0.f : 1.f;
   q.side = tx ? 0 : 1;
-  const bool out = (unsigned)q.mx >= (unsigned)S || (unsigned)q.my >= (unsigned)S;
-  q.done = out || cell_set<MAPK>(p, smap, q.my * S + q.mx);
+  if (CHECK) {
+    const bool out = (unsigned)q.mx >= (unsigned)S || (unsigned)q.my >= (unsigned)S;
+    q.done = out || cell_set<MAPK>(p, smap, q.my * S + q.mx);
+  } else {
+    q.done = cell_set<MAPK>(p, smap, q.my * S + q.mx);
+  }
+}
+
+// Whether rays of the staged map can skip the bounds test: every border cell
+// is solid in the staged map (locked doors of held keys already cleared) and
+// the agent's cell is not on the border, so a ray meets a solid cell before
+// it could leave the map, and the agent, blocked by the border, stays inside.
+// Kept in the warp's object words (obj[7]); recomputed whenever the staged map
+// or the keys change. ASCII maps, whose unlocked doors open on contact, always
+// take the bounds test.
+template <int MAPK>
+__device__ __forceinline__ void mark_border(const Params& p, const WarpSmem& ws, int cx, int cy, int lane) {
+  const int S = p.S;
+  bool ok = p.task != kTaskAscii && cx > 0 && cy > 0 && cx < S - 1 && cy < S - 1;
+  if (ok) {
+    const uint8_t* smap = ws.map(p);
+    for (int i = lane; i < S; i += 32)
+      ok = ok && cell_set<MAPK>(p, smap, i) && cell_set<MAPK>(p, smap, (S - 1) * S + i) &&
+           cell_set<MAPK>(p, smap, i * S) && cell_set<MAPK>(p, smap, i * S + S - 1);
+    ok = __all_sync(0xffffffffu, ok);
+  }
+  if (lane == 0) ws.obj(p)[7] = ok ? 1 : 0;
+  __syncwarp();
 }
 
 // A finished ray's hit: perpendicular distance, face, and the hit cell's
@@ -1354,6 +1383,7 @@ __device__ __forceinline__ void cast_columns(const Params& p, int e, const Env& 
   const int W = p.W, S = p.S;
   const uint8_t* smap = ws.map(p);
   const int max_it = 4 * S + 8;
+  const bool inside = ws.obj(p)[7] != 0;  // rays need no bounds test (mark_border)
   // single steps (latency-bound) finish a lane's hit after its next ray;
   // the other modes at once (a rollout keeps more state live across the loop)
   constexpr bool kDefer = MODE == MODE_STEP;
@@ -1369,14 +1399,26 @@ __device__ __forceinline__ void cast_columns(const Params& p, int e, const Env& 
       const float k = m == 0 ? k01.x : (m == 1 ? k01.y : __ldg(p.col_k + (valid ? col : 0)));
       ray_init(q[j], r, fmaf(-k, s, c), fmaf(k, c, s), valid);
     }
-    for (int it = 0; it < max_it; ++it) {
-      bool all = true;
+    if (inside) {
+      for (int it = 0; it < max_it; ++it) {
+        bool all = true;
 #pragma unroll
-      for (int j = 0; j < COLS; ++j) {
-        if (!q[j].done) ray_advance<MAPK>(p, q[j], smap, S);
-        all = all && q[j].done;
+        for (int j = 0; j < COLS; ++j) {
+          if (!q[j].done) ray_advance<MAPK, false>(p, q[j], smap, S);
+          all = all && q[j].done;
+        }
+        if (__all_sync(0xffffffffu, all)) break;
       }
-      if (__all_sync(0xffffffffu, all)) break;
+    } else {
+      for (int it = 0; it < max_it; ++it) {
+        bool all = true;
+#pragma unroll
+        for (int j = 0; j < COLS; ++j) {
+          if (!q[j].done) ray_advance<MAPK, true>(p, q[j], smap, S);
+          all = all && q[j].done;
+        }
+        if (__all_sync(0xffffffffu, all)) break;
+      }
     }
 #pragma unroll
     for (int j = 0; j < COLS; ++j)
@@ -1747,27 +1789,42 @@ __device__ __forceinline__ Prefetch prefetch(const Params& p, int e, int t0, int
 }
 
 // The prefetched objects, sprites and map into the warp's shared memory
-// (maps too large to prefetch are staged here); ends with __syncwarp. False
-// when the map's copy was lost (see stage_map).
+// (maps too large to prefetch are staged here), and the border flag of
+// mark_border (taken from the prefetched rows for 32 x 32 bit planes); ends
+// with __syncwarp. False when the map's copy was lost (see stage_map).
 template <int MAPK>
 __device__ __forceinline__ bool stage_prefetched(const Params& p, const WarpSmem& ws, int e, const Prefetch& q,
                                                  int lane) {
   if (lane < 6) ws.obj(p)[lane] = q.obj;
   if (lane == 6) ws.obj(p)[6] = q.obj > p.K ? p.K : q.obj;  // sprites in use
   if (lane < p.K) ws.spr_in(p)[lane] = q.spr;
-  if (!small_map<MAPK>(p)) return stage<MAPK>(p, e, ws.map(p), lane);  // ends with __syncwarp
+  if (!small_map<MAPK>(p)) {
+    if (!stage<MAPK>(p, e, ws.map(p), lane)) return false;  // ends with __syncwarp
+    mark_border<MAPK>(p, ws, q.r.cx, q.r.cy, lane);
+    return true;
+  }
   const int n = p.S * p.S;
   if (map_bits<MAPK>(p)) {
-    if (lane < (n >> 5))
-      reinterpret_cast<uint32_t*>(ws.map(p))[lane] =
-          nonzero4(q.m0.x) | nonzero4(q.m0.y) << 4 | nonzero4(q.m0.z) << 8 | nonzero4(q.m0.w) << 12 |
-          nonzero4(q.m1.x) << 16 | nonzero4(q.m1.y) << 20 | nonzero4(q.m1.z) << 24 | nonzero4(q.m1.w) << 28;
+    const uint32_t w = nonzero4(q.m0.x) | nonzero4(q.m0.y) << 4 | nonzero4(q.m0.z) << 8 | nonzero4(q.m0.w) << 12 |
+                       nonzero4(q.m1.x) << 16 | nonzero4(q.m1.y) << 20 | nonzero4(q.m1.z) << 24 |
+                       nonzero4(q.m1.w) << 28;
+    if (lane < (n >> 5)) reinterpret_cast<uint32_t*>(ws.map(p))[lane] = w;
+    if (p.S == 32) {  // word `lane` is row `lane`: its end cells, and all of rows 0 and 31, solid
+      const int S = 32, cx = q.r.cx, cy = q.r.cy;
+      const bool row_ok = (w & 0x80000001u) == 0x80000001u && ((lane != 0 && lane != S - 1) || w == 0xffffffffu);
+      const bool ok = __all_sync(0xffffffffu, row_ok) && p.task != kTaskAscii && cx > 0 && cy > 0 && cx < S - 1 &&
+                      cy < S - 1;
+      if (lane == 0) ws.obj(p)[7] = ok ? 1 : 0;
+      __syncwarp();
+      return true;
+    }
   } else {
     uint4* dst = reinterpret_cast<uint4*>(ws.map(p));
     if (lane < (n >> 4)) dst[lane] = q.m0;
     if (lane + 32 < (n >> 4)) dst[lane + 32] = q.m1;
   }
   __syncwarp();
+  mark_border<MAPK>(p, ws, q.r.cx, q.r.cy, lane);
   return true;
 }
 
@@ -1795,6 +1852,7 @@ __device__ __forceinline__ void next_episode(const Params& p, int e, Env& r, con
   load_objects(p, ws, e, lane);
   __syncwarp();
   heading(p, r, c, s);
+  mark_border<MAPK>(p, ws, r.cx, r.cy, lane);
 }
 
 // Everything one launch does for env e: MODE_ROLLOUT runs the launch's steps
@@ -1813,6 +1871,7 @@ __device__ __forceinline__ bool run_env(const Params& p, int e, uint8_t* wbase, 
     const Env r = load_env(p, e);
     load_objects(p, ws, e, lane);
     __syncwarp();
+    mark_border<MAPK>(p, ws, r.cx, r.cy, lane);
     float c, s;
     heading(p, r, c, s);
     render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot, p.frames + (size_t)e * frame_bytes,
@@ -1824,7 +1883,10 @@ __device__ __forceinline__ bool run_env(const Params& p, int e, uint8_t* wbase, 
   if (store_pal) store_palette(p, ws, pal, lane);
   Env r = q.r;
   if (!stage_prefetched<MAPK>(p, ws, e, q, lane)) return false;  // ends with __syncwarp
-  if (r.keys != 0) open_doors<MAPK>(p, e, r.keys, ws, lane);
+  if (r.keys != 0) {  // doors of held keys open: the border flag again
+    open_doors<MAPK>(p, e, r.keys, ws, lane);
+    mark_border<MAPK>(p, ws, r.cx, r.cy, lane);
+  }
   if (MODE == MODE_ROLLOUT) {
     int a_next = q.action;
     for (int t = t0; t < t1; ++t) {
@@ -1837,7 +1899,10 @@ __device__ __forceinline__ bool run_env(const Params& p, int e, uint8_t* wbase, 
       heading(p, r, c, s);
       if (__builtin_expect(step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), ws.spr_in(p), lane, c, s, a, out, false), 0))
         next_episode<MAPK>(p, e, r, ws, scratch, lane, c, s);
-      if (__builtin_expect(r.keys != keys0, 0)) open_doors<MAPK>(p, e, r.keys, ws, lane);
+      if (__builtin_expect(r.keys != keys0, 0)) {
+        open_doors<MAPK>(p, e, r.keys, ws, lane);
+        mark_border<MAPK>(p, ws, r.cx, r.cy, lane);
+      }
       render_env<MODE, MAPK, COLS, GRAY>(p, e, r, c, s, ws, lane, slot,
                                          p.frames + (size_t)t * p.frame_step + (size_t)e * frame_bytes, q.k01);
       __syncwarp();
@@ -1863,8 +1928,10 @@ __device__ __forceinline__ bool run_env(const Params& p, int e, uint8_t* wbase, 
     if (__builtin_expect(step_env<MAPK>(p, e, r, ws.map(p), ws.obj(p), ws.spr_in(p), lane, c, s, a, (size_t)e, true),
                          0))
       next_episode<MAPK>(p, e, r, ws, scratch, lane, c, s);
-    else if (r.keys != keys0)
+    else if (r.keys != keys0) {
       open_doors<MAPK>(p, e, r.keys, ws, lane);
+      mark_border<MAPK>(p, ws, r.cx, r.cy, lane);
+    }
   } else {
     heading(p, r, c, s);
   }

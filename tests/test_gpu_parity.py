@@ -187,6 +187,65 @@ def test_degenerate_poses_axis_rays_and_boundaries():
     stats.check()
 
 
+def test_open_border_takes_the_bounds_test():
+    """Rays skip the bounds test only while the staged map's border is solid and
+    the agent's cell is inside it. Maps with holes in the border (set through
+    jx_set_state: floor cells, and a locked door of a held key) and an agent on
+    a border cell must still read cells outside the map as wall 1, as the
+    oracle does: frames, rays and lockstep steps, in single steps and in a
+    rollout long enough for hand-off chunks."""
+    cfg = inputs.maze_keydoor(n_envs=8, map_side=16, seed=14, horizon=0)
+    S = cfg["map_side"]
+
+    def opened(run):
+        run.reset()
+        blob = run.env.get_state()
+        f = run.env.fields(blob)
+        m = f["map"]
+        m[0, 0, 1:S - 1] = 0  # top row open
+        m[1, 1:S - 1, S - 1] = 0  # right column open
+        m[2, 5, 0] = 16  # a red locked door on the border, its key held
+        f["flags"][2] = 1
+        m[3, 0, 3:8] = 0  # an agent standing on an opened border cell
+        m[3, 1, 3:8] = 0
+        f["cell_x"][3], f["cell_y"][3], f["frac_x"][3], f["frac_y"][3] = 5, 0, 0.5, 0.5
+        f["turn"][:] = np.arange(8) * 9
+        f["turn"][3] = 54  # facing -y: every ray leaves through the top
+        run.env.set_state(blob)
+        return blob
+
+    run = Run(cfg)
+    blob = opened(run)
+    run.env.render(run.frames)
+    torch.cuda.synchronize()
+    ref = render_ref(run.ocfg, to_oracle(run.env, blob))
+    stats = Stats()
+    compare_frames(run.frames.cpu().numpy(), ref, stats)
+    hits, perp = run.rays()
+    compare_rays(hits, perp, ref, stats)
+    assert (hits[3, :, 1] == -1).sum() >= 16  # env 3's central rays left the map at the top
+    lockstep(run, stats, 30, seed=5)
+    stats.check()
+    # the same steps in one rollout launch (hand-off chunks) equal single steps
+    a, b = Run(cfg), Run(cfg)
+    opened(a)
+    opened(b)
+    T, N, H, W = 70, cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
+    acts = torch.from_numpy(inputs.action_stream(15, T, N)).to(b.dev)
+    frames = torch.zeros((T, N, H, W, 3), dtype=torch.uint8, device=b.dev)
+    rewards = torch.zeros((T, N), dtype=torch.float32, device=b.dev)
+    dones = torch.zeros((T, N), dtype=torch.uint8, device=b.dev)
+    b.env.rollout(acts, frames, rewards, dones)
+    for t in range(T):
+        a.actions.copy_(acts[t])
+        a.env.step(a.actions, a.frames, a.rewards, a.dones)
+        assert torch.equal(a.frames, frames[t]), t
+    torch.cuda.synchronize()
+    assert (a.env.get_state() == b.env.get_state()).all()
+    a.env.sync_status()
+    b.env.sync_status()
+
+
 @pytest.mark.parametrize("patch", [dict(wall_prob=1.0), dict(wall_prob=0.0), dict(horizon=1), dict(move_step=0.0),
                                    dict(radius=0.0)])
 def test_edge_configs(patch):
