@@ -135,9 +135,10 @@ typedef struct {
  * the handle, owned by the caller until jx_destroy.
  * Maze tasks (JX_TASK_MAZE_KEYDOOR, JX_TASK_MAZE_ROOMS) with map_side >= 64
  * and a multiple of 4 also reserve a next-episode block (the state without
- * the grayscale stack, plus 4 bytes per maze node per env of work space):
- * when many envs will start episodes within the next few launches, one lane
- * per env builds them ahead there, spread over those launches. Without that
+ * the grayscale stack, plus about 4.4 bytes per maze node per env of work
+ * space): in batches of many envs with a horizon, one lane per env builds each
+ * env's next episode there while the current one runs, its walk spread over
+ * the launches before the horizon (all at once at a reset). Without that
  * memory the env works as for other configs. Results do not depend on it. */
 jx_status jx_create(const jx_config* cfg, int device, jx_env** out);
 
@@ -316,9 +317,10 @@ jx_status jx_sync_status(jx_env* env, void* stream);
 
 /* Number of kernel launches this env has issued since creation. For maze
  * configs with a next-episode block (see jx_create), jx_reset, jx_step and
- * jx_rollout each also launch the two kernels that build episodes ahead (a
- * count, then the build, after a 4-byte cudaMemsetAsync on the same stream;
- * all capturable in a CUDA graph). */
+ * jx_rollout each also launch the three kernels that build episodes ahead (a
+ * count, the walls of builds that start, then the build's share of the launch,
+ * after a 4-byte cudaMemsetAsync on the same stream; all capturable in a CUDA
+ * graph). */
 jx_status jx_launch_count(const jx_env* env, uint64_t* count);
 
 /* Launch shape of the fused step kernel: grid blocks, threads per block,

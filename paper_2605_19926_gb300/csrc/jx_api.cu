@@ -505,8 +505,11 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
     const size_t stride = jx::pregen_work_bytes(c.map_side);
     const size_t off_ep = align256(nx_bytes), off_count = off_ep + align256(4 * N);
     const size_t off_work = off_count + 256;
-    if (cudaMalloc(&env->nx_mem, off_work + stride * N) == cudaSuccess &&
-        cudaMemset(env->nx_mem + off_ep, 0xFF, 4 * N) == cudaSuccess) {
+    const size_t off_words = align256(off_work + stride * N);
+    const size_t words_bytes = jx::pregen_words_bytes(c.map_side) * N;
+    if (cudaMalloc(&env->nx_mem, off_words + words_bytes) == cudaSuccess &&
+        cudaMemset(env->nx_mem + off_ep, 0xFF, 4 * N) == cudaSuccess &&
+        cudaMemset(env->nx_mem + off_work, 0, stride * N) == cudaSuccess) {
       auto nx = [&](int f) { return env->nx_mem + env->field_off[f]; };
       p.nx = jx::State{reinterpret_cast<int16_t*>(nx(JX_F_CELL_X)), reinterpret_cast<int16_t*>(nx(JX_F_CELL_Y)),
                        reinterpret_cast<float*>(nx(JX_F_FRAC_X)), reinterpret_cast<float*>(nx(JX_F_FRAC_Y)),
@@ -519,7 +522,10 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
       p.nx_ep = reinterpret_cast<uint32_t*>(env->nx_mem + off_ep);
       p.nx_work = env->nx_mem + off_work;
       p.nx_work_stride = stride;
-      p.nx_lanes = (int32_t)N;
+      p.nx_words = reinterpret_cast<uint32_t*>(env->nx_mem + off_words);
+      int lanes = 0;
+      (void)jx::pregen_resident_lanes(c.map_side, env->num_sms, &lanes);
+      p.nx_lanes = (int32_t)((size_t)lanes < N ? (size_t)lanes : N);
       p.nx_count = reinterpret_cast<uint32_t*>(env->nx_mem + off_count);
       // one lane builds a maze in about three times a warp's time: ahead of
       // the launch pays once a launch would start mazes on about three times

@@ -700,14 +700,16 @@ __host__ __device__ __forceinline__ int pregen_lane_words(int S) {
 // kept; the stack depth is a counter, and the door's path nodes (at depths
 // ceil(d / 2) - 1 and ceil(d / 2) on the path to the deepest node, depth d)
 // are found afterwards by walking up from that node. The discovery and finish
-// counters go to the lane's work slot in global memory (written in the walk,
+// counters go to the env's work slot in global memory (written in the walk,
 // read once for the key). After the walk the words hold the floor-cell counts
 // of 256-cell chunks for the distractor draws.
 //
-// The lanes of warp_mask build mazes of one side together: every walk takes
-// exactly 2 n - 1 iterations (n - 1 pushes, n pops), and the lanes meet at
-// each iteration, so the warp runs the 32 walks side by side instead of one
-// diverged lane after another.
+// A build is resumable: lane_walk_begin lays the walls and starts the walk,
+// lane_walk_step takes one of its 2 n - 1 steps (n - 1 carves, n
+// backtracks), and lane_walk_finish places the door, key, rooms and sprites.
+// Between launches the walk's scalars and shared-memory words are kept in the
+// env's work slot (lane_walk_save, lane_walk_load), so that the building of
+// an episode can be spread over the launches of the episode before it.
 __device__ __forceinline__ uint32_t lds32(uint32_t addr) {
   uint32_t v;
   asm volatile("ld.shared.u32 %0, [%1];\n" : "=r"(v) : "r"(addr));
@@ -717,93 +719,190 @@ __device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(addr), "r"(v) : "memory");
 }
 
-__device__ void gen_maze_lane(const Params& p, int e, uint32_t ep, uint8_t* work, uint32_t* sm, int vstride,
-                              uint32_t warp_mask) {
-  const int S = p.S, n_cells = S * S;
-  const int nn = (S - 2) / 2, n = nn * nn;
-  const int vwords = (n + 31) >> 5, dwords = (n + 15) >> 4;
-  uint8_t* smap = p.nx.map + (size_t)e * n_cells;
-  uint16_t* disc = reinterpret_cast<uint16_t*>(work);  // 16-byte aligned (the key search reads it 8 at a time)
-  uint16_t* fin = reinterpret_cast<uint16_t*>(work + align16(2 * n));
-  // the walk state through shared-space addresses: its loads need not wait
-  // for the lane's global stores (map bytes, counters), which never alias it
-  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm), sstride = 4u * (uint32_t)vstride;
-  const uint32_t dbase = sbase + (uint32_t)vwords * sstride;
-  for (int w = 0; w < vwords; ++w) sts32(sbase + (uint32_t)w * sstride, 0u);
-  for (int w = 0; w < dwords; ++w) sts32(dbase + (uint32_t)w * sstride, 0u);
-  auto seen = [&](int u) { return (lds32(sbase + (uint32_t)(u >> 5) * sstride) >> (u & 31)) & 1u; };
-  auto mark = [&](int u) {
-    const uint32_t a = sbase + (uint32_t)(u >> 5) * sstride;
+// The walk's scalars, all saved as 32-bit words.
+struct LaneWalk {
+  int vx, vy, v, sp, pushes, best_v, best_d, start, it, carved;
+};
+constexpr int kLaneWalkWords = 10;
+
+// Byte offsets in an env's work slot for side S: the discovery counters, the
+// finish counters, and the record (the episode being built, whether its walk
+// is in progress, the walk's scalars). The walk's saved words live apart
+// (lane_walk_save).
+struct LaneSlot {
+  int n, nn, vwords, dwords, off_fin, off_rec, bytes;
+};
+__host__ __device__ __forceinline__ LaneSlot lane_slot(int S) {
+  LaneSlot L;
+  L.nn = (S - 2) / 2;
+  L.n = L.nn * L.nn;
+  L.vwords = (L.n + 31) >> 5;
+  L.dwords = (L.n + 15) >> 4;
+  L.off_fin = align16(2 * L.n);
+  L.off_rec = L.off_fin + align16(2 * L.n);
+  L.bytes = L.off_rec + 4 * (2 + kLaneWalkWords);
+  return L;
+}
+
+// The lane's visited and parent words in shared memory, through shared-space
+// addresses: their loads need not wait for the lane's global stores (map
+// bytes, counters), which never alias them.
+struct LaneWords {
+  uint32_t sbase, dbase, sstride;
+  int vwords, dwords;
+  __device__ uint32_t word(int w) const { return sbase + (uint32_t)w * sstride; }
+  __device__ uint32_t seen(int u) const { return (lds32(word(u >> 5)) >> (u & 31)) & 1u; }
+  __device__ void mark(int u) const {
+    const uint32_t a = word(u >> 5);
     sts32(a, lds32(a) | 1u << (u & 31));
-  };
-  auto parent_dir = [&](int u) { return (int)((lds32(dbase + (uint32_t)(u >> 4) * sstride) >> (2 * (u & 15))) & 3u); };
-  auto set_parent_dir = [&](int u, int d) {  // d: 0 N, 1 E, 2 S, 3 W; the word's old bits of u are 0
+  }
+  __device__ int parent_dir(int u) const {
+    return (int)((lds32(dbase + (uint32_t)(u >> 4) * sstride) >> (2 * (u & 15))) & 3u);
+  }
+  __device__ void set_parent_dir(int u, int d) const {  // d: 0 N, 1 E, 2 S, 3 W; the old bits of u are 0
     const uint32_t a = dbase + (uint32_t)(u >> 4) * sstride;
     sts32(a, lds32(a) | (uint32_t)d << (2 * (u & 15)));
-  };
+  }
+};
+__device__ __forceinline__ LaneWords lane_words(uint32_t* sm, int vstride, const LaneSlot& L) {
+  LaneWords W;
+  W.sbase = (uint32_t)__cvta_generic_to_shared(sm);
+  W.sstride = 4u * (uint32_t)vstride;
+  W.dbase = W.sbase + (uint32_t)L.vwords * W.sstride;
+  W.vwords = L.vwords;
+  W.dwords = L.dwords;
+  return W;
+}
+
+// Sixteen wall cells i .. i + 15 of episode ep of env e (walls typed like
+// gen_maze's), into its next-episode map.
+__device__ __forceinline__ void lane_walls16(const Params& p, int e, uint32_t ep, int i) {
   const uint64_t kw = stream_key(p.seed, (uint32_t)e, ep, P_WALL);
-  for (int i = 0; i < n_cells; i += 16) {
-    uint32_t w[4];
+  uint32_t q4[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint32_t v = 0;
+  for (int q = 0; q < 4; ++q) {
+    uint32_t v = 0;
 #pragma unroll
-      for (int b = 0; b < 4; ++b) v |= (1u + (uint32_t)(draw_at(kw, (uint32_t)(i + 4 * q + b)) & 3)) << (8 * b);
-      w[q] = v;
-    }
-    *reinterpret_cast<uint4*>(smap + i) = make_uint4(w[0], w[1], w[2], w[3]);
+    for (int b = 0; b < 4; ++b) v |= (1u + (uint32_t)(draw_at(kw, (uint32_t)(i + 4 * q + b)) & 3)) << (8 * b);
+    q4[q] = v;
   }
-  const uint64_t kd = stream_key(p.seed, (uint32_t)e, ep, P_DFS);
-  const int start = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_SPAWN), 0), (uint32_t)n);
-  int vx = 2 * (start % nn) + 1, vy = 2 * (start / nn) + 1, v = start;
-  smap[vy * S + vx] = 0;
-  mark(v);
-  int sp = 1, pushes = 0;  // stack size: the current node's depth is sp - 1
-  uint32_t carved = 0;
-  disc[v] = (uint16_t)pushes++;
-  int best_v = start, best_d = 0;
-  for (int it = 0; it < 2 * n - 1; ++it) {
-    __syncwarp(warp_mask);
-    // the draw a carve in this iteration takes (its high 32 bits), computed by
-    // every lane of the warp together whether it carves or backtracks: lanes
-    // carve at different iterations, and a draw computed only where it is
-    // used would run once for every different set of carving lanes
-    uint32_t hi = (uint32_t)(draw_at(kd, carved) >> 32);
-    asm volatile("" : "+r"(hi));  // keeps the draw ahead of the branch
-    const uint32_t open = (uint32_t)(vy > 1 && !seen(v - nn)) | ((uint32_t)(vx < S - 3 && !seen(v + 1)) << 1) |
-                          ((uint32_t)(vy < S - 3 && !seen(v + nn)) << 2) | ((uint32_t)(vx > 1 && !seen(v - 1)) << 3);
-    if (open == 0) {
-      fin[v] = (uint16_t)pushes;
-      if (--sp == 0) continue;  // the spawn, finished: the walk's last iteration
-      const int d = parent_dir(v);  // back to the parent
-      vx += d == 1 ? 2 : (d == 3 ? -2 : 0);
-      vy += d == 2 ? 2 : (d == 0 ? -2 : 0);
-      v = (vy >> 1) * nn + (vx >> 1);
-      continue;
-    }
-    // the r-th unvisited neighbour in N, E, S, W order
-    ++carved;
-    uint32_t bits = open;
-    const uint32_t r = below32(hi, (uint32_t)__popc(open));  // below 4: drop the r lowest set bits
-    if (r > 0u) bits &= bits - 1u;
-    if (r > 1u) bits &= bits - 1u;
-    if (r > 2u) bits &= bits - 1u;
-    const int d = __ffs(bits) - 1;
-    const int dx = d == 1 ? 1 : (d == 3 ? -1 : 0), dy = d == 0 ? -1 : (d == 2 ? 1 : 0);
-    smap[(vy + dy) * S + vx + dx] = 0;
-    vx += 2 * dx;
-    vy += 2 * dy;
-    smap[vy * S + vx] = 0;
-    v = (vy >> 1) * nn + (vx >> 1);
-    mark(v);
-    set_parent_dir(v, d ^ 2);
-    const int depth = sp++;
-    disc[v] = (uint16_t)pushes++;
-    if (depth > best_d || (depth == best_d && v < best_v)) {
-      best_v = v;
-      best_d = depth;
-    }
+  *reinterpret_cast<uint4*>(p.nx.map + (size_t)e * p.S * p.S + i) = make_uint4(q4[0], q4[1], q4[2], q4[3]);
+}
+
+// The walk of episode ep of env e started at the spawn node (the walls are
+// laid already, by lane_walls16), its words cleared.
+__device__ LaneWalk lane_walk_begin(const Params& p, int e, uint32_t ep, const LaneWords& W, uint8_t* work,
+                                    const LaneSlot& L) {
+  const int S = p.S, n_cells = S * S, nn = L.nn;
+  uint8_t* smap = p.nx.map + (size_t)e * n_cells;
+  uint16_t* disc = reinterpret_cast<uint16_t*>(work);
+  for (int w = 0; w < W.vwords + W.dwords; ++w) sts32(W.word(w), 0u);
+  LaneWalk w;
+  w.start = (int)below(draw_at(stream_key(p.seed, (uint32_t)e, ep, P_SPAWN), 0), (uint32_t)L.n);
+  w.v = w.start;
+  w.vx = 2 * (w.start % nn) + 1;
+  w.vy = 2 * (w.start / nn) + 1;
+  smap[w.vy * S + w.vx] = 0;
+  W.mark(w.v);
+  w.sp = 1;  // stack size: the current node's depth is sp - 1
+  w.pushes = 0;
+  w.carved = 0;
+  disc[w.v] = (uint16_t)w.pushes++;
+  w.best_v = w.start;
+  w.best_d = 0;
+  w.it = 0;
+  return w;
+}
+
+// One step of the walk: a carve to the r-th unvisited neighbour in N, E, S, W
+// order, or a backtrack to the parent when there is none.
+__device__ __forceinline__ void lane_walk_step(const Params& p, const LaneWords& W, LaneWalk& w, uint64_t kd,
+                                               uint8_t* smap, uint16_t* disc, uint16_t* fin, int nn) {
+  const int S = p.S;
+  // the draw a carve in this step takes (its high 32 bits), computed by every
+  // lane of the warp together whether it carves or backtracks: lanes carve at
+  // different steps, and a draw computed only where it is used would run once
+  // for every different set of carving lanes
+  uint32_t hi = (uint32_t)(draw_at(kd, (uint32_t)w.carved) >> 32);
+  asm volatile("" : "+r"(hi));  // keeps the draw ahead of the branch
+  ++w.it;
+  const int vx = w.vx, vy = w.vy, v = w.v;
+  const uint32_t open = (uint32_t)(vy > 1 && !W.seen(v - nn)) | ((uint32_t)(vx < S - 3 && !W.seen(v + 1)) << 1) |
+                        ((uint32_t)(vy < S - 3 && !W.seen(v + nn)) << 2) | ((uint32_t)(vx > 1 && !W.seen(v - 1)) << 3);
+  if (open == 0) {
+    fin[v] = (uint16_t)w.pushes;
+    if (--w.sp == 0) return;  // the spawn, finished: the walk's last step
+    const int d = W.parent_dir(v);  // back to the parent
+    w.vx += d == 1 ? 2 : (d == 3 ? -2 : 0);
+    w.vy += d == 2 ? 2 : (d == 0 ? -2 : 0);
+    w.v = (w.vy >> 1) * nn + (w.vx >> 1);
+    return;
   }
+  ++w.carved;
+  uint32_t bits = open;
+  const uint32_t r = below32(hi, (uint32_t)__popc(open));  // below 4: drop the r lowest set bits
+  if (r > 0u) bits &= bits - 1u;
+  if (r > 1u) bits &= bits - 1u;
+  if (r > 2u) bits &= bits - 1u;
+  const int d = __ffs(bits) - 1;
+  const int dx = d == 1 ? 1 : (d == 3 ? -1 : 0), dy = d == 0 ? -1 : (d == 2 ? 1 : 0);
+  smap[(vy + dy) * S + vx + dx] = 0;
+  w.vx = vx + 2 * dx;
+  w.vy = vy + 2 * dy;
+  smap[w.vy * S + w.vx] = 0;
+  w.v = (w.vy >> 1) * nn + (w.vx >> 1);
+  W.mark(w.v);
+  W.set_parent_dir(w.v, d ^ 2);
+  const int depth = w.sp++;
+  disc[w.v] = (uint16_t)w.pushes++;
+  if (depth > w.best_d || (depth == w.best_d && w.v < w.best_v)) {
+    w.best_v = w.v;
+    w.best_d = depth;
+  }
+}
+
+// A walk in progress into the env's record and the words array (word i of
+// env e at words[i * n_envs + e], so that the lanes of a warp, consecutive
+// envs, move consecutive words), or back into the lane's shared memory.
+__device__ __forceinline__ void lane_walk_save(const LaneWords& W, const LaneWalk& w, uint8_t* work,
+                                               const LaneSlot& L, uint32_t ep, uint32_t* words, int e, int n_envs) {
+  for (int i = 0; i < W.vwords + W.dwords; ++i) words[(size_t)i * n_envs + e] = lds32(W.word(i));
+  uint32_t* rec = reinterpret_cast<uint32_t*>(work + L.off_rec);
+  const int s[kLaneWalkWords] = {w.vx, w.vy, w.v, w.sp, w.pushes, w.best_v, w.best_d, w.start, w.it, w.carved};
+#pragma unroll
+  for (int i = 0; i < kLaneWalkWords; ++i) rec[2 + i] = (uint32_t)s[i];
+  rec[0] = ep;
+  rec[1] = 1u;
+}
+__device__ __forceinline__ LaneWalk lane_walk_load(const LaneWords& W, const uint8_t* work, const LaneSlot& L,
+                                                   const uint32_t* words, int e, int n_envs) {
+  for (int i = 0; i < W.vwords + W.dwords; ++i) sts32(W.word(i), words[(size_t)i * n_envs + e]);
+  const uint32_t* rec = reinterpret_cast<const uint32_t*>(work + L.off_rec);
+  LaneWalk w;
+  w.vx = (int)rec[2];
+  w.vy = (int)rec[3];
+  w.v = (int)rec[4];
+  w.sp = (int)rec[5];
+  w.pushes = (int)rec[6];
+  w.best_v = (int)rec[7];
+  w.best_d = (int)rec[8];
+  w.start = (int)rec[9];
+  w.it = (int)rec[10];
+  w.carved = (int)rec[11];
+  return w;
+}
+
+// The door, key, rooms and distractor sprites of a finished walk, and the
+// episode's state fields into the next-episode block.
+__device__ void lane_walk_finish(const Params& p, int e, uint32_t ep, const LaneWalk& w, const LaneWords& W,
+                                 uint32_t* sm, int vstride, uint8_t* work, const LaneSlot& L) {
+  const int S = p.S, n_cells = S * S;
+  const int nn = L.nn, n = L.n;
+  uint8_t* smap = p.nx.map + (size_t)e * n_cells;
+  const uint16_t* disc = reinterpret_cast<const uint16_t*>(work);
+  const uint16_t* fin = reinterpret_cast<const uint16_t*>(work + L.off_fin);
+  const int best_v = w.best_v, best_d = w.best_d, start = w.start;
+  auto parent_dir = [&](int u) { return W.parent_dir(u); };
   // the door sits on edge ceil(d / 2) of the path to the deepest node: between
   // its path nodes at depths j - 1 (a) and j (b), j = ceil(d / 2)
   const int j = (best_d + 1) / 2;

@@ -48,8 +48,8 @@ struct jx_env {
 
 namespace jx {
 
-// kernels one pregen_launch launches: the count and the build
-constexpr int kPregenKernels = 2;
+// kernels one pregen_launch launches: the count, the walls and the build
+constexpr int kPregenKernels = 3;
 
 namespace host {
 

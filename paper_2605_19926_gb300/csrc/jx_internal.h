@@ -78,15 +78,18 @@ struct Params {
   // The next episode of each env, built ahead by the lane-parallel
   // pre-generation kernel (mazes of side >= kPregenMinSide), or all null:
   // the state fields generation writes, the episode number they hold
-  // (0xFFFFFFFF: none), and one work slot per pre-generation lane.
+  // (0xFFFFFFFF: none), and one work slot per env (the build's counters, and
+  // a build in progress between launches; zero at creation).
   State nx;
   uint32_t* nx_ep;
   uint8_t* nx_work;
   size_t nx_work_stride;
-  int32_t nx_lanes;
-  // the envs that need a pre-built episode are counted first; they are built
-  // ahead only when at least nx_min of them do (fewer are faster built where
-  // they start: one lane's build takes longer than a warp's)
+  uint32_t* nx_words;  // [pregen_lane_words][n]: the walk words of builds in progress
+  int32_t nx_lanes;  // lanes of the pre-generation grid (a lane takes envs lane, lane + nx_lanes, ...)
+  // nx_count[0]: the envs that need a pre-built episode, nx_count[1]: those
+  // whose build starts, counted first (none: the walls or the build kernel
+  // returns at once); batches of fewer than nx_min envs are built where
+  // episodes start (one lane's build takes longer than a warp's)
   uint32_t* nx_count;
   int32_t nx_min;
   const uint8_t* actions;
@@ -146,13 +149,17 @@ void layout_warp_smem(Params& p);
 int block_smem_bytes(const Params& p);
 size_t gen_scratch_bytes(int task, int S);
 // Lane-parallel pre-generation: for maze tasks of side >= kPregenMinSide (a
-// multiple of 4) with a horizon, one lane per env builds the episode the env
-// will start within the next `steps` steps (reset: episode 0) into p.nx.
+// multiple of 4), one lane per env advances the build of the env's next
+// episode (reset: episode 0) into p.nx by its share of the launches left
+// before the horizon (each launch runs `steps` steps).
 constexpr int kPregenMinSide = 64;
 constexpr int kPregenThreads = 32;  // pre-generation lanes per block (each with its walk state in shared memory)
-constexpr int kPregenSpread = 4;    // coinciding horizons are built over this many launches ahead
+constexpr int kPregenLaunches = 20;  // a build's walk goes into at most this many launches
 bool pregen_wanted(int task, int S, int horizon);
 size_t pregen_work_bytes(int S);
+size_t pregen_words_bytes(int S);  // per env: the saved walk words of a build in progress
+// Lanes of the pre-generation kernel resident at once on num_sms SMs (its grid).
+cudaError_t pregen_resident_lanes(int S, int num_sms, int* lanes);
 cudaError_t pregen_launch(const Params& p, int steps, bool reset, cudaStream_t stream);
 
 // Configure (attributes) and query occupancy of the kernel for `mode`.

@@ -111,50 +111,117 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   if (lane == 0) bulk_wait_read_all();
 }
 
-// Whether env e needs a pre-built episode, and which: the one it starts
-// soon, or for a reset episode 0, unless the next-episode block holds it
-// already. "Soon" spreads the builds of envs whose horizons coincide over the
-// last kPregenSpread launches before it, a contiguous part of the envs in
-// each (so a warp's lanes build together): env e of part q = e * kPregenSpread
-// / n is built once its horizon falls within the next steps * (1 + q) steps.
-__device__ __forceinline__ bool pregen_need(const Params& p, int e, int steps, int reset, uint32_t& ep) {
+// Whether env e needs a pre-built episode, and which: episode 0 at a reset,
+// else the one after its current episode (with a horizon, which bounds when it
+// starts), unless the next-episode block holds it already.
+__device__ __forceinline__ bool pregen_need(const Params& p, int e, int reset, uint32_t& ep) {
   if (reset) {
     ep = 0;
     return p.nx_ep[e] != 0u;
   }
   ep = p.st.episode[e] + 1;
-  const int q = (int)(((int64_t)e * kPregenSpread) / p.n);
-  return p.horizon > 0 && p.st.t[e] + steps * (1 + q) >= p.horizon && p.nx_ep[e] != ep;
+  return p.horizon > 0 && p.nx_ep[e] != ep;
 }
 
-// Counts the envs that need a pre-built episode into *p.nx_count (zeroed before).
-__global__ void __launch_bounds__(128) pregen_count_kernel(const __grid_constant__ Params p, int steps, int reset) {
+// Whether env e's build of episode ep starts over in this launch: no walk of
+// that episode is in progress in its work slot.
+__device__ __forceinline__ bool pregen_fresh(const Params& p, int e, uint32_t ep) {
+  const uint32_t* rec = reinterpret_cast<const uint32_t*>(p.nx_work + (size_t)e * p.nx_work_stride +
+                                                          lane_slot(p.S).off_rec);
+  return !(rec[1] == 1u && rec[0] == ep);
+}
+
+// Counts the envs that need a pre-built episode into nx_count[0], and those
+// whose build starts in this launch into nx_count[1] (both zeroed before).
+__global__ void __launch_bounds__(128) pregen_count_kernel(const __grid_constant__ Params p, int reset) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t ep;
-  const bool need = e < p.n && pregen_need(p, e, steps, reset, ep);
-  const uint32_t b = __ballot_sync(0xffffffffu, need);
+  uint32_t ep = 0;
+  const bool need = e < p.n && pregen_need(p, e, reset, ep);
+  const bool fresh = need && pregen_fresh(p, e, ep);
+  const uint32_t b = __ballot_sync(0xffffffffu, need), f = __ballot_sync(0xffffffffu, fresh);
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(p.nx_count, (uint32_t)__popc(b));
+  if ((threadIdx.x & 31) == 0 && f) atomicAdd(p.nx_count + 1, (uint32_t)__popc(f));
 }
 
-// Lane-parallel pre-generation: lane i builds, for envs i, i + lanes, ...,
-// the episode each needs, when at least nx_min envs need one. Each lane keeps
-// its walk's state in shared memory (kPregenThreads lanes a block,
-// pregen_lane_words words each: under 48 KB a block for side 128).
+// The walls of the builds that start in this launch, 16 cells a thread (the
+// draws of all cells at once, with the GPU's full occupancy; the walk needs
+// them laid before its first step).
+__global__ void __launch_bounds__(256) pregen_walls_kernel(const __grid_constant__ Params p, int reset) {
+  if (p.nx_count[1] == 0u || p.n < p.nx_min) return;  // the whole grid: no build starts
+  const int per_env = p.S * p.S / 16;
+  const int64_t items = (int64_t)p.n * per_env;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < items;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int e = (int)(idx / per_env);
+    uint32_t ep = 0;
+    if (pregen_need(p, e, reset, ep) && pregen_fresh(p, e, ep)) lane_walls16(p, e, ep, (int)(idx % per_env) * 16);
+  }
+}
+
+// Lane-parallel pre-generation, one lane per env (batches of at least nx_min
+// envs; smaller ones build where episodes start, where one warp is faster
+// than one lane). Each launch advances the build of every env's next episode
+// by its share of the walk's steps: the steps left over the launches left
+// before the one in which the episode can end at the horizon (that launch
+// only takes the entry over), and at least 1 / kPregenLaunches of them; all
+// of them at a reset or when one launch is left. The build of an episode is
+// so spread over the first launches of the episode before it, and a finished
+// entry is published by its episode number (nx_ep). Each lane keeps the walk's words in shared memory while it runs
+// (kPregenThreads lanes a block, pregen_lane_words words each: under 48 KB a
+// block for side 128) and in the words array between launches.
 __global__ void __launch_bounds__(kPregenThreads) pregen_kernel(const __grid_constant__ Params p, int steps, int reset) {
   extern __shared__ uint32_t pregen_sm[];
-  if (*p.nx_count < (uint32_t)p.nx_min) return;  // the whole grid
-  const int lane_id = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  // lanes below nx_lanes own a work slot; the loop runs the same iterations
-  // in all lanes of a warp (its condition is the warp's first env)
-  for (int e = lane_id; e - lane < p.n; e += p.nx_lanes) {
+  if (*p.nx_count == 0u || p.n < p.nx_min) return;  // the whole grid
+  const LaneSlot L = lane_slot(p.S);
+  const LaneWords W = lane_words(pregen_sm + threadIdx.x, blockDim.x, L);
+  const int total = 2 * L.n - 1;
+  // a block (one warp) takes 32 consecutive envs at a time, one a lane
+  for (int base = blockIdx.x * kPregenThreads; base < p.n; base += gridDim.x * kPregenThreads) {
+    const int e = base + (int)threadIdx.x;
     uint32_t ep = 0;
-    const bool need = lane_id < p.nx_lanes && e < p.n && pregen_need(p, e, steps, reset, ep);
-    const uint32_t m = __ballot_sync(0xffffffffu, need);
+    const bool need = e < p.n && pregen_need(p, e, reset, ep);
+    if (__ballot_sync(0xffffffffu, need) == 0u) continue;  // the whole warp
+    uint8_t* work = p.nx_work + (size_t)(need ? e : 0) * p.nx_work_stride;
+    const uint32_t* rec = reinterpret_cast<const uint32_t*>(work + L.off_rec);
+    LaneWalk w{};
+    int budget = 0;
     if (need) {
-      gen_maze_lane(p, e, ep, p.nx_work + (size_t)lane_id * p.nx_work_stride, pregen_sm + threadIdx.x, blockDim.x, m);
-      p.nx_ep[e] = ep;
+      const bool resume = rec[1] == 1u && rec[0] == ep;
+      w = resume ? lane_walk_load(W, work, L, p.nx_words, e, p.n) : lane_walk_begin(p, e, ep, W, work, L);
+      int launches = 1;  // the launches left for the remaining steps
+      if (!reset) {
+        const int left = p.horizon - p.st.t[e];
+        launches = left > steps ? (left + steps - 1) / steps - 1 : 1;
+      }
+      // a build's steps go into at most kPregenLaunches launches after the
+      // one that lays its walls (fewer saves and loads of the walk), and
+      // always in time for the horizon
+      const int share = (total + kPregenLaunches - 1) / kPregenLaunches;
+      const int due = (total - w.it + launches - 1) / launches;
+      budget = launches > 1 && !resume ? 0 : (share > due ? share : due);
+      budget = budget < total - w.it ? budget : total - w.it;
     }
+    // the warp's lanes step together (each its own walk), as many rounds as
+    // the largest share
+    const int rounds = __reduce_max_sync(0xffffffffu, budget);
+    const uint64_t kd = stream_key(p.seed, (uint32_t)e, ep, P_DFS);
+    uint8_t* smap = p.nx.map + (size_t)(need ? e : 0) * p.S * p.S;
+    uint16_t* disc = reinterpret_cast<uint16_t*>(work);
+    uint16_t* fin = reinterpret_cast<uint16_t*>(work + L.off_fin);
+    for (int k = 0; k < rounds; ++k) {
+      __syncwarp();
+      if (k < budget) lane_walk_step(p, W, w, kd, smap, disc, fin, L.nn);
+    }
+    if (need) {
+      if (w.it == total) {
+        lane_walk_finish(p, e, ep, w, W, pregen_sm + threadIdx.x, blockDim.x, work, L);
+        reinterpret_cast<uint32_t*>(work + L.off_rec)[1] = 0u;
+        p.nx_ep[e] = ep;  // the entry is complete: read by later kernels only
+      } else {
+        lane_walk_save(W, w, work, L, ep, p.nx_words, e, p.n);
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -227,19 +294,33 @@ bool pregen_wanted(int task, int S, int horizon) {
   return (task == 1 || task == 2) && S >= kPregenMinSide && S % 4 == 0;
 }
 
+size_t pregen_words_bytes(int S) { return 4 * (size_t)pregen_lane_words(S); }
+
+cudaError_t pregen_resident_lanes(int S, int num_sms, int* lanes) {
+  int blocks = 0;
+  const size_t lane_bytes = (size_t)kPregenThreads * pregen_lane_words(S) * sizeof(uint32_t);
+  cudaError_t err = cudaFuncSetAttribute(pregen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lane_bytes);
+  if (err == cudaSuccess)
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, pregen_kernel, kPregenThreads, lane_bytes);
+  *lanes = (blocks > 0 ? blocks : 1) * num_sms * kPregenThreads;
+  return err;
+}
+
 size_t pregen_work_bytes(int S) {
-  const size_t n = (size_t)((S - 2) / 2) * ((S - 2) / 2);
-  return (4 * n + 16 + 255) & ~(size_t)255;  // discovery and finish counters (uint16, the first 16-byte aligned)
+  // discovery and finish counters (uint16), the saved walk words and record
+  return ((size_t)lane_slot(S).bytes + 255) & ~(size_t)255;
 }
 
 cudaError_t pregen_launch(const Params& p, int steps, bool reset, cudaStream_t stream) {
   if (p.nx_ep == nullptr || p.nx_lanes <= 0) return cudaSuccess;
-  cudaError_t err = cudaMemsetAsync(p.nx_count, 0, sizeof(uint32_t), stream);
+  cudaError_t err = cudaMemsetAsync(p.nx_count, 0, 2 * sizeof(uint32_t), stream);
   if (err != cudaSuccess) return err;
-  pregen_count_kernel<<<(p.n + 127) / 128, 128, 0, stream>>>(p, steps, reset ? 1 : 0);
+  pregen_count_kernel<<<(p.n + 127) / 128, 128, 0, stream>>>(p, reset ? 1 : 0);
+  const int64_t wall_blocks = ((int64_t)p.n * (p.S * p.S / 16) + 255) / 256;
+  pregen_walls_kernel<<<(unsigned)(wall_blocks < 4096 ? wall_blocks : 4096), 256, 0, stream>>>(p, reset ? 1 : 0);
   const size_t lane_bytes = (size_t)kPregenThreads * pregen_lane_words(p.S) * sizeof(uint32_t);
   pregen_kernel<<<(p.nx_lanes + kPregenThreads - 1) / kPregenThreads, kPregenThreads, lane_bytes, stream>>>(
-      p, steps, reset ? 1 : 0);
+      p, steps, reset ? 1 : 0);  // nx_lanes: the resident lanes (pregen_resident_lanes)
   return cudaGetLastError();
 }
 
