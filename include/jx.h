@@ -267,6 +267,17 @@ jx_status jx_step_host_static(jx_env* env, void* stream, const uint8_t* h_action
  * kernel, and its tuned batch). JX_EINVAL for rounds < 0. */
 jx_status jx_debug_wait_limit(jx_env* env, int32_t rounds);
 
+/* Test and debug hook: the number of polls a warp makes, in a rollout in
+ * hand-off chunks (see jx_rollout), for the warp that ran the previous chunk
+ * of an env to publish its state, before the wait counts as late (default
+ * 4194304, about a second). A late wait sets bit 2 of the device error word
+ * and the chunk runs on whatever state the env holds then, so the results of
+ * that launch are undefined; the launch still ends, and later launches start
+ * from clean hand-off words. 0 makes every wait late, exercising that path on
+ * a healthy device. Applies to later rollouts of the env's own kernel.
+ * JX_EINVAL for polls < 0. */
+jx_status jx_debug_handoff_limit(jx_env* env, int32_t polls);
+
 /* Per-column ray results of the current state (test and debug hook):
  *  d_hits [N][W][4] int32: hit cell x, hit cell y, side (0: x face, 1: y face),
  *         slice height h in rows;

@@ -331,6 +331,7 @@ jx_status create_impl(const jx_config* cfg, int device, void* ext, size_t ext_by
         (float)(c.step_reward + ((ev & 1) ? c.key_reward : 0.0) + ((ev & 2) ? c.goal_reward : 0.0));
   p.seed = c.seed;
   p.bulk_wait_rounds = jx::kBulkWaitRounds;
+  p.handoff_polls = jx::kHandoffPolls;
   // wall iff k * 2^-53 < wall_prob for the 53-bit integer k = draw >> 11
   p.wall_thr = (uint64_t)std::ceil(c.wall_prob * 9007199254740992.0);
 
@@ -963,7 +964,8 @@ jx_status jx_sync_status(jx_env* env, void* stream) {
   if (word) {
     cudaMemset(env->base.err, 0, 4);
     return fail(JX_EDEVICE, "device error word 0x%x (1: action outside 0..6; 2: a bulk map copy completed late, or "
-                            "was lost and its warp left that env and its later envs unstepped)", word);
+                            "was lost and its warp left that env and its later envs unstepped; 4: a rollout hand-off between "
+                            "warps ran out of its bounded wait)", word);
   }
   return JX_OK;
 }
@@ -977,6 +979,13 @@ jx_status jx_debug_wait_limit(jx_env* env, int32_t rounds) {
     if (jx_status st = jx_batch_get_tiling(env->tuned, &t)) return st;
     return jx_batch_set_tiling(env->tuned, &t);
   }
+  return JX_OK;
+}
+
+jx_status jx_debug_handoff_limit(jx_env* env, int32_t polls) {
+  if (jx_status st = check_env(env)) return st;
+  if (polls < 0) return fail(JX_EINVAL, "polls must be >= 0 (got %d)", polls);
+  env->base.handoff_polls = polls;
   return JX_OK;
 }
 

@@ -18,7 +18,7 @@ constexpr int kWarpsPerBlock = 2;  // envs in flight per block of the env kernel
 constexpr int kThreads = kWarpsPerBlock * 32;
 constexpr int kMaxStaging = 2;  // frame row-block staging buffers per warp: 1 or 2
 constexpr int kMinBlocksPerSm = 28;  // register budget: 28 warps resident per SM
-constexpr int kHandoffPolls = 1 << 22;  // polls (about 0.25 us apart) before a rollout hand-off counts as late
+constexpr int kHandoffPolls = 1 << 22;  // default polls (about 0.25 us apart) before a rollout hand-off counts as late
 constexpr int kHandoffMinSteps = 64;    // rollouts of at least this many steps run in hand-off chunks
 constexpr int kHandoffChunk = 12;       // steps per hand-off chunk
 
@@ -109,6 +109,7 @@ struct Params {
   // warp + warps, ...).
   uint32_t* work;
   int32_t chunk;
+  int32_t handoff_polls;  // polls of a hand-off wait before it counts as late (jx_debug_handoff_limit)
   int32_t out_stride;  // envs per step in the action / reward / done arrays (n, or a batch's total)
   size_t frame_step;   // bytes per step in the frame array (n frames, or a batch's total)
   int32_t map_bits;    // the map is staged as a bit plane (see MapKind)

@@ -21,10 +21,10 @@ __device__ __forceinline__ uint32_t take_item(const Params& p, int lane) {
 // Waits until chunk k - 1 of env e is published (work[2 + e] == k). The
 // warp that holds it is running: it took the item before this warp took a
 // later one, and waits only on earlier items itself. False after
-// kHandoffPolls polls.
+// p.handoff_polls polls (kHandoffPolls unless a test lowered it).
 __device__ __forceinline__ bool await_chunk(const Params& p, int e, uint32_t k) {
   const uint32_t* f = p.work + 2 + e;
-  for (int i = 0; i < kHandoffPolls; ++i) {
+  for (int i = 0; i < p.handoff_polls; ++i) {
     uint32_t v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
     if (__all_sync(0xffffffffu, v == k)) return true;
@@ -54,7 +54,8 @@ __device__ __forceinline__ void publish_chunk(const Params& p, int e, uint32_t v
 // attribute these instructions do nothing.
 // The end of a launch that hands out work from Params::work: the warp's bulk
 // stores have read its shared memory, and the last warp to get here zeroes
-// the counters for the next launch.
+// the counters for the next launch, and the envs' hand-off words too when a
+// hand-off ran late (two warps may then have published an env out of order).
 __device__ __forceinline__ void finish_items(const Params& p, int nw, int lane) {
   if (lane == 0) {
     bulk_wait_read_all();
@@ -62,6 +63,8 @@ __device__ __forceinline__ void finish_items(const Params& p, int nw, int lane) 
     if (atomicAdd(p.work + 1, 1u) == (uint32_t)nw - 1) {
       atomicExch(p.work, 0u);
       atomicExch(p.work + 1, 0u);
+      if (*reinterpret_cast<volatile uint32_t*>(p.err) & 4u)
+        for (int e = 0; e < p.n; ++e) p.work[2 + e] = 0u;
     }
   }
 }

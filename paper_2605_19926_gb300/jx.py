@@ -34,7 +34,7 @@ FIELDS = {
 # Entry points declared in include/jx.h (checked by the ABI test).
 SYMBOLS = [
     "jx_create", "jx_create_ascii", "jx_destroy", "jx_reset", "jx_step", "jx_rollout", "jx_render", "jx_step_host",
-    "jx_step_host_static", "jx_debug_rays", "jx_debug_wait_limit",
+    "jx_step_host_static", "jx_debug_rays", "jx_debug_wait_limit", "jx_debug_handoff_limit",
     "jx_state_bytes", "jx_state_field", "jx_get_state", "jx_set_state", "jx_sync_status", "jx_launch_count",
     "jx_rollout_shape",
     "jx_launch_shape", "jx_last_error",
@@ -121,6 +121,7 @@ def _load() -> ctypes.CDLL:
         "jx_step_host_static": [P, P, P, P, P, P],
         "jx_debug_rays": [P, P, P, P],
         "jx_debug_wait_limit": [P, i32],
+        "jx_debug_handoff_limit": [P, i32],
         "jx_state_bytes": [P, P],
         "jx_state_field": [P, i32, P, P],
         "jx_get_state": [P, P, sz],
@@ -293,6 +294,10 @@ class Env:
     def debug_wait_limit(self, rounds: int):
         """Polls before a bulk map copy counts as late (0: every copy is late)."""
         _check(lib.jx_debug_wait_limit(self._h, int(rounds)))
+
+    def debug_handoff_limit(self, polls: int):
+        """Polls before a rollout hand-off wait counts as late (0: every wait is late)."""
+        _check(lib.jx_debug_handoff_limit(self._h, int(polls)))
 
     def sync_status(self, stream=None):
         _check(lib.jx_sync_status(self._h, _stream(stream)))

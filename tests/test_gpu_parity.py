@@ -688,3 +688,41 @@ def test_unlocked_door_opens_when_bumped():
     f = run.env.fields(run.env.get_state())
     assert (f["cell_x"] == 4).all()
     stats.check()
+
+
+def test_late_handoff_is_reported_and_later_rollouts_exact():
+    """With the hand-off wait limit at 0 polls every hand-off of a chunked
+    rollout counts as late: the launch still ends, the device error word says
+    so (bit 2), and after the limit is restored and the env reset, rollouts are
+    again equal to single steps (the late launch left the hand-off words clean)."""
+    cfg = CASES["maze32_ragged"]
+    N, H, W = cfg["n_envs"], cfg["frame_h"], cfg["frame_w"]
+    T = 70
+    run = Run(cfg)
+    run.reset()
+    acts = torch.from_numpy(inputs.action_stream(33, T, N)).to(run.dev)
+    frames = torch.zeros((T, N, H, W, 3), dtype=torch.uint8, device=run.dev)
+    rewards = torch.zeros((T, N), dtype=torch.float32, device=run.dev)
+    dones = torch.zeros((T, N), dtype=torch.uint8, device=run.dev)
+    run.env.debug_handoff_limit(0)
+    run.env.rollout(acts, frames, rewards, dones)
+    torch.cuda.synchronize()
+    with pytest.raises(jx.JxError) as ei:
+        run.env.sync_status()
+    assert ei.value.status == jx.EDEVICE and "hand-off" in str(ei.value)
+    run.env.debug_handoff_limit(1 << 22)
+    run.env.sync_status()  # cleared by the read above
+    with pytest.raises(jx.JxError):
+        run.env.debug_handoff_limit(-1)
+    # from a fresh reset, one chunked launch equals single steps again
+    ref = Run(cfg)
+    run.reset()
+    ref.reset()
+    run.env.rollout(acts, frames, rewards, dones)
+    for t in range(T):
+        ref.actions.copy_(acts[t])
+        ref.env.step(ref.actions, ref.frames, ref.rewards, ref.dones)
+        assert torch.equal(ref.frames, frames[t]), t
+    torch.cuda.synchronize()
+    assert (ref.env.get_state() == run.env.get_state()).all()
+    run.env.sync_status()
