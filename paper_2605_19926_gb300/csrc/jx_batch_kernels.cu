@@ -21,7 +21,6 @@ __global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
   init_warp_header(wbase, lane);
   const int gw = blockIdx.x * wpb + warp;
   int slot = 0;
-  const uint3 no_palette = make_uint3(0u, 0u, 0u);  // written once per group (write_palette), not per env
   bool fresh = true;  // nothing of an earlier group is pending in the ring
   bool lost = false;  // a map copy of this warp was lost: it takes no further env
   for (int g = 0; g < bp.n_groups && !lost; ++g) {
@@ -45,9 +44,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, kBatchMinBlocks)
       if (lane == 0) next = atomicAdd(bp.queue + g, 1u);
       const int e = (int)ticket;
       if (SPEC == 1)
-        lost = !run_env<MODE, MAP_BITS, COLS, 0>(p, e, wbase, scratch, lane, slot, no_palette, false, 0, p.steps);
+        lost = !run_env<MODE, MAP_BITS, COLS, 0>(p, e, wbase, scratch, lane, slot, 0, p.steps);
       else
-        lost = !run_env<MODE, MAP_RUNTIME, COLS, 2>(p, e, wbase, scratch, lane, slot, no_palette, false, 0, p.steps);
+        lost = !run_env<MODE, MAP_RUNTIME, COLS, 2>(p, e, wbase, scratch, lane, slot, 0, p.steps);
       if (lost) break;  // the counters are still cleared below: every warp reaches the end
       ticket = __shfl_sync(0xffffffffu, next, 0);
     }

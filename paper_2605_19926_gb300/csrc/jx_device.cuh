@@ -1957,15 +1957,13 @@ __device__ __forceinline__ void next_episode(const Params& p, int e, Env& r, con
 // Everything one launch does for env e: MODE_ROLLOUT runs the launch's steps
 // t0 .. t1 - 1 with the env's scalar state in registers and its map in shared
 // memory (the state is loaded before step t0 and stored after step t1 - 1).
-// The palette `pal` (this lane's words) is stored first when store_pal is set.
 // Returns false when the env's map copy was lost: the warp must stop.
 template <int MODE, int MAPK, int COLS, int GRAY>
 __device__ __forceinline__ bool run_env(const Params& p, int e, uint8_t* wbase, uint8_t* scratch, int lane,
-                                        int& slot, const uint3& pal, bool store_pal, int t0 = 0, int t1 = 0) {
+                                        int& slot, int t0 = 0, int t1 = 0) {
   const WarpSmem ws{wbase, fill_lane(p, lane)};
   const size_t frame_bytes = (size_t)3 * p.H * p.W;
   if (MODE == MODE_RESET) {
-    if (store_pal) store_palette(p, ws, pal, lane);
     generate<MAPK>(p, e, 0u, wbase, scratch, lane);
     const Env r = load_env(p, e);
     load_objects(p, ws, e, lane);
@@ -1979,7 +1977,6 @@ __device__ __forceinline__ bool run_env(const Params& p, int e, uint8_t* wbase, 
     return true;
   }
   const Prefetch q = prefetch<MODE, MAPK>(p, e, t0, lane);
-  if (store_pal) store_palette(p, ws, pal, lane);
   Env r = q.r;
   if (!stage_prefetched<MAPK>(p, ws, e, q, lane)) return false;  // ends with __syncwarp
   if (r.keys != 0) {  // doors of held keys open: the border flag again

@@ -80,7 +80,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
   write_palette(p, WarpSmem{wbase, FillLane{}}, lane);  // a constant table: before the wait
   // the header's mbarrier serves only bulk copies of byte maps of 4 KB or more
   if (!p.map_bits && p.S * p.S >= 4096) init_warp_header(wbase, lane);
-  const uint3 pal = make_uint3(0u, 0u, 0u);  // stored above, not per env
   asm volatile("griddepcontrol.wait;" ::: "memory");
   const int gw = blockIdx.x * kWarpsPerBlock + warp;
   const int nw = gridDim.x * kWarpsPerBlock;
@@ -98,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
       const int t0 = (int)k * p.chunk, t1 = t0 + p.chunk < p.steps ? t0 + p.chunk : p.steps;
       // after a lost map copy the warp only passes its items on (their envs
       // keep their state; the error word says so) and never touches the ring
-      if (!lost) lost = !run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, false, t0, t1);
+      if (!lost) lost = !run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, t0, t1);
       publish_chunk(p, e, k + 1 == nch ? 0u : k + 1, lane);
       item = next;
     }
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSm / kWarpsPerBlock)
     return;
   }
   for (int e = gw; e < p.n; e += nw)
-    if (!run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, pal, false, 0, p.steps))
+    if (!run_env<MODE, MAPK, 1, GRAY>(p, e, wbase, scratch, lane, slot, 0, p.steps))
       break;  // a copy was lost
   if (!kEarlyRelease) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // shared memory stays allocated until the bulk stores have read it
