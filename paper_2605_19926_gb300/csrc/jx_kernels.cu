@@ -1,6 +1,8 @@
-// jx_kernels.cu — the env kernel (one env config per launch), the kernels
-// that build next episodes ahead (a count, then one lane per env), and their
-// host side: launch shape queries, launches, the per-warp shared memory layout.
+// jx_kernels.cu — the env kernel (one env config per launch, rollouts in
+// hand-off chunks), the kernels that build next episodes ahead (a count, the
+// walls of the builds that start, then one lane per env advancing its build),
+// and their host side: launch shape queries, launches, the per-warp shared
+// memory layout.
 #include "jx_device.cuh"
 
 namespace jx {
