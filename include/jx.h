@@ -437,7 +437,8 @@ jx_status jx_batch_autotune(jx_batch* batch, void* stream, int32_t mode, int32_t
                             int32_t* n_trials, jx_tiling* trials, float* ms_per_step);
 
 /* Autotuner of a single env: times the env's own kernel (trial 0, reported as
- * the all-zero tiling) and the batched kernel over this env alone under every
+ * the all-zero tiling; for mode 1, the launch jx_rollout makes for `steps`,
+ * in hand-off chunks from 64 steps) and the batched kernel over this env alone under every
  * tiling of jx_batch_autotune's search space (the first max_trials - 1), with
  * jx_batch_autotune's protocol, and keeps the fastest: afterwards jx_reset,
  * jx_step, jx_rollout and jx_render of the env launch the chosen kernel

@@ -801,6 +801,7 @@ jx_status jx_autotune(jx_env* env, void* stream, int32_t mode, int32_t steps, in
         p.actions = base;
         p.frames = frames;
         p.steps = steps;
+        p.chunk = rollout_chunk(env, steps);  // the launch jx_rollout makes
         return run(env, p, jx::MODE_ROLLOUT, s);
       }
       for (size_t k = 0; k < T; ++k) {
